@@ -1,0 +1,209 @@
+"""Seeded synthetic inputs shared by the oracle tests and the CUDA path.
+
+This module only describes workloads and draws their inputs: instrument geometry, beam
+parameters, material constants, the synthetic S(Q,E) table and the seeded target
+histograms.  It holds none of the ray-tracing arithmetic and imports neither the oracle nor
+the CUDA library; each side turns these plain descriptions into its own structures.
+
+The workloads stand in for the paper's instruments and samples (section 3: ARCS-like
+8-pack detector systems with 128-pixel tubes, 1e8-packet powder runs, incident energies of
+50-120 meV); no measured data is used.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+# CODATA 2018, used only to describe inputs (gas density, thermal factor of the table)
+BOLTZMANN_J_PER_K = 1.380649e-23
+BOLTZMANN_MEV_PER_K = 1.380649e-23 / 1.602176634e-22
+ATM_PA = 101325.0
+
+SOLID_CYL, HOLLOW_CYL, BLOCK = 0, 1, 2
+K_ISO, K_SQE, K_BVK = 0, 1, 2
+DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
+
+
+@dataclass
+class Beam:
+    ei_mev: float
+    ei_rel_sigma: float = 0.0
+    div_sigma_rad: float = 0.0
+    width_m: float = 0.0
+    height_m: float = 0.0
+    z0_m: float = 0.5          # start plane, upstream of the sample centre
+    l1_m: float = 11.6         # source to sample distance
+
+
+@dataclass
+class Scatterer:
+    kind: int
+    dims: tuple                # SOLID: (r, h); HOLLOW: (r_in, r_out, h); BLOCK: (wx, wy, wz) [m]
+    n_per_A3: float
+    sig_abs_b: float           # at 2200 m/s, 1/v law
+    kernels: list              # [(kernel kind, sigma_b), ...] (1 or 2 entries)
+    rot_y: float = 0.0
+
+
+@dataclass
+class Detector:
+    kind: int
+    tof_min_s: float
+    tof_max_s: float
+    n_tof: int
+    radius_m: float = 3.0
+    # surface cylinder
+    height_m: float = 1.0
+    n_phi: int = 32
+    n_y: int = 32
+    # 8-pack tube rows
+    n_rows: int = 3
+    packs: tuple = (38, 39, 38)
+    row_y_m: tuple = (-1.0, 0.0, 1.0)
+    tubes_per_pack: int = 8
+    pixels_per_tube: int = 128
+    tube_r_m: float = 0.0127
+    tube_len_m: float = 1.0
+    tube_pitch_m: float = 0.028
+    pack_gap_m: float = 0.01
+    phi0_rad: float = math.radians(-30.0)
+    he3_n_per_A3: float = 10.0 * ATM_PA / (BOLTZMANN_J_PER_K * 295.0) * 1e-30
+    he3_sig_abs_b: float = 5333.0
+
+    @property
+    def n_pixels(self) -> int:
+        if self.kind == DET_SURFACE:
+            return self.n_phi * self.n_y
+        if self.kind == DET_TUBES:
+            return sum(self.packs[: self.n_rows]) * self.tubes_per_pack * self.pixels_per_tube
+        return 0
+
+    @property
+    def n_bins(self) -> int:
+        return self.n_pixels * self.n_tof
+
+
+@dataclass
+class SqeGrid:
+    table: np.ndarray          # float32 [nq, ne]
+    q_max: float = 12.0
+    e_min: float = -90.0
+    e_max: float = 90.0
+
+    @property
+    def nq(self):
+        return self.table.shape[0]
+
+    @property
+    def ne(self):
+        return self.table.shape[1]
+
+
+@dataclass
+class Bvk:
+    phi_Nm: float = 10.0
+    mass_u: float = 27.0
+    a_A: float = 4.05
+    msd_A2: float = 0.0
+    temperature_K: float = 300.0
+
+
+@dataclass
+class Workload:
+    name: str
+    beam: Beam
+    scatterers: List[Scatterer]
+    detector: Optional[Detector]
+    n: int
+    max_orders: int = 5
+    min_prob: float = 0.0
+    sqe: Optional[SqeGrid] = None
+    bvk: Optional[Bvk] = None
+    seed: int = 0
+    sim_id: int = 0
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+# ---- synthetic S(Q,E) -------------------------------------------------------------------
+def sqe_table(nq=200, ne=400, q_max=12.0, e_min=-90.0, e_max=90.0, omega_amp=40.0,
+              omega_k=1.57, width=3.0, temperature=300.0, omega_scale=1.0) -> np.ndarray:
+    """Tabulated S(Q,E) of a powder with one dispersive mode, on bin centres, FP32.
+
+    S(Q,E) = 1/2 [G(E - w(Q)) + G(E + w(Q))] f(E), with w(Q) = omega_amp |sin(omega_k Q)|,
+    G a unit-area Gaussian of standard deviation `width` (meV), and
+    f(E) = (E/kT) / (1 - exp(-E/kT)) (f(0) = 1), so that S(Q,-E) = exp(-E/kT) S(Q,E):
+    detailed balance at `temperature`.  E is the energy the neutron loses.
+    """
+    q = (np.arange(nq) + 0.5) * (q_max / nq)
+    e = e_min + (np.arange(ne) + 0.5) * ((e_max - e_min) / ne)
+    w = omega_scale * omega_amp * np.abs(np.sin(omega_k * q))[:, None]
+    E = e[None, :]
+    g = lambda x: np.exp(-0.5 * (x / width) ** 2) / (width * math.sqrt(2.0 * math.pi))
+    x = E / (BOLTZMANN_MEV_PER_K * temperature)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        f = np.where(x == 0.0, 1.0, x / -np.expm1(-x))
+    s = 0.5 * (g(E - w) + g(E + w)) * f
+    return s.astype(np.float32)
+
+
+# ---- workloads --------------------------------------------------------------------------
+def surface_detector() -> Detector:
+    """Ideal cylindrical surface, r = 3 m, h = 1 m, 32 x 32 pixels, 200 tof bins of 1 us."""
+    return Detector(kind=DET_SURFACE, tof_min_s=4.2e-3, tof_max_s=4.4e-3, n_tof=200,
+                    radius_m=3.0, height_m=1.0, n_phi=32, n_y=32)
+
+
+def tube_detector(n_tof=1000, packs=(38, 39, 38), pixels_per_tube=128) -> Detector:
+    """ARCS-like system: 3 rows of 8-packs of 128-pixel 3He tubes (10 atm) on r = 3 m."""
+    return Detector(kind=DET_TUBES, tof_min_s=2.9e-3, tof_max_s=5.4e-3, n_tof=n_tof,
+                    packs=tuple(packs), pixels_per_tube=pixels_per_tube)
+
+
+def config1(n=100_000) -> Workload:
+    """Plain single scattering: 60 meV pencil beam on a vanadium-like solid cylinder."""
+    sample = Scatterer(kind=SOLID_CYL, dims=(0.005, 0.02), n_per_A3=0.0603, sig_abs_b=0.23,
+                       kernels=[(K_ISO, 5.0)])
+    return Workload(name="single-scattering-cylinder-1e5", beam=Beam(ei_mev=60.0),
+                    scatterers=[sample], detector=surface_detector(), n=n, max_orders=1)
+
+
+def powder_sample() -> Scatterer:
+    return Scatterer(kind=HOLLOW_CYL, dims=(0.008, 0.010, 0.04), n_per_A3=0.0603,
+                     sig_abs_b=0.23, kernels=[(K_SQE, 5.0)])
+
+
+def powder_beam(ei=100.0) -> Beam:
+    return Beam(ei_mev=ei, ei_rel_sigma=0.01, div_sigma_rad=0.005, width_m=0.05,
+                height_m=0.05)
+
+
+def config2(n=100_000_000, omega_scale=1.0) -> Workload:
+    """Powder S(Q,E), hollow cylinder, up to 5 orders, 117,760-pixel tube system."""
+    return Workload(name="powder-sqe-hollow-cylinder-1e8", beam=powder_beam(),
+                    scatterers=[powder_sample()], detector=tube_detector(), n=n,
+                    max_orders=5, sqe=SqeGrid(sqe_table(omega_scale=omega_scale)))
+
+
+def config4(n=10_000_000) -> Workload:
+    """The configuration whose chi-squared gradient is taken (powder run, 1e7 neutrons)."""
+    w = config2(n=n)
+    return w.replace(name="powder-sqe-gradient-1e7")
+
+
+def can_scatterer() -> Scatterer:
+    """1.5 mm aluminium annular can around the powder sample (isotropic scatterer)."""
+    return Scatterer(kind=HOLLOW_CYL, dims=(0.012, 0.0135, 0.04), n_per_A3=0.0603,
+                     sig_abs_b=0.23, kernels=[(K_ISO, 1.5)])
+
+
+def poisson_target(hist: np.ndarray, scale_c: float, seed: int = 2) -> np.ndarray:
+    """T_b ~ Poisson(c I_b), drawn with numpy's PCG64 (the seeded target of the fit)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lam = np.clip(scale_c * np.asarray(hist, dtype=np.float64), 0.0, None)
+    return rng.poisson(lam).astype(np.float64)

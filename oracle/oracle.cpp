@@ -1,0 +1,982 @@
+// Oracle for the MCViNE neutron ray-tracing hot path.
+//
+// TEST INFRASTRUCTURE ONLY: a plain, slow, single-threaded FP64 CPU restatement of the
+// method, written from the paper, used to check the CUDA library.  The product path never
+// loads it.  It shares no code, header or constant with the CUDA library.
+// Built with -ffp-contract=off so every product and sum is rounded separately.
+//
+// Parity unpinned: absolute kernel normalisation against measured data (none available).
+#include "oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+// ---- physical constants (CODATA 2018) -------------------------------------------------
+const double kNeutronMass = 1.67492749804e-27;   // kg
+const double kHbar = 1.054571817e-34;            // J s
+const double kElemCharge = 1.602176634e-19;      // C
+const double kBoltzmann = 1.380649e-23;          // J/K
+const double kAtomicMass = 1.66053906660e-27;    // kg
+const double kPi = 3.14159265358979323846;
+// E[meV] = kMeVPerV2 * v^2 (v in m/s);  k[1/A] = kKPerV * v
+const double kMeVPerV2 = 0.5 * kNeutronMass / (kElemCharge * 1e-3);
+const double kKPerV = kNeutronMass / kHbar * 1e-10;
+const double kInf = std::numeric_limits<double>::infinity();
+
+struct Vec3 {
+  double x, y, z;
+};
+Vec3 add(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+Vec3 scale(Vec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+Vec3 cross(Vec3 a, Vec3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// ---- random numbers -------------------------------------------------------------------
+// Counter slot of (event, block): four blocks per event, event -1 is beam generation.
+uint32_t slot_of(int event, int block) { return (uint32_t)(4 * (event + 1) + block); }
+
+double u01_from(uint32_t hi, uint32_t lo) {
+  // 53 random bits -> (k + 1/2) 2^-53, strictly inside (0,1)
+  uint64_t k = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+  return (double)k * 0x1p-53 + 0x1p-54;
+}
+
+// ---- geometry -------------------------------------------------------------------------
+// Interval of s in which the line r + s d lies inside the infinite cylinder x^2+z^2 < R^2
+// (axis along y through the origin).  Written with the point of closest approach, which
+// stays accurate when the start point is far from the axis compared with R.
+bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2) {
+  double a = d.x * d.x + d.z * d.z;
+  if (a == 0.0) {
+    if (r.x * r.x + r.z * r.z < R * R) {
+      *s1 = -kInf;
+      *s2 = kInf;
+      return true;
+    }
+    return false;
+  }
+  double tc = -(r.x * d.x + r.z * d.z) / a;
+  double px = r.x + tc * d.x, pz = r.z + tc * d.z;
+  double g = R * R - (px * px + pz * pz);
+  if (!(g > 0.0)) return false;
+  double half = std::sqrt(g / a);
+  *s1 = tc - half;
+  *s2 = tc + half;
+  return true;
+}
+
+// Interval of s in which |p + s dp| < half.
+bool slab_interval(double half, double p, double dp, double* s1, double* s2) {
+  if (dp == 0.0) {
+    if (std::fabs(p) < half) {
+      *s1 = -kInf;
+      *s2 = kInf;
+      return true;
+    }
+    return false;
+  }
+  double a = (-half - p) / dp;
+  double b = (half - p) / dp;
+  *s1 = std::min(a, b);
+  *s2 = std::max(a, b);
+  return true;
+}
+
+// Keep [a,b] clipped to s >= 0 if it has positive length.
+int push_segment(double a, double b, double* sa, double* sb, int n) {
+  double lo = std::max(a, 0.0);
+  if (b > lo) {
+    sa[n] = lo;
+    sb[n] = b;
+    return n + 1;
+  }
+  return n;
+}
+
+int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double sb[2]) {
+  // Shapes and their combination (the hollow cylinder is a difference of two cylinders),
+  // paper section 2.4.2 ("Shapes" and constructive solid geometry).
+  double y1, y2, c1, c2;
+  if (sc.kind == ORC_SOLID_CYL) {
+    if (!cylinder_interval(sc.dims[0], r, d, &c1, &c2)) return 0;
+    if (!slab_interval(0.5 * sc.dims[1], r.y, d.y, &y1, &y2)) return 0;
+    return push_segment(std::max(c1, y1), std::min(c2, y2), sa, sb, 0);
+  }
+  if (sc.kind == ORC_HOLLOW_CYL) {
+    if (!cylinder_interval(sc.dims[1], r, d, &c1, &c2)) return 0;
+    if (!slab_interval(0.5 * sc.dims[2], r.y, d.y, &y1, &y2)) return 0;
+    double lo = std::max(c1, y1), hi = std::min(c2, y2);
+    if (!(hi > lo)) return 0;
+    double i1, i2;
+    if (!cylinder_interval(sc.dims[0], r, d, &i1, &i2)) return push_segment(lo, hi, sa, sb, 0);
+    int n = 0;
+    n = push_segment(lo, std::min(hi, i1), sa, sb, n);
+    n = push_segment(std::max(lo, i2), hi, sa, sb, n);
+    return n;
+  }
+  if (sc.kind == ORC_BLOCK) {
+    // body frame: the block is rotated by rot_y about +y, so body = R^T lab
+    double c = std::cos(sc.rot_y), s = std::sin(sc.rot_y);
+    Vec3 rb = {c * r.x - s * r.z, r.y, s * r.x + c * r.z};
+    Vec3 db = {c * d.x - s * d.z, d.y, s * d.x + c * d.z};
+    double lo = -kInf, hi = kInf, a, b;
+    if (!slab_interval(0.5 * sc.dims[0], rb.x, db.x, &a, &b)) return 0;
+    lo = std::max(lo, a);
+    hi = std::min(hi, b);
+    if (!slab_interval(0.5 * sc.dims[1], rb.y, db.y, &a, &b)) return 0;
+    lo = std::max(lo, a);
+    hi = std::min(hi, b);
+    if (!slab_interval(0.5 * sc.dims[2], rb.z, db.z, &a, &b)) return 0;
+    lo = std::max(lo, a);
+    hi = std::min(hi, b);
+    return push_segment(lo, hi, sa, sb, 0);
+  }
+  return 0;
+}
+
+struct Segment {
+  double sa, sb;
+  int j;  // scatterer index
+};
+
+// All material segments ahead of the ray, sorted by entry distance (ray tracing in a
+// composite scatterer, section 2.4.3 "Ray Tracing").
+int assembly_segments(const orc_config& cfg, Vec3 r, Vec3 d, Segment* out) {
+  int n = 0;
+  for (int j = 0; j < cfg.n_scat; ++j) {
+    double sa[2], sb[2];
+    int m = shape_segments(cfg.scat[j], r, d, sa, sb);
+    for (int i = 0; i < m; ++i) out[n++] = {sa[i], sb[i], j};
+  }
+  for (int i = 1; i < n; ++i) {  // insertion sort by entry
+    Segment key = out[i];
+    int k = i - 1;
+    while (k >= 0 && out[k].sa > key.sa) {
+      out[k + 1] = out[k];
+      --k;
+    }
+    out[k + 1] = key;
+  }
+  return n;
+}
+
+double sigma_scatt(const orc_scatterer& sc) {
+  double s = 0.0;
+  for (int k = 0; k < sc.nk; ++k) s += sc.ksig_b[k];
+  return s;
+}
+
+// attenuation coefficients in 1/m: mu[1/cm] = n[1/A^3] sigma[barn]; absorption ~ 1/v
+double mu_total(const orc_scatterer& sc, double speed) {
+  return 100.0 * sc.n_per_A3 * (sigma_scatt(sc) + sc.sig_abs_b * 2200.0 / speed);
+}
+double mu_scatt(const orc_scatterer& sc) { return 100.0 * sc.n_per_A3 * sigma_scatt(sc); }
+
+// unit vector at polar angle (cos c, sin s) and azimuth phi about unit vector d
+Vec3 rotate_about(Vec3 d, double c, double s, double phi) {
+  Vec3 a = (std::fabs(d.z) < 0.9) ? Vec3{0.0, 0.0, 1.0} : Vec3{1.0, 0.0, 0.0};
+  Vec3 e1 = cross(a, d);
+  e1 = scale(e1, 1.0 / std::sqrt(dot(e1, e1)));
+  Vec3 e2 = cross(d, e1);
+  double cp = std::cos(phi), sp = std::sin(phi);
+  return add(scale(d, c), scale(add(scale(e1, cp), scale(e2, sp)), s));
+}
+
+// ---- state of one neutron packet ------------------------------------------------------
+struct Neutron {
+  Vec3 r;        // m
+  Vec3 d;        // unit direction
+  double speed;  // m/s
+  double t;      // s
+  double w;      // probability weight
+};
+
+// Synthetic source at the sample: Gaussian energy spread, uniform rectangular footprint,
+// Gaussian divergence (it replaces the McStas beam simulation of section 3's first step).
+bool make_beam(const orc_config& cfg, int64_t nid, Neutron* n) {
+  double u[2];
+  orc_uniforms(cfg.seed, cfg.sim_id, nid, -1, 0, u);
+  double zE = std::sqrt(-2.0 * std::log(u[0])) * std::cos(2.0 * kPi * u[1]);
+  double E = cfg.ei_mev * (1.0 + cfg.ei_rel_sigma * zE);
+  orc_uniforms(cfg.seed, cfg.sim_id, nid, -1, 1, u);
+  double x = (u[0] - 0.5) * cfg.width_m;
+  double y = (u[1] - 0.5) * cfg.height_m;
+  orc_uniforms(cfg.seed, cfg.sim_id, nid, -1, 2, u);
+  double rr = std::sqrt(-2.0 * std::log(u[0]));
+  double ax = cfg.div_sigma_rad * (rr * std::cos(2.0 * kPi * u[1]));
+  double ay = cfg.div_sigma_rad * (rr * std::sin(2.0 * kPi * u[1]));
+  if (!(E > 0.0)) return false;
+  double tx = std::tan(ax), ty = std::tan(ay);
+  double norm = std::sqrt(tx * tx + ty * ty + 1.0);
+  n->d = {tx / norm, ty / norm, 1.0 / norm};
+  n->speed = std::sqrt(E / kMeVPerV2);
+  n->r = {x, y, -cfg.z0_m};
+  n->t = (cfg.l1_m - cfg.z0_m) / (n->speed * n->d.z);
+  n->w = 1.0;
+  return true;
+}
+
+int64_t n_pixels(const orc_config& cfg) {
+  if (cfg.det_kind == ORC_DET_SURFACE) return (int64_t)cfg.n_phi * cfg.n_y;
+  if (cfg.det_kind == ORC_DET_TUBES) {
+    int64_t packs = 0;
+    for (int i = 0; i < cfg.n_rows; ++i) packs += cfg.packs[i];
+    return packs * cfg.tubes_per_pack * cfg.pixels_per_tube;
+  }
+  return 0;
+}
+
+// larger root of the ray with the cylinder of radius R (the ray starts inside it)
+bool exit_cylinder(double R, Vec3 r, Vec3 d, double* s) {
+  double s1, s2;
+  if (!cylinder_interval(R, r, d, &s1, &s2)) return false;
+  if (!(s2 > 0.0) || s2 == kInf) return false;
+  *s = s2;
+  return true;
+}
+
+// Detector system ray tracing (section 2.4.3 "Ray tracing in a detector system").
+int64_t detect(const orc_config& cfg, Vec3 r, Vec3 d, double speed, double t, double w,
+               double u_det, int32_t* pixel, double* tof, double* w_det) {
+  *pixel = -1;
+  *tof = 0.0;
+  *w_det = 0.0;
+  if (cfg.det_kind == ORC_DET_SURFACE) {
+    // ideal cylindrical surface of efficiency 1
+    double s;
+    if (!exit_cylinder(cfg.det_radius_m, r, d, &s)) return -1;
+    double yh = r.y + s * d.y;
+    double half = 0.5 * cfg.det_height_m;
+    if (yh < -half || yh >= half) return -1;
+    double xh = r.x + s * d.x, zh = r.z + s * d.z;
+    double phi = std::atan2(xh, zh);
+    int64_t ip = (int64_t)std::floor((phi + kPi) / (2.0 * kPi) * cfg.n_phi);
+    ip = std::min<int64_t>(std::max<int64_t>(ip, 0), cfg.n_phi - 1);
+    int64_t iy = (int64_t)std::floor((yh + half) / cfg.det_height_m * cfg.n_y);
+    iy = std::min<int64_t>(std::max<int64_t>(iy, 0), cfg.n_y - 1);
+    *pixel = (int32_t)(ip * cfg.n_y + iy);
+    *tof = t + s / speed;
+    *w_det = w;
+  } else if (cfg.det_kind == ORC_DET_TUBES) {
+    // coarse test: crossing of the circle through the tube centres
+    double R = cfg.det_radius_m;
+    double sR;
+    if (!exit_cylinder(R, r, d, &sR)) return -1;
+    Vec3 P = add(r, scale(d, sR));
+    int row = -1, row_off = 0;
+    for (int i = 0, off = 0; i < cfg.n_rows; off += cfg.packs[i], ++i) {
+      if (std::fabs(P.y - cfg.row_y_m[i]) <= 0.5 * cfg.tube_len_m) {
+        row = i;
+        row_off = off;
+        break;
+      }
+    }
+    if (row < 0) return -1;
+    // the pack and tube nearest to the crossing, then the exact chord of the candidates
+    const int tpp = cfg.tubes_per_pack;
+    double period = tpp * cfg.tube_pitch_m + cfg.pack_gap_m;
+    double arc = (std::atan2(P.x, P.z) - cfg.phi0_rad) * R;
+    double p = std::floor(arc / period);
+    double within = arc - p * period;
+    double k = std::floor(within / cfg.tube_pitch_m);
+    if (k > tpp - 1) k = tpp - 1;
+    int64_t g = (int64_t)p * tpp + (int64_t)k;
+    int64_t n_tubes_row = (int64_t)cfg.packs[row] * tpp;
+    double y_lo = cfg.row_y_m[row] - 0.5 * cfg.tube_len_m;
+    double y_hi = cfg.row_y_m[row] + 0.5 * cfg.tube_len_m;
+    int64_t best = -1;
+    double best_in = kInf, best_out = 0.0;
+    for (int64_t c = g - 1; c <= g + 1; ++c) {
+      if (c < 0 || c >= n_tubes_row) continue;
+      int64_t pc = c / tpp, tc = c % tpp;
+      double phic = cfg.phi0_rad + (pc * period + (tc + 0.5) * cfg.tube_pitch_m) / R;
+      Vec3 rc = {r.x - R * std::sin(phic), r.y, r.z - R * std::cos(phic)};
+      double s1, s2;
+      if (!cylinder_interval(cfg.tube_r_m, rc, d, &s1, &s2)) continue;
+      if (s1 == -kInf) continue;  // vertical ray: no chord length
+      double ys1, ys2;
+      if (d.y == 0.0) {
+        if (!(r.y >= y_lo && r.y <= y_hi)) continue;
+        ys1 = -kInf;
+        ys2 = kInf;
+      } else {
+        double a = (y_lo - r.y) / d.y, b = (y_hi - r.y) / d.y;
+        ys1 = std::min(a, b);
+        ys2 = std::max(a, b);
+      }
+      double s_in = std::max(std::max(s1, ys1), 0.0);
+      double s_out = std::min(s2, ys2);
+      if (!(s_out > s_in)) continue;
+      if (s_in < best_in) {
+        best = c;
+        best_in = s_in;
+        best_out = s_out;
+      }
+    }
+    if (best < 0) return -1;
+    // 3He gas absorption with a 1/v cross section; absorption depth from the truncated
+    // exponential; weight multiplied by the absorption probability
+    double L = best_out - best_in;
+    double mu = 100.0 * cfg.he3_n_per_A3 * cfg.he3_sig_abs_b * 2200.0 / speed;
+    double pabs = -std::expm1(-mu * L);
+    double x = -std::log1p(-u_det * pabs) / mu;
+    double s_abs = best_in + x;
+    double y_abs = r.y + s_abs * d.y;
+    double pix_len = cfg.tube_len_m / cfg.pixels_per_tube;
+    int64_t j = (int64_t)std::floor((y_abs - y_lo) / pix_len);
+    j = std::min<int64_t>(std::max<int64_t>(j, 0), cfg.pixels_per_tube - 1);
+    int64_t pc = best / tpp, tc = best % tpp;
+    *pixel = (int32_t)(((row_off + pc) * tpp + tc) * cfg.pixels_per_tube + j);
+    *tof = t + s_abs / speed;
+    *w_det = w * pabs;
+  } else {
+    return -1;
+  }
+  double dt = (cfg.tof_max_s - cfg.tof_min_s) / cfg.n_tof;
+  double fb = std::floor((*tof - cfg.tof_min_s) / dt);
+  if (!(fb >= 0.0 && fb < (double)cfg.n_tof)) return -2;
+  return (int64_t)(*pixel) * cfg.n_tof + (int64_t)fb;
+}
+
+// ---- scattering kernels (supplement "Scattering kernels used in the examples") --------
+struct KernelOut {
+  double speed;
+  Vec3 d;
+  double factor;     // weight multiplier = s_value * rest
+  double rest;       // the factor without the table value
+  double s_value;    // table value (SQE) or 1
+  int entry;         // table entry or -1
+  double q, e, ki, kf;
+  Vec3 qvec;
+};
+
+// incoherent elastic: isotropic, speed unchanged (d sigma/d Omega = sigma_inc/4pi N e^-2W,
+// with the Debye-Waller factor taken as 1)
+void kernel_iso(double speed, Vec3 d, const double u[4], KernelOut* o) {
+  double ct = 2.0 * u[0] - 1.0;
+  double phi = 2.0 * kPi * u[1];
+  double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+  o->d = {st * std::cos(phi), st * std::sin(phi), ct};
+  o->speed = speed;
+  o->factor = 1.0;
+  o->rest = 1.0;
+  o->s_value = 1.0;
+  o->entry = -1;
+  double k = kKPerV * speed;
+  o->ki = k;
+  o->kf = k;
+  o->e = 0.0;
+  o->qvec = add(scale(d, k), scale(o->d, -k));
+  o->q = std::sqrt(dot(o->qvec, o->qvec));
+}
+
+// tabulated isotropic S(Q,E): d2 sigma/dOmega dEf = sigma/4pi (kf/ki) N S(Q,E).
+// E uniform on [e_min, min(e_max, Ei)], Q uniform on [|ki-kf|, min(ki+kf, q_max)], azimuth
+// uniform; the weight factor is the cross section over the sampling density,
+// S Q dE dQ / (2 ki^2).  Nearest-bin lookup (histogram form of S(Q,E)).
+bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], KernelOut* o) {
+  double Ei = kMeVPerV2 * speed * speed;
+  double ki = kKPerV * speed;
+  double e_lo = cfg.e_min, e_hi = std::min(cfg.e_max, Ei);
+  if (!(e_hi > e_lo)) return false;
+  double dE = e_hi - e_lo;
+  double E = e_lo + u[0] * dE;
+  double Ef = Ei - E;
+  if (!(Ef > 0.0)) return false;
+  double speed_f = std::sqrt(Ef / kMeVPerV2);
+  double kf = kKPerV * speed_f;
+  double q_lo = std::fabs(ki - kf);
+  double q_hi = std::min(ki + kf, cfg.q_max);
+  if (!(q_hi > q_lo)) return false;
+  double dQ = q_hi - q_lo;
+  double Q = q_lo + u[1] * dQ;
+  double c2t = (ki * ki + kf * kf - Q * Q) / (2.0 * ki * kf);
+  c2t = std::min(1.0, std::max(-1.0, c2t));
+  double s2t = std::sqrt(std::max(0.0, 1.0 - c2t * c2t));
+  double phi = 2.0 * kPi * u[2];
+  double bq = cfg.q_max / cfg.nq, be = (cfg.e_max - cfg.e_min) / cfg.ne;
+  double fq = std::floor(Q / bq), fe = std::floor((E - cfg.e_min) / be);
+  if (!(fq >= 0.0 && fq < cfg.nq && fe >= 0.0 && fe < cfg.ne)) return false;
+  int entry = (int)fq * cfg.ne + (int)fe;
+  double S = (double)cfg.sqe[entry];
+  o->d = rotate_about(d, c2t, s2t, phi);
+  o->speed = speed_f;
+  o->s_value = S;
+  o->entry = entry;
+  o->rest = Q * dE * dQ / (2.0 * ki * ki);
+  o->factor = S * o->rest;
+  o->q = Q;
+  o->e = E;
+  o->ki = ki;
+  o->kf = kf;
+  o->qvec = add(scale(d, ki), scale(o->d, -kf));
+  return true;
+}
+
+bool kernel_scatter(const orc_config& cfg, int ktype, double speed, Vec3 d, const double u[4],
+                    KernelOut* o) {
+  if (ktype == ORC_K_ISO) {
+    kernel_iso(speed, d, u, o);
+    return true;
+  }
+  if (ktype == ORC_K_SQE) return kernel_sqe(cfg, speed, d, u, o);
+  return false;
+}
+
+void draw_kernel_uniforms(const orc_config& cfg, int64_t nid, int order, double u[4]) {
+  double a[2], b[2];
+  orc_uniforms(cfg.seed, cfg.sim_id, nid, order, 1, a);
+  orc_uniforms(cfg.seed, cfg.sim_id, nid, order, 2, b);
+  u[0] = a[0];
+  u[1] = a[1];
+  u[2] = b[0];
+  u[3] = b[1];
+}
+
+// ---- chain-mode tracer ----------------------------------------------------------------
+// Per-scatter record kept for the adjoint.
+struct ScatterRecord {
+  double a_factor;   // weight factor of the scatter without the table value
+  double s_value;    // table value or 1
+  int entry;         // table entry or -1
+  double dlog_abs;   // d ln(a_factor) / d sigma_abs of the differentiated scatterer
+  double dlog_s;     // d ln(a_factor) / d sigma_s of the differentiated scatterer
+};
+struct EmitRecord {
+  int order;
+  Neutron n;
+  double w;          // emitted weight
+  double atten;      // exp(-tau_tot) of this emission
+  double dlog_abs, dlog_s;
+};
+
+// One neutron through the sample assembly, as a chain of at most N_max scatterings.
+// Each scattering splits the packet (section 2.4.3 "Multiple Scattering"): the transmitted
+// part leaves with weight w e^{-tau}; the scattered part continues from a point picked
+// uniformly along the forward path, with the kernel picked at random.  The paper's
+// recursion (supplement, scatterM / interactM_path1 / interactM1) samples the point on
+// the first segment only and handles later segments in further rounds; here the point is
+// picked on all segments ahead at once, which gives the same expectation.
+// stop_on_zero: stop when the weight is exactly zero (it cannot contribute); the adjoint
+// keeps tracing such paths because their derivative need not be zero.
+template <class Emit, class Scat>
+void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Emit emit,
+               Scat on_scatter, double* tallies) {
+  Neutron n;
+  if (!make_beam(cfg, nid, &n)) return;
+  for (int o = 0;; ++o) {
+    if (n.w < cfg.min_prob) break;
+    if (stop_on_zero && n.w == 0.0) break;
+    Segment seg[8];
+    int ns = assembly_segments(cfg, n.r, n.d, seg);
+    double tau = 0.0, L = 0.0, Lg = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      double len = seg[i].sb - seg[i].sa;
+      tau += mu_total(cfg.scat[seg[i].j], n.speed) * len;
+      L += len;
+      if (seg[i].j == gs) Lg += len;
+    }
+    if (o == 0 && L > 0.0 && tallies) tallies[ORC_T_NHIT] += 1.0;
+    EmitRecord em;
+    em.order = o;
+    em.n = n;
+    em.atten = std::exp(-tau);
+    em.w = n.w * em.atten;
+    em.dlog_abs = 0.0;
+    em.dlog_s = 0.0;
+    if (gs >= 0) {
+      const orc_scatterer& g = cfg.scat[gs];
+      em.dlog_abs = -100.0 * g.n_per_A3 * (2200.0 / n.speed) * Lg;
+      em.dlog_s = -100.0 * g.n_per_A3 * Lg;
+    }
+    emit(em);
+    if (o == cfg.max_orders || !(L > 0.0)) break;
+    double u[2];
+    orc_uniforms(cfg.seed, cfg.sim_id, nid, o, 0, u);
+    // scattering point, uniform over the material length ahead
+    double ell = u[0] * L;
+    double acc = 0.0, tau_pt = 0.0, s_pt = 0.0, lg_pt = 0.0;
+    int j = seg[ns - 1].j;
+    for (int i = 0; i < ns; ++i) {
+      double len = seg[i].sb - seg[i].sa;
+      double mu = mu_total(cfg.scat[seg[i].j], n.speed);
+      if (ell < acc + len || i == ns - 1) {
+        double part = ell - acc;
+        s_pt = seg[i].sa + part;
+        tau_pt += mu * part;
+        if (seg[i].j == gs) lg_pt += part;
+        j = seg[i].j;
+        break;
+      }
+      acc += len;
+      tau_pt += mu * len;
+      if (seg[i].j == gs) lg_pt += len;
+    }
+    const orc_scatterer& sc = cfg.scat[j];
+    ScatterRecord rec;
+    rec.a_factor = mu_scatt(sc) * L * std::exp(-tau_pt);
+    rec.dlog_abs = 0.0;
+    rec.dlog_s = 0.0;
+    if (gs >= 0) {
+      const orc_scatterer& g = cfg.scat[gs];
+      rec.dlog_abs = -100.0 * g.n_per_A3 * (2200.0 / n.speed) * lg_pt;
+      rec.dlog_s = -100.0 * g.n_per_A3 * lg_pt + (j == gs ? 1.0 / sigma_scatt(g) : 0.0);
+    }
+    n.r = add(n.r, scale(n.d, s_pt));
+    n.t = n.t + s_pt / n.speed;
+    // kernel choice with probability sigma_k / sigma_s (weight unchanged)
+    int k = 0;
+    if (sc.nk == 2 && !(u[1] * (sc.ksig_b[0] + sc.ksig_b[1]) < sc.ksig_b[0])) k = 1;
+    double uk[4];
+    draw_kernel_uniforms(cfg, nid, o, uk);
+    KernelOut ko;
+    if (!kernel_scatter(cfg, sc.ktype[k], n.speed, n.d, uk, &ko)) break;
+    rec.s_value = ko.s_value;
+    rec.entry = ko.entry;
+    n.w = n.w * rec.a_factor * ko.factor;
+    rec.a_factor = rec.a_factor * ko.rest;
+    n.d = ko.d;
+    n.speed = ko.speed;
+    on_scatter(o + 1, sc.ktype[k], j, ko, rec, n.w);
+  }
+}
+
+void add_tally(double* tallies, int i, double v) {
+  if (tallies) tallies[i] += v;
+}
+
+void record_detection(const orc_config& cfg, int64_t nid, const EmitRecord& em, orc_packet* pk,
+                      double* hist, double* tallies) {
+  if (em.order == 0) {
+    add_tally(tallies, ORC_T_BEAMSTOP, em.w);
+    if (pk) {
+      pk->pixel = -1;
+      pk->tof = 0.0;
+      pk->w_det = 0.0;
+      pk->bin = -1;
+    }
+    return;
+  }
+  double u[2];
+  orc_uniforms(cfg.seed, cfg.sim_id, nid, em.order, 3, u);
+  int32_t pixel;
+  double tof, w_det;
+  int64_t bin = detect(cfg, em.n.r, em.n.d, em.n.speed, em.n.t, em.w, u[0], &pixel, &tof, &w_det);
+  if (bin >= 0) {
+    if (hist) hist[bin] += w_det;
+    add_tally(tallies, ORC_T_WDET, w_det);
+    add_tally(tallies, ORC_T_NDET, 1.0);
+  } else if (bin == -2) {
+    add_tally(tallies, ORC_T_WOVER, w_det);
+    add_tally(tallies, ORC_T_NOVER, 1.0);
+  } else {
+    add_tally(tallies, ORC_T_NMISS, 1.0);
+  }
+  if (pk) {
+    pk->pixel = pixel;
+    pk->tof = tof;
+    pk->w_det = w_det;
+    pk->bin = bin;
+  }
+}
+
+void fill_packet(int64_t nid, const EmitRecord& em, orc_packet* pk) {
+  pk->nid = nid;
+  pk->order = em.order;
+  pk->x = em.n.r.x;
+  pk->y = em.n.r.y;
+  pk->z = em.n.r.z;
+  pk->vx = em.n.speed * em.n.d.x;
+  pk->vy = em.n.speed * em.n.d.y;
+  pk->vz = em.n.speed * em.n.d.z;
+  pk->t = em.n.t;
+  pk->w = em.w;
+}
+
+bool config_ok(const orc_config* cfg) {
+  if (!cfg || cfg->n_scat < 0 || cfg->n_scat > 4 || cfg->max_orders < 0) return false;
+  for (int j = 0; j < cfg->n_scat; ++j) {
+    const orc_scatterer& s = cfg->scat[j];
+    if (s.nk < 1 || s.nk > 2) return false;
+    for (int k = 0; k < s.nk; ++k)
+      if (s.ktype[k] == ORC_K_SQE && (!cfg->sqe || cfg->nq <= 0 || cfg->ne <= 0)) return false;
+  }
+  if (cfg->det_kind != ORC_DET_NONE && cfg->n_tof <= 0) return false;
+  return true;
+}
+
+// ---- paper-literal recursive estimator ------------------------------------------------
+struct PaperPacket {
+  Neutron n;
+  int m;  // number of scatterings so far
+};
+
+struct PaperRun {
+  const orc_config& cfg;
+  int64_t nid;
+  int event = 0;  // running event counter for this neutron's random draws
+  double* hist;
+  double* tallies;
+};
+
+void paper_emit(PaperRun& pr, const PaperPacket& p) {
+  EmitRecord em;
+  em.order = p.m;
+  em.n = p.n;
+  em.w = p.n.w;
+  if (p.m == 0) {
+    add_tally(pr.tallies, ORC_T_BEAMSTOP, em.w);
+    return;
+  }
+  double u[2];
+  orc_uniforms(pr.cfg.seed, pr.cfg.sim_id ^ 0x80000000u, pr.nid, pr.event++, 3, u);
+  int32_t pixel;
+  double tof, w_det;
+  int64_t bin = detect(pr.cfg, p.n.r, p.n.d, p.n.speed, p.n.t, p.n.w, u[0], &pixel, &tof, &w_det);
+  if (bin >= 0) {
+    if (pr.hist) pr.hist[bin] += w_det;
+    add_tally(pr.tallies, ORC_T_WDET, w_det);
+    add_tally(pr.tallies, ORC_T_NDET, 1.0);
+  } else if (bin == -2) {
+    add_tally(pr.tallies, ORC_T_WOVER, w_det);
+    add_tally(pr.tallies, ORC_T_NOVER, 1.0);
+  } else {
+    add_tally(pr.tallies, ORC_T_NMISS, 1.0);
+  }
+}
+
+// interactM1 of a homogeneous scatterer: the transmitted packet leaves the first segment
+// attenuated; the scattered one is taken at a uniform point of the first segment.
+bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* transmitted,
+                     PaperPacket* scattered) {
+  const orc_config& cfg = pr.cfg;
+  const orc_scatterer& sc = cfg.scat[j];
+  double sa[2], sb[2];
+  int ns = shape_segments(sc, in.n.r, in.n.d, sa, sb);
+  if (ns == 0) return false;
+  double len = sb[0] - sa[0];
+  double mu = mu_total(sc, in.n.speed);
+  *transmitted = in;
+  transmitted->n.r = add(in.n.r, scale(in.n.d, sb[0]));
+  transmitted->n.t = in.n.t + sb[0] / in.n.speed;
+  transmitted->n.w = in.n.w * std::exp(-mu * len);
+  const uint32_t sim = cfg.sim_id ^ 0x80000000u;
+  double u[2];
+  orc_uniforms(cfg.seed, sim, pr.nid, pr.event, 0, u);
+  double ell = u[0] * len;
+  double s = sa[0] + ell;
+  PaperPacket p = in;
+  p.n.r = add(in.n.r, scale(in.n.d, s));
+  p.n.t = in.n.t + s / in.n.speed;
+  p.n.w = in.n.w * mu_scatt(sc) * len * std::exp(-mu * ell);
+  int k = 0;
+  if (sc.nk == 2 && !(u[1] * (sc.ksig_b[0] + sc.ksig_b[1]) < sc.ksig_b[0])) k = 1;
+  double a[2], b[2];
+  orc_uniforms(cfg.seed, sim, pr.nid, pr.event, 1, a);
+  orc_uniforms(cfg.seed, sim, pr.nid, pr.event, 2, b);
+  pr.event++;
+  double uk[4] = {a[0], a[1], b[0], b[1]};
+  KernelOut ko;
+  if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko)) return true;
+  p.n.w = p.n.w * ko.factor;
+  p.n.d = ko.d;
+  p.n.speed = ko.speed;
+  p.m = in.m + 1;
+  *scattered = p;
+  return true;
+}
+
+// the packet still inside a scatterer after its last allowed scattering leaves with the
+// attenuation of all material ahead
+PaperPacket paper_propagate_out(const orc_config& cfg, PaperPacket p) {
+  Segment seg[8];
+  int ns = assembly_segments(cfg, p.n.r, p.n.d, seg);
+  double tau = 0.0;
+  for (int i = 0; i < ns; ++i) tau += mu_total(cfg.scat[seg[i].j], p.n.speed) * (seg[i].sb - seg[i].sa);
+  p.n.w = p.n.w * std::exp(-tau);
+  return p;
+}
+
+void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies) {
+  PaperRun pr{cfg, nid, 0, hist, tallies};
+  Neutron n0;
+  if (!make_beam(cfg, nid, &n0)) return;
+  {
+    Segment seg[8];
+    if (assembly_segments(cfg, n0.r, n0.d, seg) > 0) add_tally(tallies, ORC_T_NHIT, 1.0);
+  }
+  std::vector<PaperPacket> toscatter{PaperPacket{n0, 0}};
+  const int kRoundLimit = 64;
+  for (int rounds = 0; !toscatter.empty() && rounds < kRoundLimit; ++rounds) {
+    std::vector<PaperPacket> scattered;
+    for (const PaperPacket& p : toscatter) {
+      if (p.n.w < cfg.min_prob) continue;
+      Segment seg[8];
+      int ns = assembly_segments(cfg, p.n.r, p.n.d, seg);
+      if (ns == 0) {  // exiting: nothing ahead
+        paper_emit(pr, p);
+        continue;
+      }
+      if (p.m >= cfg.max_orders) {  // maximum order reached: leave with attenuation
+        paper_emit(pr, paper_propagate_out(cfg, p));
+        continue;
+      }
+      // interactM_path1 of the composite: the first constituent met delegates
+      int j = seg[0].j;
+      PaperPacket cur = p;
+      bool alive = true;
+      // interactM_path1 of the homogeneous scatterer: repeated interactM1 while the
+      // scattered packet stays inside; what is left is handed back to the next round
+      while (cur.m < cfg.max_orders) {
+        if (cur.n.w < cfg.min_prob) {
+          alive = false;
+          break;
+        }
+        PaperPacket tr, sc;
+        sc.m = -1;
+        if (!paper_interact1(pr, j, cur, &tr, &sc)) break;
+        scattered.push_back(tr);
+        if (sc.m < 0) {
+          alive = false;
+          break;
+        }
+        cur = sc;
+      }
+      if (alive) scattered.push_back(cur);
+    }
+    toscatter.swap(scattered);
+  }
+  for (const PaperPacket& p : toscatter) paper_emit(pr, paper_propagate_out(cfg, p));
+}
+
+}  // namespace
+
+// ---- C entry points -------------------------------------------------------------------
+extern "C" {
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  // Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round multiplies
+  // two words by fixed odd constants, swaps and xors the high halves with the other words
+  // and the key; the key is bumped by the Weyl constants between rounds.
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+void orc_uniforms(uint32_t seed, uint32_t sim_id, int64_t nid, int event, int block, double u[2]) {
+  uint32_t ctr[4] = {(uint32_t)((uint64_t)nid & 0xffffffffu), (uint32_t)((uint64_t)nid >> 32),
+                     slot_of(event, block), 0u};
+  uint32_t key[2] = {seed, sim_id};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  u[0] = u01_from(o[0], o[1]);
+  u[1] = u01_from(o[2], o[3]);
+}
+
+int orc_shape_segments(const orc_scatterer* sc, const double r[3], const double d[3],
+                       double sa[2], double sb[2]) {
+  return shape_segments(*sc, Vec3{r[0], r[1], r[2]}, Vec3{d[0], d[1], d[2]}, sa, sb);
+}
+
+int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const double d[3],
+                       const double u[4], double* speed_out, double d_out[3], double* factor,
+                       orc_event* ev) {
+  KernelOut ko;
+  if (!kernel_scatter(*cfg, ktype, speed, Vec3{d[0], d[1], d[2]}, u, &ko)) return 0;
+  *speed_out = ko.speed;
+  d_out[0] = ko.d.x;
+  d_out[1] = ko.d.y;
+  d_out[2] = ko.d.z;
+  *factor = ko.factor;
+  if (ev) {
+    ev->kernel = ktype;
+    ev->entry = ko.entry;
+    ev->q = ko.q;
+    ev->e = ko.e;
+    ev->ki = ko.ki;
+    ev->kf = ko.kf;
+    ev->factor = ko.factor;
+    ev->qvec[0] = ko.qvec.x;
+    ev->qvec[1] = ko.qvec.y;
+    ev->qvec[2] = ko.qvec.z;
+  }
+  return 1;
+}
+
+int64_t orc_detect(const orc_config* cfg, const double r[3], const double v[3], double t,
+                   double w, double u_det, int32_t* pixel, double* tof, double* w_det) {
+  double speed = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  Vec3 d = {v[0] / speed, v[1] / speed, v[2] / speed};
+  return detect(*cfg, Vec3{r[0], r[1], r[2]}, d, speed, t, w, u_det, pixel, tof, w_det);
+}
+
+int64_t orc_n_pixels(const orc_config* cfg) { return n_pixels(*cfg); }
+
+int orc_trace(const orc_config* cfg, int64_t first_id, int64_t n, orc_packet* packets,
+              orc_event* events, double* hist, double* tallies) {
+  if (!config_ok(cfg) || n < 0) return 1;
+  const int slots = cfg->max_orders + 1;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t nid = first_id + i;
+    orc_packet* base = packets ? packets + i * slots : nullptr;
+    if (base)
+      for (int s = 0; s < slots; ++s) {
+        std::memset(&base[s], 0, sizeof(orc_packet));
+        base[s].nid = nid;
+        base[s].order = -1;
+        base[s].pixel = -1;
+        base[s].bin = -1;
+      }
+    orc_event* ev = events ? events + i * cfg->max_orders : nullptr;
+    if (ev)
+      for (int s = 0; s < cfg->max_orders; ++s) {
+        std::memset(&ev[s], 0, sizeof(orc_event));
+        ev[s].nid = nid;
+        ev[s].order = -1;
+        ev[s].entry = -1;
+      }
+    auto emit = [&](const EmitRecord& em) {
+      if (em.order < 8) add_tally(tallies, ORC_T_NPACK0 + em.order, 1.0);
+      orc_packet* pk = base ? &base[em.order] : nullptr;
+      if (pk) fill_packet(nid, em, pk);
+      if (cfg->det_kind != ORC_DET_NONE || em.order == 0)
+        record_detection(*cfg, nid, em, pk, hist, tallies);
+    };
+    auto on_scatter = [&](int order, int ktype, int j, const KernelOut& ko,
+                          const ScatterRecord&, double w_after) {
+      if (!ev) return;
+      orc_event& e = ev[order - 1];
+      e.order = order;
+      e.kernel = ktype;
+      e.scatterer = j;
+      e.entry = ko.entry;
+      e.q = ko.q;
+      e.e = ko.e;
+      e.ki = ko.ki;
+      e.kf = ko.kf;
+      e.factor = ko.factor;
+      e.w = w_after;
+      e.qvec[0] = ko.qvec.x;
+      e.qvec[1] = ko.qvec.y;
+      e.qvec[2] = ko.qvec.z;
+    };
+    chain_one(*cfg, nid, true, -1, emit, on_scatter, tallies);
+  }
+  return 0;
+}
+
+int orc_trace_paper(const orc_config* cfg, int64_t first_id, int64_t n, double* hist,
+                    double* tallies) {
+  if (!config_ok(cfg) || n < 0) return 1;
+  for (int64_t i = 0; i < n; ++i) paper_one(*cfg, first_id + i, hist, tallies);
+  return 0;
+}
+
+static double chi2_and_grad(const orc_config& cfg, const double* hist, const double* target,
+                            double c, double* g) {
+  int64_t nb = n_pixels(cfg) * cfg.n_tof;
+  double loss = 0.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    double den = std::max(target[b], 1.0);
+    double r = c * hist[b] - target[b];
+    loss += r * r / den;
+    if (g) g[b] = 2.0 * c * r / den;
+  }
+  return loss;
+}
+
+int orc_loss(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
+             double scale_c, double* hist_work, double* loss) {
+  if (!config_ok(cfg) || n < 0 || cfg->det_kind == ORC_DET_NONE) return 1;
+  int64_t nb = n_pixels(*cfg) * cfg->n_tof;
+  std::fill(hist_work, hist_work + nb, 0.0);
+  orc_trace(cfg, first_id, n, nullptr, nullptr, hist_work, nullptr);
+  *loss = chi2_and_grad(*cfg, hist_work, target, scale_c, nullptr);
+  return 0;
+}
+
+// Adjoint of the chi-squared loss along fixed random paths: every packet weight is a
+// product of factors, so d w / d theta follows from the factors' derivatives.
+int orc_grad(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
+             double scale_c, int gs, double* hist_out, double* loss, double* dsqe,
+             double* dsig) {
+  if (!config_ok(cfg) || n < 0 || cfg->det_kind == ORC_DET_NONE) return 1;
+  if (gs < 0 || gs >= cfg->n_scat) return 1;
+  int64_t nb = n_pixels(*cfg) * cfg->n_tof;
+  std::fill(hist_out, hist_out + nb, 0.0);
+  orc_trace(cfg, first_id, n, nullptr, nullptr, hist_out, nullptr);
+  std::vector<double> g(nb);
+  *loss = chi2_and_grad(*cfg, hist_out, target, scale_c, g.data());
+  if (cfg->sqe) std::fill(dsqe, dsqe + (int64_t)cfg->nq * cfg->ne, 0.0);
+  dsig[0] = 0.0;
+  dsig[1] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t nid = first_id + i;
+    std::vector<ScatterRecord> recs;
+    auto on_scatter = [&](int, int, int, const KernelOut&, const ScatterRecord& r, double) {
+      recs.push_back(r);
+    };
+    auto emit = [&](const EmitRecord& em) {
+      if (em.order == 0) return;
+      double u[2];
+      orc_uniforms(cfg->seed, cfg->sim_id, nid, em.order, 3, u);
+      int32_t pixel;
+      double tof, w_det;
+      int64_t bin = detect(*cfg, em.n.r, em.n.d, em.n.speed, em.n.t, em.w, u[0], &pixel, &tof,
+                           &w_det);
+      if (bin < 0) return;
+      // detector factor (independent of the sample parameters)
+      double pabs;
+      detect(*cfg, em.n.r, em.n.d, em.n.speed, em.n.t, 1.0, u[0], &pixel, &tof, &pabs);
+      double gb = g[bin];
+      // sigma: d w_det / d sigma = w_det * sum of log-derivatives
+      double la = em.dlog_abs, ls = em.dlog_s;
+      for (int k = 0; k < em.order; ++k) {
+        la += recs[k].dlog_abs;
+        ls += recs[k].dlog_s;
+      }
+      dsig[0] += gb * w_det * la;
+      dsig[1] += gb * w_det * ls;
+      // table: product of every other factor
+      for (int k = 0; k < em.order; ++k) {
+        if (recs[k].entry < 0) continue;
+        double prod = em.atten * pabs;
+        for (int m = 0; m < em.order; ++m) {
+          prod *= recs[m].a_factor;
+          if (m != k) prod *= recs[m].s_value;
+        }
+        dsqe[recs[k].entry] += gb * prod;
+      }
+    };
+    chain_one(*cfg, nid, false, gs, emit, on_scatter, nullptr);
+  }
+  return 0;
+}
+
+}  // extern "C"

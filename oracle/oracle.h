@@ -1,0 +1,150 @@
+/*
+ * Oracle for the neutron ray-tracing hot path of MCViNE (Lin et al., "MCViNE -- An
+ * object oriented Monte Carlo neutron ray tracing simulation package").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded FP64 CPU restatement
+ * of what the hot path computes.  It exists so that the CUDA path can be checked against
+ * something written straight from the paper.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it; the product path never does.  It shares
+ * no code, header or constant table with the CUDA library.
+ *
+ * Every function cites the passage of the paper it follows.  Where the paper is silent
+ * the reading taken is stated next to the code.
+ *
+ * Parity unpinned: the absolute normalisation of the kernels against measured data
+ * (no experimental data is available); everything else is pinned by the CPU tests.
+ */
+#ifndef MCV_ORACLE_H
+#define MCV_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* shape kinds (all centred at the origin, axis or rotation axis along +y) */
+enum { ORC_SOLID_CYL = 0, ORC_HOLLOW_CYL = 1, ORC_BLOCK = 2 };
+/* kernel kinds */
+enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2 };
+/* detector kinds */
+enum { ORC_DET_NONE = 0, ORC_DET_SURFACE = 1, ORC_DET_TUBES = 2 };
+
+typedef struct {
+  int kind;
+  double dims[3];      /* SOLID: r,h   HOLLOW: r_in,r_out,h   BLOCK: wx,wy,wz  (m) */
+  double rot_y;        /* rotation of the body about +y (rad) */
+  double n_per_A3;     /* number density (1/A^3) */
+  double sig_abs_b;    /* absorption cross section at 2200 m/s (barn), 1/v law */
+  int nk;              /* number of kernels (1 or 2) */
+  int ktype[2];        /* ORC_K_* */
+  double ksig_b[2];    /* scattering cross section of each kernel (barn) */
+} orc_scatterer;
+
+typedef struct {
+  /* beam (source -> sample) */
+  double ei_mev, ei_rel_sigma, div_sigma_rad, width_m, height_m, z0_m, l1_m;
+  /* sample assembly */
+  int n_scat;
+  orc_scatterer scat[4];
+  int max_orders;      /* N_max: maximum number of scatterings of one packet */
+  double min_prob;     /* packets with weight below this are dropped */
+  /* tabulated S(Q,E), FP32, row-major [iq][ie], bin centred grid */
+  const float* sqe;
+  int nq, ne;
+  double q_max, e_min, e_max;
+  /* single-crystal Born-von Karman kernel (fcc, nearest-neighbour central force) */
+  double bvk_phi_Nm, bvk_mass_u, bvk_a_A, bvk_msd_A2, temperature_K;
+  /* detector */
+  int det_kind;
+  double det_radius_m, det_height_m; /* SURFACE */
+  int n_phi, n_y;                    /* SURFACE */
+  int n_rows, packs[3];              /* TUBES */
+  double row_y_m[3];
+  int tubes_per_pack, pixels_per_tube;
+  double tube_r_m, tube_len_m, tube_pitch_m, pack_gap_m, phi0_rad;
+  double he3_n_per_A3, he3_sig_abs_b;
+  double tof_min_s, tof_max_s;
+  int n_tof;
+  /* random streams */
+  uint32_t seed, sim_id;
+} orc_config;
+
+/* one emitted packet (the transmitted neutron of one order) and what the detector made of it */
+typedef struct {
+  int64_t nid;
+  int32_t order;       /* -1: slot unused */
+  int32_t pixel;       /* -1: missed the detector */
+  double x, y, z, vx, vy, vz, t, w;
+  double tof, w_det;
+  int64_t bin;         /* pixel*n_tof + tof bin; -1 missed, -2 tof out of range */
+} orc_packet;
+
+/* per-scatter record (debug / pins) */
+typedef struct {
+  int64_t nid;
+  int32_t order;       /* the order of the packet created by this scatter (1..N_max) */
+  int32_t kernel;      /* ORC_K_* */
+  int32_t scatterer;
+  int32_t entry;       /* S(Q,E) table entry, -1 if none */
+  double q, e, ki, kf, factor;
+  double w;            /* packet weight right after this scatter */
+  double qvec[3];      /* ki_vec - kf_vec */
+} orc_event;
+
+enum { ORC_T_BEAMSTOP = 0, ORC_T_WDET, ORC_T_WOVER, ORC_T_NDET, ORC_T_NOVER, ORC_T_NMISS,
+       ORC_T_NHIT, ORC_T_NPACK0, ORC_NTALLY = ORC_T_NPACK0 + 8 };
+
+/* counter-based generator (Philox4x32-10, Salmon et al. SC'11) */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* the two uniforms in (0,1) drawn for (neutron id, event, block); event -1 = beam */
+void orc_uniforms(uint32_t seed, uint32_t sim_id, int64_t nid, int event, int block,
+                  double u[2]);
+
+/* geometry: segments [s_a, s_b] of the ray r + s d (s >= 0) inside scatterer sc.
+   returns the count (<= 2). */
+int orc_shape_segments(const orc_scatterer* sc, const double r[3], const double d[3],
+                       double sa[2], double sb[2]);
+
+/* one kernel scatter: in = speed and unit direction; writes the new speed, direction,
+   weight factor; returns 0 if the kernel kills the packet. */
+int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const double d[3],
+                       const double u[4], double* speed_out, double d_out[3],
+                       double* factor, orc_event* ev);
+
+/* detect one packet: returns bin (>= 0), -1 miss, -2 tof overflow */
+int64_t orc_detect(const orc_config* cfg, const double r[3], const double v[3], double t,
+                   double w, double u_det, int32_t* pixel, double* tof, double* w_det);
+
+/* chain-mode tracer.  packets: n*(max_orders+1) slots or NULL; events: n*max_orders slots
+   or NULL; hist: n_pixels*n_tof, accumulated into, or NULL; tallies: ORC_NTALLY doubles,
+   accumulated into, or NULL. */
+int orc_trace(const orc_config* cfg, int64_t first_id, int64_t n, orc_packet* packets,
+              orc_event* events, double* hist, double* tallies);
+
+/* paper-literal recursive estimator (scatterM / interactM_path1 / interactM1);
+   histogram and tallies only */
+int orc_trace_paper(const orc_config* cfg, int64_t first_id, int64_t n, double* hist,
+                    double* tallies);
+
+int64_t orc_n_pixels(const orc_config* cfg);
+
+/* chi-squared loss on the histogram and its adjoint gradient with respect to the S(Q,E)
+   table entries (dsqe, nq*ne) and the absorption and scattering cross sections of
+   scatterer `gs` (dsig[0] = d/d sig_abs, dsig[1] = d/d sig_s).  hist_out (n_pixels*n_tof)
+   receives the forward histogram. */
+int orc_grad(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
+             double scale_c, int gs, double* hist_out, double* loss, double* dsqe,
+             double* dsig);
+
+/* loss only (for finite differences) */
+int orc_loss(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
+             double scale_c, double* hist_work, double* loss);
+
+/* Born-von Karman fcc dispersion: q in 1/A (crystal frame); energies (meV, ascending) and
+   eigenvectors (columns, e[3*i+b] = component i of branch b) */
+void orc_bvk_modes(const orc_config* cfg, const double q[3], double hw[3], double evec[9]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
