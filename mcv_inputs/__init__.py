@@ -35,7 +35,7 @@ class Beam:
     div_sigma_rad: float = 0.0
     width_m: float = 0.0
     height_m: float = 0.0
-    z0_m: float = 0.5          # start plane, upstream of the sample centre
+    z0_m: float = 0.05         # start plane, upstream of the sample centre
     l1_m: float = 11.6         # source to sample distance
 
 

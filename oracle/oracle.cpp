@@ -50,8 +50,9 @@ double u01_from(uint32_t hi, uint32_t lo) {
 
 // ---- geometry -------------------------------------------------------------------------
 // Interval of s in which the line r + s d lies inside the infinite cylinder x^2+z^2 < R^2
-// (axis along y through the origin).  Written with the point of closest approach, which
-// stays accurate when the start point is far from the axis compared with R.
+// (axis along y through the origin).  Written with the point of closest approach: its
+// squared distance to the axis is (r x d)^2 / a in the xz-plane, which stays accurate when
+// the start point is far from the axis compared with R.
 bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2) {
   double a = d.x * d.x + d.z * d.z;
   if (a == 0.0) {
@@ -63,8 +64,29 @@ bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2) {
     return false;
   }
   double tc = -(r.x * d.x + r.z * d.z) / a;
-  double px = r.x + tc * d.x, pz = r.z + tc * d.z;
-  double g = R * R - (px * px + pz * pz);
+  double cr = r.x * d.z - r.z * d.x;
+  double g = R * R - cr * cr / a;
+  if (!(g > 0.0)) return false;
+  double half = std::sqrt(g / a);
+  *s1 = tc - half;
+  *s2 = tc + half;
+  return true;
+}
+
+// The same for a vertical tube of radius rt whose axis crosses the xz-plane at R (ux, uz),
+// (ux, uz) a unit vector: coordinates are taken along and across that direction, so that
+// the large distance R cancels exactly once.
+bool tube_interval(double R, double ux, double uz, double rt, Vec3 r, Vec3 d, double* s1,
+                   double* s2) {
+  double a = d.x * d.x + d.z * d.z;
+  if (a == 0.0) return false;
+  double o_rad = r.x * ux + r.z * uz - R;
+  double o_tan = r.x * uz - r.z * ux;
+  double d_rad = d.x * ux + d.z * uz;
+  double d_tan = d.x * uz - d.z * ux;
+  double tc = -(o_rad * d_rad + o_tan * d_tan) / a;
+  double cr = o_rad * d_tan - o_tan * d_rad;
+  double g = rt * rt - cr * cr / a;
   if (!(g > 0.0)) return false;
   double half = std::sqrt(g / a);
   *s1 = tc - half;
@@ -297,10 +319,9 @@ int64_t detect(const orc_config& cfg, Vec3 r, Vec3 d, double speed, double t, do
       if (c < 0 || c >= n_tubes_row) continue;
       int64_t pc = c / tpp, tc = c % tpp;
       double phic = cfg.phi0_rad + (pc * period + (tc + 0.5) * cfg.tube_pitch_m) / R;
-      Vec3 rc = {r.x - R * std::sin(phic), r.y, r.z - R * std::cos(phic)};
       double s1, s2;
-      if (!cylinder_interval(cfg.tube_r_m, rc, d, &s1, &s2)) continue;
-      if (s1 == -kInf) continue;  // vertical ray: no chord length
+      if (!tube_interval(R, std::sin(phic), std::cos(phic), cfg.tube_r_m, r, d, &s1, &s2))
+        continue;
       double ys1, ys2;
       if (d.y == 0.0) {
         if (!(r.y >= y_lo && r.y <= y_hi)) continue;
