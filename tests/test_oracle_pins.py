@@ -601,9 +601,10 @@ def test_gradient_zero_table_entry_continues_path():
     wl, target, c = _grad_case(n=6000)
     wl = wl.replace(min_prob=-1e300)
     g = oracle.grad(wl, target, c)
-    zero = np.flatnonzero((wl.sqe.table.ravel() == 0) & (g["dsqe"].ravel() != 0))
+    dsq = g["dsqe"].ravel()
+    zero = np.flatnonzero((wl.sqe.table.ravel() == 0) & (dsq != 0))
     assert zero.size > 0
-    for e in zero[:3]:
+    for e in zero[np.argsort(-np.abs(dsq[zero]))][:3]:
         vals = []
         for sgn in (1, -1):
             t = wl.sqe.table.copy()
