@@ -602,9 +602,10 @@ def test_gradient_zero_table_entry_continues_path():
     wl = wl.replace(min_prob=-1e300)
     g = oracle.grad(wl, target, c)
     dsq = g["dsqe"].ravel()
-    zero = np.flatnonzero((wl.sqe.table.ravel() == 0) & (dsq != 0))
+    # entries whose derivative stands above the rounding noise of the loss differences
+    zero = np.flatnonzero((wl.sqe.table.ravel() == 0) & (np.abs(dsq) > 1e-7))
     assert zero.size > 0
-    for e in zero[np.argsort(-np.abs(dsq[zero]))][:3]:
+    for e in zero[:3]:
         vals = []
         for sgn in (1, -1):
             t = wl.sqe.table.copy()
