@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the powder S(Q,E) run: 1e8 neutrons per GPU per step through a hollow
+cylinder (up to 5 scattering orders) into a 117,760-pixel x 1000-bin FP64 histogram.
+
+A step is one pass of the whole hot path: the source drawn in registers, the sample
+assembly, the detector system and the histogram, all in one fused kernel (plus the kernel
+that clears the histogram).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it is launched by torch.distributed.run; each rank simulates its own neutron-id
+range (weak scaling, no collective in the timed region).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "neutrons/s + fraction of roofline (1e8-n powder S(Q,E), 1×GB300) vs plain FP64 fwd"
+WORKLOAD = ("powder S(Q,E), hollow cylinder r_out=1 cm wall 2 mm h=4 cm, Ei=100 meV +-1%, "
+            "5 mrad, 5x5 cm beam, up to 5 scattering orders, 115 8-packs x 128 pixels "
+            "(117,760) x 1000 tof bins FP64")
+N_DEFAULT = 100_000_000
+
+# Algorithmic cost model of the path (lane operations: FP32/INT32 arithmetic, each
+# transcendental counted as its instruction sequence), per event type.  Derivation in
+# DESIGN.md ("Roofline").  Event counts come from the run's own tallies.
+COST = {
+    "beam": 480,        # 3 Philox blocks, 2 Box-Muller pairs, 2 tan, direction, speed, time
+    "order": 85,        # segments ahead (hollow cylinder: 2 cylinder spans + slab), tau, exp
+    "scatter": 465,     # scattering point (Philox, exp, move) + S(Q,E) kernel (2 Philox,
+                        # kinematics, 2 sqrt, table lookup, rotation with sincos)
+    "detect": 280,      # circle crossing, atan2, 3 tube chords, absorption (Philox, expm1,
+                        # log1p), pixel, tof
+    "hist": 6,          # bin index and one FP64 atomic add
+}
+
+
+def ops_per_step(n, t):
+    """Lane operations of one step from its event counts (n incident neutrons; tallies t)."""
+    from paper_1504_02776_gb300 import binding as B
+    emitted = t[B.T_NEMIT]
+    return (n * (COST["beam"] + COST["order"]) + emitted * (COST["scatter"] + COST["order"]
+            + COST["detect"]) + t[B.T_NDET] * COST["hist"])
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1504_02776_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes per neutron of the trace kernel from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "trace_fp32_powder_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    return d.get("dram_bytes_per_neutron")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(self.rows),
+                "reasons": reasons}
+
+
+# ---- oracle timing (the CPU baseline and the reference arm) -------------------------------
+def _oracle_shard(args):
+    first, n = args
+    import mcv_inputs as mi
+    import oracle
+    wl = mi.config2(n=n)
+    t0 = time.perf_counter()
+    oracle.trace(wl, first_id=first, n=n, packets=False, hist=True)
+    return n, time.perf_counter() - t0
+
+
+def oracle_throughput(per_worker, workers, first=0):
+    """Neutrons/s of the oracle on `workers` host processes (spawned), each tracing its own
+    id range of `per_worker` neutrons of the same workload."""
+    import multiprocessing as mp
+    ctxm = mp.get_context("spawn")
+    with ctxm.Pool(workers) as pool:
+        pool.map(_oracle_shard, [(first + 10**12 + i, 10) for i in range(workers)])  # warm
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_shard, [(first + i * per_worker, per_worker)
+                                       for i in range(workers)])
+        wall = time.perf_counter() - t0
+    n = sum(r[0] for r in res)
+    return n / wall, n, wall
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    workers = os.cpu_count() or 1
+    per = args.ref_per_worker
+    vals = []
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        oracle_throughput(per // 10 or 1, workers)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        v, n, wall = oracle_throughput(per, workers, first=k * per * workers)
+        vals.append(wall)
+    total = time.perf_counter() - t0
+    n_step = per * workers
+    value = n_step * args.steps / sum(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "neutrons/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(vals) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "neutrons_per_step": n_step,
+                   "sample": "bounded sample of the 1e8-neutron workload"},
+        "cpu_baseline": {"value": value, "unit": "neutrons/s", "cores": workers,
+                         "kind": "oracle",
+                         "sample": "%d neutrons per step (%d per process)" % (n_step, per)},
+        "e2e": {"value": value, "unit": "neutrons/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": total,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- our arm --------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import mcv_inputs as mi
+    from paper_1504_02776_gb300 import api, binding as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before the first GPU call: spawned processes only
+        workers = os.cpu_count() or 1
+        v, n_cpu, wall = oracle_throughput(args.cpu_per_worker, workers)
+        cpu_base = {"value": v, "unit": "neutrons/s", "cores": workers, "kind": "oracle",
+                    "sample": "%d neutrons of the same workload (%d per process, ids from 0), "
+                              "%.1f s wall" % (n_cpu, args.cpu_per_worker, wall)}
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    N = args.n
+    ctx = api.Context(local)
+    wl = mi.config2(n=N)
+    table = ctx.table(wl)
+    counts, tallies = ctx.new_hist(wl.detector)
+    stream = torch.cuda.current_stream()
+    first = rank * N
+    sample32 = api.sample_struct(wl, B.FP32, table)
+    det = api.detector_struct(wl.detector)
+    beam = api.beam_struct(wl.beam)
+    hist = B.Hist(counts.data_ptr(), tallies.data_ptr())
+    sptr = __import__("ctypes").c_void_p(stream.cuda_stream)
+
+    def step(sample, ev=None):
+        B.mcv_zero(ctx.handle, counts.data_ptr(), counts.numel(), sptr)
+        B.mcv_zero(ctx.handle, tallies.data_ptr(), tallies.numel(), sptr)
+        if ev is not None:
+            ev[0].record(stream)
+        B.mcv_trace_sample(ctx.handle, sample, beam, None, wl.seed, wl.sim_id, first, N, det,
+                           hist, None, sptr)
+        if ev is not None:
+            ev[1].record(stream)
+
+    # ---- FP32 fast mode (the product path)
+    for _ in range(args.warmup):
+        step(sample32)
+    ctx.sync()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(sample32, evs[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ctx.sync()
+    ms = e0.elapsed_time(e1)
+    trace_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    t = tallies.cpu().numpy()
+    tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    ms = float(tm.item())
+    value = world * N * args.steps / (ms / 1e3)
+    det_per_s = world * t[B.T_NDET] * args.steps / (ms / 1e3)
+
+    # ---- plain FP64 forward, one simulation per launch, same workload and histogram
+    sample64 = api.sample_struct(wl, B.FP64, table)
+    step(sample64)
+    ctx.sync()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    f0.record(stream)
+    for _ in range(args.fp64_steps):
+        step(sample64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    fm = torch.tensor([ms64], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(fm, op=dist.ReduceOp.MAX)
+    ms64 = float(fm.item())
+    value64 = world * N * args.fp64_steps / (ms64 / 1e3)
+    ctx.sync()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_table = torch.from_numpy(wl.sqe.table).pin_memory()
+        host_counts = torch.empty(counts.numel(), dtype=torch.float64).pin_memory()
+        host_tallies = torch.empty(tallies.numel(), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            table.copy_(host_table.view(-1).view_as(table), non_blocking=True)
+            step(sample32)
+            host_counts.copy_(counts, non_blocking=True)
+            host_tallies.copy_(tallies, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        g0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1)
+        gm = torch.tensor([gms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(gm, op=dist.ReduceOp.MAX)
+        gms = float(gm.item())
+        e2e = {"value": world * N * args.e2e_steps / (gms / 1e3), "unit": "neutrons/s",
+               "h2d_bytes_per_step": int(host_table.numel() * 4),
+               "d2h_bytes_per_step": int((host_counts.numel() + host_tallies.numel()) * 8),
+               "ms_per_step": gms / args.e2e_steps}
+        ctx.sync()
+
+    # ---- roofline of the fused trace kernel (ALU bound)
+    props = torch.cuda.get_device_properties(local)
+    peaks = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * sm_mhz * 1e6   # FP32/INT32 lanes x clock
+    ops = ops_per_step(N, t)
+    achieved = ops / (trace_ms / 1e3)
+    traffic_per_n = load_traffic()
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+            "unit": "Tops/s", "frac": achieved / peak_ops,
+            "traffic": None if traffic_per_n is None else traffic_per_n * N,
+            "kernel": "trace_kernel<float,1,TUBES>", "kernel_ms": trace_ms,
+            "ops_per_launch": ops,
+            "peak_basis": "%d SMs x 128 FP32/INT32 lanes x %.0f MHz (max SM clock, "
+                          "MEASURED_PEAKS.json)" % (props.multi_processor_count, sm_mhz),
+            "hbm_gbs_algorithmic": (N * 0 + t[B.T_NDET] * 16) / (trace_ms / 1e3) / 1e9,
+            "hbm_peak_gbs_measured": peaks.get("hbm_gbs")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "neutrons/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "neutrons_per_gpu_per_step": N,
+                   "precision": "FP32 geometry and kernel sampling; FP64 time of flight, "
+                                "tallies and histogram",
+                   "l2": "inputs larger than L2: the 942 MB histogram is cleared and "
+                         "rewritten every step",
+                   "parallelism": "neutron-id shards per GPU" if world > 1 else "1 GPU"},
+        "detected_events_per_s": det_per_s,
+        "fp64_forward": {"value": value64, "unit": "neutrons/s",
+                         "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                         "speedup_fp32_over_fp64": value / value64},
+        "roofline": roof,
+        "cpu_baseline": cpu_base,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-per-worker", type=int, default=1_000_000)
+    ap.add_argument("--ref-per-worker", type=int, default=400_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,240 @@
+/*
+ * mcv.h -- C ABI of the GB300 neutron ray-tracing library (libmcv.so).
+ *
+ * The library implements the data-parallel hot path of MCViNE's method (Lin et al.,
+ * "MCViNE -- An object oriented Monte Carlo neutron ray tracing simulation package"):
+ * Monte Carlo ray tracing of neutron packets through a sample assembly and a pixelated
+ * 3He detector system into a time-of-flight histogram.  The calls follow the paper's
+ * component chain (section 2.2 and section 3's workflow): a source (mcv_beam), the sample
+ * assembly (mcv_trace_sample, section 2.4.3 "Ray Tracing" and "Multiple Scattering"), the
+ * detector system (mcv_detect, section 2.4.3 "Ray tracing in a detector system").  The
+ * adjoint (mcv_grad) and the batched launch (mcv_trace_batch) have no counterpart in the
+ * paper.
+ *
+ * Conventions for every call
+ *   - Frame: beam along +z, y up, the sample centred at the origin.  Lengths in m (sample
+ *     and detector), velocities in m/s, times in s, energies in meV, momenta in 1/A,
+ *     number densities in 1/A^3, cross sections in barn (absorption quoted at 2200 m/s and
+ *     scaled as 1/v).
+ *   - All array arguments are DEVICE pointers owned by the caller, on the device the
+ *     context was created for.  The library allocates device memory only inside the
+ *     context (mcv_create) and never frees caller memory.
+ *   - Calls are asynchronous on the caller's CUDA stream (`stream`, a cudaStream_t; NULL is
+ *     the legacy default stream).  Argument errors are reported before anything is
+ *     launched (MCV_EINVAL, nothing written).  Launch failures return MCV_ECUDA.  Errors
+ *     found by the kernels themselves (index out of range) set a flag in the context that
+ *     mcv_sync reports as MCV_EDEVICE.
+ *   - Histograms and tallies are ACCUMULATED into; callers zero them (cudaMemset or
+ *     mcv_zero) before the first call, and split runs over neutron-id ranges add up.
+ *   - Random numbers: Philox4x32-10 with key (seed, sim_id) and counter (neutron id low
+ *     32 bits, high 32 bits, 4*(event+1)+block, 0); event -1 is beam generation, event o
+ *     the o-th scattering order.  A neutron's history depends only on (seed, sim_id, id),
+ *     never on launch shape, so results are reproducible and resumable by id range.
+ *   - Nothing throws across the ABI; the message of the last error of the calling thread
+ *     is returned by mcv_last_error().
+ */
+#ifndef MCV_H
+#define MCV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MCV_OK = 0,
+  MCV_EINVAL = 1,    /* invalid argument: nothing was launched */
+  MCV_ENOMEM = 2,    /* the context could not allocate its own device memory */
+  MCV_ECUDA = 3,     /* a CUDA call failed (message in mcv_last_error) */
+  MCV_ETIMEOUT = 4,  /* a bounded device wait ran out */
+  MCV_EDEVICE = 5    /* a kernel found an out-of-range index (reported by mcv_sync) */
+} mcv_status;
+
+enum { MCV_MAX_SCATTERERS = 4, MCV_MAX_TUBES_PER_ROW = 512, MCV_NTALLY = 8 };
+enum { MCV_SHAPE_SOLID_CYL = 0, MCV_SHAPE_HOLLOW_CYL = 1, MCV_SHAPE_BLOCK = 2 };
+enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2 };
+enum { MCV_DET_NONE = 0, MCV_DET_SURFACE = 1, MCV_DET_TUBES = 2 };
+enum { MCV_FP64 = 0, MCV_FP32 = 1 };
+
+/* tally slots (FP64 accumulators) */
+enum {
+  MCV_T_BEAMSTOP = 0, /* summed weight of the unscattered (order-0) packets */
+  MCV_T_WDET = 1,     /* summed detected weight inside the tof range */
+  MCV_T_WOVER = 2,    /* summed detected weight outside the tof range */
+  MCV_T_NDET = 3,     /* detected packets inside the tof range */
+  MCV_T_NOVER = 4,    /* detected packets outside the tof range */
+  MCV_T_NMISS = 5,    /* scattered packets that missed every tube / the surface */
+  MCV_T_NHIT = 6,     /* incident neutrons whose path crosses the sample */
+  MCV_T_NEMIT = 7     /* scattered packets emitted (orders >= 1) */
+};
+
+typedef struct mcv_ctx mcv_ctx;
+
+/* Synthetic source at the sample position (stands in for the beam simulation, section 3's
+ * first step): energy ~ N(ei, (ei_rel_sigma*ei)^2); start point uniform on a width x
+ * height rectangle in the plane z = -z0_m; horizontal and vertical divergence angles
+ * ~ N(0, div_sigma_rad^2); time of flight from a source l1_m upstream of the origin. */
+typedef struct {
+  double ei_mev, ei_rel_sigma, div_sigma_rad, width_m, height_m, z0_m, l1_m;
+} mcv_beam_params;
+
+/* One homogeneous scatterer (section 2.4.1-2.4.2: one shape, one or two kernels).
+ * shape SOLID_CYL dims = (r, h); HOLLOW_CYL dims = (r_in, r_out, h); BLOCK dims =
+ * (wx, wy, wz) rotated by rot_y_rad about +y.  Cylinders have their axis along y. */
+typedef struct {
+  int shape;
+  double dims[3];
+  double rot_y_rad;
+  double n_per_A3;
+  double sig_abs_b;        /* at 2200 m/s */
+  int n_kernels;           /* 1 or 2; kernel k is picked with probability sig_k / sum */
+  int kernel[2];           /* MCV_KERNEL_* */
+  double kernel_sig_b[2];  /* scattering cross section of each kernel */
+} mcv_scatterer;
+
+/* Tabulated isotropic S(Q,E) (supplement "Multi-phonon scattering" form
+ * d2sigma/dOmega dEf = sigma/4pi kf/ki N S(Q,E)); FP32, row-major [iq][ie], nearest bin,
+ * Q bins [0, q_max), E bins [e_min, e_max) where E = Ei - Ef. */
+typedef struct {
+  const float* table;      /* device, nq*ne */
+  int nq, ne;
+  double q_max, e_min, e_max;
+} mcv_sqe;
+
+/* Single-crystal fcc Born-von Karman kernel parameters (coherent one-phonon) */
+typedef struct {
+  double phi_Nm, mass_u, a_A, msd_A2, temperature_K;
+} mcv_bvk;
+
+/* The sample assembly: a flat list of scatterers (the composite of section 2.4.1, one level
+ * deep).  max_orders = maximum number of scatterings of a packet; packets whose weight
+ * drops below min_prob are discarded (section 2.4.3); fp_mode MCV_FP64 traces in FP64,
+ * MCV_FP32 traces geometry and kernels in FP32 with FP64 time of flight. */
+typedef struct {
+  int n_scatterers;
+  mcv_scatterer scat[MCV_MAX_SCATTERERS];
+  int max_orders;          /* 0..7 */
+  double min_prob;
+  int fp_mode;
+  mcv_sqe sqe;
+  mcv_bvk bvk;
+} mcv_sample;
+
+/* Detector system.  SURFACE: ideal cylinder of radius_m, height_m, efficiency 1, n_phi x
+ * n_y pixels, pixel = i_phi*n_y + i_y with phi = atan2(x, z) in [-pi, pi).  TUBES: n_rows
+ * rows of packs of tubes_per_pack vertical 3He tubes (radius tube_r_m, active length
+ * tube_len_m, centred on the circle radius_m, row centre heights row_y_m), tube pitch and
+ * pack gap along the circle, first pack edge at phi0_rad; pixel = ((pack)*tubes_per_pack +
+ * tube)*pixels_per_tube + i along y, packs numbered row by row.  tof bins: n_tof equal
+ * bins on [tof_min_s, tof_max_s). */
+typedef struct {
+  int kind;
+  double radius_m;
+  double height_m;
+  int n_phi, n_y;
+  int n_rows;
+  int packs[3];
+  double row_y_m[3];
+  int tubes_per_pack, pixels_per_tube;
+  double tube_r_m, tube_len_m, tube_pitch_m, pack_gap_m, phi0_rad;
+  double he3_n_per_A3, he3_sig_abs_b;
+  double tof_min_s, tof_max_s;
+  int n_tof;
+} mcv_detector;
+
+/* Structure-of-arrays neutron packets (device).  x..vz and w are float arrays in
+ * MCV_FP32 and double arrays in MCV_FP64; t is always double.  id and order may be NULL
+ * where a call says so.  n = number of slots. */
+typedef struct {
+  void *x, *y, *z, *vx, *vy, *vz;
+  double* t;
+  void* w;
+  int64_t* id;
+  int32_t* order;          /* -1 marks an empty slot */
+  int64_t n;
+} mcv_neutrons;
+
+/* Histogram I[pixel][tof bin] (FP64, n_pixels*n_tof) and MCV_NTALLY FP64 tallies; either
+ * pointer may be NULL. */
+typedef struct {
+  double* counts;
+  double* tallies;
+} mcv_hist;
+
+/* Per-packet detector results (device, one entry per packet slot); any pointer may be
+ * NULL.  bin = pixel*n_tof + tof bin, -1 missed, -2 tof out of range. */
+typedef struct {
+  int32_t* pixel;
+  double* tof;
+  double* w_det;
+  int64_t* bin;
+} mcv_events;
+
+/* ---- context ------------------------------------------------------------------------- */
+/* Creates a context on `device` (allocates a small device block: error flag, work queue).
+ * Returns MCV_EINVAL for a bad device or out pointer, MCV_ECUDA/MCV_ENOMEM on failure. */
+mcv_status mcv_create(int device, mcv_ctx** out);
+/* Frees the context and its device memory; NULL is ignored. */
+mcv_status mcv_destroy(mcv_ctx* ctx);
+/* Message of the last error returned to the calling thread ("" if none). */
+const char* mcv_last_error(void);
+/* Waits for `stream`, then reports and clears the device error flag (MCV_EDEVICE). */
+mcv_status mcv_sync(mcv_ctx* ctx, void* stream);
+/* Number of pixels of a detector description (0 if invalid). */
+int64_t mcv_detector_pixels(const mcv_detector* det);
+/* Sets n doubles at dst (device) to zero on `stream` with the library's own fill kernel. */
+mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream);
+
+/* ---- the component chain ------------------------------------------------------------- */
+/* Source: writes n packets with ids first_id..first_id+n-1 into out (slots 0..n-1; out->id
+ * and out->order, if given, receive the id and 0).  fp_mode selects the array types. */
+mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint32_t seed,
+                    uint32_t sim_id, int64_t first_id, int64_t n, mcv_neutrons* out,
+                    void* stream);
+
+/* Sample assembly (section 2.4.3, multiple scattering as a bounded chain of at most
+ * max_orders scatterings per neutron; the paper's recursion samples the scattering point
+ * on the first path segment and handles later segments in later rounds, this chain samples
+ * it on all segments ahead at once, with the same expectation).
+ * Incident neutrons: `in` (slots 0..n-1, id taken from in->id or first_id + slot) or, if
+ * `in` is NULL, generated in registers from `beam` with ids first_id.. (fused source).
+ * Outputs (at least one):
+ *   det + hist : each scattered packet is traced through the detector and histogrammed in
+ *                the same kernel (fused path); order-0 packets go to MCV_T_BEAMSTOP;
+ *   packets    : n*(max_orders+1) slots, slot i*(max_orders+1)+o holds the packet of
+ *                order o of the i-th neutron (order -1 if none) with its id.
+ * Errors: MCV_EINVAL for NULL/ill-formed descriptions, n < 0, unsupported combinations. */
+mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample,
+                            const mcv_beam_params* beam, const mcv_neutrons* in,
+                            uint32_t seed, uint32_t sim_id, int64_t first_id, int64_t n,
+                            const mcv_detector* det, mcv_hist* hist, mcv_neutrons* packets,
+                            void* stream);
+
+/* Detector system (section 2.4.3, "Ray tracing in a detector system"): every packet slot
+ * with order >= 1 is traced to the first tube (or the surface) it meets; the absorption
+ * point is drawn from the truncated exponential of the 3He path, the weight is multiplied
+ * by the absorption probability, and (pixel, tof) is histogrammed.  Slots with order 0
+ * add their weight to MCV_T_BEAMSTOP; order -1 slots are skipped.  packets->id and
+ * packets->order are required (the detector draw uses them).  fp_mode as the packets. */
+mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
+                      const mcv_neutrons* packets, uint32_t seed, uint32_t sim_id,
+                      mcv_hist* hist, mcv_events* events, void* stream);
+
+/* Adjoint (no counterpart in the paper): chi2 = sum_b (c I_b - T_b)^2 / max(T_b, 1) of the
+ * histogram of neutrons first_id..first_id+n-1, and its gradient with respect to the S(Q,E)
+ * table entries and the absorption and scattering cross sections of scatterer
+ * grad_scatterer, differentiating packet weights along the fixed random paths.
+ * hist->counts (n_bins) receives I (cleared first), g_work (n_bins) receives dchi2/dI,
+ * loss (1), dsqe (nq*ne) and dsig (2: d/dsig_abs, d/dsig_s) are FP64 device outputs and
+ * are overwritten. */
+mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
+                    const mcv_detector* det, uint32_t seed, uint32_t sim_id,
+                    int64_t first_id, int64_t n, const double* target, double scale_c,
+                    int grad_scatterer, mcv_hist* hist, double* g_work, double* loss,
+                    double* dsqe, double* dsig, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -383,7 +383,7 @@ struct KernelOut {
 void kernel_iso(double speed, Vec3 d, const double u[4], KernelOut* o) {
   double ct = 2.0 * u[0] - 1.0;
   double phi = 2.0 * kPi * u[1];
-  double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+  double st = 2.0 * std::sqrt(u[0] * (1.0 - u[0]));  // sqrt(1 - ct^2) without cancellation
   o->d = {st * std::cos(phi), st * std::sin(phi), ct};
   o->speed = speed;
   o->factor = 1.0;
@@ -418,9 +418,16 @@ bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], 
   if (!(q_hi > q_lo)) return false;
   double dQ = q_hi - q_lo;
   double Q = q_lo + u[1] * dQ;
-  double c2t = (ki * ki + kf * kf - Q * Q) / (2.0 * ki * kf);
+  // scattering angle from Q^2 = ki^2 + kf^2 - 2 ki kf cos(2theta), written through
+  // 1 - cos = (Q - q_lo)(Q + q_lo) / (2 ki kf) and 1 + cos = (ki + kf - Q)(ki + kf + Q) /
+  // (2 ki kf), whose small factors are the sampled offsets from the ends of the Q range
+  double den = 2.0 * ki * kf;
+  double one_m = (u[1] * dQ) * (Q + q_lo) / den;
+  double top = (q_hi == ki + kf) ? (1.0 - u[1]) * dQ : (ki + kf) - Q;
+  double one_p = top * (ki + kf + Q) / den;
+  double c2t = (one_m <= one_p) ? 1.0 - one_m : one_p - 1.0;
   c2t = std::min(1.0, std::max(-1.0, c2t));
-  double s2t = std::sqrt(std::max(0.0, 1.0 - c2t * c2t));
+  double s2t = std::sqrt(std::max(0.0, one_m * one_p));
   double phi = 2.0 * kPi * u[2];
   double bq = cfg.q_max / cfg.nq, be = (cfg.e_max - cfg.e_min) / cfg.ne;
   double fq = std::floor(Q / bq), fe = std::floor((E - cfg.e_min) / be);

@@ -1,0 +1,261 @@
+"""Torch-facing layer over the C ABI: builds the mcv.h structures from workload descriptions
+(mcv_inputs) and owns the device buffers of a run.  Marshalling only: the ray tracing,
+the detector and the histogram all run in libmcv.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import binding as B
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def beam_struct(beam):
+    return B.BeamParams(beam.ei_mev, beam.ei_rel_sigma, beam.div_sigma_rad, beam.width_m,
+                        beam.height_m, beam.z0_m, beam.l1_m)
+
+
+def detector_struct(det):
+    d = B.Detector()
+    d.kind = det.kind
+    d.radius_m, d.height_m = det.radius_m, det.height_m
+    d.n_phi, d.n_y, d.n_rows = det.n_phi, det.n_y, det.n_rows
+    d.packs[:] = list(det.packs) + [0] * (3 - len(det.packs))
+    d.row_y_m[:] = list(det.row_y_m) + [0.0] * (3 - len(det.row_y_m))
+    d.tubes_per_pack, d.pixels_per_tube = det.tubes_per_pack, det.pixels_per_tube
+    d.tube_r_m, d.tube_len_m, d.tube_pitch_m = det.tube_r_m, det.tube_len_m, det.tube_pitch_m
+    d.pack_gap_m, d.phi0_rad = det.pack_gap_m, det.phi0_rad
+    d.he3_n_per_A3, d.he3_sig_abs_b = det.he3_n_per_A3, det.he3_sig_abs_b
+    d.tof_min_s, d.tof_max_s, d.n_tof = det.tof_min_s, det.tof_max_s, det.n_tof
+    return d
+
+
+def sample_struct(wl, fp_mode, table=None):
+    """mcv_sample from a workload; `table` is the device FP32 S(Q,E) tensor (if any)."""
+    s = B.Sample()
+    s.n_scatterers = len(wl.scatterers)
+    for j, sc in enumerate(wl.scatterers):
+        t = s.scat[j]
+        t.shape = sc.kind
+        t.dims[:] = list(sc.dims) + [0.0] * (3 - len(sc.dims))
+        t.rot_y_rad = sc.rot_y
+        t.n_per_A3, t.sig_abs_b = sc.n_per_A3, sc.sig_abs_b
+        t.n_kernels = len(sc.kernels)
+        for k, (kt, ks) in enumerate(sc.kernels):
+            t.kernel[k] = kt
+            t.kernel_sig_b[k] = ks
+    s.max_orders, s.min_prob, s.fp_mode = wl.max_orders, wl.min_prob, fp_mode
+    if wl.sqe is not None:
+        if table is None:
+            raise ValueError("the S(Q,E) table must be on the device")
+        s.sqe.table = table.data_ptr()
+        s.sqe.nq, s.sqe.ne = wl.sqe.nq, wl.sqe.ne
+        s.sqe.q_max, s.sqe.e_min, s.sqe.e_max = wl.sqe.q_max, wl.sqe.e_min, wl.sqe.e_max
+    if wl.bvk is not None:
+        v = wl.bvk
+        s.bvk.phi_Nm, s.bvk.mass_u, s.bvk.a_A = v.phi_Nm, v.mass_u, v.a_A
+        s.bvk.msd_A2, s.bvk.temperature_K = v.msd_A2, v.temperature_K
+    return s
+
+
+class NeutronBuffers:
+    """Caller-owned SoA device arrays for `n` packet slots."""
+
+    def __init__(self, n, fp_mode, device="cuda"):
+        dt = torch.float32 if fp_mode == B.FP32 else torch.float64
+        self.n = n
+        self.fp_mode = fp_mode
+        mk = lambda: torch.empty(n, dtype=dt, device=device)
+        self.x, self.y, self.z, self.vx, self.vy, self.vz, self.w = (mk() for _ in range(7))
+        self.t = torch.empty(n, dtype=torch.float64, device=device)
+        self.id = torch.empty(n, dtype=torch.int64, device=device)
+        self.order = torch.full((n,), -1, dtype=torch.int32, device=device)
+
+    def struct(self):
+        return B.Neutrons(*(t.data_ptr() for t in (self.x, self.y, self.z, self.vx, self.vy,
+                                                    self.vz, self.t, self.w, self.id,
+                                                    self.order)), self.n)
+
+    def to_dict(self):
+        return {k: getattr(self, k).cpu().numpy() for k in
+                ("x", "y", "z", "vx", "vy", "vz", "t", "w", "id", "order")}
+
+
+class Context:
+    """One mcv_ctx on one CUDA device."""
+
+    def __init__(self, device=0):
+        torch.cuda.set_device(device)
+        self.device = device
+        self.handle = B.mcv_create(device)
+
+    def close(self):
+        if self.handle is not None:
+            B.mcv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        B.mcv_sync(self.handle, _stream())
+
+    # ---- forward path --------------------------------------------------------------
+    def table(self, wl):
+        if wl.sqe is None:
+            return None
+        return torch.from_numpy(wl.sqe.table).to("cuda", non_blocking=False).contiguous()
+
+    def new_hist(self, det):
+        counts = torch.zeros(det.n_bins, dtype=torch.float64, device="cuda")
+        tallies = torch.zeros(B.MCV_NTALLY, dtype=torch.float64, device="cuda")
+        return counts, tallies
+
+    def trace(self, wl, fp_mode=B.FP64, n=None, first_id=0, table=None, counts=None,
+              tallies=None, beam_in=None, sync=True):
+        """Fused path: source -> sample -> detector -> histogram; returns (counts, tallies)."""
+        n = wl.n if n is None else n
+        if table is None:
+            table = self.table(wl)
+        if counts is None and tallies is None:
+            counts, tallies = self.new_hist(wl.detector)
+        sample = sample_struct(wl, fp_mode, table)
+        det = detector_struct(wl.detector)
+        hist = B.Hist(_ptr(counts), _ptr(tallies))
+        inp = beam_in.struct() if beam_in is not None else None
+        B.mcv_trace_sample(self.handle, sample, beam_struct(wl.beam), inp, wl.seed, wl.sim_id,
+                           first_id, n, det, hist, None, _stream())
+        if sync:
+            self.sync()
+        return counts, tallies
+
+    def trace_packets(self, wl, fp_mode=B.FP64, n=None, first_id=0, table=None, beam_in=None,
+                      tallies=None, sync=True):
+        """Unfused sample step: every emitted packet into n*(max_orders+1) slots."""
+        n = wl.n if n is None else n
+        if table is None:
+            table = self.table(wl)
+        pk = NeutronBuffers(n * (wl.max_orders + 1), fp_mode)
+        sample = sample_struct(wl, fp_mode, table)
+        hist = B.Hist(None, _ptr(tallies)) if tallies is not None else None
+        inp = beam_in.struct() if beam_in is not None else None
+        B.mcv_trace_sample(self.handle, sample, beam_struct(wl.beam), inp, wl.seed, wl.sim_id,
+                           first_id, n, None, hist, pk.struct(), _stream())
+        if sync:
+            self.sync()
+        return pk
+
+    def beam(self, wl, fp_mode=B.FP64, n=None, first_id=0, sync=True):
+        n = wl.n if n is None else n
+        out = NeutronBuffers(n, fp_mode)
+        B.mcv_beam(self.handle, beam_struct(wl.beam), fp_mode, wl.seed, wl.sim_id, first_id, n,
+                   out.struct(), _stream())
+        if sync:
+            self.sync()
+        return out
+
+    def detect(self, wl, packets, counts=None, tallies=None, events=True, sync=True):
+        """Detector step on stored packets; returns (counts, tallies, events dict)."""
+        det = detector_struct(wl.detector)
+        if counts is None and tallies is None:
+            counts, tallies = self.new_hist(wl.detector)
+        ev = None
+        evs = None
+        if events:
+            n = packets.n
+            ev = {"pixel": torch.empty(n, dtype=torch.int32, device="cuda"),
+                  "tof": torch.empty(n, dtype=torch.float64, device="cuda"),
+                  "w_det": torch.empty(n, dtype=torch.float64, device="cuda"),
+                  "bin": torch.empty(n, dtype=torch.int64, device="cuda")}
+            evs = B.Events(*(ev[k].data_ptr() for k in ("pixel", "tof", "w_det", "bin")))
+        hist = B.Hist(_ptr(counts), _ptr(tallies))
+        B.mcv_detect(self.handle, det, packets.fp_mode, packets.struct(), wl.seed, wl.sim_id,
+                     hist, evs, _stream())
+        if sync:
+            self.sync()
+        return counts, tallies, ev
+
+
+def _grad_call(c, wl, target, scale_c, fp_mode, n, first_id, table, sig_abs, sig_s,
+               grad_scatterer, counts=None, g_work=None):
+    """mcv_grad with the cross sections of `grad_scatterer` replaced by sig_abs, sig_s (the
+    kernels' cross sections scaled together)."""
+    sample = sample_struct(wl, fp_mode, table)
+    sc = sample.scat[grad_scatterer]
+    if sig_abs is not None:
+        sc.sig_abs_b = float(sig_abs)
+    if sig_s is not None:
+        total = sum(sc.kernel_sig_b[k] for k in range(sc.n_kernels))
+        for k in range(sc.n_kernels):
+            sc.kernel_sig_b[k] = sc.kernel_sig_b[k] * float(sig_s) / total
+    nb = wl.detector.n_bins
+    if counts is None:
+        counts = torch.empty(nb, dtype=torch.float64, device="cuda")
+    if g_work is None:
+        g_work = torch.empty(nb, dtype=torch.float64, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    dsqe = torch.empty(wl.sqe.table.size if wl.sqe is not None else 1, dtype=torch.float64,
+                       device="cuda")
+    dsig = torch.empty(2, dtype=torch.float64, device="cuda")
+    hist = B.Hist(_ptr(counts), None)
+    B.mcv_grad(c.handle, sample, beam_struct(wl.beam), detector_struct(wl.detector), wl.seed,
+               wl.sim_id, first_id, n, _ptr(target), float(scale_c), grad_scatterer, hist,
+               _ptr(g_work), _ptr(loss), _ptr(dsqe), _ptr(dsig), _stream())
+    return {"loss": loss, "dsqe": dsqe, "dsig": dsig, "hist": counts, "g": g_work}
+
+
+def _grad_method(self, wl, target, scale_c, fp_mode=B.FP64, n=None, first_id=0, table=None,
+                 grad_scatterer=0, sync=True, counts=None, g_work=None):
+    """Chi-squared loss of the simulated histogram and its adjoint gradient (FP64 outputs)."""
+    n = wl.n if n is None else n
+    if table is None:
+        table = self.table(wl)
+    out = _grad_call(self, wl, target, scale_c, fp_mode, n, first_id, table, None, None,
+                     grad_scatterer, counts, g_work)
+    if sync:
+        self.sync()
+    return out
+
+
+Context.grad = _grad_method
+
+
+class Chi2Loss(torch.autograd.Function):
+    """loss = chi2(I(table, sig_abs, sig_s), target) with the hand-written adjoint kernel as
+    its backward.  `table` is the FP32 S(Q,E) tensor on the device; sig_abs and sig_s are
+    0-d tensors (barn) of scatterer `grad_scatterer`."""
+
+    @staticmethod
+    def forward(fctx, table, sig_abs, sig_s, run):
+        c, wl, target, scale_c, fp_mode, n, first_id, gs = run
+        out = _grad_call(c, wl, target, scale_c, fp_mode, n, first_id, table.detach().contiguous(),
+                         sig_abs.item(), sig_s.item(), gs)
+        fctx.save_for_backward(out["dsqe"], out["dsig"])
+        fctx.shapes = (table.shape, table.dtype, sig_abs.dtype, sig_s.dtype)
+        return out["loss"][0].to(torch.float64)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        dsqe, dsig = fctx.saved_tensors
+        shape, tdt, adt, sdt = fctx.shapes
+        g_table = (grad_out * dsqe).reshape(shape).to(tdt)
+        return g_table, (grad_out * dsig[0]).to(adt), (grad_out * dsig[1]).to(sdt), None
+
+
+def chi2_loss(ctx, wl, table, sig_abs, sig_s, target, scale_c, fp_mode=B.FP32, n=None,
+              first_id=0, grad_scatterer=0):
+    n = wl.n if n is None else n
+    run = (ctx, wl, target, scale_c, fp_mode, n, first_id, grad_scatterer)
+    return Chi2Loss.apply(table, sig_abs, sig_s, run)

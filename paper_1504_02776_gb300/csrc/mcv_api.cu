@@ -1,0 +1,529 @@
+// C ABI of libmcv.so (declared in include/mcv.h): argument checking, derived constants,
+// launch shapes.  No call here allocates device memory except mcv_create.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "mcv_launch.h"
+
+struct mcv_ctx {
+  int device;
+  int sm_count;
+  int* d_err;          // device error flag (kernels set it; mcv_sync reads and clears it)
+  unsigned long long* d_queue;  // work-queue counters of the batched launch
+  int occ[2][3][3];    // cached blocks per SM of the chain kernel: [fp][ns 1,2,4][det]
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mcv_status fail(mcv_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+mcv_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(MCV_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+// ---- descriptions -> device parameter blocks -------------------------------------------
+mcv_status build_beam(const mcv_beam_params* b, mcv::DBeam* B) {
+  if (!b) return fail(MCV_EINVAL, "beam parameters are NULL");
+  const double v[] = {b->ei_mev, b->ei_rel_sigma, b->div_sigma_rad, b->width_m, b->height_m,
+                      b->z0_m, b->l1_m};
+  for (double x : v)
+    if (!is_finite(x)) return fail(MCV_EINVAL, "beam parameter is not finite");
+  if (!(b->ei_mev > 0.0)) return fail(MCV_EINVAL, "beam energy must be positive");
+  if (b->ei_rel_sigma < 0 || b->div_sigma_rad < 0 || b->width_m < 0 || b->height_m < 0)
+    return fail(MCV_EINVAL, "beam spreads must be non-negative");
+  if (!(b->l1_m >= b->z0_m)) return fail(MCV_EINVAL, "beam needs l1_m >= z0_m");
+  B->ei = b->ei_mev;
+  B->rel = b->ei_rel_sigma;
+  B->div = b->div_sigma_rad;
+  B->width = b->width_m;
+  B->height = b->height_m;
+  B->z0 = b->z0_m;
+  B->l1 = b->l1_m;
+  B->speed0 = std::sqrt(b->ei_mev / mcv::kMeVPerV2);
+  B->t0 = (b->l1_m - b->z0_m) / B->speed0;
+  return MCV_OK;
+}
+
+mcv_status build_sample(const mcv_sample* s, mcv::DSample* S) {
+  if (!s) return fail(MCV_EINVAL, "sample is NULL");
+  std::memset(S, 0, sizeof(*S));
+  if (s->n_scatterers < 1 || s->n_scatterers > MCV_MAX_SCATTERERS)
+    return fail(MCV_EINVAL, "n_scatterers must be 1..4");
+  if (s->max_orders < 0 || s->max_orders > 7) return fail(MCV_EINVAL, "max_orders must be 0..7");
+  if (s->fp_mode != MCV_FP64 && s->fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
+  if (std::isnan(s->min_prob)) return fail(MCV_EINVAL, "min_prob is NaN");
+  S->ns = s->n_scatterers;
+  S->max_orders = s->max_orders;
+  S->min_prob = s->min_prob;
+  bool need_sqe = false;
+  for (int j = 0; j < s->n_scatterers; ++j) {
+    const mcv_scatterer& a = s->scat[j];
+    mcv::DScat& d = S->s[j];
+    for (double x : {a.dims[0], a.dims[1], a.dims[2], a.rot_y_rad, a.n_per_A3, a.sig_abs_b,
+                     a.kernel_sig_b[0], a.kernel_sig_b[1]})
+      if (!is_finite(x)) return fail(MCV_EINVAL, "scatterer parameter is not finite");
+    if (a.n_per_A3 < 0 || a.sig_abs_b < 0) return fail(MCV_EINVAL, "negative density or cross section");
+    if (a.n_kernels < 1 || a.n_kernels > 2) return fail(MCV_EINVAL, "n_kernels must be 1 or 2");
+    double sig = 0.0;
+    for (int k = 0; k < a.n_kernels; ++k) {
+      if (a.kernel[k] != MCV_KERNEL_ISO && a.kernel[k] != MCV_KERNEL_SQE)
+        return fail(MCV_EINVAL, "kernel kind not supported by this build");
+      if (a.kernel_sig_b[k] < 0) return fail(MCV_EINVAL, "negative kernel cross section");
+      if (a.kernel[k] == MCV_KERNEL_SQE) need_sqe = true;
+      sig += a.kernel_sig_b[k];
+    }
+    d.shape = a.shape;
+    d.dim0 = a.dims[0];
+    d.dim1 = a.dims[1];
+    d.dim2 = a.dims[2];
+    if (a.shape == MCV_SHAPE_SOLID_CYL) {
+      if (!(a.dims[0] > 0 && a.dims[1] > 0)) return fail(MCV_EINVAL, "cylinder needs r, h > 0");
+      d.half_h = 0.5 * a.dims[1];
+    } else if (a.shape == MCV_SHAPE_HOLLOW_CYL) {
+      if (!(a.dims[0] >= 0 && a.dims[1] > a.dims[0] && a.dims[2] > 0))
+        return fail(MCV_EINVAL, "hollow cylinder needs 0 <= r_in < r_out, h > 0");
+      d.half_h = 0.5 * a.dims[2];
+    } else if (a.shape == MCV_SHAPE_BLOCK) {
+      if (!(a.dims[0] > 0 && a.dims[1] > 0 && a.dims[2] > 0))
+        return fail(MCV_EINVAL, "block needs positive sides");
+    } else {
+      return fail(MCV_EINVAL, "unknown shape");
+    }
+    d.cos_rot = std::cos(a.rot_y_rad);
+    d.sin_rot = std::sin(a.rot_y_rad);
+    d.nk = a.n_kernels;
+    d.ktype0 = a.kernel[0];
+    d.ktype1 = a.n_kernels == 2 ? a.kernel[1] : a.kernel[0];
+    d.ksig0 = a.kernel_sig_b[0];
+    d.ksig_sum = a.n_kernels == 2 ? a.kernel_sig_b[0] + a.kernel_sig_b[1] : a.kernel_sig_b[0];
+    d.sig_s = sig;
+    d.n100 = 100.0 * a.n_per_A3;
+    d.mu_s = 100.0 * a.n_per_A3 * sig;
+    d.mu_a_v = 100.0 * a.n_per_A3 * a.sig_abs_b * 2200.0;
+  }
+  if (need_sqe) {
+    const mcv_sqe& q = s->sqe;
+    if (!q.table || q.nq <= 0 || q.ne <= 0) return fail(MCV_EINVAL, "S(Q,E) table missing");
+    if ((int64_t)q.nq * q.ne > (int64_t)1 << 30) return fail(MCV_EINVAL, "S(Q,E) table too large");
+    if (!(q.q_max > 0 && q.e_max > q.e_min && is_finite(q.q_max) && is_finite(q.e_min) && is_finite(q.e_max)))
+      return fail(MCV_EINVAL, "bad S(Q,E) grid");
+    S->sqe = q.table;
+    S->nq = q.nq;
+    S->ne = q.ne;
+    S->q_max = q.q_max;
+    S->e_min = q.e_min;
+    S->e_max = q.e_max;
+    S->dq = q.q_max / q.nq;
+    S->de = (q.e_max - q.e_min) / q.ne;
+    S->has_sqe = 1;
+  }
+  return MCV_OK;
+}
+
+mcv_status build_detector(const mcv_detector* d, mcv::DDet* D) {
+  if (!d) return fail(MCV_EINVAL, "detector is NULL");
+  std::memset(D, 0, sizeof(*D));
+  if (d->kind != MCV_DET_SURFACE && d->kind != MCV_DET_TUBES)
+    return fail(MCV_EINVAL, "unknown detector kind");
+  if (d->n_tof < 1 || !(d->tof_max_s > d->tof_min_s) || !is_finite(d->tof_min_s) || !is_finite(d->tof_max_s))
+    return fail(MCV_EINVAL, "bad tof binning");
+  if (!(d->radius_m > 0) || !is_finite(d->radius_m)) return fail(MCV_EINVAL, "bad detector radius");
+  D->kind = d->kind;
+  D->radius = d->radius_m;
+  D->n_tof = d->n_tof;
+  D->tof_min = d->tof_min_s;
+  D->dt = (d->tof_max_s - d->tof_min_s) / d->n_tof;
+  D->inv_dt = 1.0 / D->dt;
+  int64_t npix = 0;
+  if (d->kind == MCV_DET_SURFACE) {
+    if (d->n_phi < 1 || d->n_y < 1 || !(d->height_m > 0) || !is_finite(d->height_m))
+      return fail(MCV_EINVAL, "bad surface detector");
+    D->height = d->height_m;
+    D->half_h = 0.5 * d->height_m;
+    D->n_phi = d->n_phi;
+    D->n_y = d->n_y;
+    npix = (int64_t)d->n_phi * d->n_y;
+  } else {
+    if (d->n_rows < 1 || d->n_rows > 3 || d->tubes_per_pack < 1 || d->pixels_per_tube < 1)
+      return fail(MCV_EINVAL, "bad tube detector layout");
+    for (double x : {d->tube_r_m, d->tube_len_m, d->tube_pitch_m, d->pack_gap_m, d->phi0_rad,
+                     d->he3_n_per_A3, d->he3_sig_abs_b})
+      if (!is_finite(x)) return fail(MCV_EINVAL, "tube parameter is not finite");
+    if (!(d->tube_r_m > 0 && d->tube_len_m > 0 && d->tube_pitch_m > 0 && d->pack_gap_m >= 0 &&
+          d->he3_n_per_A3 > 0 && d->he3_sig_abs_b > 0))
+      return fail(MCV_EINVAL, "bad tube dimensions or gas");
+    int max_packs = 0, off = 0;
+    for (int i = 0; i < d->n_rows; ++i) {
+      if (d->packs[i] < 1) return fail(MCV_EINVAL, "a row needs at least one pack");
+      if (!is_finite(d->row_y_m[i])) return fail(MCV_EINVAL, "row height is not finite");
+      D->packs[i] = d->packs[i];
+      D->row_y[i] = d->row_y_m[i];
+      D->row_off[i] = off;
+      off += d->packs[i];
+      if (d->packs[i] > max_packs) max_packs = d->packs[i];
+    }
+    if ((int64_t)max_packs * d->tubes_per_pack > MCV_MAX_TUBES_PER_ROW)
+      return fail(MCV_EINVAL, "more than 512 tubes in a row");
+    D->n_rows = d->n_rows;
+    D->tubes_per_pack = d->tubes_per_pack;
+    D->pixels_per_tube = d->pixels_per_tube;
+    D->max_tubes_row = max_packs * d->tubes_per_pack;
+    D->tube_r = d->tube_r_m;
+    D->half_len = 0.5 * d->tube_len_m;
+    D->pitch = d->tube_pitch_m;
+    D->period = d->tubes_per_pack * d->tube_pitch_m + d->pack_gap_m;
+    D->phi0 = d->phi0_rad;
+    D->pix_len = d->tube_len_m / d->pixels_per_tube;
+    D->mu_he_v = 100.0 * d->he3_n_per_A3 * d->he3_sig_abs_b * 2200.0;
+    for (int c = 0; c < D->max_tubes_row; ++c) {
+      const int pc = c / d->tubes_per_pack, tc = c % d->tubes_per_pack;
+      const double phic =
+          d->phi0_rad + (pc * D->period + (tc + 0.5) * d->tube_pitch_m) / d->radius_m;
+      D->tube_u[2 * c] = std::sin(phic);
+      D->tube_u[2 * c + 1] = std::cos(phic);
+    }
+    npix = (int64_t)off * d->tubes_per_pack * d->pixels_per_tube;
+  }
+  if (npix > ((int64_t)1 << 31) - 1) return fail(MCV_EINVAL, "too many pixels");
+  D->n_bins = npix * d->n_tof;
+  return MCV_OK;
+}
+
+bool neutrons_ok(const mcv_neutrons* a, bool need_ids) {
+  if (!a) return false;
+  if (!a->x || !a->y || !a->z || !a->vx || !a->vy || !a->vz || !a->t || !a->w) return false;
+  if (need_ids && (!a->id || !a->order)) return false;
+  return a->n >= 0;
+}
+
+int ns_index(int ns) { return ns <= 1 ? 0 : (ns == 2 ? 1 : 2); }
+
+mcv_status check_ctx(mcv_ctx* ctx) {
+  if (!ctx) return fail(MCV_EINVAL, "context is NULL");
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != ctx->device) {
+    e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  }
+  return MCV_OK;
+}
+
+int grid_for(mcv_ctx* ctx, int64_t items, int per_sm) {
+  const int64_t full = (int64_t)ctx->sm_count * per_sm;
+  const int64_t need = (items + mcv::trace_threads() - 1) / mcv::trace_threads();
+  int64_t g = need < full ? need : full;
+  return (int)(g < 1 ? 1 : g);
+}
+
+const int64_t kMaxNeutrons = (int64_t)1 << 40;
+
+}  // namespace
+
+extern "C" {
+
+const char* mcv_last_error(void) { return g_last_error.c_str(); }
+
+mcv_status mcv_create(int device, mcv_ctx** out) {
+  if (!out) return fail(MCV_EINVAL, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(MCV_EINVAL, "no such device");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  mcv_ctx* c = new mcv_ctx();
+  c->device = device;
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  e = cudaMalloc(&c->d_err, 256);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(MCV_ENOMEM, "cannot allocate the context's device block");
+  }
+  c->d_queue = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->d_err) + 128);
+  e = cudaMemset(c->d_err, 0, 256);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_err);
+    delete c;
+    return cuda_fail(e, "cudaMemset");
+  }
+  std::memset(c->occ, 0, sizeof(c->occ));
+  *out = c;
+  return MCV_OK;
+}
+
+mcv_status mcv_destroy(mcv_ctx* ctx) {
+  if (!ctx) return MCV_OK;
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->d_err);
+  delete ctx;
+  return MCV_OK;
+}
+
+mcv_status mcv_sync(mcv_ctx* ctx, void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int flag = 0;
+  e = cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  if (flag) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return fail(MCV_EDEVICE, "a kernel found an out-of-range index");
+  }
+  return MCV_OK;
+}
+
+int64_t mcv_detector_pixels(const mcv_detector* det) {
+  mcv::DDet D;
+  if (build_detector(det, &D) != MCV_OK) return 0;
+  return D.n_bins / D.n_tof;
+}
+
+mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  if (n < 0 || (n > 0 && !dst)) return fail(MCV_EINVAL, "bad buffer");
+  cudaError_t e = mcv::launch_zero(dst, n, ctx->sm_count * 8, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "zero kernel launch");
+  return MCV_OK;
+}
+
+mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint32_t seed,
+                    uint32_t sim_id, int64_t first_id, int64_t n, mcv_neutrons* out,
+                    void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  if (fp_mode != MCV_FP64 && fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
+  if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
+    return fail(MCV_EINVAL, "bad neutron range");
+  if (!neutrons_ok(out, false) || out->n < n) return fail(MCV_EINVAL, "bad output arrays");
+  mcv::TraceArgs A;
+  std::memset(&A, 0, sizeof(A));
+  st = build_beam(beam, &A.B);
+  if (st != MCV_OK) return st;
+  if (n == 0) return MCV_OK;
+  A.seed = seed;
+  A.sim_id = sim_id;
+  A.first_id = first_id;
+  A.n = n;
+  A.pk_x = out->x;
+  A.pk_y = out->y;
+  A.pk_z = out->z;
+  A.pk_vx = out->vx;
+  A.pk_vy = out->vy;
+  A.pk_vz = out->vz;
+  A.pk_w = out->w;
+  A.pk_t = out->t;
+  A.pk_id = out->id;
+  A.pk_order = out->order;
+  cudaError_t e = mcv::launch_beam(A, fp_mode, grid_for(ctx, n, 16), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "beam kernel launch");
+  return MCV_OK;
+}
+
+mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
+                            const mcv_neutrons* in, uint32_t seed, uint32_t sim_id,
+                            int64_t first_id, int64_t n, const mcv_detector* det, mcv_hist* hist,
+                            mcv_neutrons* packets, void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  mcv::TraceArgs A;
+  std::memset(&A, 0, sizeof(A));
+  st = build_sample(sample, &A.S);
+  if (st != MCV_OK) return st;
+  if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
+    return fail(MCV_EINVAL, "bad neutron range");
+  if (in) {
+    if (!neutrons_ok(in, false) || in->n < n) return fail(MCV_EINVAL, "bad input arrays");
+  } else {
+    st = build_beam(beam, &A.B);
+    if (st != MCV_OK) return st;
+  }
+  const bool fused = det != nullptr;
+  if (fused) {
+    st = build_detector(det, &A.D);
+    if (st != MCV_OK) return st;
+    if (!hist || (!hist->counts && !hist->tallies))
+      return fail(MCV_EINVAL, "a detector needs a histogram or tallies");
+  }
+  if (packets) {
+    if (!neutrons_ok(packets, true)) return fail(MCV_EINVAL, "bad packet arrays");
+    if (packets->n / (A.S.max_orders + 1) < n) return fail(MCV_EINVAL, "too few packet slots");
+  }
+  if (!fused && !packets && !(hist && hist->tallies))
+    return fail(MCV_EINVAL, "no output requested");
+  if (n == 0) return MCV_OK;
+  A.seed = seed;
+  A.sim_id = sim_id;
+  A.first_id = first_id;
+  A.n = n;
+  A.stop_on_zero = 1;
+  if (hist) {
+    A.hist = fused ? hist->counts : nullptr;
+    A.tallies = hist->tallies;
+  }
+  if (in) {
+    A.in_x = in->x;
+    A.in_y = in->y;
+    A.in_z = in->z;
+    A.in_vx = in->vx;
+    A.in_vy = in->vy;
+    A.in_vz = in->vz;
+    A.in_w = in->w;
+    A.in_t = in->t;
+    A.in_id = in->id;
+  }
+  if (packets) {
+    A.pk_x = packets->x;
+    A.pk_y = packets->y;
+    A.pk_z = packets->z;
+    A.pk_vx = packets->vx;
+    A.pk_vy = packets->vy;
+    A.pk_vz = packets->vz;
+    A.pk_w = packets->w;
+    A.pk_t = packets->t;
+    A.pk_id = packets->id;
+    A.pk_order = packets->order;
+  }
+  A.err = ctx->d_err;
+  const int detk = fused ? A.D.kind : MCV_DET_NONE;
+  const int fp = sample->fp_mode;
+  int& occ = ctx->occ[fp][ns_index(A.S.ns)][detk];
+  if (occ == 0) {
+    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.S.ns, detk, &occ);
+    if (e != cudaSuccess || occ < 1) occ = 1;
+  }
+  const int grid = grid_for(ctx, n, occ);
+  cudaError_t e = mcv::launch_trace(A, fp, detk, grid, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
+  return MCV_OK;
+}
+
+mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
+                      const mcv_neutrons* packets, uint32_t seed, uint32_t sim_id, mcv_hist* hist,
+                      mcv_events* events, void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  if (fp_mode != MCV_FP64 && fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
+  mcv::TraceArgs A;
+  std::memset(&A, 0, sizeof(A));
+  st = build_detector(det, &A.D);
+  if (st != MCV_OK) return st;
+  if (!neutrons_ok(packets, true)) return fail(MCV_EINVAL, "bad packet arrays (id and order required)");
+  if (!hist && !events) return fail(MCV_EINVAL, "no output requested");
+  if (packets->n == 0) return MCV_OK;
+  A.seed = seed;
+  A.sim_id = sim_id;
+  A.n = packets->n;
+  A.in_x = packets->x;
+  A.in_y = packets->y;
+  A.in_z = packets->z;
+  A.in_vx = packets->vx;
+  A.in_vy = packets->vy;
+  A.in_vz = packets->vz;
+  A.in_w = packets->w;
+  A.in_t = packets->t;
+  A.in_id = packets->id;
+  A.in_order = packets->order;
+  if (hist) {
+    A.hist = hist->counts;
+    A.tallies = hist->tallies;
+  }
+  A.err = ctx->d_err;
+  mcv::EventsArgs E{nullptr, nullptr, nullptr, nullptr};
+  if (events) E = mcv::EventsArgs{events->pixel, events->tof, events->w_det, events->bin};
+  cudaError_t e = mcv::launch_detect(A, E, fp_mode, A.D.kind, grid_for(ctx, packets->n, 16),
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "detect kernel launch");
+  return MCV_OK;
+}
+
+mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
+                    const mcv_detector* det, uint32_t seed, uint32_t sim_id, int64_t first_id,
+                    int64_t n, const double* target, double scale_c, int grad_scatterer,
+                    mcv_hist* hist, double* g_work, double* loss, double* dsqe, double* dsig,
+                    void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  mcv::TraceArgs A;
+  std::memset(&A, 0, sizeof(A));
+  st = build_sample(sample, &A.S);
+  if (st != MCV_OK) return st;
+  st = build_beam(beam, &A.B);
+  if (st != MCV_OK) return st;
+  st = build_detector(det, &A.D);
+  if (st != MCV_OK) return st;
+  if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
+    return fail(MCV_EINVAL, "bad neutron range");
+  if (!target || !g_work || !loss || !dsig || !hist || !hist->counts)
+    return fail(MCV_EINVAL, "mcv_grad needs target, hist->counts, g_work, loss and dsig");
+  if (A.S.has_sqe && !dsqe) return fail(MCV_EINVAL, "mcv_grad needs dsqe for an S(Q,E) sample");
+  if (grad_scatterer < 0 || grad_scatterer >= A.S.ns)
+    return fail(MCV_EINVAL, "grad_scatterer out of range");
+  if (!(A.S.s[grad_scatterer].sig_s > 0.0))
+    return fail(MCV_EINVAL, "the differentiated scatterer needs a positive cross section");
+  if (!is_finite(scale_c)) return fail(MCV_EINVAL, "scale_c is not finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int zgrid = ctx->sm_count * 8;
+  cudaError_t e = mcv::launch_zero(hist->counts, A.D.n_bins, zgrid, s);
+  if (e == cudaSuccess && hist->tallies) e = mcv::launch_zero(hist->tallies, MCV_NTALLY, 1, s);
+  if (e == cudaSuccess) e = mcv::launch_zero(loss, 1, 1, s);
+  if (e == cudaSuccess) e = mcv::launch_zero(dsig, 2, 1, s);
+  if (e == cudaSuccess && A.S.has_sqe) e = mcv::launch_zero(dsqe, (int64_t)A.S.nq * A.S.ne, zgrid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "zero kernel launch");
+  A.seed = seed;
+  A.sim_id = sim_id;
+  A.first_id = first_id;
+  A.n = n;
+  A.err = ctx->d_err;
+  A.gs = grad_scatterer;
+  const int fp = sample->fp_mode;
+  if (n > 0) {
+    // forward: the histogram of this neutron range
+    A.hist = hist->counts;
+    A.tallies = hist->tallies;
+    A.stop_on_zero = 1;
+    int& occ = ctx->occ[fp][ns_index(A.S.ns)][A.D.kind];
+    if (occ == 0) {
+      e = mcv::trace_blocks_per_sm(fp, A.S.ns, A.D.kind, &occ);
+      if (e != cudaSuccess || occ < 1) occ = 1;
+    }
+    e = mcv::launch_trace(A, fp, A.D.kind, grid_for(ctx, n, occ), s);
+    if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
+  }
+  e = mcv::launch_chi2(hist->counts, target, scale_c, A.D.n_bins, g_work, loss, ctx->sm_count * 8, s);
+  if (e != cudaSuccess) return cuda_fail(e, "chi2 kernel launch");
+  if (n > 0) {
+    // adjoint: the same paths, traced through zero weights
+    A.hist = nullptr;
+    A.tallies = nullptr;
+    A.stop_on_zero = 0;
+    A.g = g_work;
+    A.dsqe = A.S.has_sqe ? dsqe : nullptr;
+    A.dsig = dsig;
+    e = mcv::launch_adjoint(A, fp, A.D.kind, grid_for(ctx, n, 2), s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+  }
+  return MCV_OK;
+}
+
+}  // extern "C"

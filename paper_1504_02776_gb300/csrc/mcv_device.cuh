@@ -1,0 +1,670 @@
+// Device-side building blocks of the neutron ray-tracing hot path (MCViNE, Lin et al.):
+// counter-based random numbers, ray/shape intersection, the scattering kernels, the
+// detector system and the per-neutron chain of scatterings.  Everything is templated on
+// the real type R (float: the FP32 fast mode, double: the FP64 mode); time of flight is
+// always carried in double.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "mcv_params.h"
+
+namespace mcv {
+
+// ---- math by real type ----------------------------------------------------------------
+template <typename R>
+struct Mth;
+
+template <>
+struct Mth<float> {
+  static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float exp(float x) { return expf(x); }
+  static __device__ __forceinline__ float log(float x) { return logf(x); }
+  static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
+  static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
+  static __device__ __forceinline__ float tan(float x) { return tanf(x); }
+  static __device__ __forceinline__ float atan2(float y, float x) { return atan2f(y, x); }
+  static __device__ __forceinline__ float floor(float x) { return floorf(x); }
+  static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
+  static __device__ __forceinline__ float fmin(float a, float b) { return fminf(a, b); }
+  static __device__ __forceinline__ float fmax(float a, float b) { return fmaxf(a, b); }
+  // sin and cos of 2 pi u
+  static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) {
+    sincospif(2.0f * u, s, c);
+  }
+  static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
+};
+
+template <>
+struct Mth<double> {
+  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
+  static __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
+  static __device__ __forceinline__ double tan(double x) { return ::tan(x); }
+  static __device__ __forceinline__ double atan2(double y, double x) { return ::atan2(y, x); }
+  static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
+  static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
+  static __device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
+  static __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
+  static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) {
+    ::sincospi(2.0 * u, s, c);
+  }
+  static __device__ __forceinline__ double inf() { return CUDART_INF; }
+};
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------------------------
+struct Words {
+  uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ Words philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return Words{c0, c1, c2, c3};
+}
+
+// 53 random bits -> (k + 1/2) 2^-53 in (0,1); the FP32 mode rounds the same number to float
+template <typename R>
+__device__ __forceinline__ R to_unit(uint32_t hi, uint32_t lo);
+
+template <>
+__device__ __forceinline__ double to_unit<double>(uint32_t hi, uint32_t lo) {
+  const uint64_t k = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+  return __fma_rn((double)k, 0x1p-53, 0x1p-54);
+}
+
+template <>
+__device__ __forceinline__ float to_unit<float>(uint32_t hi, uint32_t lo) {
+  const uint64_t k = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+  const float u = __ull2float_rn(2ull * k + 1ull) * 0x1p-54f;
+  return fminf(u, 0x1.fffffep-1f);
+}
+
+// The stream of one neutron: key (seed, sim), counter (id lo, id hi, 4*(event+1)+block, 0).
+struct NeutronRng {
+  uint32_t k0, k1, n0, n1;
+  __device__ __forceinline__ NeutronRng(uint32_t seed, uint32_t sim, int64_t nid)
+      : k0(seed), k1(sim), n0((uint32_t)((uint64_t)nid & 0xffffffffu)),
+        n1((uint32_t)((uint64_t)nid >> 32)) {}
+  template <typename R>
+  __device__ __forceinline__ void pair(int event, int block, R* u0, R* u1) const {
+    const Words w = philox10(n0, n1, (uint32_t)(4 * (event + 1) + block), 0u, k0, k1);
+    *u0 = to_unit<R>(w.a, w.b);
+    *u1 = to_unit<R>(w.c, w.d);
+  }
+  template <typename R>
+  __device__ __forceinline__ R first(int event, int block) const {
+    const Words w = philox10(n0, n1, (uint32_t)(4 * (event + 1) + block), 0u, k0, k1);
+    return to_unit<R>(w.a, w.b);
+  }
+};
+
+// ---- packet state ---------------------------------------------------------------------
+template <typename R>
+struct Ray {
+  R x, y, z;        // m
+  R dx, dy, dz;     // unit direction
+  R speed;          // m/s
+  double t;         // s
+  R w;              // probability weight
+};
+
+// ---- source -----------------------------------------------------------------------------
+// Synthetic beam at the sample: Gaussian energy, uniform footprint, Gaussian divergence.
+// Returns false when the drawn energy is not positive (no packet).
+template <typename R>
+__device__ __forceinline__ bool make_beam(const DBeam& B, const NeutronRng& rng, Ray<R>* n);
+
+template <>
+__device__ __forceinline__ bool make_beam<double>(const DBeam& B, const NeutronRng& rng,
+                                                  Ray<double>* n) {
+  using M = Mth<double>;
+  double u0, u1, s, c;
+  rng.pair<double>(-1, 0, &u0, &u1);
+  M::sincos2pi(u1, &s, &c);
+  const double zE = M::sqrt(-2.0 * M::log(u0)) * c;
+  const double E = B.ei * (1.0 + B.rel * zE);
+  rng.pair<double>(-1, 1, &u0, &u1);
+  n->x = (u0 - 0.5) * B.width;
+  n->y = (u1 - 0.5) * B.height;
+  rng.pair<double>(-1, 2, &u0, &u1);
+  M::sincos2pi(u1, &s, &c);
+  const double rr = M::sqrt(-2.0 * M::log(u0));
+  const double ax = B.div * (rr * c), ay = B.div * (rr * s);
+  if (!(E > 0.0)) return false;
+  const double tx = M::tan(ax), ty = M::tan(ay);
+  const double norm = M::sqrt(tx * tx + ty * ty + 1.0);
+  n->dx = tx / norm;
+  n->dy = ty / norm;
+  n->dz = 1.0 / norm;
+  n->speed = M::sqrt(E / kMeVPerV2);
+  n->z = -B.z0;
+  n->t = (B.l1 - B.z0) / (n->speed * n->dz);
+  n->w = 1.0;
+  return true;
+}
+
+// FP32: speed and the flight time to the start plane are written as the nominal values
+// (computed once in FP64 on the host) times small FP32 corrections, so that the FP64 time
+// keeps ~1e-12 s accuracy: speed = v0 (1 + eta), eta = d/(1 + sqrt(1 + d)), d = rel z;
+// path/speed = t0 (1 + xi)/(1 + eta), xi = e/(1 + sqrt(1 + e)), e = tan^2 ax + tan^2 ay.
+template <>
+__device__ __forceinline__ bool make_beam<float>(const DBeam& B, const NeutronRng& rng,
+                                                 Ray<float>* n) {
+  using M = Mth<float>;
+  float u0, u1, s, c;
+  rng.pair<float>(-1, 0, &u0, &u1);
+  M::sincos2pi(u1, &s, &c);
+  const float zE = M::sqrt(-2.0f * M::log(u0)) * c;
+  const float dE = (float)B.rel * zE;
+  rng.pair<float>(-1, 1, &u0, &u1);
+  n->x = (u0 - 0.5f) * (float)B.width;
+  n->y = (u1 - 0.5f) * (float)B.height;
+  rng.pair<float>(-1, 2, &u0, &u1);
+  M::sincos2pi(u1, &s, &c);
+  const float rr = M::sqrt(-2.0f * M::log(u0));
+  const float ax = (float)B.div * (rr * c), ay = (float)B.div * (rr * s);
+  if (!(1.0f + dE > 0.0f)) return false;
+  const float tx = M::tan(ax), ty = M::tan(ay);
+  const float e = tx * tx + ty * ty;
+  const float sq = M::sqrt(1.0f + e);
+  n->dx = tx / sq;
+  n->dy = ty / sq;
+  n->dz = 1.0f / sq;
+  const float eta = dE / (1.0f + M::sqrt(1.0f + dE));
+  const float xi = e / (1.0f + sq);
+  n->speed = (float)B.speed0 * (1.0f + eta);
+  n->z = -(float)B.z0;
+  n->t = B.t0 + (double)((float)B.t0 * ((xi - eta) / (1.0f + eta)));
+  n->w = 1.0f;
+  return true;
+}
+
+// ---- geometry ----------------------------------------------------------------------------
+// Line r + s d inside the infinite cylinder x^2 + z^2 < rad^2 (axis y): closest-approach
+// form, squared axis distance (r x d)^2 / a with a = dx^2 + dz^2.
+template <typename R>
+__device__ __forceinline__ bool cyl_span(R rad, R x, R z, R dx, R dz, R* s1, R* s2) {
+  using M = Mth<R>;
+  const R a = dx * dx + dz * dz;
+  if (a == R(0)) {
+    if (x * x + z * z < rad * rad) {
+      *s1 = -M::inf();
+      *s2 = M::inf();
+      return true;
+    }
+    return false;
+  }
+  const R tc = -(x * dx + z * dz) / a;
+  const R cr = x * dz - z * dx;
+  const R g = rad * rad - cr * cr / a;
+  if (!(g > R(0))) return false;
+  const R half = M::sqrt(g / a);
+  *s1 = tc - half;
+  *s2 = tc + half;
+  return true;
+}
+
+// |p + s dp| < half
+template <typename R>
+__device__ __forceinline__ bool slab_span(R half, R p, R dp, R* s1, R* s2) {
+  using M = Mth<R>;
+  if (dp == R(0)) {
+    if (M::fabs(p) < half) {
+      *s1 = -M::inf();
+      *s2 = M::inf();
+      return true;
+    }
+    return false;
+  }
+  const R a = (-half - p) / dp, b = (half - p) / dp;
+  *s1 = M::fmin(a, b);
+  *s2 = M::fmax(a, b);
+  return true;
+}
+
+template <typename R>
+struct Seg {
+  R a, b;
+  int j;
+};
+
+template <typename R>
+__device__ __forceinline__ void put_seg(R a, R b, int j, Seg<R>* out, int* cnt) {
+  const R lo = Mth<R>::fmax(a, R(0));
+  if (b > lo) {
+    out[*cnt].a = lo;
+    out[*cnt].b = b;
+    out[*cnt].j = j;
+    *cnt += 1;
+  }
+}
+
+// Segments of one scatterer's shape (section 2.4.2, shapes combined by CSG: the hollow
+// cylinder is a difference).  Writes up to two segments at out[0..1].
+template <typename R>
+__device__ __forceinline__ int shape_segs(const DScat& S, int j, const Ray<R>& n, Seg<R>* out) {
+  using M = Mth<R>;
+  int cnt = 0;
+  R c1, c2, y1, y2;
+  if (S.shape == MCV_SHAPE_SOLID_CYL) {
+    if (cyl_span<R>((R)S.dim0, n.x, n.z, n.dx, n.dz, &c1, &c2) &&
+        slab_span<R>((R)S.half_h, n.y, n.dy, &y1, &y2))
+      put_seg<R>(M::fmax(c1, y1), M::fmin(c2, y2), j, out, &cnt);
+  } else if (S.shape == MCV_SHAPE_HOLLOW_CYL) {
+    if (cyl_span<R>((R)S.dim1, n.x, n.z, n.dx, n.dz, &c1, &c2) &&
+        slab_span<R>((R)S.half_h, n.y, n.dy, &y1, &y2)) {
+      const R lo = M::fmax(c1, y1), hi = M::fmin(c2, y2);
+      if (hi > lo) {
+        R i1, i2;
+        if (!cyl_span<R>((R)S.dim0, n.x, n.z, n.dx, n.dz, &i1, &i2)) {
+          put_seg<R>(lo, hi, j, out, &cnt);
+        } else {
+          put_seg<R>(lo, M::fmin(hi, i1), j, out, &cnt);
+          put_seg<R>(M::fmax(lo, i2), hi, j, out, &cnt);
+        }
+      }
+    }
+  } else if (S.shape == MCV_SHAPE_BLOCK) {
+    const R c = (R)S.cos_rot, s = (R)S.sin_rot;
+    const R xb = c * n.x - s * n.z, zb = s * n.x + c * n.z;
+    const R dxb = c * n.dx - s * n.dz, dzb = s * n.dx + c * n.dz;
+    R lo = -M::inf(), hi = M::inf(), a, b;
+    bool ok = slab_span<R>((R)(0.5 * S.dim0), xb, dxb, &a, &b);
+    lo = M::fmax(lo, a);
+    hi = M::fmin(hi, b);
+    ok = ok && slab_span<R>((R)(0.5 * S.dim1), n.y, n.dy, &a, &b);
+    lo = M::fmax(lo, a);
+    hi = M::fmin(hi, b);
+    ok = ok && slab_span<R>((R)(0.5 * S.dim2), zb, dzb, &a, &b);
+    lo = M::fmax(lo, a);
+    hi = M::fmin(hi, b);
+    if (ok) put_seg<R>(lo, hi, j, out, &cnt);
+  }
+  return cnt;
+}
+
+// All segments ahead in the sample assembly, sorted by entry (ray tracing in a composite,
+// section 2.4.3).  NS = number of scatterers (compile time); unused entries get a = +inf.
+template <typename R, int NS>
+__device__ __forceinline__ int assembly_segs(const DSample& S, const Ray<R>& n, Seg<R> (&seg)[2 * NS]) {
+  using M = Mth<R>;
+  int total = 0;
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    Seg<R> two[2];
+    two[0].a = M::inf();
+    two[1].a = M::inf();
+    two[0].b = two[1].b = R(0);
+    two[0].j = two[1].j = j;
+    const int c = (j < S.ns) ? shape_segs<R>(S.s[j], j, n, two) : 0;
+    seg[2 * j] = two[0];
+    seg[2 * j + 1] = two[1];
+    total += c;
+  }
+  // stable odd-even transposition sort on the entry distance
+#pragma unroll
+  for (int pass = 0; pass < 2 * NS; ++pass) {
+#pragma unroll
+    for (int i = (pass & 1); i + 1 < 2 * NS; i += 2) {
+      if (seg[i].a > seg[i + 1].a) {
+        const Seg<R> t = seg[i];
+        seg[i] = seg[i + 1];
+        seg[i + 1] = t;
+      }
+    }
+  }
+  return total;
+}
+
+template <typename R, int NS>
+__device__ __forceinline__ R pick_mu(const R (&mu)[NS], int j) {
+  R m = mu[0];
+#pragma unroll
+  for (int k = 1; k < NS; ++k)
+    if (j == k) m = mu[k];
+  return m;
+}
+
+// ---- scattering kernels (supplement: "Scattering kernels used in the examples") -----------
+template <typename R>
+struct Scatter {
+  R factor;   // weight multiplier
+  R rest;     // the multiplier without the table value
+  R s_value;  // table value or 1
+  int entry;  // table entry or -1
+  R q, e;
+};
+
+// unit vector at polar angle (c, s) and azimuth 2 pi u about the unit vector d
+template <typename R>
+__device__ __forceinline__ void turn(R c, R s, R u, R* dx, R* dy, R* dz) {
+  using M = Mth<R>;
+  const R x = *dx, y = *dy, z = *dz;
+  R e1x, e1y, e1z;
+  if (M::fabs(z) < R(0.9)) {  // (0,0,1) x d
+    e1x = -y;
+    e1y = x;
+    e1z = R(0);
+  } else {                    // (1,0,0) x d
+    e1x = R(0);
+    e1y = -z;
+    e1z = y;
+  }
+  const R inv = R(1) / M::sqrt(e1x * e1x + e1y * e1y + e1z * e1z);
+  e1x *= inv;
+  e1y *= inv;
+  e1z *= inv;
+  const R e2x = y * e1z - z * e1y, e2y = z * e1x - x * e1z, e2z = x * e1y - y * e1x;
+  R sp, cp;
+  M::sincos2pi(u, &sp, &cp);
+  *dx = x * c + (e1x * cp + e2x * sp) * s;
+  *dy = y * c + (e1y * cp + e2y * sp) * s;
+  *dz = z * c + (e1z * cp + e2z * sp) * s;
+}
+
+// incoherent elastic: isotropic, speed unchanged (Debye-Waller factor taken as 1)
+template <typename R>
+__device__ __forceinline__ void kernel_iso(const NeutronRng& rng, int o, Ray<R>* n, Scatter<R>* sc) {
+  using M = Mth<R>;
+  R u0, u1, sp, cp;
+  rng.pair<R>(o, 1, &u0, &u1);
+  const R ct = R(2) * u0 - R(1);
+  const R st = R(2) * M::sqrt(u0 * (R(1) - u0));
+  M::sincos2pi(u1, &sp, &cp);
+  n->dx = st * cp;
+  n->dy = st * sp;
+  n->dz = ct;
+  sc->factor = R(1);
+  sc->rest = R(1);
+  sc->s_value = R(1);
+  sc->entry = -1;
+  sc->q = R(0);
+  sc->e = R(0);
+}
+
+// tabulated isotropic S(Q,E): E uniform on [e_min, min(e_max, Ei)], Q uniform on
+// [|ki - kf|, min(ki + kf, q_max)], azimuth uniform; weight S Q dE dQ / (2 ki^2); nearest bin.
+// Returns false when the kernel cannot scatter (empty range or outside the table).
+template <typename R>
+__device__ __forceinline__ bool kernel_sqe(const DSample& S, const NeutronRng& rng, int o,
+                                           Ray<R>* n, Scatter<R>* sc, int* err) {
+  using M = Mth<R>;
+  const R Ei = (R)kMeVPerV2 * n->speed * n->speed;
+  const R ki = (R)kKPerV * n->speed;
+  const R e_lo = (R)S.e_min, e_hi = M::fmin((R)S.e_max, Ei);
+  if (!(e_hi > e_lo)) return false;
+  const R dE = e_hi - e_lo;
+  R u0, u1;
+  rng.pair<R>(o, 1, &u0, &u1);
+  const R E = e_lo + u0 * dE;
+  const R Ef = Ei - E;
+  if (!(Ef > R(0))) return false;
+  const R speed_f = M::sqrt(Ef / (R)kMeVPerV2);
+  const R kf = (R)kKPerV * speed_f;
+  const R q_lo = M::fabs(ki - kf);
+  const R q_hi = M::fmin(ki + kf, (R)S.q_max);
+  if (!(q_hi > q_lo)) return false;
+  const R dQ = q_hi - q_lo;
+  const R Q = q_lo + u1 * dQ;
+  // cos and sin of the scattering angle from 1 -/+ cos, each a product whose small factor
+  // is the sampled offset from an end of the Q range (no cancellation near 0 or pi)
+  const R den = R(2) * ki * kf;
+  const R one_m = (u1 * dQ) * (Q + q_lo) / den;
+  const R top = (q_hi == ki + kf) ? (R(1) - u1) * dQ : (ki + kf) - Q;
+  const R one_p = top * (ki + kf + Q) / den;
+  R c2t = (one_m <= one_p) ? R(1) - one_m : one_p - R(1);
+  c2t = M::fmin(R(1), M::fmax(R(-1), c2t));
+  const R s2t = M::sqrt(M::fmax(R(0), one_m * one_p));
+  const R fq = M::floor(Q / (R)S.dq), fe = M::floor((E - (R)S.e_min) / (R)S.de);
+  if (!(fq >= R(0) && fq < (R)S.nq && fe >= R(0) && fe < (R)S.ne)) return false;
+  const int entry = (int)fq * S.ne + (int)fe;
+  if (entry < 0 || entry >= S.nq * S.ne) {
+    *err = 1;
+    return false;
+  }
+  const R Sv = (R)__ldg(S.sqe + entry);
+  const R u2 = rng.first<R>(o, 2);
+  turn<R>(c2t, s2t, u2, &n->dx, &n->dy, &n->dz);
+  n->speed = speed_f;
+  sc->rest = Q * dE * dQ / (R(2) * ki * ki);
+  sc->factor = Sv * sc->rest;
+  sc->s_value = Sv;
+  sc->entry = entry;
+  sc->q = Q;
+  sc->e = E;
+  return true;
+}
+
+// ---- detector system (section 2.4.3, "Ray tracing in a detector system") -----------------
+template <typename R>
+struct Hit {
+  int64_t bin;      // >= 0 in range, -1 miss, -2 tof out of range
+  int32_t pixel;
+  double tof;
+  R w_det;
+  R pabs;           // detector weight factor (1 for the ideal surface)
+};
+
+// larger root of the ray with the origin-centred cylinder (the ray starts inside it)
+template <typename R>
+__device__ __forceinline__ bool exit_cyl(R rad, const Ray<R>& n, R* s) {
+  R s1, s2;
+  if (!cyl_span<R>(rad, n.x, n.z, n.dx, n.dz, &s1, &s2)) return false;
+  if (!(s2 > R(0)) || s2 == Mth<R>::inf()) return false;
+  *s = s2;
+  return true;
+}
+
+// Chord of a vertical tube (axis through R (ux, uz)) in coordinates along / across the
+// tube direction, so the large distance R cancels once.
+template <typename R>
+__device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>& n, R* s1, R* s2) {
+  const R a = n.dx * n.dx + n.dz * n.dz;
+  if (a == R(0)) return false;
+  const R o_rad = n.x * ux + n.z * uz - Rad;
+  const R o_tan = n.x * uz - n.z * ux;
+  const R d_rad = n.dx * ux + n.dz * uz;
+  const R d_tan = n.dx * uz - n.dz * ux;
+  const R tc = -(o_rad * d_rad + o_tan * d_tan) / a;
+  const R cr = o_rad * d_tan - o_tan * d_rad;
+  const R g = rt * rt - cr * cr / a;
+  if (!(g > R(0))) return false;
+  const R half = Mth<R>::sqrt(g / a);
+  *s1 = tc - half;
+  *s2 = tc + half;
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ double add_time(double t, R s, R speed) {
+  return t + (double)(s / speed);
+}
+
+// tof bin (FP64 mode: as written; FP32 mode: the offset from tof_min is taken in double,
+// then scaled in float)
+template <typename R>
+__device__ __forceinline__ int64_t tof_bin(const DDet& D, double tof);
+template <>
+__device__ __forceinline__ int64_t tof_bin<double>(const DDet& D, double tof) {
+  const double fb = ::floor((tof - D.tof_min) / D.dt);
+  if (!(fb >= 0.0 && fb < (double)D.n_tof)) return -1;
+  return (int64_t)fb;
+}
+template <>
+__device__ __forceinline__ int64_t tof_bin<float>(const DDet& D, double tof) {
+  const float fb = floorf((float)(tof - D.tof_min) * (float)D.inv_dt);
+  if (!(fb >= 0.0f && fb < (float)D.n_tof)) return -1;
+  return (int64_t)fb;
+}
+
+template <typename R>
+__device__ __forceinline__ Hit<R> detect_surface(const DDet& D, const Ray<R>& n) {
+  using M = Mth<R>;
+  Hit<R> h;
+  h.bin = -1;
+  h.pixel = -1;
+  h.tof = 0.0;
+  h.w_det = R(0);
+  h.pabs = R(0);
+  R s;
+  if (!exit_cyl<R>((R)D.radius, n, &s)) return h;
+  const R yh = n.y + s * n.dy;
+  const R half = (R)D.half_h;
+  if (yh < -half || yh >= half) return h;
+  const R xh = n.x + s * n.dx, zh = n.z + s * n.dz;
+  const R phi = M::atan2(xh, zh);
+  int ip = (int)M::floor((phi + (R)kPi) / (R)(2.0 * kPi) * (R)D.n_phi);
+  ip = min(max(ip, 0), D.n_phi - 1);
+  int iy = (int)M::floor((yh + half) / (R)D.height * (R)D.n_y);
+  iy = min(max(iy, 0), D.n_y - 1);
+  h.pixel = ip * D.n_y + iy;
+  h.tof = add_time<R>(n.t, s, n.speed);
+  h.w_det = n.w;
+  h.pabs = R(1);
+  const int64_t tb = tof_bin<R>(D, h.tof);
+  h.bin = (tb < 0) ? -2 : (int64_t)h.pixel * D.n_tof + tb;
+  return h;
+}
+
+// tube centre directions staged in shared memory: tu[2*i] = sin(phi_i), tu[2*i+1] = cos(phi_i)
+template <typename R>
+__device__ __forceinline__ Hit<R> detect_tubes(const DDet& D, const R* __restrict__ tu,
+                                               const Ray<R>& n, R u_det) {
+  using M = Mth<R>;
+  Hit<R> h;
+  h.bin = -1;
+  h.pixel = -1;
+  h.tof = 0.0;
+  h.w_det = R(0);
+  h.pabs = R(0);
+  const R Rad = (R)D.radius;
+  R sR;
+  if (!exit_cyl<R>(Rad, n, &sR)) return h;
+  const R Px = n.x + sR * n.dx, Py = n.y + sR * n.dy, Pz = n.z + sR * n.dz;
+  int row = -1, row_off = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (row < 0 && i < D.n_rows && M::fabs(Py - (R)D.row_y[i]) <= (R)D.half_len) {
+      row = i;
+      row_off = D.row_off[i];
+    }
+  }
+  if (row < 0) return h;
+  const int tpp = D.tubes_per_pack;
+  const R period = (R)D.period, pitch = (R)D.pitch;
+  const R arc = (M::atan2(Px, Pz) - (R)D.phi0) * Rad;
+  const R p = M::floor(arc / period);
+  const R within = arc - p * period;
+  R k = M::floor(within / pitch);
+  if (k > (R)(tpp - 1)) k = (R)(tpp - 1);
+  const int g = (int)p * tpp + (int)k;
+  const int n_tubes_row = D.packs[row] * tpp;
+  const R y_lo = (R)D.row_y[row] - (R)D.half_len;
+  const R y_hi = (R)D.row_y[row] + (R)D.half_len;
+  int best = -1;
+  R best_in = M::inf(), best_out = R(0);
+#pragma unroll
+  for (int dc = -1; dc <= 1; ++dc) {
+    const int c = g + dc;
+    if (c < 0 || c >= n_tubes_row) continue;
+    R s1, s2;
+    if (!tube_span<R>(Rad, tu[2 * c], tu[2 * c + 1], (R)D.tube_r, n, &s1, &s2)) continue;
+    R ys1, ys2;
+    if (n.dy == R(0)) {
+      if (!(n.y >= y_lo && n.y <= y_hi)) continue;
+      ys1 = -M::inf();
+      ys2 = M::inf();
+    } else {
+      const R a = (y_lo - n.y) / n.dy, b = (y_hi - n.y) / n.dy;
+      ys1 = M::fmin(a, b);
+      ys2 = M::fmax(a, b);
+    }
+    const R s_in = M::fmax(M::fmax(s1, ys1), R(0));
+    const R s_out = M::fmin(s2, ys2);
+    if (!(s_out > s_in)) continue;
+    if (s_in < best_in) {
+      best = c;
+      best_in = s_in;
+      best_out = s_out;
+    }
+  }
+  if (best < 0) return h;
+  const R L = best_out - best_in;
+  const R mu = (R)D.mu_he_v / n.speed;
+  const R pabs = -M::expm1(-mu * L);
+  const R x = -M::log1p(-u_det * pabs) / mu;
+  const R s_abs = best_in + x;
+  const R y_abs = n.y + s_abs * n.dy;
+  int j = (int)M::floor((y_abs - y_lo) / (R)D.pix_len);
+  j = min(max(j, 0), D.pixels_per_tube - 1);
+  const int pc = best / tpp, tc = best - pc * tpp;
+  h.pixel = ((row_off + pc) * tpp + tc) * D.pixels_per_tube + j;
+  h.tof = add_time<R>(n.t, s_abs, n.speed);
+  h.pabs = pabs;
+  h.w_det = n.w * pabs;
+  const int64_t tb = tof_bin<R>(D, h.tof);
+  h.bin = (tb < 0) ? -2 : (int64_t)h.pixel * D.n_tof + tb;
+  return h;
+}
+
+template <typename R, int DET>
+__device__ __forceinline__ Hit<R> detect(const DDet& D, const R* tu, const NeutronRng& rng,
+                                         int order, const Ray<R>& n) {
+  if (DET == MCV_DET_SURFACE) return detect_surface<R>(D, n);
+  const R u = rng.first<R>(order, 3);
+  return detect_tubes<R>(D, tu, n, u);
+}
+
+// ---- tallies ---------------------------------------------------------------------------
+// FP64 accumulators in FP64 mode; compensated (Kahan) FP32 sums in FP32 mode
+template <typename R>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+struct Counts {
+  uint32_t ndet = 0, nover = 0, nmiss = 0, nhit = 0, nemit = 0;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+  return __reduce_add_sync(0xffffffffu, v);
+}
+
+}  // namespace mcv

@@ -1,0 +1,28 @@
+// Host-side entry points of the kernels (mcv_trace.cu, mcv_grad.cu), used by the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mcv_params.h"
+
+namespace mcv {
+
+struct EventsArgs {
+  int32_t* pixel;
+  double* tof;
+  double* w_det;
+  int64_t* bin;
+};
+
+int trace_threads();
+cudaError_t trace_blocks_per_sm(int fp_mode, int ns, int det, int* blocks);
+cudaError_t launch_trace(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
+cudaError_t launch_beam(const TraceArgs& A, int fp_mode, int grid, cudaStream_t s);
+cudaError_t launch_detect(const TraceArgs& A, const EventsArgs& E, int fp_mode, int det, int grid,
+                          cudaStream_t s);
+cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
+                        double* g, double* loss, int grid, cudaStream_t s);
+cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
+
+}  // namespace mcv

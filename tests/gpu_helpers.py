@@ -1,0 +1,37 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI and bring the
+results back as numpy arrays in the oracle's layout."""
+import numpy as np
+
+FIELDS = ("x", "y", "z", "vx", "vy", "vz", "t", "w")
+
+
+def ctx():
+    from paper_1504_02776_gb300 import api
+    return api.Context(0)
+
+
+def packets(c, wl, fp_mode, n=None, first_id=0, beam_in=None):
+    pk = c.trace_packets(wl, fp_mode=fp_mode, n=n, first_id=first_id, beam_in=beam_in)
+    return pk, pk.to_dict()
+
+
+def compare_packets(gpu, orc, rtol=None):
+    """Relative deviation of each packet's state over the slots both sides filled:
+    position |dr| / max(|r|, 1 cm), velocity |dv| / |v|, time |dt| / t, weight |dw| / w."""
+    assert np.array_equal(gpu["order"], orc["order"]), "packet orders differ"
+    m = orc["order"] >= 0
+    assert np.array_equal(gpu["id"][m], orc["nid"][m])
+    g = {f: gpu[f][m].astype(np.float64) for f in FIELDS}
+    o = {f: orc[f][m] for f in FIELDS}
+    dr = np.sqrt(sum((g[f] - o[f]) ** 2 for f in ("x", "y", "z")))
+    rr = np.sqrt(sum(o[f] ** 2 for f in ("x", "y", "z")))
+    dv = np.sqrt(sum((g[f] - o[f]) ** 2 for f in ("vx", "vy", "vz")))
+    vv = np.sqrt(sum(o[f] ** 2 for f in ("vx", "vy", "vz")))
+    ow = np.where(o["w"] == 0, 1.0, np.abs(o["w"]))
+    return {"r": dr / np.maximum(rr, 1e-2), "v": dv / vv, "t": np.abs(g["t"] - o["t"]) / o["t"],
+            "w": np.abs(g["w"] - o["w"]) / ow}
+
+
+def run_events(c, wl, pk):
+    counts, tallies, ev = c.detect(wl, pk, events=True)
+    return counts, tallies, {k: v.cpu().numpy() for k, v in ev.items()}
