@@ -23,7 +23,7 @@ PACKET_DTYPE = np.dtype([
     ("x", np.float64), ("y", np.float64), ("z", np.float64),
     ("vx", np.float64), ("vy", np.float64), ("vz", np.float64),
     ("t", np.float64), ("w", np.float64), ("tof", np.float64), ("w_det", np.float64),
-    ("bin", np.int64)], align=True)
+    ("bin", np.int64), ("kappa", np.float64), ("kappa_det", np.float64)], align=True)
 
 EVENT_DTYPE = np.dtype([
     ("nid", np.int64), ("order", np.int32), ("kernel", np.int32), ("scatterer", np.int32),

@@ -48,6 +48,12 @@ double u01_from(uint32_t hi, uint32_t lo) {
   return (double)k * 0x1p-53 + 0x1p-54;
 }
 
+// ---- conditioning ---------------------------------------------------------------------
+// Condition estimate of the current packet's weight: each chord or range width that
+// subtracts nearly equal numbers adds its amplification factor (|value| / |difference|).
+// It only sets the tolerances the tests compare rounding-sensitive results with.
+thread_local double g_kappa = 0.0;
+
 // ---- geometry -------------------------------------------------------------------------
 // Interval of s in which the line r + s d lies inside the infinite cylinder x^2+z^2 < R^2
 // (axis along y through the origin).  Written with the point of closest approach: its
@@ -67,6 +73,7 @@ bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2) {
   double cr = r.x * d.z - r.z * d.x;
   double g = R * R - cr * cr / a;
   if (!(g > 0.0)) return false;
+  g_kappa += R * R / g;
   double half = std::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
@@ -88,6 +95,9 @@ bool tube_interval(double R, double ux, double uz, double rt, Vec3 r, Vec3 d, do
   double cr = o_rad * d_tan - o_tan * d_rad;
   double g = rt * rt - cr * cr / a;
   if (!(g > 0.0)) return false;
+  // the chord is sensitive to the tube radius (rt^2/g) and, through the lever arm, to the
+  // direction of the ray (closest-approach distance h, distance |tc| sqrt(a))
+  g_kappa += rt * rt / g + std::fabs(tc) * std::fabs(cr) / g;
   double half = std::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
@@ -111,10 +121,12 @@ bool slab_interval(double half, double p, double dp, double* s1, double* s2) {
   return true;
 }
 
-// Keep [a,b] clipped to s >= 0 if it has positive length.
+// Keep [a,b] clipped to s >= 0 if it has positive length.  Its length b - lo loses the
+// relative precision |a| + |b| over b - lo (a point close to the exit surface).
 int push_segment(double a, double b, double* sa, double* sb, int n) {
   double lo = std::max(a, 0.0);
   if (b > lo) {
+    g_kappa += (std::fabs(a) + std::fabs(b)) / (b - lo);
     sa[n] = lo;
     sb[n] = b;
     return n + 1;
@@ -409,7 +421,9 @@ bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], 
   if (!(e_hi > e_lo)) return false;
   double dE = e_hi - e_lo;
   double E = e_lo + u[0] * dE;
-  double Ef = Ei - E;
+  // Ef = Ei - E; when the range ends at Ei it is the sampled offset from that end, which
+  // keeps slow final neutrons accurate
+  double Ef = (e_hi == Ei) ? (1.0 - u[0]) * dE : Ei - E;
   if (!(Ef > 0.0)) return false;
   double speed_f = std::sqrt(Ef / kMeVPerV2);
   double kf = kKPerV * speed_f;
@@ -417,6 +431,7 @@ bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], 
   double q_hi = std::min(ki + kf, cfg.q_max);
   if (!(q_hi > q_lo)) return false;
   double dQ = q_hi - q_lo;
+  g_kappa += (ki + kf) / dQ;
   double Q = q_lo + u[1] * dQ;
   // scattering angle from Q^2 = ki^2 + kf^2 - 2 ki kf cos(2theta), written through
   // 1 - cos = (Q - q_lo)(Q + q_lo) / (2 ki kf) and 1 + cos = (ki + kf - Q)(ki + kf + Q) /
@@ -483,6 +498,7 @@ struct EmitRecord {
   double w;          // emitted weight
   double atten;      // exp(-tau_tot) of this emission
   double dlog_abs, dlog_s;
+  double kappa;      // condition estimate of w
 };
 
 // One neutron through the sample assembly, as a chain of at most N_max scatterings.
@@ -498,6 +514,7 @@ template <class Emit, class Scat>
 void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Emit emit,
                Scat on_scatter, double* tallies) {
   Neutron n;
+  g_kappa = 1.0;
   if (!make_beam(cfg, nid, &n)) return;
   for (int o = 0;; ++o) {
     if (n.w < cfg.min_prob) break;
@@ -515,6 +532,7 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     EmitRecord em;
     em.order = o;
     em.n = n;
+    em.kappa = g_kappa;
     em.atten = std::exp(-tau);
     em.w = n.w * em.atten;
     em.dlog_abs = 0.0;
@@ -596,7 +614,12 @@ void record_detection(const orc_config& cfg, int64_t nid, const EmitRecord& em, 
   orc_uniforms(cfg.seed, cfg.sim_id, nid, em.order, 3, u);
   int32_t pixel;
   double tof, w_det;
+  const double k_before = g_kappa;
+  g_kappa = 0.0;
   int64_t bin = detect(cfg, em.n.r, em.n.d, em.n.speed, em.n.t, em.w, u[0], &pixel, &tof, &w_det);
+  const double k_det = g_kappa;
+  g_kappa = k_before;
+  if (pk) pk->kappa_det = em.kappa + k_det;
   if (bin >= 0) {
     if (hist) hist[bin] += w_det;
     add_tally(tallies, ORC_T_WDET, w_det);
@@ -626,6 +649,8 @@ void fill_packet(int64_t nid, const EmitRecord& em, orc_packet* pk) {
   pk->vz = em.n.speed * em.n.d.z;
   pk->t = em.n.t;
   pk->w = em.w;
+  pk->kappa = em.kappa;
+  pk->kappa_det = em.kappa;
 }
 
 bool config_ok(const orc_config* cfg) {

@@ -77,6 +77,9 @@ typedef struct {
   double x, y, z, vx, vy, vz, t, w;
   double tof, w_det;
   int64_t bin;         /* pixel*n_tof + tof bin; -1 missed, -2 tof out of range */
+  double kappa;        /* condition estimate of w: relative change of w per relative
+                          rounding of the inputs, summed over the packet's history */
+  double kappa_det;    /* the same for w_det (adds the tube chord) */
 } orc_packet;
 
 /* per-scatter record (debug / pins) */

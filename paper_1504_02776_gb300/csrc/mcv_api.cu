@@ -33,7 +33,7 @@ mcv_status cuda_fail(cudaError_t e, const char* where) {
 bool is_finite(double v) { return std::isfinite(v); }
 
 // ---- descriptions -> device parameter blocks -------------------------------------------
-mcv_status build_beam(const mcv_beam_params* b, mcv::DBeam* B) {
+mcv_status build_beam(const mcv_beam_params* b, mcv::BeamP<double>* B) {
   if (!b) return fail(MCV_EINVAL, "beam parameters are NULL");
   const double v[] = {b->ei_mev, b->ei_rel_sigma, b->div_sigma_rad, b->width_m, b->height_m,
                       b->z0_m, b->l1_m};
@@ -52,10 +52,12 @@ mcv_status build_beam(const mcv_beam_params* b, mcv::DBeam* B) {
   B->l1 = b->l1_m;
   B->speed0 = std::sqrt(b->ei_mev / mcv::kMeVPerV2);
   B->t0 = (b->l1_m - b->z0_m) / B->speed0;
+  B->t0_hi = (float)B->t0;
+  B->t0_lo = (float)(B->t0 - (double)B->t0_hi);
   return MCV_OK;
 }
 
-mcv_status build_sample(const mcv_sample* s, mcv::DSample* S) {
+mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
   if (!s) return fail(MCV_EINVAL, "sample is NULL");
   std::memset(S, 0, sizeof(*S));
   if (s->n_scatterers < 1 || s->n_scatterers > MCV_MAX_SCATTERERS)
@@ -69,7 +71,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::DSample* S) {
   bool need_sqe = false;
   for (int j = 0; j < s->n_scatterers; ++j) {
     const mcv_scatterer& a = s->scat[j];
-    mcv::DScat& d = S->s[j];
+    mcv::ScatP<double>& d = S->s[j];
     for (double x : {a.dims[0], a.dims[1], a.dims[2], a.rot_y_rad, a.n_per_A3, a.sig_abs_b,
                      a.kernel_sig_b[0], a.kernel_sig_b[1]})
       if (!is_finite(x)) return fail(MCV_EINVAL, "scatterer parameter is not finite");
@@ -110,7 +112,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::DSample* S) {
     d.sig_s = sig;
     d.n100 = 100.0 * a.n_per_A3;
     d.mu_s = 100.0 * a.n_per_A3 * sig;
-    d.mu_a_v = 100.0 * a.n_per_A3 * a.sig_abs_b * 2200.0;
+    d.sab2200 = a.sig_abs_b * 2200.0;
   }
   if (need_sqe) {
     const mcv_sqe& q = s->sqe;
@@ -131,7 +133,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::DSample* S) {
   return MCV_OK;
 }
 
-mcv_status build_detector(const mcv_detector* d, mcv::DDet* D) {
+mcv_status build_detector(const mcv_detector* d, mcv::DetP<double>* D) {
   if (!d) return fail(MCV_EINVAL, "detector is NULL");
   std::memset(D, 0, sizeof(*D));
   if (d->kind != MCV_DET_SURFACE && d->kind != MCV_DET_TUBES)
@@ -144,7 +146,9 @@ mcv_status build_detector(const mcv_detector* d, mcv::DDet* D) {
   D->n_tof = d->n_tof;
   D->tof_min = d->tof_min_s;
   D->dt = (d->tof_max_s - d->tof_min_s) / d->n_tof;
-  D->inv_dt = 1.0 / D->dt;
+  D->inv_dt = (float)(1.0 / D->dt);
+  D->tmin_hi = (float)d->tof_min_s;
+  D->tmin_lo = (float)(d->tof_min_s - (double)D->tmin_hi);
   int64_t npix = 0;
   if (d->kind == MCV_DET_SURFACE) {
     if (d->n_phi < 1 || d->n_y < 1 || !(d->height_m > 0) || !is_finite(d->height_m))
@@ -198,6 +202,95 @@ mcv_status build_detector(const mcv_detector* d, mcv::DDet* D) {
   if (npix > ((int64_t)1 << 31) - 1) return fail(MCV_EINVAL, "too many pixels");
   D->n_bins = npix * d->n_tof;
   return MCV_OK;
+}
+
+// float copies of the parameter blocks for the FP32 kernels
+void cast_beam(const mcv::BeamP<double>& d, mcv::BeamP<float>* f) {
+  f->ei = (float)d.ei;
+  f->rel = (float)d.rel;
+  f->div = (float)d.div;
+  f->width = (float)d.width;
+  f->height = (float)d.height;
+  f->z0 = (float)d.z0;
+  f->l1 = (float)d.l1;
+  f->speed0 = (float)d.speed0;
+  f->t0 = d.t0;
+  f->t0_hi = d.t0_hi;
+  f->t0_lo = d.t0_lo;
+}
+
+void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
+  f->ns = d.ns;
+  f->max_orders = d.max_orders;
+  f->nq = d.nq;
+  f->ne = d.ne;
+  f->has_sqe = d.has_sqe;
+  f->min_prob = (float)d.min_prob;
+  for (int j = 0; j < MCV_MAX_SCATTERERS; ++j) {
+    const mcv::ScatP<double>& a = d.s[j];
+    mcv::ScatP<float>& b = f->s[j];
+    b.shape = a.shape;
+    b.nk = a.nk;
+    b.ktype0 = a.ktype0;
+    b.ktype1 = a.ktype1;
+    b.dim0 = (float)a.dim0;
+    b.dim1 = (float)a.dim1;
+    b.dim2 = (float)a.dim2;
+    b.half_h = (float)a.half_h;
+    b.cos_rot = (float)a.cos_rot;
+    b.sin_rot = (float)a.sin_rot;
+    b.n100 = (float)a.n100;
+    b.sig_s = (float)a.sig_s;
+    b.sab2200 = (float)a.sab2200;
+    b.mu_s = (float)a.mu_s;
+    b.ksig0 = (float)a.ksig0;
+    b.ksig_sum = (float)a.ksig_sum;
+  }
+  f->sqe = d.sqe;
+  f->q_max = (float)d.q_max;
+  f->e_min = (float)d.e_min;
+  f->e_max = (float)d.e_max;
+  f->dq = (float)d.dq;
+  f->de = (float)d.de;
+}
+
+void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
+  f->kind = d.kind;
+  f->n_phi = d.n_phi;
+  f->n_y = d.n_y;
+  f->n_rows = d.n_rows;
+  for (int i = 0; i < 3; ++i) {
+    f->packs[i] = d.packs[i];
+    f->row_off[i] = d.row_off[i];
+    f->row_y[i] = (float)d.row_y[i];
+  }
+  f->tubes_per_pack = d.tubes_per_pack;
+  f->pixels_per_tube = d.pixels_per_tube;
+  f->max_tubes_row = d.max_tubes_row;
+  f->n_tof = d.n_tof;
+  f->n_bins = d.n_bins;
+  f->radius = (float)d.radius;
+  f->height = (float)d.height;
+  f->half_h = (float)d.half_h;
+  f->tube_r = (float)d.tube_r;
+  f->half_len = (float)d.half_len;
+  f->pitch = (float)d.pitch;
+  f->period = (float)d.period;
+  f->phi0 = (float)d.phi0;
+  f->pix_len = (float)d.pix_len;
+  f->mu_he_v = (float)d.mu_he_v;
+  f->tof_min = d.tof_min;
+  f->dt = d.dt;
+  f->tmin_hi = d.tmin_hi;
+  f->tmin_lo = d.tmin_lo;
+  f->inv_dt = d.inv_dt;
+  for (int i = 0; i < 2 * MCV_MAX_TUBES_PER_ROW; ++i) f->tube_u[i] = (float)d.tube_u[i];
+}
+
+void cast_all(mcv::TraceArgs* A) {
+  cast_beam(A->Bd, &A->Bf);
+  cast_sample(A->Sd, &A->Sf);
+  cast_detector(A->Dd, &A->Df);
 }
 
 bool neutrons_ok(const mcv_neutrons* a, bool need_ids) {
@@ -293,7 +386,7 @@ mcv_status mcv_sync(mcv_ctx* ctx, void* stream) {
 }
 
 int64_t mcv_detector_pixels(const mcv_detector* det) {
-  mcv::DDet D;
+  mcv::DetP<double> D;
   if (build_detector(det, &D) != MCV_OK) return 0;
   return D.n_bins / D.n_tof;
 }
@@ -318,7 +411,7 @@ mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint
   if (!neutrons_ok(out, false) || out->n < n) return fail(MCV_EINVAL, "bad output arrays");
   mcv::TraceArgs A;
   std::memset(&A, 0, sizeof(A));
-  st = build_beam(beam, &A.B);
+  st = build_beam(beam, &A.Bd);
   if (st != MCV_OK) return st;
   if (n == 0) return MCV_OK;
   A.seed = seed;
@@ -335,6 +428,7 @@ mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint
   A.pk_t = out->t;
   A.pk_id = out->id;
   A.pk_order = out->order;
+  cast_all(&A);
   cudaError_t e = mcv::launch_beam(A, fp_mode, grid_for(ctx, n, 16), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "beam kernel launch");
   return MCV_OK;
@@ -348,26 +442,26 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   if (st != MCV_OK) return st;
   mcv::TraceArgs A;
   std::memset(&A, 0, sizeof(A));
-  st = build_sample(sample, &A.S);
+  st = build_sample(sample, &A.Sd);
   if (st != MCV_OK) return st;
   if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
     return fail(MCV_EINVAL, "bad neutron range");
   if (in) {
     if (!neutrons_ok(in, false) || in->n < n) return fail(MCV_EINVAL, "bad input arrays");
   } else {
-    st = build_beam(beam, &A.B);
+    st = build_beam(beam, &A.Bd);
     if (st != MCV_OK) return st;
   }
   const bool fused = det != nullptr;
   if (fused) {
-    st = build_detector(det, &A.D);
+    st = build_detector(det, &A.Dd);
     if (st != MCV_OK) return st;
     if (!hist || (!hist->counts && !hist->tallies))
       return fail(MCV_EINVAL, "a detector needs a histogram or tallies");
   }
   if (packets) {
     if (!neutrons_ok(packets, true)) return fail(MCV_EINVAL, "bad packet arrays");
-    if (packets->n / (A.S.max_orders + 1) < n) return fail(MCV_EINVAL, "too few packet slots");
+    if (packets->n / (A.Sd.max_orders + 1) < n) return fail(MCV_EINVAL, "too few packet slots");
   }
   if (!fused && !packets && !(hist && hist->tallies))
     return fail(MCV_EINVAL, "no output requested");
@@ -405,14 +499,15 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
     A.pk_order = packets->order;
   }
   A.err = ctx->d_err;
-  const int detk = fused ? A.D.kind : MCV_DET_NONE;
+  const int detk = fused ? A.Dd.kind : MCV_DET_NONE;
   const int fp = sample->fp_mode;
-  int& occ = ctx->occ[fp][ns_index(A.S.ns)][detk];
+  int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][detk];
   if (occ == 0) {
-    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.S.ns, detk, &occ);
+    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, detk, &occ);
     if (e != cudaSuccess || occ < 1) occ = 1;
   }
   const int grid = grid_for(ctx, n, occ);
+  cast_all(&A);
   cudaError_t e = mcv::launch_trace(A, fp, detk, grid, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
   return MCV_OK;
@@ -426,7 +521,7 @@ mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
   if (fp_mode != MCV_FP64 && fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
   mcv::TraceArgs A;
   std::memset(&A, 0, sizeof(A));
-  st = build_detector(det, &A.D);
+  st = build_detector(det, &A.Dd);
   if (st != MCV_OK) return st;
   if (!neutrons_ok(packets, true)) return fail(MCV_EINVAL, "bad packet arrays (id and order required)");
   if (!hist && !events) return fail(MCV_EINVAL, "no output requested");
@@ -451,7 +546,8 @@ mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
   A.err = ctx->d_err;
   mcv::EventsArgs E{nullptr, nullptr, nullptr, nullptr};
   if (events) E = mcv::EventsArgs{events->pixel, events->tof, events->w_det, events->bin};
-  cudaError_t e = mcv::launch_detect(A, E, fp_mode, A.D.kind, grid_for(ctx, packets->n, 16),
+  cast_all(&A);
+  cudaError_t e = mcv::launch_detect(A, E, fp_mode, A.Dd.kind, grid_for(ctx, packets->n, 16),
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "detect kernel launch");
   return MCV_OK;
@@ -466,29 +562,29 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
   if (st != MCV_OK) return st;
   mcv::TraceArgs A;
   std::memset(&A, 0, sizeof(A));
-  st = build_sample(sample, &A.S);
+  st = build_sample(sample, &A.Sd);
   if (st != MCV_OK) return st;
-  st = build_beam(beam, &A.B);
+  st = build_beam(beam, &A.Bd);
   if (st != MCV_OK) return st;
-  st = build_detector(det, &A.D);
+  st = build_detector(det, &A.Dd);
   if (st != MCV_OK) return st;
   if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
     return fail(MCV_EINVAL, "bad neutron range");
   if (!target || !g_work || !loss || !dsig || !hist || !hist->counts)
     return fail(MCV_EINVAL, "mcv_grad needs target, hist->counts, g_work, loss and dsig");
-  if (A.S.has_sqe && !dsqe) return fail(MCV_EINVAL, "mcv_grad needs dsqe for an S(Q,E) sample");
-  if (grad_scatterer < 0 || grad_scatterer >= A.S.ns)
+  if (A.Sd.has_sqe && !dsqe) return fail(MCV_EINVAL, "mcv_grad needs dsqe for an S(Q,E) sample");
+  if (grad_scatterer < 0 || grad_scatterer >= A.Sd.ns)
     return fail(MCV_EINVAL, "grad_scatterer out of range");
-  if (!(A.S.s[grad_scatterer].sig_s > 0.0))
+  if (!(A.Sd.s[grad_scatterer].sig_s > 0.0))
     return fail(MCV_EINVAL, "the differentiated scatterer needs a positive cross section");
   if (!is_finite(scale_c)) return fail(MCV_EINVAL, "scale_c is not finite");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int zgrid = ctx->sm_count * 8;
-  cudaError_t e = mcv::launch_zero(hist->counts, A.D.n_bins, zgrid, s);
+  cudaError_t e = mcv::launch_zero(hist->counts, A.Dd.n_bins, zgrid, s);
   if (e == cudaSuccess && hist->tallies) e = mcv::launch_zero(hist->tallies, MCV_NTALLY, 1, s);
   if (e == cudaSuccess) e = mcv::launch_zero(loss, 1, 1, s);
   if (e == cudaSuccess) e = mcv::launch_zero(dsig, 2, 1, s);
-  if (e == cudaSuccess && A.S.has_sqe) e = mcv::launch_zero(dsqe, (int64_t)A.S.nq * A.S.ne, zgrid, s);
+  if (e == cudaSuccess && A.Sd.has_sqe) e = mcv::launch_zero(dsqe, (int64_t)A.Sd.nq * A.Sd.ne, zgrid, s);
   if (e != cudaSuccess) return cuda_fail(e, "zero kernel launch");
   A.seed = seed;
   A.sim_id = sim_id;
@@ -496,21 +592,22 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
   A.n = n;
   A.err = ctx->d_err;
   A.gs = grad_scatterer;
+  cast_all(&A);
   const int fp = sample->fp_mode;
   if (n > 0) {
     // forward: the histogram of this neutron range
     A.hist = hist->counts;
     A.tallies = hist->tallies;
     A.stop_on_zero = 1;
-    int& occ = ctx->occ[fp][ns_index(A.S.ns)][A.D.kind];
+    int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][A.Dd.kind];
     if (occ == 0) {
-      e = mcv::trace_blocks_per_sm(fp, A.S.ns, A.D.kind, &occ);
+      e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, &occ);
       if (e != cudaSuccess || occ < 1) occ = 1;
     }
-    e = mcv::launch_trace(A, fp, A.D.kind, grid_for(ctx, n, occ), s);
+    e = mcv::launch_trace(A, fp, A.Dd.kind, grid_for(ctx, n, occ), s);
     if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
   }
-  e = mcv::launch_chi2(hist->counts, target, scale_c, A.D.n_bins, g_work, loss, ctx->sm_count * 8, s);
+  e = mcv::launch_chi2(hist->counts, target, scale_c, A.Dd.n_bins, g_work, loss, ctx->sm_count * 8, s);
   if (e != cudaSuccess) return cuda_fail(e, "chi2 kernel launch");
   if (n > 0) {
     // adjoint: the same paths, traced through zero weights
@@ -518,9 +615,9 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
     A.tallies = nullptr;
     A.stop_on_zero = 0;
     A.g = g_work;
-    A.dsqe = A.S.has_sqe ? dsqe : nullptr;
+    A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
     A.dsig = dsig;
-    e = mcv::launch_adjoint(A, fp, A.D.kind, grid_for(ctx, n, 2), s);
+    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_for(ctx, n, 2), s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
   }
   return MCV_OK;

@@ -38,75 +38,90 @@ __device__ __forceinline__ bool load_input(const TraceArgs& A, int64_t i, Ray<R>
   n->dy = vy / sp;
   n->dz = vz / sp;
   n->speed = sp;
-  n->t = A.in_t[i];
+  n->t.set(A.in_t[i]);
   n->w = static_cast<const R*>(A.in_w)[i];
   return true;
 }
 
-// One order of one neutron: segments ahead, emission of the transmitted packet, then the
-// scattered packet continues from a point uniform over the material ahead with a kernel
-// picked at random (section 2.4.3 "Multiple Scattering", as a bounded chain).  Returns
-// whether the neutron is still alive.
-template <typename R, int NS, int DET, class P>
-__device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane<R>& L, P& pol) {
-  using M = Mth<R>;
-  const DSample& S = A.S;
-  const NeutronRng rng(A.seed, A.sim_id, L.nid);
+// What the first half of an order step leaves for the second: the material segments
+// ahead, their attenuation coefficients and lengths.
+template <typename R, int NS>
+struct StepState {
   Seg<R> seg[2 * NS];
-  const int ns = assembly_segs<R, NS>(S, L.n, seg);
   R mu[NS];
+  int ns;
+  R len_tot, atten, lg;
+};
+
+// First half of one order: segments ahead of the packet and the weight of the transmitted
+// packet we = w e^{-tau} (section 2.4.3: the packet split into a transmitted and a
+// scattered part).  lg: path length inside scatterer A.gs (only when WANTS_GS).
+template <typename R, int NS, bool WANTS_GS>
+__device__ __forceinline__ R step_segments(const TraceArgs& A, const SampleP<R>& S,
+                                           const Lane<R>& L, StepState<R, NS>& st) {
+  using M = Mth<R>;
+  st.ns = assembly_segs<R, NS>(S, L.n, st.seg);
 #pragma unroll
-  for (int j = 0; j < NS; ++j) mu[j] = (R)S.s[j].mu_s + (R)S.s[j].mu_a_v / L.n.speed;
+  for (int j = 0; j < NS; ++j)
+    st.mu[j] = S.s[j].n100 * (S.s[j].sig_s + S.s[j].sab2200 / L.n.speed);
   R tau = R(0), len_tot = R(0), lg = R(0);
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) {
-    if (k < ns) {
-      const R len = seg[k].b - seg[k].a;
-      tau += pick_mu<R, NS>(mu, seg[k].j) * len;
+    if (k < st.ns) {
+      const R len = st.seg[k].b - st.seg[k].a;
+      tau += pick_mu<R, NS>(st.mu, st.seg[k].j) * len;
       len_tot += len;
-      if (P::kWantsGs && seg[k].j == A.gs) lg += len;
+      if (WANTS_GS && st.seg[k].j == A.gs) lg += len;
     }
   }
-  const R atten = M::exp(-tau);
-  const R we = L.n.w * atten;
-  pol.emit(A, tu, rng, L, we, atten, lg, len_tot);
-  if (L.o == S.max_orders || !(len_tot > R(0))) {
-    pol.clear(A, L.idx, L.o + 1);
-    return false;
-  }
+  st.len_tot = len_tot;
+  st.lg = lg;
+  st.atten = M::exp(-tau);
+  return L.n.w * st.atten;
+}
+
+// Second half: the scattered packet continues from a point uniform over the material
+// ahead, with a kernel picked at random (section 2.4.3 "Multiple Scattering", bounded
+// chain).  Call only when the packet has material ahead and L.o < max_orders.  Returns
+// whether the neutron is still alive.
+template <typename R, int NS, class P>
+__device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R>& S,
+                                             const NeutronRng& rng, Lane<R>& L,
+                                             const StepState<R, NS>& st, P& pol) {
+  using M = Mth<R>;
   R u_pt, u_k;
   rng.pair<R>(L.o, 0, &u_pt, &u_k);
-  const R ell = u_pt * len_tot;
+  const R ell = u_pt * st.len_tot;
   R acc = R(0), tau_pt = R(0), s_pt = R(0), lg_pt = R(0);
   int j = 0;
   bool found = false;
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) {
-    if (k < ns && !found) {
-      const R len = seg[k].b - seg[k].a;
-      const R m = pick_mu<R, NS>(mu, seg[k].j);
-      if (ell < acc + len || k == ns - 1) {
+    if (k < st.ns && !found) {
+      const R len = st.seg[k].b - st.seg[k].a;
+      const R m = pick_mu<R, NS>(st.mu, st.seg[k].j);
+      if (ell < acc + len || k == st.ns - 1) {
         const R part = ell - acc;
-        s_pt = seg[k].a + part;
+        s_pt = st.seg[k].a + part;
         tau_pt += m * part;
-        if (P::kWantsGs && seg[k].j == A.gs) lg_pt += part;
-        j = seg[k].j;
+        if (P::kWantsGs && st.seg[k].j == A.gs) lg_pt += part;
+        j = st.seg[k].j;
         found = true;
       } else {
         acc += len;
         tau_pt += m * len;
-        if (P::kWantsGs && seg[k].j == A.gs) lg_pt += len;
+        if (P::kWantsGs && st.seg[k].j == A.gs) lg_pt += len;
       }
     }
   }
-  const DScat& sc = S.s[j];
-  const R a_fac = (R)sc.mu_s * len_tot * M::exp(-tau_pt);
+  const ScatP<R>& sc = S.s[j];
+  const R a_fac = sc.mu_s * st.len_tot * M::exp(-tau_pt);
   const R speed_in = L.n.speed;
   L.n.x += s_pt * L.n.dx;
   L.n.y += s_pt * L.n.dy;
   L.n.z += s_pt * L.n.dz;
-  L.n.t = add_time<R>(L.n.t, s_pt, L.n.speed);
-  const int kk = (sc.nk == 2 && !(u_k * (R)sc.ksig_sum < (R)sc.ksig0)) ? 1 : 0;
+  L.n.t.add(s_pt / L.n.speed);
+  const int kk = (sc.nk == 2 && !(u_k * sc.ksig_sum < sc.ksig0)) ? 1 : 0;
   const int ktype = kk ? sc.ktype1 : sc.ktype0;
   Scatter<R> out;
   bool ok = false;
@@ -123,11 +138,27 @@ __device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane
   L.n.w = L.n.w * a_fac * out.factor;
   pol.scatter(A, L, j, a_fac, out, lg_pt, speed_in);
   L.o += 1;
-  if (L.n.w < (R)S.min_prob || (A.stop_on_zero && L.n.w == R(0))) {
+  if (L.n.w < S.min_prob || (A.stop_on_zero && L.n.w == R(0))) {
     pol.clear(A, L.idx, L.o);
     return false;
   }
   return true;
+}
+
+// One order of one neutron: segments ahead, emission of the transmitted packet, then the
+// scattered packet continues.  Returns whether the neutron is still alive.
+template <typename R, int NS, int DET, class P>
+__device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane<R>& L, P& pol) {
+  const SampleP<R>& S = Sof<R>(A);
+  const NeutronRng rng(A.seed, A.sim_id, L.nid);
+  StepState<R, NS> st;
+  const R we = step_segments<R, NS, P::kWantsGs>(A, S, L, st);
+  pol.emit(A, tu, rng, L, we, st.atten, st.lg, st.len_tot);
+  if (L.o == S.max_orders || !(st.len_tot > R(0))) {
+    pol.clear(A, L.idx, L.o + 1);
+    return false;
+  }
+  return step_scatter<R, NS, P>(A, S, rng, L, st, pol);
 }
 
 // Warp loop: each warp owns ids [lo, hi) of the launch; lanes whose neutron finished take
@@ -161,9 +192,9 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
             ok = load_input<R>(A, i, &L.n);
           } else {
             const NeutronRng rng(A.seed, A.sim_id, L.nid);
-            ok = make_beam<R>(A.B, rng, &L.n);
+            ok = make_beam<R>(Bof<R>(A), rng, &L.n);
           }
-          ok = ok && !(L.n.w < (R)A.S.min_prob) && !(A.stop_on_zero && L.n.w == R(0));
+          ok = ok && !(L.n.w < Sof<R>(A).min_prob) && !(A.stop_on_zero && L.n.w == R(0));
           if (!ok) pol.clear(A, i, 0);
           if (ok) pol.start(L);
           L.active = ok;
@@ -183,7 +214,8 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
 template <typename R, int DET>
 __device__ __forceinline__ void stage_tubes(const TraceArgs& A, R* tu) {
   if (DET == MCV_DET_TUBES) {
-    for (int i = threadIdx.x; i < 2 * A.D.max_tubes_row; i += blockDim.x) tu[i] = (R)A.D.tube_u[i];
+    const DetP<R>& D = Dof<R>(A);
+    for (int i = threadIdx.x; i < 2 * D.max_tubes_row; i += blockDim.x) tu[i] = D.tube_u[i];
     __syncthreads();
   }
 }

@@ -50,8 +50,9 @@ struct Mth<double> {
   static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
   static __device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
   static __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
+  // the FP64 mode evaluates sin and cos of (2 pi) u as written
   static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) {
-    ::sincospi(2.0 * u, s, c);
+    ::sincos(2.0 * kPi * u, s, c);
   }
   static __device__ __forceinline__ double inf() { return CUDART_INF; }
 };
@@ -89,11 +90,17 @@ __device__ __forceinline__ double to_unit<double>(uint32_t hi, uint32_t lo) {
   return __fma_rn((double)k, 0x1p-53, 0x1p-54);
 }
 
+// FP32: the same 53-bit number rounded to float, built on the integer and FP32 pipes only
+// (exact small-integer to float through the 2^23 bias; one rounding in the final FMA).
+__device__ __forceinline__ float small_int_to_float(uint32_t v) {  // v < 2^23, exact
+  return __int_as_float(0x4b000000u | v) - 8388608.0f;
+}
 template <>
 __device__ __forceinline__ float to_unit<float>(uint32_t hi, uint32_t lo) {
-  const uint64_t k = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
-  const float u = __ull2float_rn(2ull * k + 1ull) * 0x1p-54f;
-  return fminf(u, 0x1.fffffep-1f);
+  // u = (hi 2^21 + (lo >> 11) + 1/2) 2^-53 = hi 2^-32 + c,  c = (2 (lo >> 11) + 1) 2^-54
+  const float h = __fmaf_rn(small_int_to_float(hi >> 16), 65536.0f, small_int_to_float(hi & 0xffffu));
+  const float c = small_int_to_float(((lo >> 11) << 1) | 1u) * 0x1p-54f;
+  return fminf(__fmaf_rn(h, 0x1p-32f, c), 0x1.fffffep-1f);
 }
 
 // The stream of one neutron: key (seed, sim), counter (id lo, id hi, 4*(event+1)+block, 0).
@@ -115,24 +122,80 @@ struct NeutronRng {
   }
 };
 
+// ---- time of flight ---------------------------------------------------------------------
+// FP64 mode: a double.  FP32 mode: an unevaluated sum of two floats (48 significant bits,
+// ~1e-17 s over millisecond flights) accumulated with the FP32 pipes only.
+template <typename R>
+struct Tof;
+
+template <>
+struct Tof<double> {
+  double v;
+  __device__ __forceinline__ void set(double t) { v = t; }
+  __device__ __forceinline__ void add(double dt) { v = v + dt; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+template <>
+struct Tof<float> {
+  float hi, lo;
+  __device__ __forceinline__ void set(double t) {
+    hi = (float)t;
+    lo = (float)(t - (double)hi);
+  }
+  __device__ __forceinline__ void set2(float h, float l) {
+    const float s = h + l;
+    lo = l - (s - h);
+    hi = s;
+  }
+  // |dt| <= |hi| for flight increments after the start: fast two-sum
+  __device__ __forceinline__ void add(float dt) {
+    const float s = hi + dt;
+    const float e = dt - (s - hi);
+    hi = s;
+    lo = lo + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ---- packet state ---------------------------------------------------------------------
 template <typename R>
 struct Ray {
   R x, y, z;        // m
   R dx, dy, dz;     // unit direction
   R speed;          // m/s
-  double t;         // s
+  Tof<R> t;         // s
   R w;              // probability weight
 };
+
+// ---- parameter blocks of one real type ---------------------------------------------------
+template <typename R>
+__device__ __forceinline__ const SampleP<R>& Sof(const TraceArgs& A);
+template <>
+__device__ __forceinline__ const SampleP<float>& Sof<float>(const TraceArgs& A) { return A.Sf; }
+template <>
+__device__ __forceinline__ const SampleP<double>& Sof<double>(const TraceArgs& A) { return A.Sd; }
+template <typename R>
+__device__ __forceinline__ const DetP<R>& Dof(const TraceArgs& A);
+template <>
+__device__ __forceinline__ const DetP<float>& Dof<float>(const TraceArgs& A) { return A.Df; }
+template <>
+__device__ __forceinline__ const DetP<double>& Dof<double>(const TraceArgs& A) { return A.Dd; }
+template <typename R>
+__device__ __forceinline__ const BeamP<R>& Bof(const TraceArgs& A);
+template <>
+__device__ __forceinline__ const BeamP<float>& Bof<float>(const TraceArgs& A) { return A.Bf; }
+template <>
+__device__ __forceinline__ const BeamP<double>& Bof<double>(const TraceArgs& A) { return A.Bd; }
 
 // ---- source -----------------------------------------------------------------------------
 // Synthetic beam at the sample: Gaussian energy, uniform footprint, Gaussian divergence.
 // Returns false when the drawn energy is not positive (no packet).
 template <typename R>
-__device__ __forceinline__ bool make_beam(const DBeam& B, const NeutronRng& rng, Ray<R>* n);
+__device__ __forceinline__ bool make_beam(const BeamP<R>& B, const NeutronRng& rng, Ray<R>* n);
 
 template <>
-__device__ __forceinline__ bool make_beam<double>(const DBeam& B, const NeutronRng& rng,
+__device__ __forceinline__ bool make_beam<double>(const BeamP<double>& B, const NeutronRng& rng,
                                                   Ray<double>* n) {
   using M = Mth<double>;
   double u0, u1, s, c;
@@ -155,7 +218,7 @@ __device__ __forceinline__ bool make_beam<double>(const DBeam& B, const NeutronR
   n->dz = 1.0 / norm;
   n->speed = M::sqrt(E / kMeVPerV2);
   n->z = -B.z0;
-  n->t = (B.l1 - B.z0) / (n->speed * n->dz);
+  n->t.set((B.l1 - B.z0) / (n->speed * n->dz));
   n->w = 1.0;
   return true;
 }
@@ -165,21 +228,21 @@ __device__ __forceinline__ bool make_beam<double>(const DBeam& B, const NeutronR
 // keeps ~1e-12 s accuracy: speed = v0 (1 + eta), eta = d/(1 + sqrt(1 + d)), d = rel z;
 // path/speed = t0 (1 + xi)/(1 + eta), xi = e/(1 + sqrt(1 + e)), e = tan^2 ax + tan^2 ay.
 template <>
-__device__ __forceinline__ bool make_beam<float>(const DBeam& B, const NeutronRng& rng,
+__device__ __forceinline__ bool make_beam<float>(const BeamP<float>& B, const NeutronRng& rng,
                                                  Ray<float>* n) {
   using M = Mth<float>;
   float u0, u1, s, c;
   rng.pair<float>(-1, 0, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const float zE = M::sqrt(-2.0f * M::log(u0)) * c;
-  const float dE = (float)B.rel * zE;
+  const float dE = B.rel * zE;
   rng.pair<float>(-1, 1, &u0, &u1);
-  n->x = (u0 - 0.5f) * (float)B.width;
-  n->y = (u1 - 0.5f) * (float)B.height;
+  n->x = (u0 - 0.5f) * B.width;
+  n->y = (u1 - 0.5f) * B.height;
   rng.pair<float>(-1, 2, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const float rr = M::sqrt(-2.0f * M::log(u0));
-  const float ax = (float)B.div * (rr * c), ay = (float)B.div * (rr * s);
+  const float ax = B.div * (rr * c), ay = B.div * (rr * s);
   if (!(1.0f + dE > 0.0f)) return false;
   const float tx = M::tan(ax), ty = M::tan(ay);
   const float e = tx * tx + ty * ty;
@@ -189,9 +252,10 @@ __device__ __forceinline__ bool make_beam<float>(const DBeam& B, const NeutronRn
   n->dz = 1.0f / sq;
   const float eta = dE / (1.0f + M::sqrt(1.0f + dE));
   const float xi = e / (1.0f + sq);
-  n->speed = (float)B.speed0 * (1.0f + eta);
-  n->z = -(float)B.z0;
-  n->t = B.t0 + (double)((float)B.t0 * ((xi - eta) / (1.0f + eta)));
+  n->speed = B.speed0 * (1.0f + eta);
+  n->z = -B.z0;
+  n->t.set2(B.t0_hi, B.t0_lo);
+  n->t.add(B.t0_hi * ((xi - eta) / (1.0f + eta)));
   n->w = 1.0f;
   return true;
 }
@@ -259,7 +323,7 @@ __device__ __forceinline__ void put_seg(R a, R b, int j, Seg<R>* out, int* cnt) 
 // Segments of one scatterer's shape (section 2.4.2, shapes combined by CSG: the hollow
 // cylinder is a difference).  Writes up to two segments at out[0..1].
 template <typename R>
-__device__ __forceinline__ int shape_segs(const DScat& S, int j, const Ray<R>& n, Seg<R>* out) {
+__device__ __forceinline__ int shape_segs(const ScatP<R>& S, int j, const Ray<R>& n, Seg<R>* out) {
   using M = Mth<R>;
   int cnt = 0;
   R c1, c2, y1, y2;
@@ -286,13 +350,13 @@ __device__ __forceinline__ int shape_segs(const DScat& S, int j, const Ray<R>& n
     const R xb = c * n.x - s * n.z, zb = s * n.x + c * n.z;
     const R dxb = c * n.dx - s * n.dz, dzb = s * n.dx + c * n.dz;
     R lo = -M::inf(), hi = M::inf(), a, b;
-    bool ok = slab_span<R>((R)(0.5 * S.dim0), xb, dxb, &a, &b);
+    bool ok = slab_span<R>(R(0.5) * S.dim0, xb, dxb, &a, &b);
     lo = M::fmax(lo, a);
     hi = M::fmin(hi, b);
-    ok = ok && slab_span<R>((R)(0.5 * S.dim1), n.y, n.dy, &a, &b);
+    ok = ok && slab_span<R>(R(0.5) * S.dim1, n.y, n.dy, &a, &b);
     lo = M::fmax(lo, a);
     hi = M::fmin(hi, b);
-    ok = ok && slab_span<R>((R)(0.5 * S.dim2), zb, dzb, &a, &b);
+    ok = ok && slab_span<R>(R(0.5) * S.dim2, zb, dzb, &a, &b);
     lo = M::fmax(lo, a);
     hi = M::fmin(hi, b);
     if (ok) put_seg<R>(lo, hi, j, out, &cnt);
@@ -303,7 +367,7 @@ __device__ __forceinline__ int shape_segs(const DScat& S, int j, const Ray<R>& n
 // All segments ahead in the sample assembly, sorted by entry (ray tracing in a composite,
 // section 2.4.3).  NS = number of scatterers (compile time); unused entries get a = +inf.
 template <typename R, int NS>
-__device__ __forceinline__ int assembly_segs(const DSample& S, const Ray<R>& n, Seg<R> (&seg)[2 * NS]) {
+__device__ __forceinline__ int assembly_segs(const SampleP<R>& S, const Ray<R>& n, Seg<R> (&seg)[2 * NS]) {
   using M = Mth<R>;
   int total = 0;
 #pragma unroll
@@ -403,7 +467,7 @@ __device__ __forceinline__ void kernel_iso(const NeutronRng& rng, int o, Ray<R>*
 // [|ki - kf|, min(ki + kf, q_max)], azimuth uniform; weight S Q dE dQ / (2 ki^2); nearest bin.
 // Returns false when the kernel cannot scatter (empty range or outside the table).
 template <typename R>
-__device__ __forceinline__ bool kernel_sqe(const DSample& S, const NeutronRng& rng, int o,
+__device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng& rng, int o,
                                            Ray<R>* n, Scatter<R>* sc, int* err) {
   using M = Mth<R>;
   const R Ei = (R)kMeVPerV2 * n->speed * n->speed;
@@ -414,7 +478,8 @@ __device__ __forceinline__ bool kernel_sqe(const DSample& S, const NeutronRng& r
   R u0, u1;
   rng.pair<R>(o, 1, &u0, &u1);
   const R E = e_lo + u0 * dE;
-  const R Ef = Ei - E;
+  // Ef = Ei - E; when the range ends at Ei it is the sampled offset from that end
+  const R Ef = (e_hi == Ei) ? (R(1) - u0) * dE : Ei - E;
   if (!(Ef > R(0))) return false;
   const R speed_f = M::sqrt(Ef / (R)kMeVPerV2);
   const R kf = (R)kKPerV * speed_f;
@@ -457,7 +522,7 @@ template <typename R>
 struct Hit {
   int64_t bin;      // >= 0 in range, -1 miss, -2 tof out of range
   int32_t pixel;
-  double tof;
+  Tof<R> tof;
   R w_det;
   R pabs;           // detector weight factor (1 for the ideal surface)
 };
@@ -492,35 +557,31 @@ __device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>&
   return true;
 }
 
+// tof bin: FP64 mode as written; FP32 mode takes the offset from tof_min from the float
+// pair exactly (the two differences are exact or nearly so) and scales it in float
 template <typename R>
-__device__ __forceinline__ double add_time(double t, R s, R speed) {
-  return t + (double)(s / speed);
-}
-
-// tof bin (FP64 mode: as written; FP32 mode: the offset from tof_min is taken in double,
-// then scaled in float)
-template <typename R>
-__device__ __forceinline__ int64_t tof_bin(const DDet& D, double tof);
+__device__ __forceinline__ int64_t tof_bin(const DetP<R>& D, const Tof<R>& tof);
 template <>
-__device__ __forceinline__ int64_t tof_bin<double>(const DDet& D, double tof) {
-  const double fb = ::floor((tof - D.tof_min) / D.dt);
+__device__ __forceinline__ int64_t tof_bin<double>(const DetP<double>& D, const Tof<double>& tof) {
+  const double fb = ::floor((tof.v - D.tof_min) / D.dt);
   if (!(fb >= 0.0 && fb < (double)D.n_tof)) return -1;
   return (int64_t)fb;
 }
 template <>
-__device__ __forceinline__ int64_t tof_bin<float>(const DDet& D, double tof) {
-  const float fb = floorf((float)(tof - D.tof_min) * (float)D.inv_dt);
+__device__ __forceinline__ int64_t tof_bin<float>(const DetP<float>& D, const Tof<float>& tof) {
+  const float off = (tof.hi - D.tmin_hi) + (tof.lo - D.tmin_lo);
+  const float fb = floorf(off * D.inv_dt);
   if (!(fb >= 0.0f && fb < (float)D.n_tof)) return -1;
   return (int64_t)fb;
 }
 
 template <typename R>
-__device__ __forceinline__ Hit<R> detect_surface(const DDet& D, const Ray<R>& n) {
+__device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const Ray<R>& n) {
   using M = Mth<R>;
   Hit<R> h;
   h.bin = -1;
   h.pixel = -1;
-  h.tof = 0.0;
+  h.tof = n.t;
   h.w_det = R(0);
   h.pabs = R(0);
   R s;
@@ -535,7 +596,7 @@ __device__ __forceinline__ Hit<R> detect_surface(const DDet& D, const Ray<R>& n)
   int iy = (int)M::floor((yh + half) / (R)D.height * (R)D.n_y);
   iy = min(max(iy, 0), D.n_y - 1);
   h.pixel = ip * D.n_y + iy;
-  h.tof = add_time<R>(n.t, s, n.speed);
+  h.tof.add(s / n.speed);
   h.w_det = n.w;
   h.pabs = R(1);
   const int64_t tb = tof_bin<R>(D, h.tof);
@@ -545,13 +606,13 @@ __device__ __forceinline__ Hit<R> detect_surface(const DDet& D, const Ray<R>& n)
 
 // tube centre directions staged in shared memory: tu[2*i] = sin(phi_i), tu[2*i+1] = cos(phi_i)
 template <typename R>
-__device__ __forceinline__ Hit<R> detect_tubes(const DDet& D, const R* __restrict__ tu,
+__device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const R* __restrict__ tu,
                                                const Ray<R>& n, R u_det) {
   using M = Mth<R>;
   Hit<R> h;
   h.bin = -1;
   h.pixel = -1;
-  h.tof = 0.0;
+  h.tof = n.t;
   h.w_det = R(0);
   h.pabs = R(0);
   const R Rad = (R)D.radius;
@@ -616,7 +677,7 @@ __device__ __forceinline__ Hit<R> detect_tubes(const DDet& D, const R* __restric
   j = min(max(j, 0), D.pixels_per_tube - 1);
   const int pc = best / tpp, tc = best - pc * tpp;
   h.pixel = ((row_off + pc) * tpp + tc) * D.pixels_per_tube + j;
-  h.tof = add_time<R>(n.t, s_abs, n.speed);
+  h.tof.add(s_abs / n.speed);
   h.pabs = pabs;
   h.w_det = n.w * pabs;
   const int64_t tb = tof_bin<R>(D, h.tof);
@@ -625,7 +686,7 @@ __device__ __forceinline__ Hit<R> detect_tubes(const DDet& D, const R* __restric
 }
 
 template <typename R, int DET>
-__device__ __forceinline__ Hit<R> detect(const DDet& D, const R* tu, const NeutronRng& rng,
+__device__ __forceinline__ Hit<R> detect(const DetP<R>& D, const R* tu, const NeutronRng& rng,
                                          int order, const Ray<R>& n) {
   if (DET == MCV_DET_SURFACE) return detect_surface<R>(D, n);
   const R u = rng.first<R>(order, 3);

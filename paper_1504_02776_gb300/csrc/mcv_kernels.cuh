@@ -1,0 +1,642 @@
+// Kernel templates of the hot path, instantiated once per real type: mcv_fp32.cu (FP32
+// fast mode) and mcv_fp64.cu (FP64 mode, compiled without FMA contraction so that its
+// arithmetic rounds like the plain restatement of the method).
+//
+// The chain kernel: one neutron per lane, a persistent grid, and each warp owning a
+// contiguous range of neutron ids.  A lane whose neutron has finished (missed the sample,
+// left it, reached max_orders, or was dropped) takes the next id of its warp's range at
+// the top of the next step, so every step of the loop runs the same code on all 32 lanes
+// (the warp-level compaction of surviving neutrons between scattering orders).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mcv_chain.cuh"
+#include "mcv_launch.h"
+
+namespace mcv {
+
+constexpr int kThreads = 128;
+
+
+
+template <typename R>
+__device__ __forceinline__ void store_slot(const TraceArgs& A, int64_t slot, const Ray<R>& n, R w,
+                                           int64_t nid, int order) {
+  static_cast<R*>(A.pk_x)[slot] = n.x;
+  static_cast<R*>(A.pk_y)[slot] = n.y;
+  static_cast<R*>(A.pk_z)[slot] = n.z;
+  static_cast<R*>(A.pk_vx)[slot] = n.speed * n.dx;
+  static_cast<R*>(A.pk_vy)[slot] = n.speed * n.dy;
+  static_cast<R*>(A.pk_vz)[slot] = n.speed * n.dz;
+  static_cast<R*>(A.pk_w)[slot] = w;
+  A.pk_t[slot] = n.t.value();
+  A.pk_id[slot] = nid;
+  A.pk_order[slot] = order;
+}
+
+// Forward policy: packets go to the packet slots and/or through the detector into the
+// histogram; order-0 packets go to the beam stop.
+template <typename R, int DET>
+struct Forward {
+  static constexpr bool kWantsGs = false;
+  Acc<R> a_bs, a_det, a_over;
+  Counts cnt;
+  int err = 0;
+
+  __device__ __forceinline__ void start(const Lane<R>&) {}
+
+  __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const NeutronRng& rng,
+                                       const Lane<R>& L, R we, R, R, R len_tot) {
+    if (L.o == 0 && len_tot > R(0)) cnt.nhit++;
+    if (A.pk_order) store_slot<R>(A, L.idx * (Sof<R>(A).max_orders + 1) + L.o, L.n, we, L.nid, L.o);
+    if (L.o == 0) {
+      a_bs.add(we);
+      return;
+    }
+    cnt.nemit++;
+    if (DET == MCV_DET_NONE) return;
+    Ray<R> pe = L.n;
+    pe.w = we;
+    record(A, detect<R, DET>(Dof<R>(A), tu, rng, L.o, pe));
+  }
+
+  // a packet's detector result into the histogram and the tallies
+  __device__ __forceinline__ void record(const TraceArgs& A, const Hit<R>& h) {
+    if (h.bin >= 0) {
+      if (h.bin >= Dof<R>(A).n_bins) {
+        err = 1;
+        return;
+      }
+      if (A.hist) atomicAdd(A.hist + h.bin, (double)h.w_det);
+      a_det.add(h.w_det);
+      cnt.ndet++;
+    } else if (h.bin == -2) {
+      a_over.add(h.w_det);
+      cnt.nover++;
+    } else {
+      cnt.nmiss++;
+    }
+  }
+
+  __device__ __forceinline__ void scatter(const TraceArgs&, const Lane<R>&, int, R,
+                                          const Scatter<R>&, R, R) {}
+
+  __device__ __forceinline__ void clear(const TraceArgs& A, int64_t idx, int first) {
+    if (!A.pk_order) return;
+    const int slots = Sof<R>(A).max_orders + 1;
+    for (int o = first; o < slots; ++o) {
+      A.pk_order[idx * slots + o] = -1;
+      A.pk_id[idx * slots + o] = -1;
+    }
+  }
+
+  __device__ __forceinline__ void flush(const TraceArgs& A, int lane) {
+    if (A.tallies) {
+      const double v_bs = warp_sum(a_bs.value());
+      const double v_det = warp_sum(a_det.value());
+      const double v_over = warp_sum(a_over.value());
+      const uint32_t n_det = warp_sum(cnt.ndet), n_over = warp_sum(cnt.nover);
+      const uint32_t n_miss = warp_sum(cnt.nmiss), n_hit = warp_sum(cnt.nhit);
+      const uint32_t n_emit = warp_sum(cnt.nemit);
+      if (lane == 0) {
+        atomicAdd(A.tallies + MCV_T_BEAMSTOP, v_bs);
+        atomicAdd(A.tallies + MCV_T_WDET, v_det);
+        atomicAdd(A.tallies + MCV_T_WOVER, v_over);
+        atomicAdd(A.tallies + MCV_T_NDET, (double)n_det);
+        atomicAdd(A.tallies + MCV_T_NOVER, (double)n_over);
+        atomicAdd(A.tallies + MCV_T_NMISS, (double)n_miss);
+        atomicAdd(A.tallies + MCV_T_NHIT, (double)n_hit);
+        atomicAdd(A.tallies + MCV_T_NEMIT, (double)n_emit);
+      }
+    }
+    if (__any_sync(0xffffffffu, err != 0) && lane == 0 && A.err) atomicOr(A.err, 1);
+  }
+};
+
+// ---- the fused forward path, organised as waves --------------------------------------------
+// Three stages per warp, each run by all 32 lanes on their own work items:
+//   source:   32 new neutrons at a time; those that miss the sample only add their weight
+//             to the beam stop, those that meet it are queued (warp queue in shared memory);
+//   sample:   one order step of every lane's neutron (idle lanes take queued neutrons); the
+//             transmitted packets of orders >= 1 are queued for the detector;
+//   detector: whenever 32 packets are queued, each lane traces one through the detector
+//             system and histograms it.
+// The per-neutron arithmetic is the chain step's and the detector's: only the order in
+// which lanes do the work changes, which keeps the lanes of a warp busy on the same code.
+constexpr int kWarps = kThreads / 32;
+constexpr int kQueue = 64;  // per-warp queue capacity (at most 63 entries are ever held)
+
+template <typename R>
+struct QNeutron {  // an incident neutron that meets the sample
+  R x, y, z, dx, dy, dz, speed;
+  Tof<R> t;
+  int64_t nid;
+};
+
+template <typename R>
+struct QPacket {  // a transmitted packet of order >= 1 on its way to the detector
+  R x, y, z, dx, dy, dz, speed, w;
+  Tof<R> t;
+  int64_t nid;
+  int order;
+};
+
+template <typename R>
+constexpr size_t wave_smem_bytes() {
+  return (size_t)kWarps * kQueue * (sizeof(QNeutron<R>) + sizeof(QPacket<R>));
+}
+
+extern __shared__ __align__(16) unsigned char g_wave_smem[];
+
+// Detector stage: every lane traces one queued packet; full batches of 32, and the last
+// partial batch when `done`.  The packets of every batch go through this one call site, so
+// a packet's arithmetic never depends on which batch it falls in.  Returns `done`.
+template <typename R, int DET>
+__device__ __noinline__ bool detect_batches(const TraceArgs& A, const DetP<R>& D, const R* tu,
+                                            const QPacket<R>* dq, int& dq_n, bool done,
+                                            int lane, Forward<R, DET>& pol) {
+  while (dq_n >= 32 || (done && dq_n > 0)) {
+    const int take = dq_n < 32 ? dq_n : 32;
+    Ray<R> pe;
+    int order = 0;
+    int64_t nid = 0;
+    if (lane < take) {
+      const QPacket<R>& p = dq[dq_n - take + lane];
+      pe.x = p.x;
+      pe.y = p.y;
+      pe.z = p.z;
+      pe.dx = p.dx;
+      pe.dy = p.dy;
+      pe.dz = p.dz;
+      pe.speed = p.speed;
+      pe.t = p.t;
+      pe.w = p.w;
+      nid = p.nid;
+      order = p.order;
+    }
+    __syncwarp();
+    if (lane < take) {
+      const NeutronRng rng(A.seed, A.sim_id, nid);
+      pol.record(A, detect<R, DET>(D, tu, rng, order, pe));
+    }
+    dq_n -= take;
+  }
+  return done;
+}
+
+template <typename R, int NS, int DET>
+__device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forward<R, DET>& pol) {
+  const SampleP<R>& S = Sof<R>(A);
+  const DetP<R>& D = Dof<R>(A);
+  const unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  QNeutron<R>* hq = reinterpret_cast<QNeutron<R>*>(g_wave_smem) + wib * kQueue;
+  QPacket<R>* dq = reinterpret_cast<QPacket<R>*>(g_wave_smem + (size_t)kWarps * kQueue *
+                                                   sizeof(QNeutron<R>)) + wib * kQueue;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
+  int64_t next = lo;
+  int hq_n = 0, dq_n = 0;
+  Lane<R> L;
+  L.active = false;
+  L.o = 0;
+  L.idx = 0;
+  L.nid = 0;
+  for (;;) {
+    const unsigned idle = __ballot_sync(kFull, !L.active);
+    const int n_idle = __popc(idle);
+    // ---- source stage
+    while (hq_n < n_idle && next < hi) {
+      const int64_t i = next + lane;
+      bool hit = false;
+      Ray<R> nr;
+      int64_t nid = 0;
+      if (i < hi) {
+        nid = A.first_id + i;
+        const NeutronRng rng(A.seed, A.sim_id, nid);
+        bool ok = make_beam<R>(Bof<R>(A), rng, &nr);
+        ok = ok && !(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0));
+        if (ok) {
+          Seg<R> seg[2 * NS];
+          if (assembly_segs<R, NS>(S, nr, seg) > 0)
+            hit = true;
+          else
+            pol.a_bs.add(nr.w * Mth<R>::exp(R(0)));  // order-0 packet, no material ahead
+        }
+      }
+      const unsigned hm = __ballot_sync(kFull, hit);
+      if (hit) {
+        QNeutron<R>& q = hq[hq_n + __popc(hm & lt_mask)];
+        q.x = nr.x;
+        q.y = nr.y;
+        q.z = nr.z;
+        q.dx = nr.dx;
+        q.dy = nr.dy;
+        q.dz = nr.dz;
+        q.speed = nr.speed;
+        q.t = nr.t;
+        q.nid = nid;
+      }
+      hq_n += __popc(hm);
+      next += 32;
+      __syncwarp();
+    }
+    const int take = min(n_idle, hq_n);
+    if (!L.active) {
+      const int r = __popc(idle & lt_mask);
+      if (r < take) {
+        const QNeutron<R>& q = hq[hq_n - take + r];
+        L.n.x = q.x;
+        L.n.y = q.y;
+        L.n.z = q.z;
+        L.n.dx = q.dx;
+        L.n.dy = q.dy;
+        L.n.dz = q.dz;
+        L.n.speed = q.speed;
+        L.n.t = q.t;
+        L.n.w = R(1);
+        L.nid = q.nid;
+        L.o = 0;
+        L.active = true;
+      }
+    }
+    hq_n -= take;
+    __syncwarp();
+    if (!__any_sync(kFull, L.active)) {
+      if (next >= hi && hq_n == 0) {
+        detect_batches<R, DET>(A, D, tu, dq, dq_n, true, lane, pol);
+        break;
+      }
+      continue;
+    }
+    // ---- sample stage
+    StepState<R, NS> st;
+    R we = R(0);
+    bool to_det = false;
+    if (L.active) {
+      we = step_segments<R, NS, false>(A, S, L, st);
+      if (L.o == 0) {
+        pol.a_bs.add(we);
+        if (st.len_tot > R(0)) pol.cnt.nhit++;
+      } else {
+        to_det = true;
+        pol.cnt.nemit++;
+      }
+    }
+    const unsigned dm = __ballot_sync(kFull, to_det);
+    if (to_det) {
+      QPacket<R>& p = dq[dq_n + __popc(dm & lt_mask)];
+      p.x = L.n.x;
+      p.y = L.n.y;
+      p.z = L.n.z;
+      p.dx = L.n.dx;
+      p.dy = L.n.dy;
+      p.dz = L.n.dz;
+      p.speed = L.n.speed;
+      p.w = we;
+      p.t = L.n.t;
+      p.nid = L.nid;
+      p.order = L.o;
+    }
+    dq_n += __popc(dm);
+    if (L.active) {
+      if (L.o == S.max_orders || !(st.len_tot > R(0))) {
+        L.active = false;
+      } else {
+        const NeutronRng rng(A.seed, A.sim_id, L.nid);
+        L.active = step_scatter<R, NS, Forward<R, DET>>(A, S, rng, L, st, pol);
+      }
+    }
+    __syncwarp();
+    // ---- detector stage (full batches now, the remainder once the range is done)
+    const bool done = !__any_sync(kFull, L.active) && next >= hi && hq_n == 0;
+    if (detect_batches<R, DET>(A, D, tu, dq, dq_n, done, lane, pol)) break;
+  }
+  pol.flush(A, lane);
+}
+
+template <typename R, int NS, int DET>
+__global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__ TraceArgs A) {
+  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  stage_tubes<R, DET>(A, tu);
+  Forward<R, DET> pol;
+  run_chain<R, NS, DET, Forward<R, DET>>(A, tu, pol);
+}
+
+// resident blocks per SM the register allocation aims at (FP64 state needs more registers)
+template <typename R>
+struct WaveBlocks {
+  static constexpr int value = sizeof(R) == 4 ? 5 : 3;
+};
+
+template <typename R, int NS, int DET>
+__global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
+    wave_kernel(const __grid_constant__ TraceArgs A) {
+  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  stage_tubes<R, DET>(A, tu);
+  Forward<R, DET> pol;
+  run_waves<R, NS, DET>(A, tu, pol);
+}
+
+// the fused forward runs as waves (dynamic shared memory for the warp queues) unless it
+// stores packets or reads a stored beam
+inline bool uses_waves(const TraceArgs& A, int det) {
+  return det != MCV_DET_NONE && A.pk_order == nullptr && A.in_x == nullptr;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) beam_kernel(const __grid_constant__ TraceArgs A) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nid = A.first_id + i;
+    const NeutronRng rng(A.seed, A.sim_id, nid);
+    Ray<R> n;
+    const bool ok = make_beam<R>(Bof<R>(A), rng, &n);
+    if (!ok) {
+      n.x = n.y = n.z = R(0);
+      n.dx = n.dy = n.dz = R(0);
+      n.speed = R(0);
+      n.t.set(0.0);
+      n.w = R(0);
+    }
+    static_cast<R*>(A.pk_x)[i] = n.x;
+    static_cast<R*>(A.pk_y)[i] = n.y;
+    static_cast<R*>(A.pk_z)[i] = n.z;
+    static_cast<R*>(A.pk_vx)[i] = n.speed * n.dx;
+    static_cast<R*>(A.pk_vy)[i] = n.speed * n.dy;
+    static_cast<R*>(A.pk_vz)[i] = n.speed * n.dz;
+    static_cast<R*>(A.pk_w)[i] = n.w;
+    A.pk_t[i] = n.t.value();
+    if (A.pk_id) A.pk_id[i] = nid;
+    if (A.pk_order) A.pk_order[i] = ok ? 0 : -1;
+  }
+}
+
+template <typename R, int DET>
+__global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant__ TraceArgs A,
+                                                          EventsArgs E) {
+  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  stage_tubes<R, DET>(A, tu);
+  Acc<R> a_bs, a_det, a_over;
+  Counts cnt;
+  int err = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int o = A.in_order[i];
+    if (o < 0) continue;
+    const R w = static_cast<const R*>(A.in_w)[i];
+    if (o == 0) {
+      a_bs.add(w);
+      if (E.bin) E.bin[i] = -1;
+      if (E.pixel) E.pixel[i] = -1;
+      if (E.tof) E.tof[i] = 0.0;
+      if (E.w_det) E.w_det[i] = 0.0;
+      continue;
+    }
+    Ray<R> n;
+    if (!load_input<R>(A, i, &n)) continue;
+    cnt.nemit++;
+    const NeutronRng rng(A.seed, A.sim_id, A.in_id[i]);
+    const Hit<R> h = detect<R, DET>(Dof<R>(A), tu, rng, o, n);
+    if (h.bin >= 0) {
+      if (h.bin >= Dof<R>(A).n_bins) {
+        err = 1;
+        continue;
+      }
+      if (A.hist) atomicAdd(A.hist + h.bin, (double)h.w_det);
+      a_det.add(h.w_det);
+      cnt.ndet++;
+    } else if (h.bin == -2) {
+      a_over.add(h.w_det);
+      cnt.nover++;
+    } else {
+      cnt.nmiss++;
+    }
+    if (E.bin) E.bin[i] = h.bin;
+    if (E.pixel) E.pixel[i] = h.pixel;
+    if (E.tof) E.tof[i] = h.tof.value();
+    if (E.w_det) E.w_det[i] = (double)h.w_det;
+  }
+  const int lane = threadIdx.x & 31;
+  if (A.tallies) {
+    const double v_bs = warp_sum(a_bs.value());
+    const double v_det = warp_sum(a_det.value());
+    const double v_over = warp_sum(a_over.value());
+    const uint32_t n_det = warp_sum(cnt.ndet), n_over = warp_sum(cnt.nover);
+    const uint32_t n_miss = warp_sum(cnt.nmiss), n_emit = warp_sum(cnt.nemit);
+    if (lane == 0) {
+      atomicAdd(A.tallies + MCV_T_BEAMSTOP, v_bs);
+      atomicAdd(A.tallies + MCV_T_WDET, v_det);
+      atomicAdd(A.tallies + MCV_T_WOVER, v_over);
+      atomicAdd(A.tallies + MCV_T_NDET, (double)n_det);
+      atomicAdd(A.tallies + MCV_T_NOVER, (double)n_over);
+      atomicAdd(A.tallies + MCV_T_NMISS, (double)n_miss);
+      atomicAdd(A.tallies + MCV_T_NEMIT, (double)n_emit);
+    }
+  }
+  if (__any_sync(0xffffffffu, err != 0) && lane == 0 && A.err) atomicOr(A.err, 1);
+}
+
+// ---- adjoint (no counterpart in the paper) --------------------------------------------
+// Along a fixed random path every emitted packet's detected weight is a product of factors:
+//   w_det = e^{-tau_o} p_abs prod_k (mu_s L_k e^{-tau_k} rest_k) S_k
+// (S_k the S(Q,E) table value used by scattering k, rest_k the kernel's other factor).  The
+// scattering points, kernel choices and (Q, E) draws do not depend on the table or on the
+// cross sections, so dL/dtheta = sum over detected packets of g_b dw_det/dtheta with
+// g_b = dL/dI_b:
+//   dw/dS_e  = e^{-tau_o} p_abs prod_k a_k prod_{m != k} S_m  for each k with entry e
+//   dw/dsig  = w (sum of the log-derivatives of the attenuation and mu_s factors).
+// The adjoint kernel recomputes each neutron's path with the forward arithmetic (the shared
+// chain step) instead of storing it, keeps the per-scattering records in the thread, and
+// scatter-adds into dS (FP64 atomics, the table is L2-resident) and dsig (warp-reduced).
+constexpr int kMaxOrders = 7;
+
+template <typename R, int DET>
+struct Adjoint {
+  static constexpr bool kWantsGs = true;
+  R a[kMaxOrders];   // scattering factor without the table value
+  R s[kMaxOrders];   // table value (1 for kernels without a table)
+  int e[kMaxOrders]; // table entry or -1
+  double cum_dabs = 0.0, cum_ds = 0.0;
+  double acc_abs = 0.0, acc_s = 0.0;
+  int err = 0;
+
+  __device__ __forceinline__ void start(const Lane<R>&) {
+    cum_dabs = 0.0;
+    cum_ds = 0.0;
+  }
+
+  __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const NeutronRng& rng,
+                                       const Lane<R>& L, R we, R atten, R lg, R) {
+    if (L.o == 0) return;
+    Ray<R> pe = L.n;
+    pe.w = R(1);
+    const Hit<R> h = detect<R, DET>(Dof<R>(A), tu, rng, L.o, pe);
+    if (h.bin < 0) return;
+    if (h.bin >= Dof<R>(A).n_bins) {
+      err = 1;
+      return;
+    }
+    const double gb = A.g[h.bin];
+    if (gb == 0.0) return;
+    const ScatP<double>& g = A.Sd.s[A.gs];
+    const double w_det = (double)(we * h.pabs);
+    const double dabs = cum_dabs - g.n100 * (2200.0 / (double)L.n.speed) * (double)lg;
+    const double ds = cum_ds - g.n100 * (double)lg;
+    acc_abs += gb * w_det * dabs;
+    acc_s += gb * w_det * ds;
+    if (!A.dsqe) return;
+    R base = atten * h.pabs;
+    for (int m = 0; m < L.o; ++m) base *= a[m];
+    for (int k = 0; k < L.o; ++k) {
+      if (e[k] < 0) continue;
+      R prod = base;
+      for (int m = 0; m < L.o; ++m)
+        if (m != k) prod *= s[m];
+      atomicAdd(A.dsqe + e[k], gb * (double)prod);
+    }
+  }
+
+  __device__ __forceinline__ void scatter(const TraceArgs& A, const Lane<R>& L, int j, R a_fac,
+                                          const Scatter<R>& out, R lg_pt, R speed_in) {
+    const int k = L.o;
+    a[k] = a_fac * out.rest;
+    s[k] = out.s_value;
+    e[k] = out.entry;
+    const ScatP<double>& g = A.Sd.s[A.gs];
+    cum_dabs -= g.n100 * (2200.0 / (double)speed_in) * (double)lg_pt;
+    cum_ds -= g.n100 * (double)lg_pt;
+    if (j == A.gs) cum_ds += 1.0 / g.sig_s;
+  }
+
+  __device__ __forceinline__ void clear(const TraceArgs&, int64_t, int) {}
+
+  __device__ __forceinline__ void flush(const TraceArgs& A, int lane) {
+    const double s_abs = warp_sum(acc_abs), s_s = warp_sum(acc_s);
+    if (lane == 0) {
+      atomicAdd(A.dsig + 0, s_abs);
+      atomicAdd(A.dsig + 1, s_s);
+    }
+    if (__any_sync(0xffffffffu, err != 0) && lane == 0 && A.err) atomicOr(A.err, 1);
+  }
+};
+
+template <typename R, int NS, int DET>
+__global__ void __launch_bounds__(kThreads) adjoint_kernel(const __grid_constant__ TraceArgs A) {
+  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  stage_tubes<R, DET>(A, tu);
+  Adjoint<R, DET> pol;
+  run_chain<R, NS, DET, Adjoint<R, DET>>(A, tu, pol);
+}
+
+// ---- launchers, one set per real type -----------------------------------------------------
+template <typename R, int NS, int DET>
+cudaError_t launch_trace_k(const TraceArgs& A, int grid, cudaStream_t s) {
+  if (DET != MCV_DET_NONE && uses_waves(A, DET)) {
+    const size_t smem = wave_smem_bytes<R>();
+    cudaError_t e = cudaFuncSetAttribute(wave_kernel<R, NS, DET>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    wave_kernel<R, NS, DET><<<grid, kThreads, smem, s>>>(A);
+  } else {
+    trace_kernel<R, NS, DET><<<grid, kThreads, 0, s>>>(A);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, int NS>
+cudaError_t launch_trace_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  switch (det) {
+    case MCV_DET_SURFACE:
+      return launch_trace_k<R, NS, MCV_DET_SURFACE>(A, grid, s);
+    case MCV_DET_TUBES:
+      return launch_trace_k<R, NS, MCV_DET_TUBES>(A, grid, s);
+    default:
+      return launch_trace_k<R, NS, MCV_DET_NONE>(A, grid, s);
+  }
+}
+
+template <typename R>
+cudaError_t launch_trace_t(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  if (A.Sd.ns <= 1) return launch_trace_ns<R, 1>(A, det, grid, s);
+  if (A.Sd.ns == 2) return launch_trace_ns<R, 2>(A, det, grid, s);
+  return launch_trace_ns<R, 4>(A, det, grid, s);
+}
+
+// the kernel the fused forward of this shape launches (waves when a detector is fused)
+template <typename R, int NS>
+const void* trace_fn_ns(int det) {
+  if (det == MCV_DET_SURFACE) return (const void*)wave_kernel<R, NS, MCV_DET_SURFACE>;
+  if (det == MCV_DET_TUBES) return (const void*)wave_kernel<R, NS, MCV_DET_TUBES>;
+  return (const void*)trace_kernel<R, NS, MCV_DET_NONE>;
+}
+
+template <typename R>
+cudaError_t blocks_per_sm_t(int ns, int det, int* blocks) {
+  const void* fn = ns <= 1 ? trace_fn_ns<R, 1>(det) : (ns == 2 ? trace_fn_ns<R, 2>(det)
+                                                              : trace_fn_ns<R, 4>(det));
+  const size_t smem = det != MCV_DET_NONE ? wave_smem_bytes<R>() : 0;
+  if (smem) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem);
+}
+
+template <typename R>
+cudaError_t launch_beam_t(const TraceArgs& A, int grid, cudaStream_t s) {
+  beam_kernel<R><<<grid, kThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_detect_t(const TraceArgs& A, const EventsArgs& E, int det, int grid,
+                            cudaStream_t s) {
+  if (det == MCV_DET_SURFACE)
+    detect_kernel<R, MCV_DET_SURFACE><<<grid, kThreads, 0, s>>>(A, E);
+  else
+    detect_kernel<R, MCV_DET_TUBES><<<grid, kThreads, 0, s>>>(A, E);
+  return cudaGetLastError();
+}
+
+template <typename R, int NS>
+cudaError_t launch_adjoint_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  if (det == MCV_DET_SURFACE)
+    adjoint_kernel<R, NS, MCV_DET_SURFACE><<<grid, kThreads, 0, s>>>(A);
+  else
+    adjoint_kernel<R, NS, MCV_DET_TUBES><<<grid, kThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  if (A.Sd.ns <= 1) return launch_adjoint_ns<R, 1>(A, det, grid, s);
+  if (A.Sd.ns == 2) return launch_adjoint_ns<R, 2>(A, det, grid, s);
+  return launch_adjoint_ns<R, 4>(A, det, grid, s);
+}
+
+// defines the entry points of one real type (used once in mcv_fp32.cu / mcv_fp64.cu)
+#define MCV_DEFINE_ENTRY_POINTS(R, SUFFIX)                                                  \
+  cudaError_t launch_trace_##SUFFIX(const TraceArgs& A, int det, int grid, cudaStream_t s) { \
+    return launch_trace_t<R>(A, det, grid, s);                                              \
+  }                                                                                         \
+  cudaError_t blocks_per_sm_##SUFFIX(int ns, int det, int* blocks) {                        \
+    return blocks_per_sm_t<R>(ns, det, blocks);                                             \
+  }                                                                                         \
+  cudaError_t launch_beam_##SUFFIX(const TraceArgs& A, int grid, cudaStream_t s) {          \
+    return launch_beam_t<R>(A, grid, s);                                                    \
+  }                                                                                         \
+  cudaError_t launch_detect_##SUFFIX(const TraceArgs& A, const EventsArgs& E, int det,      \
+                                     int grid, cudaStream_t s) {                            \
+    return launch_detect_t<R>(A, E, det, grid, s);                                          \
+  }                                                                                         \
+  cudaError_t launch_adjoint_##SUFFIX(const TraceArgs& A, int det, int grid,                \
+                                      cudaStream_t s) {                                     \
+    return launch_adjoint_t<R>(A, det, grid, s);                                            \
+  }
+
+}  // namespace mcv

@@ -1,6 +1,8 @@
 // Launch-time parameter blocks of the ray-tracing kernels.  The host (mcv_api.cu) fills
-// them from the public descriptions in mcv.h, precomputing the derived constants once;
-// kernels receive them by value (kernel parameter space).
+// them from the public descriptions in mcv.h, precomputing the derived constants once, in
+// both real types: the FP32 kernels read only float fields (no conversion of parameters at
+// run time), the FP64 kernels only double fields.  Kernels receive them by value (kernel
+// parameter space).
 #pragma once
 
 #include <cstdint>
@@ -18,65 +20,73 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kMeVPerV2 = 0.5 * kNeutronMass / (kElemCharge * 1e-3);
 constexpr double kKPerV = kNeutronMass / kHbar * 1e-10;
 
-struct DBeam {
-  double ei, rel, div, width, height, z0, l1;
-  double speed0;   // sqrt(ei / kMeVPerV2)
-  double t0;       // (l1 - z0) / speed0
+template <typename R>
+struct BeamP {
+  R ei, rel, div, width, height, z0, l1;
+  R speed0;            // sqrt(ei / kMeVPerV2)
+  double t0;           // (l1 - z0) / speed0
+  float t0_hi, t0_lo;  // t0 as a float pair
 };
 
-struct DScat {
+template <typename R>
+struct ScatP {
   int shape;
   int nk;
   int ktype0, ktype1;
-  double dim0, dim1, dim2, half_h;  // half_h: half height of cylinders
-  double cos_rot, sin_rot;
-  double mu_s;       // 100 n sigma_s            (1/m)
-  double mu_a_v;     // 100 n sigma_abs 2200     (1/m * m/s): mu_abs(v) = mu_a_v / v
-  double ksig0, ksig_sum;
-  double n100;       // 100 n (for the adjoint)
-  double sig_s;
+  R dim0, dim1, dim2, half_h;  // half_h: half height of cylinders
+  R cos_rot, sin_rot;
+  R n100;       // 100 n   (mu[1/m] = 100 n[1/A^3] sigma[barn])
+  R sig_s;      // scattering cross section (sum of the kernels')
+  R sab2200;    // sigma_abs 2200: mu_tot(v) = 100 n (sigma_s + sab2200 / v)
+  R mu_s;       // 100 n sigma_s
+  R ksig0, ksig_sum;
 };
 
-struct DSample {
+template <typename R>
+struct SampleP {
   int ns;
   int max_orders;
-  double min_prob;
-  DScat s[MCV_MAX_SCATTERERS];
-  const float* sqe;
   int nq, ne;
-  double q_max, e_min, e_max, dq, de;
   int has_sqe;
+  R min_prob;
+  ScatP<R> s[MCV_MAX_SCATTERERS];
+  const float* sqe;
+  R q_max, e_min, e_max, dq, de;
 };
 
-struct DDet {
+template <typename R>
+struct DetP {
   int kind;
-  double radius;
-  double height, half_h;
   int n_phi, n_y;
   int n_rows;
   int packs[3];
   int row_off[3];
-  double row_y[3];
   int tubes_per_pack, pixels_per_tube;
   int max_tubes_row;
-  double tube_r, half_len, pitch, period, phi0, pix_len;
-  double mu_he_v;    // 100 n sigma 2200: mu(v) = mu_he_v / v (1/m)
-  double tof_min, dt, inv_dt;
   int n_tof;
   int64_t n_bins;
-  double tube_u[2 * MCV_MAX_TUBES_PER_ROW];  // sin, cos of every tube centre angle of a row
+  R radius, height, half_h;
+  R row_y[3];
+  R tube_r, half_len, pitch, period, phi0, pix_len;
+  R mu_he_v;        // 100 n sigma 2200: mu(v) = mu_he_v / v (1/m)
+  double tof_min, dt;
+  float tmin_hi, tmin_lo, inv_dt;  // FP32 tof binning: tof_min as a float pair
+  R tube_u[2 * MCV_MAX_TUBES_PER_ROW];  // sin, cos of every tube centre angle of a row
 };
 
 struct TraceArgs {
-  DSample S;
-  DDet D;
-  DBeam B;
+  SampleP<float> Sf;
+  SampleP<double> Sd;
+  DetP<float> Df;
+  DetP<double> Dd;
+  BeamP<float> Bf;
+  BeamP<double> Bd;
   uint32_t seed, sim_id;
   int64_t first_id, n;
   // fused outputs
   double* hist;
   double* tallies;
-  // stored input (null: generate from B)
+  // stored input (null: generate from the beam)
   const void *in_x, *in_y, *in_z, *in_vx, *in_vy, *in_vz, *in_w;
   const double* in_t;
   const int64_t* in_id;

@@ -35,3 +35,37 @@ def compare_packets(gpu, orc, rtol=None):
 def run_events(c, wl, pk):
     counts, tallies, ev = c.detect(wl, pk, events=True)
     return counts, tallies, {k: v.cpu().numpy() for k, v in ev.items()}
+
+
+# FP64 mode: relative agreement of states to 1e-12; weights to 1e-12 plus the rounding
+# amplification of the packet's history (kappa, the oracle's condition estimate) times a
+# few units of the FP64 epsilon.
+RT64 = 1e-12
+EPS64_K = 1e-15
+
+
+def fp64_weight_tol(kappa):
+    return RT64 + EPS64_K * kappa
+
+
+def hist_tolerance(packets, n_bins, fp=64):
+    """Per-bin tolerance of a histogram, from the oracle's detected packets."""
+    hit = packets["bin"] >= 0
+    b = packets["bin"][hit]
+    w = packets["w_det"][hit]
+    k = packets["kappa_det"][hit]
+    tol = np.zeros(n_bins)
+    if fp == 64:
+        np.add.at(tol, b, w * fp64_weight_tol(k))
+    else:
+        np.add.at(tol, b, w * np.maximum(1e-5, 1e-6 * k))
+    return tol
+
+
+def check_fp64_packets(gpu, orc):
+    dev = compare_packets(gpu, orc)
+    m = orc["order"] >= 0
+    k = orc["kappa"][m]
+    bad = {f: int((dev[f] > RT64).sum()) for f in ("r", "v", "t")}
+    bad["w"] = int((dev["w"] > fp64_weight_tol(k)).sum())
+    return dev, bad

@@ -39,6 +39,8 @@ def test_full_size_block_contribution(ctx, fp_mode):
     ctx.trace(wl, fp_mode=fp_mode, n=N - a - k, first_id=a + k, table=table, counts=cut,
               tallies=tc)
     diff = (full - cut).cpu().numpy()
+    # the two FP64 histograms add their events in other orders: rounding of the full bin
+    noise_b = 1e-13 * np.abs(full.cpu().numpy())
     del full, cut
     torch.cuda.empty_cache()
     ref = oracle.trace(wl, first_id=a, n=k, packets=True)
@@ -50,20 +52,23 @@ def test_full_size_block_contribution(ctx, fp_mode):
     # outside the block's bins only rounding noise remains
     mask = np.zeros(diff.size, dtype=bool)
     mask[bins] = True
-    noise = np.abs(diff[~mask]).max()
-    assert noise < 1e-9, noise
+    noise = (np.abs(diff) - noise_b)[~mask].max()
+    assert noise <= 0.0, noise
     got = diff[mask]
     want = expect[mask]
-    rel = np.abs(got - want) / np.abs(want)
+    if fp_mode == B.FP64:
+        tol = H.hist_tolerance(pk[pk["order"] >= 1], diff.size)[mask] + noise_b[mask]
+        bad = int((np.abs(got - want) > tol + 1e-13 * np.abs(want)).sum())
+        assert bad == 0, bad
+    else:
+        # FP32: weights within max(1e-5, 1e-6 kappa) (weights below the FP32 range aside); a
+        # flipped event moves its weight to another bin and shows up as two mismatches
+        tol = H.hist_tolerance(pk[pk["order"] >= 1], diff.size, fp=32)[mask] + noise_b[mask]
+        keep = want >= 1e-25
+        bad = int((np.abs(got - want) > tol + 1e-6 * np.abs(want))[keep].sum())
+        assert bad <= 2 * (1e-4 * int(hit.sum()) + 4 * np.sqrt(1e-4 * int(hit.sum())) + 1), bad
     n_events = int(hit.sum())
     assert n_events > 200
-    if fp_mode == B.FP64:
-        assert rel.max() < 1e-9, rel.max()
-    else:
-        # FP32: weights within 1e-3 (detector chord at 3 m); a flipped event moves its weight
-        # to another bin, which shows up here as a mismatch: at most max(1, 1e-4 events)
-        bad = int((rel > 1e-3).sum())
-        assert bad <= 2, (bad, n_events)
     # the tallies add up the same way
     t = (tf - tc).cpu().numpy()
     assert abs(t[B.T_NDET] - ref["tallies"][oracle.T_NDET]) <= (0 if fp_mode == B.FP64 else 2)

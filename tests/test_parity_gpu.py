@@ -43,40 +43,38 @@ def _small_c2(n):
 def test_fp64_packets_match_oracle(ctx, make, n):
     wl = make(n)
     pk, g = H.packets(ctx, wl, B.FP64)
-    o = oracle.trace(wl, hist=False)["packets"]
-    dev = H.compare_packets(g, o, RT64)
-    for f, d in dev.items():
-        assert d.size == 0 or d.max() < RT64, (f, d.max())
-    # detector on the stored packets, per packet
-    counts, tallies, ev = H.run_events(ctx, wl, pk)
     orc = oracle.trace(wl, packets=True)
     op = orc["packets"]
+    dev, bad = H.check_fp64_packets(g, op)
+    assert not any(bad.values()), (bad, {f: float(d.max()) for f, d in dev.items()})
+    # detector on the stored packets, per packet
+    counts, tallies, ev = H.run_events(ctx, wl, pk)
     m = op["order"] >= 1
     assert np.array_equal(ev["bin"][m], op["bin"][m])
     assert np.array_equal(ev["pixel"][m], op["pixel"][m])
     hit = m & (op["bin"] >= 0)
     np.testing.assert_allclose(ev["tof"][hit], op["tof"][hit], rtol=RT64)
-    np.testing.assert_allclose(ev["w_det"][hit], op["w_det"][hit], rtol=RT64)
+    wd = np.abs(ev["w_det"][hit] - op["w_det"][hit]) / op["w_det"][hit]
+    assert np.all(wd <= H.fp64_weight_tol(op["kappa_det"][hit])), float(wd.max())
     # histogram of the unfused detector step
-    hc = counts.cpu().numpy()
-    ho = orc["hist"]
-    nz = (hc != 0) | (ho != 0)
-    np.testing.assert_allclose(hc[nz], ho[nz], rtol=RT64, atol=0)
+    hc, ho = counts.cpu().numpy(), orc["hist"]
+    tol = H.hist_tolerance(op[m], ho.size)
+    assert np.all(np.abs(hc - ho) <= tol + 1e-15 * np.abs(ho))
 
 
 @pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 50000)])
 def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     wl = make(n)
     counts, tallies = ctx.trace(wl, fp_mode=B.FP64)
-    orc = oracle.trace(wl, packets=False)
+    orc = oracle.trace(wl, packets=True)
     hc, ho = counts.cpu().numpy(), orc["hist"]
-    nz = (hc != 0) | (ho != 0)
-    assert nz.sum() > 100
-    np.testing.assert_allclose(hc[nz], ho[nz], rtol=RT64, atol=0)
+    assert ((hc != 0) | (ho != 0)).sum() > 100
+    tol = H.hist_tolerance(orc["packets"], ho.size)
+    assert np.all(np.abs(hc - ho) <= tol + 1e-15 * np.abs(ho))
     t, to = tallies.cpu().numpy(), orc["tallies"]
     for gi, oi in ((B.T_BEAMSTOP, oracle.T_BEAMSTOP), (B.T_WDET, oracle.T_WDET),
                    (B.T_WOVER, oracle.T_WOVER)):
-        assert abs(t[gi] - to[oi]) <= RT64 * max(abs(to[oi]), 1e-300) + 1e-300
+        assert abs(t[gi] - to[oi]) <= 1e-12 * max(abs(to[oi]), 1e-300) + 1e-300
     assert t[B.T_NDET] == to[oracle.T_NDET]
     assert t[B.T_NOVER] == to[oracle.T_NOVER]
     assert t[B.T_NMISS] == to[oracle.T_NMISS]
@@ -90,13 +88,17 @@ def test_fp64_stored_beam_path_matches_fused(ctx):
     counts_a, tal_a = ctx.trace(wl, fp_mode=B.FP64, beam_in=beam)
     counts_b, tal_b = ctx.trace(wl, fp_mode=B.FP64)
     a, b = counts_a.cpu().numpy(), counts_b.cpu().numpy()
-    nz = (a != 0) | (b != 0)
-    np.testing.assert_allclose(a[nz], b[nz], rtol=1e-12, atol=0)
+    orc = oracle.trace(wl, packets=True)
+    tol = H.hist_tolerance(orc["packets"], a.size)
+    # the stored beam is rounded to FP64 velocity components, so ill-conditioned events may
+    # land on the other side of a bin edge: at most one moved event (two bins)
+    bad = int((np.abs(a - b) > 2 * tol + 1e-15 * np.abs(b)).sum())
+    assert bad <= 2, bad
     # the stored beam equals the oracle's incident packets (order-0 slots)
-    o = oracle.trace(wl, hist=False)["packets"].reshape(wl.n, wl.max_orders + 1)[:, 0]
+    o = orc["packets"].reshape(wl.n, wl.max_orders + 1)[:, 0]
     bd = beam.to_dict()
-    for f in H.FIELDS:
-        assert np.allclose(bd[f], o[f], rtol=1e-12, atol=1e-15) or f == "w"
+    for f in ("x", "y", "z", "vx", "vy", "vz", "t"):
+        np.testing.assert_allclose(bd[f], o[f], rtol=RT64, atol=1e-15)
 
 
 def test_fp64_large_ids_and_offsets(ctx):
@@ -105,15 +107,15 @@ def test_fp64_large_ids_and_offsets(ctx):
     first = (1 << 33) + 12345
     pk, g = H.packets(ctx, wl, B.FP64, first_id=first)
     o = oracle.trace(wl, first_id=first, hist=False)["packets"]
-    dev = H.compare_packets(g, o, RT64)
-    assert max(d.max() for d in dev.values() if d.size) < RT64
-    # additivity of split ranges
+    dev, bad = H.check_fp64_packets(g, o)
+    assert not any(bad.values()), bad
+    # additivity of split ranges (same neutrons, other launch shapes)
     c_all, _ = ctx.trace(wl, fp_mode=B.FP64, n=3000)
     c1, t1 = ctx.trace(wl, fp_mode=B.FP64, n=1234)
     ctx.trace(wl, fp_mode=B.FP64, n=3000 - 1234, first_id=1234, counts=c1, tallies=t1)
     a, b = c_all.cpu().numpy(), c1.cpu().numpy()
     nz = (a != 0) | (b != 0)
-    np.testing.assert_allclose(a[nz], b[nz], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(a[nz], b[nz], rtol=1e-13, atol=0)
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 1000, 4099])
@@ -121,8 +123,8 @@ def test_ragged_sizes(ctx, n):
     wl = mi.config1(n=n)
     pk, g = H.packets(ctx, wl, B.FP64)
     o = oracle.trace(wl, hist=False)["packets"]
-    dev = H.compare_packets(g, o, RT64)
-    assert max(d.max() for d in dev.values() if d.size) < RT64
+    dev, bad = H.check_fp64_packets(g, o)
+    assert not any(bad.values()), bad
 
 
 def test_degenerate_cases(ctx):
@@ -182,20 +184,25 @@ def test_invalid_arguments_are_rejected(ctx):
 
 
 # ---------------------------------------------------------------- FP32 fast mode
+W_FLOOR = 1e-30   # weights below this are outside the FP32 normal range
+
+
 def fp32_stats(ctx, wl):
     """Compare the FP32 fast mode with the FP64 oracle neutron by neutron.
 
-    A neutron whose FP32 history takes another discrete decision (another S(Q,E) bin, a
-    kinematic cut on the other side, another tube) has another packet structure or weights;
-    those are counted, not compared.  Returns the counts and deviations."""
+    Packets are compared while the oracle's weight is inside the FP32 normal range (FP32
+    weights below ~1e-38 underflow, which ends those histories early).  A neutron whose
+    FP32 history takes another discrete decision (another S(Q,E) bin, the other side of a
+    kinematic cut) has another packet structure; those are counted, not compared."""
     pk, g = H.packets(ctx, wl, B.FP32)
     orc = oracle.trace(wl, packets=True)
     op = orc["packets"]
     slots = wl.max_orders + 1
-    go = g["order"].reshape(-1, slots)
-    oo = op["order"].reshape(-1, slots)
+    sig = (op["order"] >= 0) & (op["w"] >= W_FLOOR)
+    go = np.where(sig, g["order"], -1).reshape(-1, slots)
+    oo = np.where(sig, op["order"], -1).reshape(-1, slots)
     same = np.all(go == oo, axis=1)
-    m = np.repeat(same, slots) & (op["order"] >= 0)
+    m = np.repeat(same, slots) & sig
     sub_g = {k: v[m] for k, v in g.items()}
     sub_o = op[m]
     dev = H.compare_packets(sub_g, sub_o)
@@ -203,28 +210,37 @@ def fp32_stats(ctx, wl):
     det = m & (op["order"] >= 1)
     events = det & ((op["bin"] >= 0) | (ev["bin"] >= 0))
     flips = int((events & (ev["bin"] != op["bin"])).sum())
-    both = det & (op["bin"] >= 0) & (ev["bin"] >= 0)
+    both = det & (op["bin"] >= 0) & (ev["bin"] >= 0) & (op["w_det"] >= W_FLOOR)
     wd = np.abs(ev["w_det"][both] - op["w_det"][both]) / op["w_det"][both]
     return {"neutrons": wl.n, "structure_diff": int((~same).sum()), "dev": dev,
+            "kappa": sub_o["kappa"], "kappa_det": op["kappa_det"][both],
             "flips": flips, "events": int(events.sum()), "wdet_dev": wd,
             "hist_gpu": counts.cpu().numpy(), "hist_orc": orc["hist"]}
 
 
-@pytest.mark.parametrize("make,n", [(mi.config1, 100000), (_small_c2, 100000)])
+def rate_bound(rate, n):
+    """Largest count consistent with a true rate `rate` over n trials (Poisson, 4 sigma)."""
+    mu = rate * n
+    return mu + 4.0 * np.sqrt(mu) + 1.0
+
+
+@pytest.mark.parametrize("make,n", [(mi.config1, 200000), (_small_c2, 200000)])
 def test_fp32_fast_mode_within_bounds(ctx, make, n):
     wl = make(n)
     st = fp32_stats(ctx, wl)
-    # discrete decisions taken differently in FP32: a small fraction of neutrons
-    assert st["structure_diff"] <= 1e-3 * n, st["structure_diff"]
-    # states of the packets whose history is the same: 1e-5, up to 1e-4 of them beyond
-    for f in ("r", "v", "t"):
+    # discrete decisions taken differently in FP32 (S(Q,E) bin edges, kinematic cuts)
+    assert st["structure_diff"] <= rate_bound(1e-3, n), st["structure_diff"]
+    # packet states within 1e-5 relative, or within the rounding amplification of the
+    # history (1e-6 kappa: ~16 FP32 unit roundoffs per unit of the condition estimate)
+    # where that is larger; at most 1e-4 of the packets beyond
+    tol = np.maximum(1e-5, 1e-6 * st["kappa"])
+    for f in ("r", "v", "t", "w"):
         d = st["dev"][f]
-        assert float((d > 1e-5).mean()) <= 1e-4, (f, float(np.quantile(d, 0.9999)))
-    d = st["dev"]["w"]
-    assert float((d > 1e-5).mean()) <= 1e-3, float(np.quantile(d, 0.999))
+        assert (d > tol).sum() <= rate_bound(1e-4, d.size), (f, float(np.quantile(d / tol, 0.9999)))
     # detector: at most 1e-4 of the events change pixel or tof bin
-    assert st["flips"] <= max(1e-4 * st["events"], 1), (st["flips"], st["events"])
-    assert float((st["wdet_dev"] > 1e-3).mean()) <= 1e-3
+    assert st["flips"] <= rate_bound(1e-4, st["events"]), (st["flips"], st["events"])
+    tol_d = np.maximum(1e-5, 1e-6 * st["kappa_det"])
+    assert (st["wdet_dev"] > tol_d).sum() <= rate_bound(1e-4, st["wdet_dev"].size)
     # histogram: total detected weight agrees within the flips
     hc, ho = st["hist_gpu"], st["hist_orc"]
-    assert abs(hc.sum() - ho.sum()) <= 2e-3 * ho.sum()
+    assert abs(hc.sum() - ho.sum()) <= 1e-4 * ho.sum()
