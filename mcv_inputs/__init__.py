@@ -105,10 +105,14 @@ class SqeGrid:
 
 @dataclass
 class Bvk:
+    """fcc lattice, nearest-neighbour central force constant phi, atomic mass, lattice
+    constant; msd_A2 = <u^2> (all three axes) of this force-constant model at 300 K from a
+    48^3 Brillouin-zone midpoint sum of hbar/(N M) sum (n + 1/2)/omega, used in the
+    Debye-Waller factor exp(-Q^2 <u^2>/3)."""
     phi_Nm: float = 10.0
     mass_u: float = 27.0
     a_A: float = 4.05
-    msd_A2: float = 0.0
+    msd_A2: float = 0.053334
     temperature_K: float = 300.0
 
 
@@ -194,6 +198,21 @@ def config4(n=10_000_000) -> Workload:
     """The configuration whose chi-squared gradient is taken (powder run, 1e7 neutrons)."""
     w = config2(n=n)
     return w.replace(name="powder-sqe-gradient-1e7")
+
+
+def crystal_sample(rot_deg=0.0) -> Scatterer:
+    """2 x 2 x 2 cm fcc single crystal (a = 4.05 A, n = 4/a^3), coherent one-phonon kernel,
+    rotated by rot_deg about the vertical axis ([100] along the beam at 0)."""
+    a = 4.05
+    return Scatterer(kind=BLOCK, dims=(0.02, 0.02, 0.02), n_per_A3=4.0 / a**3, sig_abs_b=0.23,
+                     kernels=[(K_BVK, 1.5)], rot_y=math.radians(rot_deg))
+
+
+def config3(rot_deg=0.0, n=2_000_000) -> Workload:
+    """Single crystal, one of the 181 orientations (0..180 degrees), 50 meV."""
+    return Workload(name="single-crystal-bvk-%g-deg" % rot_deg, beam=powder_beam(ei=50.0),
+                    scatterers=[crystal_sample(rot_deg)], detector=tube_detector(), n=n,
+                    max_orders=5, bvk=Bvk(), sim_id=int(round(rot_deg)))
 
 
 def can_scatterer() -> Scatterer:

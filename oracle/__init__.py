@@ -29,7 +29,7 @@ EVENT_DTYPE = np.dtype([
     ("nid", np.int64), ("order", np.int32), ("kernel", np.int32), ("scatterer", np.int32),
     ("entry", np.int32), ("q", np.float64), ("e", np.float64), ("ki", np.float64),
     ("kf", np.float64), ("factor", np.float64), ("w", np.float64),
-    ("qvec", np.float64, (3,))], align=True)
+    ("nroots", np.int32), ("mode", np.int32), ("qvec", np.float64, (3,))], align=True)
 
 T_BEAMSTOP, T_WDET, T_WOVER, T_NDET, T_NOVER, T_NMISS, T_NHIT, T_NPACK0 = range(8)
 NTALLY = T_NPACK0 + 8
@@ -86,6 +86,9 @@ def lib():
         L.orc_grad.restype = C.c_int
         L.orc_loss.argtypes = [P, C.c_int64, C.c_int64, P, C.c_double, P, P]
         L.orc_loss.restype = C.c_int
+        L.orc_bvk_modes.argtypes = [P, P, P, P]
+        L.orc_kernel_bvk.argtypes = [P, C.c_double, C.c_double, P, P, P, P, P, P]
+        L.orc_kernel_bvk.restype = C.c_int
         _lib = L
     return _lib
 
@@ -247,3 +250,24 @@ def loss(wl, target, scale_c, first_id=0, n=None):
     if rc:
         raise ValueError("oracle rejected the configuration")
     return out.value
+
+
+def bvk_modes(wl, q):
+    """Phonon energies (meV, ascending) and eigenvectors (columns) at q (1/A, crystal frame)."""
+    cfg = make_config(wl)
+    q = np.asarray(q, dtype=np.float64)
+    hw, ev = np.zeros(3), np.zeros(9)
+    lib().orc_bvk_modes(C.byref(cfg), _ptr(q), _ptr(hw), _ptr(ev))
+    return hw, ev.reshape(3, 3)
+
+
+def kernel_bvk(wl, rot_y, speed, d, u):
+    cfg = make_config(wl)
+    d = np.asarray(d, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    d_out = np.zeros(3)
+    sp, fac = C.c_double(), C.c_double()
+    ev = np.zeros(1, dtype=EVENT_DTYPE)
+    ok = lib().orc_kernel_bvk(C.byref(cfg), rot_y, speed, _ptr(d), _ptr(u), C.byref(sp),
+                              _ptr(d_out), C.byref(fac), _ptr(ev))
+    return {"ok": bool(ok), "speed": sp.value, "d": d_out, "factor": fac.value, "event": ev[0]}

@@ -388,6 +388,7 @@ struct KernelOut {
   int entry;         // table entry or -1
   double q, e, ki, kf;
   Vec3 qvec;
+  int nroots = 0, mode = 0;
 };
 
 // incoherent elastic: isotropic, speed unchanged (d sigma/d Omega = sigma_inc/4pi N e^-2W,
@@ -463,13 +464,236 @@ bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], 
   return true;
 }
 
+// ---- single-crystal coherent one-phonon kernel (Born-von Karman fcc) -------------------
+// Supplement S4 gives the coherent one-phonon cross section of a powder and the cross
+// section of one mode at Q.  For a single crystal of a Bravais lattice the sum over q and
+// tau with delta(Q - q - tau) picks q = Q (periodic dispersion), leaving per atom
+//   d2sigma/dOmega dEf = sigma/4pi (kf/ki) e^{-2W} sum_{b,s} hbar^2 (Q.e_b)^2/(2M hw_b)
+//                        N_s(hw_b) delta(Ei - Ef - s hw_b(Q)),
+// N_+ = n + 1 (creation), N_- = n (annihilation), n the Bose factor.  Sampling: direction
+// uniform, mode (b, s) uniform over 6, a root of g(Ef) = Ei - Ef - s hw_b(Q(Ef)) uniform
+// over the roots bracketed on 32 equal sub-intervals; weight 6 n_roots (kf/ki) e^{-2W}
+// R_b N_s / |g'(Ef)|.
+const double kMeVPerJ = 1.0 / (kElemCharge * 1e-3);
+
+struct BvkModel {
+  double coef;      // phi / M (1/s^2)
+  double a;         // lattice constant (A)
+  double hb2m;      // hbar^2 / (2 M) in meV A^2
+  double kT;        // meV
+  double msd;       // <u^2> (A^2)
+  double w_max;     // upper bound of hbar omega (meV): trace bound sqrt(24 phi/M)
+};
+
+BvkModel bvk_model(const orc_config& cfg) {
+  BvkModel m;
+  const double M = cfg.bvk_mass_u * kAtomicMass;
+  m.coef = cfg.bvk_phi_Nm / M;
+  m.a = cfg.bvk_a_A;
+  m.hb2m = kHbar * kHbar / (2.0 * M) * 1e20 * kMeVPerJ;
+  m.kT = kBoltzmann * cfg.temperature_K * kMeVPerJ;
+  m.msd = cfg.bvk_msd_A2;
+  m.w_max = kHbar * std::sqrt(24.0 * m.coef) * kMeVPerJ;
+  return m;
+}
+
+// the six nearest-neighbour bond directions of fcc (the other six are their negatives)
+const double kBond[6][3] = {{1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+
+// dynamical matrix D(q) = (phi/M) sum over the 12 neighbours of (1 - cos q.delta) dd^T,
+// delta = (a/2) n, d = n/sqrt(2); stored xx, yy, zz, xy, xz, yz (1/s^2)
+void bvk_dynmat(const BvkModel& m, const double q[3], double D[6]) {
+  for (int i = 0; i < 6; ++i) D[i] = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const double* n = kBond[k];
+    double qd = 0.5 * m.a * (q[0] * n[0] + q[1] * n[1] + q[2] * n[2]);
+    double c = 2.0 * m.coef * (1.0 - std::cos(qd)) * 0.5;  // two neighbours, dd^T = nn^T/2
+    D[0] += c * n[0] * n[0];
+    D[1] += c * n[1] * n[1];
+    D[2] += c * n[2] * n[2];
+    D[3] += c * n[0] * n[1];
+    D[4] += c * n[0] * n[2];
+    D[5] += c * n[1] * n[2];
+  }
+}
+
+// eigenvalues (ascending) of a symmetric 3x3 matrix, trigonometric form of Cardano's
+// solution; eigenvectors from the largest cross product of two rows of D - lambda I
+void eig_sym3(const double D[6], double lam[3], double vec[9]) {
+  const double a00 = D[0], a11 = D[1], a22 = D[2], a01 = D[3], a02 = D[4], a12 = D[5];
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  double l[3];
+  if (p1 == 0.0) {
+    l[0] = a00;
+    l[1] = a11;
+    l[2] = a22;
+    std::sort(l, l + 3);
+  } else {
+    const double q = (a00 + a11 + a22) / 3.0;
+    const double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) +
+                      2.0 * p1;
+    const double p = std::sqrt(p2 / 6.0);
+    const double b00 = (a00 - q) / p, b11 = (a11 - q) / p, b22 = (a22 - q) / p;
+    const double b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
+    double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                      b02 * (b01 * b12 - b11 * b02));
+    r = std::min(1.0, std::max(-1.0, r));
+    const double phi = std::acos(r) / 3.0;
+    l[2] = q + 2.0 * p * std::cos(phi);
+    l[0] = q + 2.0 * p * std::cos(phi + 2.0 * kPi / 3.0);
+    l[1] = 3.0 * q - l[0] - l[2];
+  }
+  for (int b = 0; b < 3; ++b) {
+    lam[b] = l[b];
+    const Vec3 r0 = {a00 - l[b], a01, a02}, r1 = {a01, a11 - l[b], a12},
+               r2 = {a02, a12, a22 - l[b]};
+    Vec3 c[3] = {cross(r0, r1), cross(r0, r2), cross(r1, r2)};
+    int best = 0;
+    double nb = dot(c[0], c[0]);
+    for (int i = 1; i < 3; ++i) {
+      double ni = dot(c[i], c[i]);
+      if (ni > nb) {
+        nb = ni;
+        best = i;
+      }
+    }
+    Vec3 e = (nb > 0.0) ? scale(c[best], 1.0 / std::sqrt(nb))
+                        : (b == 0 ? Vec3{1, 0, 0} : (b == 1 ? Vec3{0, 1, 0} : Vec3{0, 0, 1}));
+    vec[0 * 3 + b] = e.x;
+    vec[1 * 3 + b] = e.y;
+    vec[2 * 3 + b] = e.z;
+  }
+}
+
+double hbar_omega(double lam) { return kHbar * std::sqrt(std::max(lam, 0.0)) * kMeVPerJ; }
+
+// lab vector -> crystal frame: body = R^T lab for a rotation rot_y about +y; the crystal
+// axes are x_c = z_body ([100] along the beam at zero rotation), y_c = x_body, z_c = y_body
+Vec3 to_crystal(Vec3 v, double c, double s) {
+  const Vec3 b = {c * v.x - s * v.z, v.y, s * v.x + c * v.z};
+  return {b.z, b.x, b.y};
+}
+
+struct BvkEval {
+  double g;       // Ei - Ef - s hw_b
+  double hw;      // hbar omega_b (meV)
+  Vec3 Qc;        // Q in the crystal frame (1/A)
+  double lam[3], vec[9];
+};
+
+BvkEval bvk_g(const BvkModel& m, double Ei, double ki, Vec3 di, Vec3 df, double Ef, int b,
+              int s, double c, double sn) {
+  BvkEval r;
+  const double kf = kKPerV * std::sqrt(Ef / kMeVPerV2);
+  const Vec3 Q = add(scale(di, ki), scale(df, -kf));
+  r.Qc = to_crystal(Q, c, sn);
+  double D[6];
+  const double q[3] = {r.Qc.x, r.Qc.y, r.Qc.z};
+  bvk_dynmat(m, q, D);
+  eig_sym3(D, r.lam, r.vec);
+  r.hw = hbar_omega(r.lam[b]);
+  r.g = Ei - Ef - s * r.hw;
+  return r;
+}
+
+bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const double u[4],
+                KernelOut* o) {
+  const BvkModel m = bvk_model(cfg);
+  const double c = std::cos(rot_y), sn = std::sin(rot_y);
+  // outgoing direction, uniform
+  const double ct = 2.0 * u[0] - 1.0;
+  const double st = 2.0 * std::sqrt(u[0] * (1.0 - u[0]));
+  const double ph = 2.0 * kPi * u[1];
+  const Vec3 df = {st * std::cos(ph), st * std::sin(ph), ct};
+  // mode: branch b, creation (s = +1) or annihilation (s = -1)
+  int mode = (int)std::floor(6.0 * u[2]);
+  mode = std::min(std::max(mode, 0), 5);
+  const int b = mode % 3;
+  const int s = mode < 3 ? 1 : -1;
+  const double Ei = kMeVPerV2 * speed * speed;
+  const double ki = kKPerV * speed;
+  const double lo = s > 0 ? 0.0 : Ei;
+  const double hi = s > 0 ? Ei : Ei + m.w_max;
+  const int M = 32;
+  const double step = (hi - lo) / M;
+  double gk[M + 1];
+  for (int k = 0; k <= M; ++k) gk[k] = bvk_g(m, Ei, ki, d, df, lo + k * step, b, s, c, sn).g;
+  int nroots = 0;
+  for (int k = 0; k < M; ++k)
+    if ((gk[k] > 0.0) != (gk[k + 1] > 0.0)) ++nroots;
+  o->nroots = nroots;
+  o->mode = mode;
+  if (nroots == 0) return false;
+  int pick = (int)std::floor(u[3] * nroots);
+  pick = std::min(std::max(pick, 0), nroots - 1);
+  int kb = -1;
+  for (int k = 0, seen = 0; k < M; ++k) {
+    if ((gk[k] > 0.0) != (gk[k + 1] > 0.0)) {
+      if (seen == pick) {
+        kb = k;
+        break;
+      }
+      ++seen;
+    }
+  }
+  // bisection on the bracket
+  double ea = lo + kb * step, eb = lo + (kb + 1) * step;
+  const bool ga_pos = gk[kb] > 0.0;
+  for (int it = 0; it < 50; ++it) {
+    const double mid = 0.5 * (ea + eb);
+    if ((bvk_g(m, Ei, ki, d, df, mid, b, s, c, sn).g > 0.0) == ga_pos)
+      ea = mid;
+    else
+      eb = mid;
+  }
+  const double Ef = 0.5 * (ea + eb);
+  if (!(Ef > 0.0)) return false;
+  const BvkEval r = bvk_g(m, Ei, ki, d, df, Ef, b, s, c, sn);
+  if (!(r.hw >= 1e-3)) return false;
+  const Vec3 e = {r.vec[0 * 3 + b], r.vec[1 * 3 + b], r.vec[2 * 3 + b]};
+  // d hw / d Ef through Q(Ef) (Hellmann-Feynman: d lambda = e^T dD e)
+  const double kf = kKPerV * std::sqrt(Ef / kMeVPerV2);
+  const double dkf = kf / (2.0 * Ef);
+  const Vec3 dQ = scale(to_crystal(df, c, sn), -dkf);  // dQc/dEf
+  double dlam = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const double* n = kBond[k];
+    const double qd = 0.5 * m.a * (r.Qc.x * n[0] + r.Qc.y * n[1] + r.Qc.z * n[2]);
+    const double ed = (e.x * n[0] + e.y * n[1] + e.z * n[2]);
+    const double dqd = 0.5 * m.a * (dQ.x * n[0] + dQ.y * n[1] + dQ.z * n[2]);
+    dlam += 2.0 * m.coef * std::sin(qd) * dqd * ed * ed * 0.5;
+  }
+  const double dhw = kHbar * kMeVPerJ * dlam / (2.0 * std::sqrt(r.lam[b]));
+  const double gp = -1.0 - s * dhw;
+  const double nB = 1.0 / std::expm1(r.hw / m.kT);
+  const double Ns = s > 0 ? nB + 1.0 : nB;
+  const double qe = r.Qc.x * e.x + r.Qc.y * e.y + r.Qc.z * e.z;
+  const double Q2 = dot(r.Qc, r.Qc);
+  const double dw = std::exp(-Q2 * m.msd / 3.0);
+  const double Rb = m.hb2m * qe * qe / r.hw;
+  o->rest = 6.0 * nroots * (kf / ki) * dw * Rb * Ns / std::fabs(gp);
+  o->factor = o->rest;
+  o->s_value = 1.0;
+  o->entry = -1;
+  o->d = df;
+  o->speed = std::sqrt(Ef / kMeVPerV2);
+  o->q = std::sqrt(Q2);
+  o->e = Ei - Ef;
+  o->ki = ki;
+  o->kf = kf;
+  o->qvec = add(scale(d, ki), scale(df, -kf));
+  g_kappa += 1.0 / std::fabs(gp);
+  return true;
+}
+
 bool kernel_scatter(const orc_config& cfg, int ktype, double speed, Vec3 d, const double u[4],
-                    KernelOut* o) {
+                    KernelOut* o, double rot_y = 0.0) {
   if (ktype == ORC_K_ISO) {
     kernel_iso(speed, d, u, o);
     return true;
   }
   if (ktype == ORC_K_SQE) return kernel_sqe(cfg, speed, d, u, o);
+  if (ktype == ORC_K_BVK) return kernel_bvk(cfg, rot_y, speed, d, u, o);
   return false;
 }
 
@@ -583,7 +807,7 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     double uk[4];
     draw_kernel_uniforms(cfg, nid, o, uk);
     KernelOut ko;
-    if (!kernel_scatter(cfg, sc.ktype[k], n.speed, n.d, uk, &ko)) break;
+    if (!kernel_scatter(cfg, sc.ktype[k], n.speed, n.d, uk, &ko, sc.rot_y)) break;
     rec.s_value = ko.s_value;
     rec.entry = ko.entry;
     n.w = n.w * rec.a_factor * ko.factor;
@@ -658,8 +882,12 @@ bool config_ok(const orc_config* cfg) {
   for (int j = 0; j < cfg->n_scat; ++j) {
     const orc_scatterer& s = cfg->scat[j];
     if (s.nk < 1 || s.nk > 2) return false;
-    for (int k = 0; k < s.nk; ++k)
+    for (int k = 0; k < s.nk; ++k) {
       if (s.ktype[k] == ORC_K_SQE && (!cfg->sqe || cfg->nq <= 0 || cfg->ne <= 0)) return false;
+      if (s.ktype[k] == ORC_K_BVK && !(cfg->bvk_phi_Nm > 0 && cfg->bvk_mass_u > 0 &&
+                                      cfg->bvk_a_A > 0 && cfg->temperature_K > 0))
+        return false;
+    }
   }
   if (cfg->det_kind != ORC_DET_NONE && cfg->n_tof <= 0) return false;
   return true;
@@ -737,7 +965,7 @@ bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* tr
   pr.event++;
   double uk[4] = {a[0], a[1], b[0], b[1]};
   KernelOut ko;
-  if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko)) return true;
+  if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko, sc.rot_y)) return true;
   p.n.w = p.n.w * ko.factor;
   p.n.d = ko.d;
   p.n.speed = ko.speed;
@@ -891,6 +1119,44 @@ int64_t orc_detect(const orc_config* cfg, const double r[3], const double v[3], 
 
 int64_t orc_n_pixels(const orc_config* cfg) { return n_pixels(*cfg); }
 
+void orc_bvk_modes(const orc_config* cfg, const double q[3], double hw[3], double evec[9]) {
+  const BvkModel m = bvk_model(*cfg);
+  double D[6], lam[3];
+  bvk_dynmat(m, q, D);
+  eig_sym3(D, lam, evec);
+  for (int b = 0; b < 3; ++b) hw[b] = hbar_omega(lam[b]);
+}
+
+int orc_kernel_bvk(const orc_config* cfg, double rot_y, double speed, const double d[3],
+                   const double u[4], double* speed_out, double d_out[3], double* factor,
+                   orc_event* ev) {
+  KernelOut ko;
+  const bool ok = kernel_bvk(*cfg, rot_y, speed, Vec3{d[0], d[1], d[2]}, u, &ko);
+  if (ev) {
+    ev->nroots = ko.nroots;
+    ev->mode = ko.mode;
+  }
+  if (!ok) return 0;
+  *speed_out = ko.speed;
+  d_out[0] = ko.d.x;
+  d_out[1] = ko.d.y;
+  d_out[2] = ko.d.z;
+  *factor = ko.factor;
+  if (ev) {
+    ev->kernel = ORC_K_BVK;
+    ev->entry = -1;
+    ev->q = ko.q;
+    ev->e = ko.e;
+    ev->ki = ko.ki;
+    ev->kf = ko.kf;
+    ev->factor = ko.factor;
+    ev->qvec[0] = ko.qvec.x;
+    ev->qvec[1] = ko.qvec.y;
+    ev->qvec[2] = ko.qvec.z;
+  }
+  return 1;
+}
+
 int orc_trace(const orc_config* cfg, int64_t first_id, int64_t n, orc_packet* packets,
               orc_event* events, double* hist, double* tallies) {
   if (!config_ok(cfg) || n < 0) return 1;
@@ -935,6 +1201,8 @@ int orc_trace(const orc_config* cfg, int64_t first_id, int64_t n, orc_packet* pa
       e.kf = ko.kf;
       e.factor = ko.factor;
       e.w = w_after;
+      e.nroots = ko.nroots;
+      e.mode = ko.mode;
       e.qvec[0] = ko.qvec.x;
       e.qvec[1] = ko.qvec.y;
       e.qvec[2] = ko.qvec.z;

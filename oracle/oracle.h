@@ -91,6 +91,8 @@ typedef struct {
   int32_t entry;       /* S(Q,E) table entry, -1 if none */
   double q, e, ki, kf, factor;
   double w;            /* packet weight right after this scatter */
+  int32_t nroots;      /* single-crystal kernel: roots found for the drawn mode */
+  int32_t mode;        /* single-crystal kernel: branch + 3 * (annihilation) */
   double qvec[3];      /* ki_vec - kf_vec */
 } orc_event;
 
@@ -146,6 +148,11 @@ int orc_loss(const orc_config* cfg, int64_t first_id, int64_t n, const double* t
 /* Born-von Karman fcc dispersion: q in 1/A (crystal frame); energies (meV, ascending) and
    eigenvectors (columns, e[3*i+b] = component i of branch b) */
 void orc_bvk_modes(const orc_config* cfg, const double q[3], double hw[3], double evec[9]);
+
+/* single-crystal one-phonon kernel with the crystal rotated by rot_y about +y */
+int orc_kernel_bvk(const orc_config* cfg, double rot_y, double speed, const double d[3],
+                   const double u[4], double* speed_out, double d_out[3], double* factor,
+                   orc_event* ev);
 
 #ifdef __cplusplus
 }

@@ -149,42 +149,6 @@ constexpr size_t wave_smem_bytes() {
 
 extern __shared__ __align__(16) unsigned char g_wave_smem[];
 
-// Detector stage: every lane traces one queued packet; full batches of 32, and the last
-// partial batch when `done`.  The packets of every batch go through this one call site, so
-// a packet's arithmetic never depends on which batch it falls in.  Returns `done`.
-template <typename R, int DET>
-__device__ __noinline__ bool detect_batches(const TraceArgs& A, const DetP<R>& D, const R* tu,
-                                            const QPacket<R>* dq, int& dq_n, bool done,
-                                            int lane, Forward<R, DET>& pol) {
-  while (dq_n >= 32 || (done && dq_n > 0)) {
-    const int take = dq_n < 32 ? dq_n : 32;
-    Ray<R> pe;
-    int order = 0;
-    int64_t nid = 0;
-    if (lane < take) {
-      const QPacket<R>& p = dq[dq_n - take + lane];
-      pe.x = p.x;
-      pe.y = p.y;
-      pe.z = p.z;
-      pe.dx = p.dx;
-      pe.dy = p.dy;
-      pe.dz = p.dz;
-      pe.speed = p.speed;
-      pe.t = p.t;
-      pe.w = p.w;
-      nid = p.nid;
-      order = p.order;
-    }
-    __syncwarp();
-    if (lane < take) {
-      const NeutronRng rng(A.seed, A.sim_id, nid);
-      pol.record(A, detect<R, DET>(D, tu, rng, order, pe));
-    }
-    dq_n -= take;
-  }
-  return done;
-}
-
 template <typename R, int NS, int DET>
 __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forward<R, DET>& pol) {
   const SampleP<R>& S = Sof<R>(A);
@@ -266,13 +230,6 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
     }
     hq_n -= take;
     __syncwarp();
-    if (!__any_sync(kFull, L.active)) {
-      if (next >= hi && hq_n == 0) {
-        detect_batches<R, DET>(A, D, tu, dq, dq_n, true, lane, pol);
-        break;
-      }
-      continue;
-    }
     // ---- sample stage
     StepState<R, NS> st;
     R we = R(0);
@@ -312,9 +269,37 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
       }
     }
     __syncwarp();
-    // ---- detector stage (full batches now, the remainder once the range is done)
+    // ---- detector stage: full batches now, the remainder once the range is done.  This is
+    // the only place packets are detected, so a packet's arithmetic does not depend on the
+    // batch it falls in (or on the launch shape).
     const bool done = !__any_sync(kFull, L.active) && next >= hi && hq_n == 0;
-    if (detect_batches<R, DET>(A, D, tu, dq, dq_n, done, lane, pol)) break;
+    while (dq_n >= 32 || (done && dq_n > 0)) {
+      const int take = dq_n < 32 ? dq_n : 32;
+      Ray<R> pe;
+      int order = 0;
+      int64_t nid = 0;
+      if (lane < take) {
+        const QPacket<R>& p = dq[dq_n - take + lane];
+        pe.x = p.x;
+        pe.y = p.y;
+        pe.z = p.z;
+        pe.dx = p.dx;
+        pe.dy = p.dy;
+        pe.dz = p.dz;
+        pe.speed = p.speed;
+        pe.t = p.t;
+        pe.w = p.w;
+        nid = p.nid;
+        order = p.order;
+      }
+      __syncwarp();
+      if (lane < take) {
+        const NeutronRng rng(A.seed, A.sim_id, nid);
+        pol.record(A, detect<R, DET>(D, tu, rng, order, pe));
+      }
+      dq_n -= take;
+    }
+    if (done) break;
   }
   pol.flush(A, lane);
 }
@@ -328,9 +313,15 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__
 }
 
 // resident blocks per SM the register allocation aims at (FP64 state needs more registers)
+#ifndef MCV_WAVE_BLOCKS_F32
+#define MCV_WAVE_BLOCKS_F32 5
+#endif
+#ifndef MCV_WAVE_BLOCKS_F64
+#define MCV_WAVE_BLOCKS_F64 3
+#endif
 template <typename R>
 struct WaveBlocks {
-  static constexpr int value = sizeof(R) == 4 ? 5 : 3;
+  static constexpr int value = sizeof(R) == 4 ? MCV_WAVE_BLOCKS_F32 : MCV_WAVE_BLOCKS_F64;
 };
 
 template <typename R, int NS, int DET>

@@ -71,6 +71,12 @@ def test_full_size_block_contribution(ctx, fp_mode):
     assert n_events > 200
     # the tallies add up the same way
     t = (tf - tc).cpu().numpy()
-    assert abs(t[B.T_NDET] - ref["tallies"][oracle.T_NDET]) <= (0 if fp_mode == B.FP64 else 2)
+    if fp_mode == B.FP64:
+        assert t[B.T_NDET] == ref["tallies"][oracle.T_NDET]
+    else:
+        # FP32 weights below its range (~1e-38) underflow to zero and end those histories
+        sure = int((hit & (pk["w_det"] >= 1e-30)).sum())
+        maybe = int((hit & (pk["w_det"] >= 1e-46)).sum())
+        assert sure - 2 <= t[B.T_NDET] <= maybe + 2, (t[B.T_NDET], sure, maybe)
     if fp_mode == B.FP64:
         assert abs(t[B.T_BEAMSTOP] - ref["tallies"][oracle.T_BEAMSTOP]) <= 1e-6 * k
