@@ -14,7 +14,7 @@ struct mcv_ctx {
   int sm_count;
   int* d_err;          // device error flag (kernels set it; mcv_sync reads and clears it)
   unsigned long long* d_queue;  // work-queue counters of the batched launch
-  int occ[2][3][3];    // cached blocks per SM of the chain kernel: [fp][ns 1,2,4][det]
+  int occ[2][3][3][2]; // cached blocks per SM of the fused kernel: [fp][ns 1,2,4][det][bvk]
 };
 
 namespace {
@@ -68,7 +68,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
   S->ns = s->n_scatterers;
   S->max_orders = s->max_orders;
   S->min_prob = s->min_prob;
-  bool need_sqe = false;
+  bool need_sqe = false, need_bvk = false;
   for (int j = 0; j < s->n_scatterers; ++j) {
     const mcv_scatterer& a = s->scat[j];
     mcv::ScatP<double>& d = S->s[j];
@@ -79,8 +79,10 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     if (a.n_kernels < 1 || a.n_kernels > 2) return fail(MCV_EINVAL, "n_kernels must be 1 or 2");
     double sig = 0.0;
     for (int k = 0; k < a.n_kernels; ++k) {
-      if (a.kernel[k] != MCV_KERNEL_ISO && a.kernel[k] != MCV_KERNEL_SQE)
-        return fail(MCV_EINVAL, "kernel kind not supported by this build");
+      if (a.kernel[k] != MCV_KERNEL_ISO && a.kernel[k] != MCV_KERNEL_SQE &&
+          a.kernel[k] != MCV_KERNEL_BVK)
+        return fail(MCV_EINVAL, "unknown kernel kind");
+      if (a.kernel[k] == MCV_KERNEL_BVK) need_bvk = true;
       if (a.kernel_sig_b[k] < 0) return fail(MCV_EINVAL, "negative kernel cross section");
       if (a.kernel[k] == MCV_KERNEL_SQE) need_sqe = true;
       sig += a.kernel_sig_b[k];
@@ -129,6 +131,24 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     S->dq = q.q_max / q.nq;
     S->de = (q.e_max - q.e_min) / q.ne;
     S->has_sqe = 1;
+  }
+  if (need_bvk) {
+    const mcv_bvk& b = s->bvk;
+    for (double x : {b.phi_Nm, b.mass_u, b.a_A, b.msd_A2, b.temperature_K})
+      if (!is_finite(x)) return fail(MCV_EINVAL, "Born-von Karman parameter is not finite");
+    if (!(b.phi_Nm > 0 && b.mass_u > 0 && b.a_A > 0 && b.temperature_K > 0 && b.msd_A2 >= 0))
+      return fail(MCV_EINVAL, "bad Born-von Karman parameters");
+    const double kAtomicMass = 1.66053906660e-27, kBoltzmann = 1.380649e-23;
+    const double mev_per_j = 1.0 / (mcv::kElemCharge * 1e-3);
+    const double M = b.mass_u * kAtomicMass;
+    S->has_bvk = 1;
+    S->bvk_coef = b.phi_Nm / M;
+    S->bvk_ah = 0.5 * b.a_A;
+    S->bvk_hb2m = mcv::kHbar * mcv::kHbar / (2.0 * M) * 1e20 * mev_per_j;
+    S->bvk_kT = kBoltzmann * b.temperature_K * mev_per_j;
+    S->bvk_msd = b.msd_A2;
+    S->bvk_wmax = mcv::kHbar * std::sqrt(24.0 * S->bvk_coef) * mev_per_j;
+    S->bvk_hbar = mcv::kHbar * mev_per_j;
   }
   return MCV_OK;
 }
@@ -252,6 +272,14 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
   f->e_max = (float)d.e_max;
   f->dq = (float)d.dq;
   f->de = (float)d.de;
+  f->has_bvk = d.has_bvk;
+  f->bvk_coef = (float)d.bvk_coef;
+  f->bvk_ah = (float)d.bvk_ah;
+  f->bvk_hb2m = (float)d.bvk_hb2m;
+  f->bvk_kT = (float)d.bvk_kT;
+  f->bvk_msd = (float)d.bvk_msd;
+  f->bvk_wmax = (float)d.bvk_wmax;
+  f->bvk_hbar = (float)d.bvk_hbar;
 }
 
 void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
@@ -501,9 +529,9 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   A.err = ctx->d_err;
   const int detk = fused ? A.Dd.kind : MCV_DET_NONE;
   const int fp = sample->fp_mode;
-  int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][detk];
+  int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][detk][A.Sd.has_bvk ? 1 : 0];
   if (occ == 0) {
-    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, detk, &occ);
+    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, detk, A.Sd.has_bvk, &occ);
     if (e != cudaSuccess || occ < 1) occ = 1;
   }
   const int grid = grid_for(ctx, n, occ);
@@ -599,9 +627,9 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
     A.hist = hist->counts;
     A.tallies = hist->tallies;
     A.stop_on_zero = 1;
-    int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][A.Dd.kind];
+    int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.has_bvk ? 1 : 0];
     if (occ == 0) {
-      e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, &occ);
+      e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ);
       if (e != cudaSuccess || occ < 1) occ = 1;
     }
     e = mcv::launch_trace(A, fp, A.Dd.kind, grid_for(ctx, n, occ), s);

@@ -84,7 +84,11 @@ __device__ __forceinline__ R step_segments(const TraceArgs& A, const SampleP<R>&
 // ahead, with a kernel picked at random (section 2.4.3 "Multiple Scattering", bounded
 // chain).  Call only when the packet has material ahead and L.o < max_orders.  Returns
 // whether the neutron is still alive.
-template <typename R, int NS, class P>
+// kernel sets compiled into a launch: the single-crystal kernel only where it is used
+constexpr int kKernelsPowder = (1 << MCV_KERNEL_ISO) | (1 << MCV_KERNEL_SQE);
+constexpr int kKernelsAll = kKernelsPowder | (1 << MCV_KERNEL_BVK);
+
+template <typename R, int NS, int KS, class P>
 __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R>& S,
                                              const NeutronRng& rng, Lane<R>& L,
                                              const StepState<R, NS>& st, P& pol) {
@@ -125,11 +129,13 @@ __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R
   const int ktype = kk ? sc.ktype1 : sc.ktype0;
   Scatter<R> out;
   bool ok = false;
-  if (ktype == MCV_KERNEL_ISO) {
+  if ((KS & (1 << MCV_KERNEL_ISO)) && ktype == MCV_KERNEL_ISO) {
     kernel_iso<R>(rng, L.o, &L.n, &out);
     ok = true;
-  } else if (ktype == MCV_KERNEL_SQE) {
+  } else if ((KS & (1 << MCV_KERNEL_SQE)) && ktype == MCV_KERNEL_SQE) {
     ok = kernel_sqe<R>(S, rng, L.o, &L.n, &out, &pol.err);
+  } else if ((KS & (1 << MCV_KERNEL_BVK)) && ktype == MCV_KERNEL_BVK) {
+    ok = kernel_bvk<R>(S, sc.cos_rot, sc.sin_rot, rng, L.o, &L.n, &out);
   }
   if (!ok) {
     pol.clear(A, L.idx, L.o + 1);
@@ -147,7 +153,7 @@ __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R
 
 // One order of one neutron: segments ahead, emission of the transmitted packet, then the
 // scattered packet continues.  Returns whether the neutron is still alive.
-template <typename R, int NS, int DET, class P>
+template <typename R, int NS, int DET, int KS, class P>
 __device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane<R>& L, P& pol) {
   const SampleP<R>& S = Sof<R>(A);
   const NeutronRng rng(A.seed, A.sim_id, L.nid);
@@ -158,12 +164,12 @@ __device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane
     pol.clear(A, L.idx, L.o + 1);
     return false;
   }
-  return step_scatter<R, NS, P>(A, S, rng, L, st, pol);
+  return step_scatter<R, NS, KS, P>(A, S, rng, L, st, pol);
 }
 
 // Warp loop: each warp owns ids [lo, hi) of the launch; lanes whose neutron finished take
 // the next ids at the top of each step, so all 32 lanes run chain_step together.
-template <typename R, int NS, int DET, class P>
+template <typename R, int NS, int DET, int KS, class P>
 __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& pol) {
   const unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -206,7 +212,7 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
       if (next >= hi) break;
       continue;
     }
-    if (L.active) L.active = chain_step<R, NS, DET, P>(A, tu, L, pol);
+    if (L.active) L.active = chain_step<R, NS, DET, KS, P>(A, tu, L, pol);
   }
   pol.flush(A, lane);
 }

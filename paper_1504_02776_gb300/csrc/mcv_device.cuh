@@ -35,6 +35,9 @@ struct Mth<float> {
     sincospif(2.0f * u, s, c);
   }
   static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
+  static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
+  static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
+  static __device__ __forceinline__ float acos_(float x) { return acosf(x); }
 };
 
 template <>
@@ -55,6 +58,9 @@ struct Mth<double> {
     ::sincos(2.0 * kPi * u, s, c);
   }
   static __device__ __forceinline__ double inf() { return CUDART_INF; }
+  static __device__ __forceinline__ double cos_(double x) { return ::cos(x); }
+  static __device__ __forceinline__ double sin_(double x) { return ::sin(x); }
+  static __device__ __forceinline__ double acos_(double x) { return ::acos(x); }
 };
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------------------------
@@ -514,6 +520,228 @@ __device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng
   sc->entry = entry;
   sc->q = Q;
   sc->e = E;
+  return true;
+}
+
+// ---- single-crystal coherent one-phonon kernel (Born-von Karman fcc) -------------------
+// Per atom of a Bravais crystal (supplement S4, coherent one-phonon, with q = Q reduced):
+//   d2sigma/dOmega dEf = sigma/4pi (kf/ki) e^{-2W} sum_{b,s} hbar^2 (Q.e_b)^2/(2M hw_b)
+//                        N_s delta(Ei - Ef - s hw_b(Q)),  N_+ = n + 1, N_- = n.
+// Direction uniform, mode (b, s) uniform over six, root of g(Ef) = Ei - Ef - s hw_b(Q(Ef))
+// uniform over those bracketed on 32 sub-intervals and refined by bisection; weight
+// 6 n_roots (kf/ki) e^{-2W} R_b N_s / |g'|.  Dynamical matrix of the 12 nearest neighbours
+// (a/2)(+-1,+-1,0)..., eigenvalues by the trigonometric solution of the cubic.
+template <typename R>
+__device__ __forceinline__ void bvk_dynmat(const SampleP<R>& S, R qx, R qy, R qz, R D[6]) {
+  // the six bond directions n (the other six are -n): (1,1,0) (1,-1,0) (1,0,1) (1,0,-1)
+  // (0,1,1) (0,1,-1); each pair adds 2 (phi/M)(1 - cos q.delta) n n^T / 2
+  const R nb[6][3] = {{1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) D[i] = R(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const R* n = nb[k];
+    const R qd = S.bvk_ah * (qx * n[0] + qy * n[1] + qz * n[2]);
+    const R c = R(2) * S.bvk_coef * (R(1) - Mth<R>::cos_(qd)) * R(0.5);
+    D[0] += c * n[0] * n[0];
+    D[1] += c * n[1] * n[1];
+    D[2] += c * n[2] * n[2];
+    D[3] += c * n[0] * n[1];
+    D[4] += c * n[0] * n[2];
+    D[5] += c * n[1] * n[2];
+  }
+}
+
+// eigenvalues of the symmetric 3x3 matrix (xx yy zz xy xz yz), ascending
+template <typename R>
+__device__ __forceinline__ void eig3_values(const R D[6], R l[3]) {
+  using M = Mth<R>;
+  const R a00 = D[0], a11 = D[1], a22 = D[2], a01 = D[3], a02 = D[4], a12 = D[5];
+  const R p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  if (p1 == R(0)) {
+    R x = a00, y = a11, z = a22, t;
+    if (x > y) { t = x; x = y; y = t; }
+    if (y > z) { t = y; y = z; z = t; }
+    if (x > y) { t = x; x = y; y = t; }
+    l[0] = x;
+    l[1] = y;
+    l[2] = z;
+    return;
+  }
+  const R q = (a00 + a11 + a22) / R(3);
+  const R p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + R(2) * p1;
+  const R p = M::sqrt(p2 / R(6));
+  const R b00 = (a00 - q) / p, b11 = (a11 - q) / p, b22 = (a22 - q) / p;
+  const R b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
+  R r = R(0.5) * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                  b02 * (b01 * b12 - b11 * b02));
+  r = M::fmin(R(1), M::fmax(R(-1), r));
+  const R phi = M::acos_(r) / R(3);
+  l[2] = q + R(2) * p * M::cos_(phi);
+  l[0] = q + R(2) * p * M::cos_(phi + R(2) * (R)kPi / R(3));
+  l[1] = R(3) * q - l[0] - l[2];
+}
+
+// unit eigenvector of eigenvalue lam: the largest cross product of two rows of D - lam I
+template <typename R>
+__device__ __forceinline__ void eig3_vector(const R D[6], R lam, R* ex, R* ey, R* ez) {
+  const R r0x = D[0] - lam, r0y = D[3], r0z = D[4];
+  const R r1x = D[3], r1y = D[1] - lam, r1z = D[5];
+  const R r2x = D[4], r2y = D[5], r2z = D[2] - lam;
+  R cx[3], cy[3], cz[3];
+  cx[0] = r0y * r1z - r0z * r1y; cy[0] = r0z * r1x - r0x * r1z; cz[0] = r0x * r1y - r0y * r1x;
+  cx[1] = r0y * r2z - r0z * r2y; cy[1] = r0z * r2x - r0x * r2z; cz[1] = r0x * r2y - r0y * r2x;
+  cx[2] = r1y * r2z - r1z * r2y; cy[2] = r1z * r2x - r1x * r2z; cz[2] = r1x * r2y - r1y * r2x;
+  R bx = cx[0], by = cy[0], bz = cz[0];
+  R nb = bx * bx + by * by + bz * bz;
+#pragma unroll
+  for (int i = 1; i < 3; ++i) {
+    const R ni = cx[i] * cx[i] + cy[i] * cy[i] + cz[i] * cz[i];
+    if (ni > nb) {
+      nb = ni;
+      bx = cx[i];
+      by = cy[i];
+      bz = cz[i];
+    }
+  }
+  if (nb > R(0)) {
+    const R inv = R(1) / Mth<R>::sqrt(nb);
+    *ex = bx * inv;
+    *ey = by * inv;
+    *ez = bz * inv;
+  } else {
+    *ex = R(1);
+    *ey = R(0);
+    *ez = R(0);
+  }
+}
+
+// lab vector -> crystal frame (body = R^T lab, rotation about +y; x_c = z_b, y_c = x_b,
+// z_c = y_b: [100] along the beam at zero rotation)
+template <typename R>
+__device__ __forceinline__ void to_crystal(R c, R s, R vx, R vy, R vz, R* ox, R* oy, R* oz) {
+  *ox = s * vx + c * vz;
+  *oy = c * vx - s * vz;
+  *oz = vy;
+}
+
+template <typename R>
+struct BvkPoint {
+  R g, hw, qx, qy, qz;
+  R D[6];
+  R lam;
+};
+
+template <typename R>
+__device__ __forceinline__ BvkPoint<R> bvk_point(const SampleP<R>& S, R c, R s, R Ei, R ki,
+                                                  R dix, R diy, R diz, R dfx, R dfy, R dfz,
+                                                  R Ef, int b, int sg) {
+  BvkPoint<R> P;
+  const R kf = (R)kKPerV * Mth<R>::sqrt(Ef / (R)kMeVPerV2);
+  const R Qx = dix * ki - dfx * kf, Qy = diy * ki - dfy * kf, Qz = diz * ki - dfz * kf;
+  to_crystal<R>(c, s, Qx, Qy, Qz, &P.qx, &P.qy, &P.qz);
+  bvk_dynmat<R>(S, P.qx, P.qy, P.qz, P.D);
+  R l[3];
+  eig3_values<R>(P.D, l);
+  P.lam = b == 0 ? l[0] : (b == 1 ? l[1] : l[2]);
+  P.hw = S.bvk_hbar * Mth<R>::sqrt(Mth<R>::fmax(P.lam, R(0)));
+  P.g = Ei - Ef - (R)sg * P.hw;
+  return P;
+}
+
+template <typename R>
+__device__ __forceinline__ bool kernel_bvk(const SampleP<R>& S, R crot, R srot,
+                                           const NeutronRng& rng, int o, Ray<R>* n,
+                                           Scatter<R>* sc) {
+  using M = Mth<R>;
+  R u0, u1, u2, u3;
+  rng.pair<R>(o, 1, &u0, &u1);
+  rng.pair<R>(o, 2, &u2, &u3);
+  const R ct = R(2) * u0 - R(1);
+  const R st = R(2) * M::sqrt(u0 * (R(1) - u0));
+  R sp, cp;
+  M::sincos2pi(u1, &sp, &cp);
+  const R dfx = st * cp, dfy = st * sp, dfz = ct;
+  int mode = (int)M::floor(R(6) * u2);
+  mode = min(max(mode, 0), 5);
+  const int b = mode % 3;
+  const int sg = mode < 3 ? 1 : -1;
+  const R Ei = (R)kMeVPerV2 * n->speed * n->speed;
+  const R ki = (R)kKPerV * n->speed;
+  const R lo = sg > 0 ? R(0) : Ei;
+  const R hi = sg > 0 ? Ei : Ei + S.bvk_wmax;
+  constexpr int kM = 32;
+  const R step = (hi - lo) / (R)kM;
+  // signs of g on the grid, one bit per node
+  uint64_t pos = 0;
+  for (int k = 0; k <= kM; ++k) {
+    const BvkPoint<R> P = bvk_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy, dfz,
+                                       lo + (R)k * step, b, sg);
+    if (P.g > R(0)) pos |= (uint64_t)1 << k;
+  }
+  const uint64_t change = (pos ^ (pos >> 1)) & ((((uint64_t)1) << kM) - 1);
+  const int nroots = __popcll(change);
+  if (nroots == 0) return false;
+  int pick = (int)M::floor(u3 * (R)nroots);
+  pick = min(max(pick, 0), nroots - 1);
+  uint64_t ch = change;
+  for (int i = 0; i < pick; ++i) ch &= ch - 1;  // drop the lowest set bits
+  const int kb = __ffsll((long long)ch) - 1;
+  R ea = lo + (R)kb * step, eb = lo + (R)(kb + 1) * step;
+  const bool ga_pos = (pos >> kb) & 1;
+  const int iters = sizeof(R) == 8 ? 50 : 24;
+  for (int it = 0; it < iters; ++it) {
+    const R mid = R(0.5) * (ea + eb);
+    const BvkPoint<R> P = bvk_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy, dfz,
+                                       mid, b, sg);
+    if ((P.g > R(0)) == ga_pos)
+      ea = mid;
+    else
+      eb = mid;
+  }
+  const R Ef = R(0.5) * (ea + eb);
+  if (!(Ef > R(0))) return false;
+  const BvkPoint<R> P = bvk_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy, dfz,
+                                     Ef, b, sg);
+  if (!(P.hw >= R(1e-3))) return false;
+  R ex, ey, ez;
+  eig3_vector<R>(P.D, P.lam, &ex, &ey, &ez);
+  // d hw / d Ef through Q(Ef) (Hellmann-Feynman: d lambda = e^T dD e)
+  const R kf = (R)kKPerV * M::sqrt(Ef / (R)kMeVPerV2);
+  const R dkf = kf / (R(2) * Ef);
+  R dqx, dqy, dqz;
+  to_crystal<R>(crot, srot, dfx, dfy, dfz, &dqx, &dqy, &dqz);
+  dqx *= -dkf;
+  dqy *= -dkf;
+  dqz *= -dkf;
+  const R nb[6][3] = {{1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+  R dlam = R(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const R* v = nb[k];
+    const R qd = S.bvk_ah * (P.qx * v[0] + P.qy * v[1] + P.qz * v[2]);
+    const R ed = ex * v[0] + ey * v[1] + ez * v[2];
+    const R dqd = S.bvk_ah * (dqx * v[0] + dqy * v[1] + dqz * v[2]);
+    dlam += R(2) * S.bvk_coef * M::sin_(qd) * dqd * ed * ed * R(0.5);
+  }
+  const R dhw = S.bvk_hbar * dlam / (R(2) * M::sqrt(P.lam));
+  const R gp = R(-1) - (R)sg * dhw;
+  const R nB = R(1) / M::expm1(P.hw / S.bvk_kT);
+  const R Ns = sg > 0 ? nB + R(1) : nB;
+  const R qe = P.qx * ex + P.qy * ey + P.qz * ez;
+  const R Q2 = P.qx * P.qx + P.qy * P.qy + P.qz * P.qz;
+  const R dw = M::exp(-Q2 * S.bvk_msd / R(3));
+  const R Rb = S.bvk_hb2m * qe * qe / P.hw;
+  sc->rest = R(6) * (R)nroots * (kf / ki) * dw * Rb * Ns / M::fabs(gp);
+  sc->factor = sc->rest;
+  sc->s_value = R(1);
+  sc->entry = -1;
+  sc->q = M::sqrt(Q2);
+  sc->e = Ei - Ef;
+  n->dx = dfx;
+  n->dy = dfy;
+  n->dz = dfz;
+  n->speed = M::sqrt(Ef / (R)kMeVPerV2);
   return true;
 }
 

@@ -149,7 +149,7 @@ constexpr size_t wave_smem_bytes() {
 
 extern __shared__ __align__(16) unsigned char g_wave_smem[];
 
-template <typename R, int NS, int DET>
+template <typename R, int NS, int DET, int KS>
 __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forward<R, DET>& pol) {
   const SampleP<R>& S = Sof<R>(A);
   const DetP<R>& D = Dof<R>(A);
@@ -265,7 +265,7 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
         L.active = false;
       } else {
         const NeutronRng rng(A.seed, A.sim_id, L.nid);
-        L.active = step_scatter<R, NS, Forward<R, DET>>(A, S, rng, L, st, pol);
+        L.active = step_scatter<R, NS, KS, Forward<R, DET>>(A, S, rng, L, st, pol);
       }
     }
     __syncwarp();
@@ -304,12 +304,12 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
   pol.flush(A, lane);
 }
 
-template <typename R, int NS, int DET>
+template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
   Forward<R, DET> pol;
-  run_chain<R, NS, DET, Forward<R, DET>>(A, tu, pol);
+  run_chain<R, NS, DET, KS, Forward<R, DET>>(A, tu, pol);
 }
 
 // resident blocks per SM the register allocation aims at (FP64 state needs more registers)
@@ -324,13 +324,13 @@ struct WaveBlocks {
   static constexpr int value = sizeof(R) == 4 ? MCV_WAVE_BLOCKS_F32 : MCV_WAVE_BLOCKS_F64;
 };
 
-template <typename R, int NS, int DET>
+template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     wave_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
   Forward<R, DET> pol;
-  run_waves<R, NS, DET>(A, tu, pol);
+  run_waves<R, NS, DET, KS>(A, tu, pol);
 }
 
 // the fused forward runs as waves (dynamic shared memory for the warp queues) unless it
@@ -516,39 +516,45 @@ struct Adjoint {
   }
 };
 
-template <typename R, int NS, int DET>
+template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kThreads) adjoint_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
   Adjoint<R, DET> pol;
-  run_chain<R, NS, DET, Adjoint<R, DET>>(A, tu, pol);
+  run_chain<R, NS, DET, KS, Adjoint<R, DET>>(A, tu, pol);
 }
 
 // ---- launchers, one set per real type -----------------------------------------------------
-template <typename R, int NS, int DET>
+template <typename R, int NS, int DET, int KS>
 cudaError_t launch_trace_k(const TraceArgs& A, int grid, cudaStream_t s) {
   if (DET != MCV_DET_NONE && uses_waves(A, DET)) {
     const size_t smem = wave_smem_bytes<R>();
-    cudaError_t e = cudaFuncSetAttribute(wave_kernel<R, NS, DET>,
+    cudaError_t e = cudaFuncSetAttribute(wave_kernel<R, NS, DET, KS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    wave_kernel<R, NS, DET><<<grid, kThreads, smem, s>>>(A);
+    wave_kernel<R, NS, DET, KS><<<grid, kThreads, smem, s>>>(A);
   } else {
-    trace_kernel<R, NS, DET><<<grid, kThreads, 0, s>>>(A);
+    trace_kernel<R, NS, DET, KS><<<grid, kThreads, 0, s>>>(A);
   }
   return cudaGetLastError();
 }
 
-template <typename R, int NS>
-cudaError_t launch_trace_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+template <typename R, int NS, int KS>
+cudaError_t launch_trace_nk(const TraceArgs& A, int det, int grid, cudaStream_t s) {
   switch (det) {
     case MCV_DET_SURFACE:
-      return launch_trace_k<R, NS, MCV_DET_SURFACE>(A, grid, s);
+      return launch_trace_k<R, NS, MCV_DET_SURFACE, KS>(A, grid, s);
     case MCV_DET_TUBES:
-      return launch_trace_k<R, NS, MCV_DET_TUBES>(A, grid, s);
+      return launch_trace_k<R, NS, MCV_DET_TUBES, KS>(A, grid, s);
     default:
-      return launch_trace_k<R, NS, MCV_DET_NONE>(A, grid, s);
+      return launch_trace_k<R, NS, MCV_DET_NONE, KS>(A, grid, s);
   }
+}
+
+template <typename R, int NS>
+cudaError_t launch_trace_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  if (A.Sd.has_bvk) return launch_trace_nk<R, NS, kKernelsAll>(A, det, grid, s);
+  return launch_trace_nk<R, NS, kKernelsPowder>(A, det, grid, s);
 }
 
 template <typename R>
@@ -559,17 +565,22 @@ cudaError_t launch_trace_t(const TraceArgs& A, int det, int grid, cudaStream_t s
 }
 
 // the kernel the fused forward of this shape launches (waves when a detector is fused)
+template <typename R, int NS, int KS>
+const void* trace_fn_nk(int det) {
+  if (det == MCV_DET_SURFACE) return (const void*)wave_kernel<R, NS, MCV_DET_SURFACE, KS>;
+  if (det == MCV_DET_TUBES) return (const void*)wave_kernel<R, NS, MCV_DET_TUBES, KS>;
+  return (const void*)trace_kernel<R, NS, MCV_DET_NONE, KS>;
+}
+
 template <typename R, int NS>
-const void* trace_fn_ns(int det) {
-  if (det == MCV_DET_SURFACE) return (const void*)wave_kernel<R, NS, MCV_DET_SURFACE>;
-  if (det == MCV_DET_TUBES) return (const void*)wave_kernel<R, NS, MCV_DET_TUBES>;
-  return (const void*)trace_kernel<R, NS, MCV_DET_NONE>;
+const void* trace_fn_ns(int det, bool bvk) {
+  return bvk ? trace_fn_nk<R, NS, kKernelsAll>(det) : trace_fn_nk<R, NS, kKernelsPowder>(det);
 }
 
 template <typename R>
-cudaError_t blocks_per_sm_t(int ns, int det, int* blocks) {
-  const void* fn = ns <= 1 ? trace_fn_ns<R, 1>(det) : (ns == 2 ? trace_fn_ns<R, 2>(det)
-                                                              : trace_fn_ns<R, 4>(det));
+cudaError_t blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
+  const void* fn = ns <= 1 ? trace_fn_ns<R, 1>(det, bvk) : (ns == 2 ? trace_fn_ns<R, 2>(det, bvk)
+                                                                    : trace_fn_ns<R, 4>(det, bvk));
   const size_t smem = det != MCV_DET_NONE ? wave_smem_bytes<R>() : 0;
   if (smem) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -594,13 +605,19 @@ cudaError_t launch_detect_t(const TraceArgs& A, const EventsArgs& E, int det, in
   return cudaGetLastError();
 }
 
+template <typename R, int NS, int KS>
+cudaError_t launch_adjoint_nk(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  if (det == MCV_DET_SURFACE)
+    adjoint_kernel<R, NS, MCV_DET_SURFACE, KS><<<grid, kThreads, 0, s>>>(A);
+  else
+    adjoint_kernel<R, NS, MCV_DET_TUBES, KS><<<grid, kThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename R, int NS>
 cudaError_t launch_adjoint_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
-  if (det == MCV_DET_SURFACE)
-    adjoint_kernel<R, NS, MCV_DET_SURFACE><<<grid, kThreads, 0, s>>>(A);
-  else
-    adjoint_kernel<R, NS, MCV_DET_TUBES><<<grid, kThreads, 0, s>>>(A);
-  return cudaGetLastError();
+  if (A.Sd.has_bvk) return launch_adjoint_nk<R, NS, kKernelsAll>(A, det, grid, s);
+  return launch_adjoint_nk<R, NS, kKernelsPowder>(A, det, grid, s);
 }
 
 template <typename R>
@@ -615,8 +632,8 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   cudaError_t launch_trace_##SUFFIX(const TraceArgs& A, int det, int grid, cudaStream_t s) { \
     return launch_trace_t<R>(A, det, grid, s);                                              \
   }                                                                                         \
-  cudaError_t blocks_per_sm_##SUFFIX(int ns, int det, int* blocks) {                        \
-    return blocks_per_sm_t<R>(ns, det, blocks);                                             \
+  cudaError_t blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int* blocks) {               \
+    return blocks_per_sm_t<R>(ns, det, bvk, blocks);                                        \
   }                                                                                         \
   cudaError_t launch_beam_##SUFFIX(const TraceArgs& A, int grid, cudaStream_t s) {          \
     return launch_beam_t<R>(A, grid, s);                                                    \

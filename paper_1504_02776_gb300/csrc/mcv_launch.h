@@ -15,7 +15,7 @@ struct EventsArgs {
 };
 
 int trace_threads();
-cudaError_t trace_blocks_per_sm(int fp_mode, int ns, int det, int* blocks);
+cudaError_t trace_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks);
 cudaError_t launch_trace(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
 cudaError_t launch_beam(const TraceArgs& A, int fp_mode, int grid, cudaStream_t s);
 cudaError_t launch_detect(const TraceArgs& A, const EventsArgs& E, int fp_mode, int det, int grid,

@@ -9,8 +9,8 @@ namespace mcv {
 
 cudaError_t launch_trace_f32(const TraceArgs& A, int det, int grid, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceArgs& A, int det, int grid, cudaStream_t s);
-cudaError_t blocks_per_sm_f32(int ns, int det, int* blocks);
-cudaError_t blocks_per_sm_f64(int ns, int det, int* blocks);
+cudaError_t blocks_per_sm_f32(int ns, int det, int bvk, int* blocks);
+cudaError_t blocks_per_sm_f64(int ns, int det, int bvk, int* blocks);
 cudaError_t launch_beam_f32(const TraceArgs& A, int grid, cudaStream_t s);
 cudaError_t launch_beam_f64(const TraceArgs& A, int grid, cudaStream_t s);
 cudaError_t launch_detect_f32(const TraceArgs& A, const EventsArgs& E, int det, int grid,
@@ -67,8 +67,9 @@ __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hi
 
 int trace_threads() { return 128; }
 
-cudaError_t trace_blocks_per_sm(int fp_mode, int ns, int det, int* blocks) {
-  return fp_mode == MCV_FP32 ? blocks_per_sm_f32(ns, det, blocks) : blocks_per_sm_f64(ns, det, blocks);
+cudaError_t trace_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks) {
+  return fp_mode == MCV_FP32 ? blocks_per_sm_f32(ns, det, bvk, blocks)
+                             : blocks_per_sm_f64(ns, det, bvk, blocks);
 }
 
 cudaError_t launch_trace(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s) {

@@ -52,6 +52,15 @@ struct SampleP {
   ScatP<R> s[MCV_MAX_SCATTERERS];
   const float* sqe;
   R q_max, e_min, e_max, dq, de;
+  // single-crystal Born-von Karman kernel
+  int has_bvk;
+  R bvk_coef;      // phi / M (1/s^2)
+  R bvk_ah;        // a / 2 (A)
+  R bvk_hb2m;      // hbar^2 / 2M (meV A^2)
+  R bvk_kT;        // k_B T (meV)
+  R bvk_msd;       // <u^2> (A^2)
+  R bvk_wmax;      // upper bound of hbar omega (meV)
+  R bvk_hbar;      // hbar in meV s
 };
 
 template <typename R>

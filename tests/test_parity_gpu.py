@@ -244,3 +244,36 @@ def test_fp32_fast_mode_within_bounds(ctx, make, n):
     # histogram: total detected weight agrees within the flips
     hc, ho = st["hist_gpu"], st["hist_orc"]
     assert abs(hc.sum() - ho.sum()) <= 1e-4 * ho.sum()
+
+
+# ---------------------------------------------------------------- single crystal (BvK)
+def _crystal(n, rot=30.0):
+    return mi.config3(rot_deg=rot, n=n)
+
+
+@pytest.mark.parametrize("rot", [0.0, 30.0, 137.0])
+def test_fp64_crystal_packets_match_oracle(ctx, rot):
+    wl = _crystal(2000, rot)
+    pk, g = H.packets(ctx, wl, B.FP64)
+    orc = oracle.trace(wl, packets=True)
+    op = orc["packets"]
+    dev, bad = H.check_fp64_packets(g, op)
+    assert not any(bad.values()), (bad, {f: float(d.max()) for f, d in dev.items()})
+    counts, tallies, ev = H.run_events(ctx, wl, pk)
+    m = op["order"] >= 1
+    assert np.array_equal(ev["bin"][m], op["bin"][m])
+    c2, _ = ctx.trace(wl, fp_mode=B.FP64)
+    hc, ho = c2.cpu().numpy(), orc["hist"]
+    tol = H.hist_tolerance(op[m], ho.size)
+    assert np.all(np.abs(hc - ho) <= tol + 1e-15 * np.abs(ho))
+
+
+def test_fp32_crystal_within_bounds(ctx):
+    wl = _crystal(20000, 45.0)
+    st = fp32_stats(ctx, wl)
+    assert st["structure_diff"] <= rate_bound(1e-3, wl.n), st["structure_diff"]
+    tol = np.maximum(1e-5, 1e-6 * st["kappa"])
+    for f in ("r", "v", "t", "w"):
+        d = st["dev"][f]
+        assert (d > tol).sum() <= rate_bound(1e-3, d.size), (f, float(np.quantile(d / tol, 0.999)))
+    assert st["flips"] <= rate_bound(1e-3, st["events"]), (st["flips"], st["events"])
