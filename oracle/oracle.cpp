@@ -682,7 +682,14 @@ bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const
   o->ki = ki;
   o->kf = kf;
   o->qvec = add(scale(d, ki), scale(df, -kf));
-  g_kappa += 1.0 / std::fabs(gp);
+  // the weight is sensitive to the Jacobian 1/|g'| and, near a degeneracy, to the
+  // eigenvector (relative gap of the eigenvalues)
+  // and to the polarisation factor (Q.e)^2 when Q is nearly perpendicular to e, and to
+  // the root itself where |g'| is small (d Ef = d g / |g'|)
+  const double gap = std::min(r.lam[1] - r.lam[0], r.lam[2] - r.lam[1]);
+  const double ag = std::fabs(gp);
+  g_kappa += 1.0 / ag + (gap > 0.0 ? r.lam[2] / gap : 1e16) +
+             (qe != 0.0 ? 2.0 * Q2 / (qe * qe) : 1e16) + (Ei + m.w_max) / (ag * Ef) / ag;
   return true;
 }
 

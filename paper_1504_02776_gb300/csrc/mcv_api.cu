@@ -148,7 +148,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     S->bvk_kT = kBoltzmann * b.temperature_K * mev_per_j;
     S->bvk_msd = b.msd_A2;
     S->bvk_wmax = mcv::kHbar * std::sqrt(24.0 * S->bvk_coef) * mev_per_j;
-    S->bvk_hbar = mcv::kHbar * mev_per_j;
+    S->bvk_hwu = mcv::kHbar * std::sqrt(S->bvk_coef) * mev_per_j;
   }
   return MCV_OK;
 }
@@ -279,7 +279,7 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
   f->bvk_kT = (float)d.bvk_kT;
   f->bvk_msd = (float)d.bvk_msd;
   f->bvk_wmax = (float)d.bvk_wmax;
-  f->bvk_hbar = (float)d.bvk_hbar;
+  f->bvk_hwu = (float)d.bvk_hwu;
 }
 
 void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
@@ -352,6 +352,7 @@ int grid_for(mcv_ctx* ctx, int64_t items, int per_sm) {
 const int64_t kMaxNeutrons = (int64_t)1 << 40;
 
 }  // namespace
+
 
 extern "C" {
 

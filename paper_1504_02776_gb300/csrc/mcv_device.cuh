@@ -531,10 +531,12 @@ __device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng
 // uniform over those bracketed on 32 sub-intervals and refined by bisection; weight
 // 6 n_roots (kf/ki) e^{-2W} R_b N_s / |g'|.  Dynamical matrix of the 12 nearest neighbours
 // (a/2)(+-1,+-1,0)..., eigenvalues by the trigonometric solution of the cubic.
+// The dynamical matrix is kept in units of phi/M (its entries are O(1); in s^-2 their
+// squares would overflow FP32): hbar omega = hbar sqrt(phi/M) sqrt(lambda').
 template <typename R>
 __device__ __forceinline__ void bvk_dynmat(const SampleP<R>& S, R qx, R qy, R qz, R D[6]) {
   // the six bond directions n (the other six are -n): (1,1,0) (1,-1,0) (1,0,1) (1,0,-1)
-  // (0,1,1) (0,1,-1); each pair adds 2 (phi/M)(1 - cos q.delta) n n^T / 2
+  // (0,1,1) (0,1,-1); each pair adds 2 (1 - cos q.delta) n n^T / 2
   const R nb[6][3] = {{1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
 #pragma unroll
   for (int i = 0; i < 6; ++i) D[i] = R(0);
@@ -542,7 +544,7 @@ __device__ __forceinline__ void bvk_dynmat(const SampleP<R>& S, R qx, R qy, R qz
   for (int k = 0; k < 6; ++k) {
     const R* n = nb[k];
     const R qd = S.bvk_ah * (qx * n[0] + qy * n[1] + qz * n[2]);
-    const R c = R(2) * S.bvk_coef * (R(1) - Mth<R>::cos_(qd)) * R(0.5);
+    const R c = R(2) * (R(1) - Mth<R>::cos_(qd)) * R(0.5);
     D[0] += c * n[0] * n[0];
     D[1] += c * n[1] * n[1];
     D[2] += c * n[2] * n[2];
@@ -644,7 +646,7 @@ __device__ __forceinline__ BvkPoint<R> bvk_point(const SampleP<R>& S, R c, R s, 
   R l[3];
   eig3_values<R>(P.D, l);
   P.lam = b == 0 ? l[0] : (b == 1 ? l[1] : l[2]);
-  P.hw = S.bvk_hbar * Mth<R>::sqrt(Mth<R>::fmax(P.lam, R(0)));
+  P.hw = S.bvk_hwu * Mth<R>::sqrt(Mth<R>::fmax(P.lam, R(0)));
   P.g = Ei - Ef - (R)sg * P.hw;
   return P;
 }
@@ -722,9 +724,9 @@ __device__ __forceinline__ bool kernel_bvk(const SampleP<R>& S, R crot, R srot,
     const R qd = S.bvk_ah * (P.qx * v[0] + P.qy * v[1] + P.qz * v[2]);
     const R ed = ex * v[0] + ey * v[1] + ez * v[2];
     const R dqd = S.bvk_ah * (dqx * v[0] + dqy * v[1] + dqz * v[2]);
-    dlam += R(2) * S.bvk_coef * M::sin_(qd) * dqd * ed * ed * R(0.5);
+    dlam += R(2) * M::sin_(qd) * dqd * ed * ed * R(0.5);
   }
-  const R dhw = S.bvk_hbar * dlam / (R(2) * M::sqrt(P.lam));
+  const R dhw = S.bvk_hwu * dlam / (R(2) * M::sqrt(P.lam));
   const R gp = R(-1) - (R)sg * dhw;
   const R nB = R(1) / M::expm1(P.hw / S.bvk_kT);
   const R Ns = sg > 0 ? nB + R(1) : nB;

@@ -60,7 +60,7 @@ struct SampleP {
   R bvk_kT;        // k_B T (meV)
   R bvk_msd;       // <u^2> (A^2)
   R bvk_wmax;      // upper bound of hbar omega (meV)
-  R bvk_hbar;      // hbar in meV s
+  R bvk_hwu;       // hbar sqrt(phi/M) in meV: hbar omega = bvk_hwu sqrt(lambda')
 };
 
 template <typename R>
