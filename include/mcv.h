@@ -234,6 +234,30 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
                     int grad_scatterer, mcv_hist* hist, double* g_work, double* loss,
                     double* dsqe, double* dsig, void* stream);
 
+/* ---- without allocation --------------------------------------------------------------- */
+/* The paper has no counterpart to this entry point.  It is mcv_grad for callers that cannot
+ * allocate device memory: code running inside CUDA graph capture or under someone else's
+ * memory pool, processes whose allocator is locked down, or runtimes that only hand out
+ * buffers they manage themselves.  It takes no context: the device error word and the
+ * per-bin work buffer g (dchi2/dI) that mcv_grad gets from its context and its caller live
+ * in one fixed device array inside the library, MCV_NOALLOC_MAX_BINS doubles (8 MiB) plus a
+ * header, which every GPU that loads the library holds until the process exits.
+ *   - Arguments and outputs are those of mcv_grad (no ctx, no g_work); histograms with more
+ *     than MCV_NOALLOC_MAX_BINS bins are rejected with MCV_EINVAL and a message.
+ *   - It runs on the current CUDA device.  The first call on a device looks up the array's
+ *     device address (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  No call allocates or frees memory.
+ *   - Every call shares the array: the error word is cleared at the start of each call and
+ *     the work buffer is overwritten, so consecutive calls on one stream are independent, but
+ *     calls that overlap on the GPU (other streams, other host threads) race on it.
+ *   - Errors: as mcv_grad; the message is returned by mcv_last_error(). */
+#define MCV_NOALLOC_MAX_BINS (1 << 20)
+mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* beam,
+                            const mcv_detector* det, uint32_t seed, uint32_t sim_id,
+                            int64_t first_id, int64_t n, const double* target, double scale_c,
+                            int grad_scatterer, mcv_hist* hist, double* loss, double* dsqe,
+                            double* dsig, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

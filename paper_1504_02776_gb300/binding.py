@@ -106,8 +106,10 @@ def _load():
     L.mcv_detect.argtypes = [P, P, C.c_int, P, C.c_uint32, C.c_uint32, P, P, P]
     L.mcv_grad.argtypes = [P, P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
                            C.c_double, C.c_int, P, P, P, P, P, P]
+    L.mcv_grad_noalloc.argtypes = [P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
+                                   C.c_double, C.c_int, P, P, P, P, P]
     for name in ("mcv_create", "mcv_destroy", "mcv_sync", "mcv_zero", "mcv_beam",
-                 "mcv_trace_sample", "mcv_detect", "mcv_grad"):
+                 "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_grad_noalloc"):
         getattr(L, name).restype = st
     return L
 
@@ -168,3 +170,12 @@ def mcv_grad(ctx, sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
     _check(lib.mcv_grad(ctx, C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
                         first_id, n, target, scale_c, grad_scatterer, C.byref(hist), g_work,
                         loss, dsqe, dsig, stream))
+
+
+def mcv_grad_noalloc(sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
+                     grad_scatterer, hist, loss, dsqe, dsig, stream=None):
+    """mcv_grad without a context and without a caller work buffer: for callers that cannot
+    allocate device memory (the library keeps the work buffer in a fixed device array)."""
+    _check(lib.mcv_grad_noalloc(C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
+                                first_id, n, target, scale_c, grad_scatterer, C.byref(hist),
+                                loss, dsqe, dsig, stream))

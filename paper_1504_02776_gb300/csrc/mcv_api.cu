@@ -353,6 +353,22 @@ const int64_t kMaxNeutrons = (int64_t)1 << 40;
 
 }  // namespace
 
+namespace mcv {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// the parameter blocks of a gradient call (sample, beam, detector), in both real types
+mcv_status build_trace_args_for_grad(const mcv_sample* sample, const mcv_beam_params* beam,
+                                     const mcv_detector* det, TraceArgs* A) {
+  mcv_status st = build_sample(sample, &A->Sd);
+  if (st != MCV_OK) return st;
+  st = build_beam(beam, &A->Bd);
+  if (st != MCV_OK) return st;
+  st = build_detector(det, &A->Dd);
+  if (st != MCV_OK) return st;
+  cast_all(A);
+  return MCV_OK;
+}
+}  // namespace mcv
 
 extern "C" {
 

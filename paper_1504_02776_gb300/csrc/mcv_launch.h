@@ -1,6 +1,8 @@
 // Host-side entry points of the kernels (mcv_trace.cu, mcv_grad.cu), used by the C ABI.
 #pragma once
 
+#include <string>
+
 #include <cuda_runtime.h>
 
 #include "mcv_params.h"
@@ -24,5 +26,7 @@ cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
                         double* g, double* loss, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
+// sets the message mcv_last_error() returns to the calling thread
+void set_last_error(const std::string& msg);
 
 }  // namespace mcv
