@@ -53,6 +53,9 @@ double u01_from(uint32_t hi, uint32_t lo) {
 // subtracts nearly equal numbers adds its amplification factor (|value| / |difference|).
 // It only sets the tolerances the tests compare rounding-sensitive results with.
 thread_local double g_kappa = 0.0;
+// relative-error budget of the current speed (units of the FP64 epsilon), carried from
+// kernel to kernel for the condition estimate
+thread_local double g_kappa_v = 0.0;
 
 // ---- geometry -------------------------------------------------------------------------
 // Interval of s in which the line r + s d lies inside the infinite cylinder x^2+z^2 < R^2
@@ -432,7 +435,8 @@ bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], 
   double q_hi = std::min(ki + kf, cfg.q_max);
   if (!(q_hi > q_lo)) return false;
   double dQ = q_hi - q_lo;
-  g_kappa += (ki + kf) / dQ;
+  g_kappa += (ki + kf) / dQ + 2.0 * g_kappa_v * (1.0 + (ki + kf) / dQ);
+  g_kappa_v = 1.0 + 0.5 * ((Ei + std::fabs(E) + std::fabs(e_lo)) / Ef + 2.0 * (Ei / Ef) * g_kappa_v);
   double Q = q_lo + u[1] * dQ;
   // scattering angle from Q^2 = ki^2 + kf^2 - 2 ki kf cos(2theta), written through
   // 1 - cos = (Q - q_lo)(Q + q_lo) / (2 ki kf) and 1 + cos = (ki + kf - Q)(ki + kf + Q) /
@@ -501,13 +505,15 @@ BvkModel bvk_model(const orc_config& cfg) {
 const double kBond[6][3] = {{1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
 
 // dynamical matrix D(q) = (phi/M) sum over the 12 neighbours of (1 - cos q.delta) dd^T,
-// delta = (a/2) n, d = n/sqrt(2); stored xx, yy, zz, xy, xz, yz (1/s^2)
+// delta = (a/2) n, d = n/sqrt(2); stored xx, yy, zz, xy, xz, yz (1/s^2).  1 - cos x is
+// evaluated as 2 sin^2(x/2), which keeps its relative accuracy near the zone centres.
 void bvk_dynmat(const BvkModel& m, const double q[3], double D[6]) {
   for (int i = 0; i < 6; ++i) D[i] = 0.0;
   for (int k = 0; k < 6; ++k) {
     const double* n = kBond[k];
-    double qd = 0.5 * m.a * (q[0] * n[0] + q[1] * n[1] + q[2] * n[2]);
-    double c = 2.0 * m.coef * (1.0 - std::cos(qd)) * 0.5;  // two neighbours, dd^T = nn^T/2
+    const double qd = 0.5 * m.a * (q[0] * n[0] + q[1] * n[1] + q[2] * n[2]);
+    const double sh = std::sin(0.5 * qd);
+    const double c = 2.0 * m.coef * (2.0 * sh * sh) * 0.5;  // two neighbours, dd^T = nn^T/2
     D[0] += c * n[0] * n[0];
     D[1] += c * n[1] * n[1];
     D[2] += c * n[2] * n[2];
@@ -517,51 +523,106 @@ void bvk_dynmat(const BvkModel& m, const double q[3], double D[6]) {
   }
 }
 
-// eigenvalues (ascending) of a symmetric 3x3 matrix, trigonometric form of Cardano's
-// solution; eigenvectors from the largest cross product of two rows of D - lambda I
+// D v for the packed symmetric matrix
+Vec3 sym_mul(const double D[6], Vec3 v) {
+  return {D[0] * v.x + D[3] * v.y + D[4] * v.z, D[3] * v.x + D[1] * v.y + D[5] * v.z,
+          D[4] * v.x + D[5] * v.y + D[2] * v.z};
+}
+
+// Eigenvalues (ascending) and unit eigenvectors of a symmetric 3x3 matrix.
+// The trigonometric form of Cardano's solution gives estimates; its accuracy degrades where
+// two eigenvalues nearly coincide (the cubic's discriminant is formed with cancellation), so
+// it is used only to tell which eigenvalue stands apart from the other two.  That one's
+// eigenvector is the largest cross product of two rows of D - lambda I and its eigenvalue
+// the Rayleigh quotient; the other two come from the 2x2 matrix D restricted to the plane
+// orthogonal to it, solved in closed form.  Eigenvalues are then accurate to a few ulps of
+// the largest, and eigenvectors to that over the distance to the nearest other eigenvalue.
 void eig_sym3(const double D[6], double lam[3], double vec[9]) {
   const double a00 = D[0], a11 = D[1], a22 = D[2], a01 = D[3], a02 = D[4], a12 = D[5];
   const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-  double l[3];
   if (p1 == 0.0) {
-    l[0] = a00;
-    l[1] = a11;
-    l[2] = a22;
-    std::sort(l, l + 3);
-  } else {
-    const double q = (a00 + a11 + a22) / 3.0;
-    const double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) +
-                      2.0 * p1;
-    const double p = std::sqrt(p2 / 6.0);
-    const double b00 = (a00 - q) / p, b11 = (a11 - q) / p, b22 = (a22 - q) / p;
-    const double b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
-    double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
-                      b02 * (b01 * b12 - b11 * b02));
-    r = std::min(1.0, std::max(-1.0, r));
-    const double phi = std::acos(r) / 3.0;
-    l[2] = q + 2.0 * p * std::cos(phi);
-    l[0] = q + 2.0 * p * std::cos(phi + 2.0 * kPi / 3.0);
-    l[1] = 3.0 * q - l[0] - l[2];
-  }
-  for (int b = 0; b < 3; ++b) {
-    lam[b] = l[b];
-    const Vec3 r0 = {a00 - l[b], a01, a02}, r1 = {a01, a11 - l[b], a12},
-               r2 = {a02, a12, a22 - l[b]};
-    Vec3 c[3] = {cross(r0, r1), cross(r0, r2), cross(r1, r2)};
-    int best = 0;
-    double nb = dot(c[0], c[0]);
-    for (int i = 1; i < 3; ++i) {
-      double ni = dot(c[i], c[i]);
-      if (ni > nb) {
-        nb = ni;
-        best = i;
-      }
+    int idx[3] = {0, 1, 2};
+    const double d[3] = {a00, a11, a22};
+    std::stable_sort(idx, idx + 3, [&](int i, int j) { return d[i] < d[j]; });
+    for (int b = 0; b < 3; ++b) {
+      lam[b] = d[idx[b]];
+      for (int i = 0; i < 3; ++i) vec[i * 3 + b] = (i == idx[b]) ? 1.0 : 0.0;
     }
-    Vec3 e = (nb > 0.0) ? scale(c[best], 1.0 / std::sqrt(nb))
-                        : (b == 0 ? Vec3{1, 0, 0} : (b == 1 ? Vec3{0, 1, 0} : Vec3{0, 0, 1}));
-    vec[0 * 3 + b] = e.x;
-    vec[1 * 3 + b] = e.y;
-    vec[2 * 3 + b] = e.z;
+    return;
+  }
+  // Cardano estimates
+  const double q = (a00 + a11 + a22) / 3.0;
+  const double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) +
+                    2.0 * p1;
+  const double p = std::sqrt(p2 / 6.0);
+  const double b00 = (a00 - q) / p, b11 = (a11 - q) / p, b22 = (a22 - q) / p;
+  const double b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
+  double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                    b02 * (b01 * b12 - b11 * b02));
+  r = std::min(1.0, std::max(-1.0, r));
+  const double phi = std::acos(r) / 3.0;
+  const double l2 = q + 2.0 * p * std::cos(phi);
+  const double l0 = q + 2.0 * p * std::cos(phi + 2.0 * kPi / 3.0);
+  const double l1 = 3.0 * q - l0 - l2;
+  // the eigenvalue farther from the other two
+  const double li = (l1 - l0 >= l2 - l1) ? l0 : l2;
+  const Vec3 r0 = {a00 - li, a01, a02}, r1 = {a01, a11 - li, a12}, r2 = {a02, a12, a22 - li};
+  const Vec3 c[3] = {cross(r0, r1), cross(r0, r2), cross(r1, r2)};
+  int best = 0;
+  double nb = dot(c[0], c[0]);
+  for (int i = 1; i < 3; ++i) {
+    const double ni = dot(c[i], c[i]);
+    if (ni > nb) {
+      nb = ni;
+      best = i;
+    }
+  }
+  const Vec3 e = nb > 0.0 ? scale(c[best], 1.0 / std::sqrt(nb)) : Vec3{1.0, 0.0, 0.0};
+  const double lam_e = dot(e, sym_mul(D, e));
+  // orthonormal basis (u, w) of the plane orthogonal to e: u = e x (the axis least along e)
+  const double ax = std::fabs(e.x), ay = std::fabs(e.y), az = std::fabs(e.z);
+  const Vec3 axis = (ax <= ay && ax <= az) ? Vec3{1, 0, 0} : (ay <= az ? Vec3{0, 1, 0} : Vec3{0, 0, 1});
+  Vec3 u = cross(e, axis);
+  u = scale(u, 1.0 / std::sqrt(dot(u, u)));
+  const Vec3 w = cross(e, u);
+  const Vec3 Du = sym_mul(D, u), Dw = sym_mul(D, w);
+  const double A = dot(u, Du), B = dot(u, Dw), C = dot(w, Dw);
+  const double mid = 0.5 * (A + C), h = 0.5 * (A - C);
+  const double rr = std::hypot(h, B);
+  const double mu_hi = mid + rr, mu_lo = mid - rr;
+  // eigenvector of mu_hi in the (u, w) plane: (rr + h, B) or (B, rr - h), the longer one
+  double cu, cw;
+  if (h >= 0.0) {
+    cu = rr + h;
+    cw = B;
+  } else {
+    cu = B;
+    cw = rr - h;
+  }
+  const double cn = std::hypot(cu, cw);
+  if (cn > 0.0) {
+    cu /= cn;
+    cw /= cn;
+  } else {
+    cu = 1.0;
+    cw = 0.0;
+  }
+  const Vec3 v_hi = add(scale(u, cu), scale(w, cw));
+  const Vec3 v_lo = add(scale(u, -cw), scale(w, cu));
+  // ascending order
+  double L[3] = {lam_e, mu_lo, mu_hi};
+  Vec3 V[3] = {e, v_lo, v_hi};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j + 1 < 3 - i; ++j)
+      if (L[j] > L[j + 1]) {
+        std::swap(L[j], L[j + 1]);
+        std::swap(V[j], V[j + 1]);
+      }
+  for (int b = 0; b < 3; ++b) {
+    lam[b] = L[b];
+    vec[0 * 3 + b] = V[b].x;
+    vec[1 * 3 + b] = V[b].y;
+    vec[2 * 3 + b] = V[b].z;
   }
 }
 
@@ -596,22 +657,36 @@ BvkEval bvk_g(const BvkModel& m, double Ei, double ki, Vec3 di, Vec3 df, double 
   return r;
 }
 
-bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const double u[4],
-                KernelOut* o) {
-  const BvkModel m = bvk_model(cfg);
-  const double c = std::cos(rot_y), sn = std::sin(rot_y);
+// The root of one event: outgoing direction and mode (b, s) from u, the roots of
+// g(Ef) = Ei - Ef - s hw_b(Q(Ef)) bracketed on 32 sub-intervals of the allowed Ef range, one
+// picked uniformly and refined by 50 bisections.
+struct BvkRoot {
+  bool ok = false;
+  int nroots = 0, mode = 0, b = 0, s = 1;
+  double Ei = 0.0, ki = 0.0, Ef = 0.0;
+  Vec3 df;
+};
+
+BvkRoot bvk_root(const BvkModel& m, double c, double sn, double speed, Vec3 d,
+                 const double u[4]) {
+  BvkRoot R;
   // outgoing direction, uniform
   const double ct = 2.0 * u[0] - 1.0;
   const double st = 2.0 * std::sqrt(u[0] * (1.0 - u[0]));
   const double ph = 2.0 * kPi * u[1];
-  const Vec3 df = {st * std::cos(ph), st * std::sin(ph), ct};
+  R.df = {st * std::cos(ph), st * std::sin(ph), ct};
   // mode: branch b, creation (s = +1) or annihilation (s = -1)
   int mode = (int)std::floor(6.0 * u[2]);
   mode = std::min(std::max(mode, 0), 5);
-  const int b = mode % 3;
-  const int s = mode < 3 ? 1 : -1;
+  R.mode = mode;
+  R.b = mode % 3;
+  R.s = mode < 3 ? 1 : -1;
+  const int b = R.b, s = R.s;
+  const Vec3 df = R.df;
   const double Ei = kMeVPerV2 * speed * speed;
   const double ki = kKPerV * speed;
+  R.Ei = Ei;
+  R.ki = ki;
   const double lo = s > 0 ? 0.0 : Ei;
   const double hi = s > 0 ? Ei : Ei + m.w_max;
   const int M = 32;
@@ -621,9 +696,8 @@ bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const
   int nroots = 0;
   for (int k = 0; k < M; ++k)
     if ((gk[k] > 0.0) != (gk[k + 1] > 0.0)) ++nroots;
-  o->nroots = nroots;
-  o->mode = mode;
-  if (nroots == 0) return false;
+  R.nroots = nroots;
+  if (nroots == 0) return R;
   int pick = (int)std::floor(u[3] * nroots);
   pick = std::min(std::max(pick, 0), nroots - 1);
   int kb = -1;
@@ -646,23 +720,44 @@ bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const
     else
       eb = mid;
   }
-  const double Ef = 0.5 * (ea + eb);
-  if (!(Ef > 0.0)) return false;
-  const BvkEval r = bvk_g(m, Ei, ki, d, df, Ef, b, s, c, sn);
-  if (!(r.hw >= 1e-3)) return false;
+  R.Ef = 0.5 * (ea + eb);
+  R.ok = R.Ef > 0.0;
+  return R;
+}
+
+// The weight factor of an event at final energy Ef (at the root: the kernel's factor)
+//   6 n_roots (kf/ki) e^{-2W} R_b N_s / |g'(Ef)|
+// with g' from the Hellmann-Feynman derivative of the eigenvalue along Q(Ef).
+struct BvkWeight {
+  double F = 0.0, kf = 0.0, gp = 0.0, dhw = 0.0, qe = 0.0, Q2 = 0.0, grad = 0.0;
+  BvkEval r;
+  Vec3 e;
+};
+
+BvkWeight bvk_weight(const BvkModel& m, double c, double sn, const BvkRoot& R, Vec3 d,
+                     double Ef) {
+  BvkWeight W;
+  const int b = R.b, s = R.s;
+  const BvkEval r = bvk_g(m, R.Ei, R.ki, d, R.df, Ef, b, s, c, sn);
+  W.r = r;
   const Vec3 e = {r.vec[0 * 3 + b], r.vec[1 * 3 + b], r.vec[2 * 3 + b]};
+  W.e = e;
   // d hw / d Ef through Q(Ef) (Hellmann-Feynman: d lambda = e^T dD e)
   const double kf = kKPerV * std::sqrt(Ef / kMeVPerV2);
   const double dkf = kf / (2.0 * Ef);
-  const Vec3 dQ = scale(to_crystal(df, c, sn), -dkf);  // dQc/dEf
+  const Vec3 dQ = scale(to_crystal(R.df, c, sn), -dkf);  // dQc/dEf
   double dlam = 0.0;
+  Vec3 grad = {0.0, 0.0, 0.0};  // d lambda / dQc
   for (int k = 0; k < 6; ++k) {
     const double* n = kBond[k];
     const double qd = 0.5 * m.a * (r.Qc.x * n[0] + r.Qc.y * n[1] + r.Qc.z * n[2]);
     const double ed = (e.x * n[0] + e.y * n[1] + e.z * n[2]);
     const double dqd = 0.5 * m.a * (dQ.x * n[0] + dQ.y * n[1] + dQ.z * n[2]);
     dlam += 2.0 * m.coef * std::sin(qd) * dqd * ed * ed * 0.5;
+    const double gk = 2.0 * m.coef * std::sin(qd) * 0.5 * m.a * ed * ed * 0.5;
+    grad = add(grad, Vec3{gk * n[0], gk * n[1], gk * n[2]});
   }
+  W.grad = std::sqrt(dot(grad, grad));
   const double dhw = kHbar * kMeVPerJ * dlam / (2.0 * std::sqrt(r.lam[b]));
   const double gp = -1.0 - s * dhw;
   const double nB = 1.0 / std::expm1(r.hw / m.kT);
@@ -671,25 +766,82 @@ bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const
   const double Q2 = dot(r.Qc, r.Qc);
   const double dw = std::exp(-Q2 * m.msd / 3.0);
   const double Rb = m.hb2m * qe * qe / r.hw;
-  o->rest = 6.0 * nroots * (kf / ki) * dw * Rb * Ns / std::fabs(gp);
+  W.F = 6.0 * R.nroots * (kf / R.ki) * dw * Rb * Ns / std::fabs(gp);
+  W.kf = kf;
+  W.gp = gp;
+  W.dhw = dhw;
+  W.qe = qe;
+  W.Q2 = Q2;
+  return W;
+}
+
+bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const double u[4],
+                KernelOut* o) {
+  const BvkModel m = bvk_model(cfg);
+  const double c = std::cos(rot_y), sn = std::sin(rot_y);
+  const BvkRoot R = bvk_root(m, c, sn, speed, d, u);
+  o->nroots = R.nroots;
+  o->mode = R.mode;
+  if (R.nroots == 0 || !R.ok) return false;
+  const double Ef = R.Ef;
+  const BvkWeight W = bvk_weight(m, c, sn, R, d, Ef);
+  if (!(W.r.hw >= 1e-3)) return false;
+  const double Ei = R.Ei, ki = R.ki, kf = W.kf;
+  o->rest = W.F;
   o->factor = o->rest;
   o->s_value = 1.0;
   o->entry = -1;
-  o->d = df;
+  o->d = R.df;
   o->speed = std::sqrt(Ef / kMeVPerV2);
-  o->q = std::sqrt(Q2);
+  o->q = std::sqrt(W.Q2);
   o->e = Ei - Ef;
   o->ki = ki;
   o->kf = kf;
-  o->qvec = add(scale(d, ki), scale(df, -kf));
-  // the weight is sensitive to the Jacobian 1/|g'| and, near a degeneracy, to the
-  // eigenvector (relative gap of the eigenvalues)
-  // and to the polarisation factor (Q.e)^2 when Q is nearly perpendicular to e, and to
-  // the root itself where |g'| is small (d Ef = d g / |g'|)
-  const double gap = std::min(r.lam[1] - r.lam[0], r.lam[2] - r.lam[1]);
-  const double ag = std::fabs(gp);
-  g_kappa += 1.0 / ag + (gap > 0.0 ? r.lam[2] / gap : 1e16) +
-             (qe != 0.0 ? 2.0 * Q2 / (qe * qe) : 1e16) + (Ei + m.w_max) / (ag * Ef) / ag;
+  o->qvec = add(scale(d, ki), scale(R.df, -kf));
+
+  // Condition estimate (units of the FP64 epsilon): how far rounding at the scale of the
+  // epsilon can move this factor.  Sources: the computed eigenvalue (relative error kl:
+  // a few ulps of the largest eigenvalue, plus Q's rounding through the dispersion
+  // gradient), g rounded near the root, the incoming speed's own error, and the eigenvector
+  // (error over the distance to the nearest other eigenvalue).  Their effect on the factor
+  // is measured by central differences: against a common scale of the eigenvalues (the force
+  // constant), against the incoming speed (both re-solving the root), and against Ef itself.
+  const double lam_b = W.r.lam[R.b];
+  const double lmax = W.r.lam[2];
+  const double gap = std::min(R.b > 0 ? lam_b - W.r.lam[R.b - 1] : 1e300,
+                              R.b < 2 ? W.r.lam[R.b + 1] - lam_b : 1e300);
+  const double kl = 4.0 * lmax / lam_b + W.grad * (ki + kf) / lam_b;
+  const double ag = std::fabs(W.gp);
+  const double qq = std::sqrt(W.Q2) / std::max(std::fabs(W.qe), 1e-300);
+  const double eig = gap > 0.0 ? lmax / gap : 1e16;
+  const double h = 1e-7;
+  auto factor_at = [&](const BvkModel& mm, double sp, double* ef) -> double {
+    const BvkRoot Rp = bvk_root(mm, c, sn, sp, d, u);
+    if (!Rp.ok || Rp.nroots != R.nroots) return -1.0;
+    *ef = Rp.Ef;
+    return bvk_weight(mm, c, sn, Rp, d, Rp.Ef).F;
+  };
+  auto dlog = [&](double fp, double fm, double ref) -> double {
+    if (!(fp > 0.0) || !(fm > 0.0)) return 1e16;
+    (void)ref;
+    return std::fabs(std::log(fp / fm)) / (2.0 * h);
+  };
+  BvkModel mp = m, mm = m;
+  mp.coef = m.coef * (1.0 + h);
+  mm.coef = m.coef * (1.0 - h);
+  double ef_cp = Ef, ef_cm = Ef, ef_vp = Ef, ef_vm = Ef;
+  const double s_c = dlog(factor_at(mp, speed, &ef_cp), factor_at(mm, speed, &ef_cm), W.F);
+  const double s_v = dlog(factor_at(m, speed * (1.0 + h), &ef_vp),
+                          factor_at(m, speed * (1.0 - h), &ef_vm), W.F);
+  const double s_ce = std::fabs(ef_cp - ef_cm) / (2.0 * h * Ef);
+  const double s_ve = std::fabs(ef_vp - ef_vm) / (2.0 * h * Ef);
+  const double s_e = dlog(bvk_weight(m, c, sn, R, d, Ef * (1.0 + h)).F,
+                          bvk_weight(m, c, sn, R, d, Ef * (1.0 - h)).F, W.F);
+  const double root = (Ei + Ef) / (ag * Ef);  // relative error of the root from g's rounding
+  const double kv_in = g_kappa_v;
+  g_kappa += 10.0 + 2.0 * qq * (1.0 + eig) + (1.0 + std::fabs(W.dhw) * (1.0 + eig)) / ag +
+             s_c * kl + s_v * kv_in + s_e * root;
+  g_kappa_v = 1.0 + 0.5 * (s_ce * kl + root + s_ve * kv_in);
   return true;
 }
 
@@ -746,6 +898,7 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
                Scat on_scatter, double* tallies) {
   Neutron n;
   g_kappa = 1.0;
+  g_kappa_v = 2.0;
   if (!make_beam(cfg, nid, &n)) return;
   for (int o = 0;; ++o) {
     if (n.w < cfg.min_prob) break;
@@ -1096,7 +1249,8 @@ int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const dou
                        const double u[4], double* speed_out, double d_out[3], double* factor,
                        orc_event* ev) {
   KernelOut ko;
-  if (!kernel_scatter(*cfg, ktype, speed, Vec3{d[0], d[1], d[2]}, u, &ko)) return 0;
+  const double rot = cfg->n_scat > 0 ? cfg->scat[0].rot_y : 0.0;
+  if (!kernel_scatter(*cfg, ktype, speed, Vec3{d[0], d[1], d[2]}, u, &ko, rot)) return 0;
   *speed_out = ko.speed;
   d_out[0] = ko.d.x;
   d_out[1] = ko.d.y;

@@ -111,7 +111,8 @@ int orc_shape_segments(const orc_scatterer* sc, const double r[3], const double 
                        double sa[2], double sb[2]);
 
 /* one kernel scatter: in = speed and unit direction; writes the new speed, direction,
-   weight factor; returns 0 if the kernel kills the packet. */
+   weight factor; returns 0 if the kernel kills the packet.  The single-crystal kernel takes
+   the orientation of scatterer 0. */
 int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const double d[3],
                        const double u[4], double* speed_out, double d_out[3],
                        double* factor, orc_event* ev);
