@@ -234,6 +234,61 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
                     int grad_scatterer, mcv_hist* hist, double* g_work, double* loss,
                     double* dsqe, double* dsig, void* stream);
 
+/* ---- batched launches ------------------------------------------------------------------- */
+/* The paper has no counterpart to these calls.  A batch is many independent simulations
+ * (sample orientations, incident energies, neutron counts of any mix) traced in ONE
+ * persistent launch of the fused path (source -> sample -> detector -> histogram): every
+ * warp takes work items, chunks of one simulation's neutron ids, from a device queue until
+ * it is empty, so uneven simulations keep every SM busy to the end.  Each neutron's history
+ * and arithmetic are those of mcv_trace_sample with the same simulation's arguments; only
+ * the order of the FP64 histogram additions differs.
+ *
+ * One simulation of a batch.  sample, beam: as mcv_trace_sample (sample->fp_mode must be
+ * the batch's fp_mode); ids first_id..first_id+n-1 of the stream (seed, sim_id);
+ * [tof_min_s, tof_max_s): this simulation's time window (n_tof bins of the batch detector;
+ * both 0 keeps the detector's own window); hist: its histogram (n_pixels*n_tof FP64, may be
+ * shared with other simulations) and/or tallies, accumulated into. */
+typedef struct {
+  const mcv_sample* sample;
+  const mcv_beam_params* beam;
+  uint32_t seed, sim_id;
+  int64_t first_id, n;
+  double tof_min_s, tof_max_s;
+  mcv_hist hist;
+} mcv_sim;
+
+typedef struct mcv_batch mcv_batch;
+
+/* Builds the parameter blocks of nsims >= 1 simulations sharing the detector `det` and
+ * uploads them to device memory owned by the batch (this call allocates and synchronises;
+ * the sims array and what it points to may be freed afterwards, the histograms may not).
+ * The launch shape (neutrons per work item, blocks per SM) is the one mcv_batch_tune last
+ * chose on this context for the same kind of batch, else a default.
+ * Errors: MCV_EINVAL for any invalid simulation (the message names it), MCV_ENOMEM. */
+mcv_status mcv_batch_create(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
+                            const mcv_detector* det, int fp_mode, mcv_batch** out);
+/* Runs the batch on `stream`: clears the queue counter and launches the persistent kernel.
+ * Allocates nothing and does not synchronise, so it can be captured in a CUDA graph and
+ * replayed; runs of one batch must not overlap on the GPU (they share the queue). */
+mcv_status mcv_batch_run(mcv_batch* b, void* stream);
+/* Autotuner: times the batch kernel on a proportional sample of about trial_neutrons
+ * neutrons (<= 0: 2e7) of this batch for each candidate launch shape (work-item sizes
+ * 1024..65536 neutrons, blocks per SM from the occupancy limit down), with histograms in
+ * scratch memory (the simulations' own histograms are not touched), keeps the fastest for
+ * this batch and records it on the context for later batches of the same kind (real type,
+ * number of scatterers, detector kind, kernel set).  Synchronises `stream`; allocates. */
+mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream);
+/* The batch's launch shape: neutrons per work item, blocks per SM, grid size, work items. */
+mcv_status mcv_batch_shape(const mcv_batch* b, int64_t* chunk, int* blocks_per_sm,
+                           int* grid, int64_t* n_items);
+/* Frees the batch after waiting for the device (cudaDeviceSynchronize); NULL is ignored. */
+mcv_status mcv_batch_destroy(mcv_batch* b);
+/* One-shot form: create, run and free in stream order (the parameter blocks live in
+ * memory from the stream-ordered allocator, freed on `stream` after the launch; no host
+ * synchronisation).  Not for graph capture: use mcv_batch_create + mcv_batch_run there. */
+mcv_status mcv_trace_batch(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
+                           const mcv_detector* det, int fp_mode, void* stream);
+
 /* ---- without allocation --------------------------------------------------------------- */
 /* The paper has no counterpart to this entry point.  It is mcv_grad for callers that cannot
  * allocate device memory: code running inside CUDA graph capture or under someone else's

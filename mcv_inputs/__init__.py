@@ -221,6 +221,49 @@ def can_scatterer() -> Scatterer:
                      sig_abs_b=0.23, kernels=[(K_ISO, 1.5)])
 
 
+def config3_batch(n=2_000_000, orientations=None, detector=None) -> List[Workload]:
+    """The single crystal at 181 orientations (0..180 degrees in 1 degree steps), one
+    simulation (random stream sim_id = the angle) and one histogram each."""
+    angles = range(181) if orientations is None else orientations
+    out = []
+    for a in angles:
+        w = config3(rot_deg=float(a), n=n)
+        if detector is not None:
+            w = w.replace(detector=detector)
+        out.append(w)
+    return out
+
+
+def tof_window_for(ei_mev: float, base=(2.9e-3, 5.4e-3), base_ei=100.0):
+    """Time window of an incident energy: the 100 meV window scaled with the incident flight
+    time (t proportional to 1/v), so every energy of a sweep sees its elastic line and the
+    same relative range of energy transfers."""
+    f = math.sqrt(base_ei / ei_mev)
+    return base[0] * f, base[1] * f
+
+
+def config5(count_scale=1.0, seed=7, n_sims=64, detector=None) -> List[Workload]:
+    """Uneven incident-energy sweep with a sample environment: 64 simulations, Ei
+    log-spaced over 10..500 meV, neutron counts log-uniform over [1e5, 1e8] (numpy PCG64,
+    `seed`), the powder S(Q,E) sample inside the aluminium can (two scatterers, up to 5
+    orders).  count_scale shrinks every count (at least 1 neutron) for small runs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    counts = np.exp(rng.uniform(math.log(1e5), math.log(1e8), n_sims))
+    eis = np.geomspace(10.0, 500.0, n_sims)
+    table = SqeGrid(sqe_table())
+    base = tube_detector() if detector is None else detector
+    out = []
+    for k in range(n_sims):
+        ei = float(eis[k])
+        t0, t1 = tof_window_for(ei)
+        det = dataclasses.replace(base, tof_min_s=t0, tof_max_s=t1)
+        n = max(1, int(round(float(counts[k]) * count_scale)))
+        out.append(Workload(name="ei-sweep-%d-%.1fmeV" % (k, ei), beam=powder_beam(ei=ei),
+                            scatterers=[powder_sample(), can_scatterer()], detector=det,
+                            n=n, max_orders=5, sqe=table, sim_id=k))
+    return out
+
+
 def poisson_target(hist: np.ndarray, scale_c: float, seed: int = 2) -> np.ndarray:
     """T_b ~ Poisson(c I_b), drawn with numpy's PCG64 (the seeded target of the fit)."""
     rng = np.random.Generator(np.random.PCG64(seed))

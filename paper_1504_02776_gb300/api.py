@@ -188,6 +188,100 @@ class Context:
         return counts, tallies, ev
 
 
+# ---- batched launches ------------------------------------------------------------------
+def _batch_detector(workloads):
+    """The shared detector geometry of a batch (time windows may differ per simulation)."""
+    import dataclasses
+    key = lambda d: {k: v for k, v in dataclasses.asdict(d).items()
+                     if k not in ("tof_min_s", "tof_max_s")}
+    d0 = workloads[0].detector
+    for wl in workloads[1:]:
+        if key(wl.detector) != key(d0):
+            raise ValueError("the simulations of a batch share one detector geometry")
+    return d0
+
+
+def _batch_sims(ctx, workloads, fp_mode, hists, first_ids, tables):
+    """mcv_sim entries for the workloads; returns (sims, structs kept alive, hists)."""
+    keep = []
+    sims = []
+    if hists is None:
+        hists = [ctx.new_hist(wl.detector) for wl in workloads]
+    for k, wl in enumerate(workloads):
+        table = None
+        if wl.sqe is not None:
+            key = id(wl.sqe.table)
+            if key not in tables:
+                tables[key] = ctx.table(wl)
+            table = tables[key]
+        sample = sample_struct(wl, fp_mode, table)
+        beam = beam_struct(wl.beam)
+        keep += [sample, beam]
+        counts, tallies = hists[k]
+        first = 0 if first_ids is None else first_ids[k]
+        sims.append(B.Sim(C.pointer(sample), C.pointer(beam), wl.seed, wl.sim_id, first, wl.n,
+                          wl.detector.tof_min_s, wl.detector.tof_max_s,
+                          B.Hist(_ptr(counts), _ptr(tallies))))
+    return sims, keep, hists
+
+
+class Batch:
+    """Simulations that share one detector geometry, traced by one persistent launch
+    (mcv_batch_create / mcv_batch_run).  Each workload brings its sample, beam, neutron
+    count, random stream (seed, sim_id) and time window (its detector's tof_min_s,
+    tof_max_s).  `hists`: one (counts, tallies) pair of device tensors per workload,
+    accumulated into; None allocates zeroed ones (self.hists)."""
+
+    def __init__(self, ctx, workloads, fp_mode=B.FP32, hists=None, first_ids=None):
+        self.ctx = ctx
+        self.workloads = list(workloads)
+        self.tables = {}
+        self.det = detector_struct(_batch_detector(self.workloads))
+        sims, self._keep, self.hists = _batch_sims(ctx, self.workloads, fp_mode, hists,
+                                                   first_ids, self.tables)
+        self.handle = B.mcv_batch_create(ctx.handle, sims, self.det, fp_mode)
+
+    def run(self, sync=False):
+        B.mcv_batch_run(self.handle, _stream())
+        if sync:
+            self.ctx.sync()
+
+    def tune(self, trial_neutrons=0):
+        B.mcv_batch_tune(self.handle, trial_neutrons, _stream())
+        return self.shape()
+
+    def shape(self):
+        return B.mcv_batch_shape(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            B.mcv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _trace_batch(self, workloads, fp_mode=B.FP32, hists=None, first_ids=None, sync=True):
+    """One-shot batched launch (mcv_trace_batch); returns the (counts, tallies) pairs."""
+    det = detector_struct(_batch_detector(workloads))
+    tables = {}
+    sims, keep, hists = _batch_sims(self, workloads, fp_mode, hists, first_ids, tables)
+    B.mcv_trace_batch(self.handle, sims, det, fp_mode, _stream())
+    if sync:
+        self.sync()
+    del keep
+    return hists
+
+
+Context.trace_batch = _trace_batch
+Context.batch = lambda self, workloads, fp_mode=B.FP32, hists=None, first_ids=None: Batch(
+    self, workloads, fp_mode, hists, first_ids)
+
+
 def _grad_call(c, wl, target, scale_c, fp_mode, n, first_id, table, sig_abs, sig_s,
                grad_scatterer, counts=None, g_work=None):
     """mcv_grad with the cross sections of `grad_scatterer` replaced by sig_abs, sig_s (the

@@ -87,6 +87,13 @@ class Events(C.Structure):
                 ("bin", C.c_void_p)]
 
 
+class Sim(C.Structure):
+    _fields_ = [("sample", C.POINTER(Sample)), ("beam", C.POINTER(BeamParams)),
+                ("seed", C.c_uint32), ("sim_id", C.c_uint32), ("first_id", C.c_int64),
+                ("n", C.c_int64), ("tof_min_s", C.c_double), ("tof_max_s", C.c_double),
+                ("hist", Hist)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libmcv.so is not built (run __graft_entry__.build() or "
@@ -108,8 +115,17 @@ def _load():
                            C.c_double, C.c_int, P, P, P, P, P, P]
     L.mcv_grad_noalloc.argtypes = [P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
                                    C.c_double, C.c_int, P, P, P, P, P]
+    L.mcv_batch_create.argtypes = [P, P, C.c_int, P, C.c_int, C.POINTER(C.c_void_p)]
+    L.mcv_batch_run.argtypes = [P, P]
+    L.mcv_batch_tune.argtypes = [P, C.c_int64, P]
+    L.mcv_batch_shape.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int64)]
+    L.mcv_batch_destroy.argtypes = [P]
+    L.mcv_trace_batch.argtypes = [P, P, C.c_int, P, C.c_int, P]
     for name in ("mcv_create", "mcv_destroy", "mcv_sync", "mcv_zero", "mcv_beam",
-                 "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_grad_noalloc"):
+                 "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_grad_noalloc",
+                 "mcv_batch_create", "mcv_batch_run", "mcv_batch_tune", "mcv_batch_shape",
+                 "mcv_batch_destroy", "mcv_trace_batch"):
         getattr(L, name).restype = st
     return L
 
@@ -179,3 +195,40 @@ def mcv_grad_noalloc(sample, beam, det, seed, sim_id, first_id, n, target, scale
     _check(lib.mcv_grad_noalloc(C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
                                 first_id, n, target, scale_c, grad_scatterer, C.byref(hist),
                                 loss, dsqe, dsig, stream))
+
+
+def _sims(sims):
+    arr = (Sim * len(sims))(*sims)
+    return arr
+
+
+def mcv_batch_create(ctx, sims, det, fp_mode):
+    """sims: a sequence of Sim (their sample and beam pointers must stay valid for the call)."""
+    h = C.c_void_p()
+    _check(lib.mcv_batch_create(ctx, _sims(sims), len(sims), C.byref(det), fp_mode, C.byref(h)))
+    return h
+
+
+def mcv_batch_run(batch, stream=None):
+    _check(lib.mcv_batch_run(batch, stream))
+
+
+def mcv_batch_tune(batch, trial_neutrons=0, stream=None):
+    _check(lib.mcv_batch_tune(batch, trial_neutrons, stream))
+
+
+def mcv_batch_shape(batch):
+    chunk, grid, items = C.c_int64(), C.c_int(), C.c_int64()
+    bps = C.c_int()
+    _check(lib.mcv_batch_shape(batch, C.byref(chunk), C.byref(bps), C.byref(grid),
+                               C.byref(items)))
+    return {"chunk": chunk.value, "blocks_per_sm": bps.value, "grid": grid.value,
+            "n_items": items.value}
+
+
+def mcv_batch_destroy(batch):
+    _check(lib.mcv_batch_destroy(batch))
+
+
+def mcv_trace_batch(ctx, sims, det, fp_mode, stream=None):
+    _check(lib.mcv_trace_batch(ctx, _sims(sims), len(sims), C.byref(det), fp_mode, stream))

@@ -1,5 +1,6 @@
 // C ABI of libmcv.so (declared in include/mcv.h): argument checking, derived constants,
-// launch shapes.  No call here allocates device memory except mcv_create.
+// launch shapes.  No call here allocates device memory except mcv_create.  The batched
+// launches are in mcv_batch.cu.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -7,17 +8,10 @@
 
 #include <cuda_runtime.h>
 
-#include "mcv_launch.h"
+#include "mcv_host.h"
 
-struct mcv_ctx {
-  int device;
-  int sm_count;
-  int* d_err;          // device error flag (kernels set it; mcv_sync reads and clears it)
-  unsigned long long* d_queue;  // work-queue counters of the batched launch
-  int occ[2][3][3][2]; // cached blocks per SM of the fused kernel: [fp][ns 1,2,4][det][bvk]
-};
-
-namespace {
+namespace mcv {
+namespace host {
 
 thread_local std::string g_last_error;
 
@@ -163,12 +157,7 @@ mcv_status build_detector(const mcv_detector* d, mcv::DetP<double>* D) {
   if (!(d->radius_m > 0) || !is_finite(d->radius_m)) return fail(MCV_EINVAL, "bad detector radius");
   D->kind = d->kind;
   D->radius = d->radius_m;
-  D->n_tof = d->n_tof;
-  D->tof_min = d->tof_min_s;
-  D->dt = (d->tof_max_s - d->tof_min_s) / d->n_tof;
-  D->inv_dt = (float)(1.0 / D->dt);
-  D->tmin_hi = (float)d->tof_min_s;
-  D->tmin_lo = (float)(d->tof_min_s - (double)D->tmin_hi);
+  D->win = tof_window(d->tof_min_s, d->tof_max_s, d->n_tof);
   int64_t npix = 0;
   if (d->kind == MCV_DET_SURFACE) {
     if (d->n_phi < 1 || d->n_y < 1 || !(d->height_m > 0) || !is_finite(d->height_m))
@@ -295,7 +284,6 @@ void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
   f->tubes_per_pack = d.tubes_per_pack;
   f->pixels_per_tube = d.pixels_per_tube;
   f->max_tubes_row = d.max_tubes_row;
-  f->n_tof = d.n_tof;
   f->n_bins = d.n_bins;
   f->radius = (float)d.radius;
   f->height = (float)d.height;
@@ -307,11 +295,7 @@ void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
   f->phi0 = (float)d.phi0;
   f->pix_len = (float)d.pix_len;
   f->mu_he_v = (float)d.mu_he_v;
-  f->tof_min = d.tof_min;
-  f->dt = d.dt;
-  f->tmin_hi = d.tmin_hi;
-  f->tmin_lo = d.tmin_lo;
-  f->inv_dt = d.inv_dt;
+  f->win = d.win;
   for (int i = 0; i < 2 * MCV_MAX_TUBES_PER_ROW; ++i) f->tube_u[i] = (float)d.tube_u[i];
 }
 
@@ -349,9 +333,21 @@ int grid_for(mcv_ctx* ctx, int64_t items, int per_sm) {
   return (int)(g < 1 ? 1 : g);
 }
 
-const int64_t kMaxNeutrons = (int64_t)1 << 40;
+TofWin tof_window(double tof_min_s, double tof_max_s, int n_tof) {
+  TofWin w;
+  w.n_tof = n_tof;
+  w.tof_min = tof_min_s;
+  w.dt = (tof_max_s - tof_min_s) / n_tof;
+  w.inv_dt = (float)(1.0 / w.dt);
+  w.tmin_hi = (float)tof_min_s;
+  w.tmin_lo = (float)(tof_min_s - (double)w.tmin_hi);
+  return w;
+}
 
-}  // namespace
+}  // namespace host
+}  // namespace mcv
+
+using namespace mcv::host;
 
 namespace mcv {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -403,6 +399,7 @@ mcv_status mcv_create(int device, mcv_ctx** out) {
     return cuda_fail(e, "cudaMemset");
   }
   std::memset(c->occ, 0, sizeof(c->occ));
+  std::memset(c->tuned, 0, sizeof(c->tuned));
   *out = c;
   return MCV_OK;
 }
@@ -433,7 +430,7 @@ mcv_status mcv_sync(mcv_ctx* ctx, void* stream) {
 int64_t mcv_detector_pixels(const mcv_detector* det) {
   mcv::DetP<double> D;
   if (build_detector(det, &D) != MCV_OK) return 0;
-  return D.n_bins / D.n_tof;
+  return D.n_bins / D.win.n_tof;
 }
 
 mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream) {

@@ -30,6 +30,7 @@ struct Mth<float> {
   static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
   static __device__ __forceinline__ float fmin(float a, float b) { return fminf(a, b); }
   static __device__ __forceinline__ float fmax(float a, float b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ float hypot(float a, float b) { return hypotf(a, b); }
   // sin and cos of 2 pi u
   static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) {
     sincospif(2.0f * u, s, c);
@@ -53,6 +54,7 @@ struct Mth<double> {
   static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
   static __device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
   static __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
+  static __device__ __forceinline__ double hypot(double a, double b) { return ::hypot(a, b); }
   // the FP64 mode evaluates sin and cos of (2 pi) u as written
   static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) {
     ::sincos(2.0 * kPi * u, s, c);
@@ -530,7 +532,8 @@ __device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng
 // Direction uniform, mode (b, s) uniform over six, root of g(Ef) = Ei - Ef - s hw_b(Q(Ef))
 // uniform over those bracketed on 32 sub-intervals and refined by bisection; weight
 // 6 n_roots (kf/ki) e^{-2W} R_b N_s / |g'|.  Dynamical matrix of the 12 nearest neighbours
-// (a/2)(+-1,+-1,0)..., eigenvalues by the trigonometric solution of the cubic.
+// (a/2)(+-1,+-1,0)... with 1 - cos x evaluated as 2 sin^2(x/2) (accurate near the zone
+// centres); eigenpairs as described at eig3_branch.
 // The dynamical matrix is kept in units of phi/M (its entries are O(1); in s^-2 their
 // squares would overflow FP32): hbar omega = hbar sqrt(phi/M) sqrt(lambda').
 template <typename R>
@@ -544,7 +547,8 @@ __device__ __forceinline__ void bvk_dynmat(const SampleP<R>& S, R qx, R qy, R qz
   for (int k = 0; k < 6; ++k) {
     const R* n = nb[k];
     const R qd = S.bvk_ah * (qx * n[0] + qy * n[1] + qz * n[2]);
-    const R c = R(2) * (R(1) - Mth<R>::cos_(qd)) * R(0.5);
+    const R sh = Mth<R>::sin_(R(0.5) * qd);
+    const R c = R(2) * (R(2) * sh * sh) * R(0.5);
     D[0] += c * n[0] * n[0];
     D[1] += c * n[1] * n[1];
     D[2] += c * n[2] * n[2];
@@ -554,22 +558,34 @@ __device__ __forceinline__ void bvk_dynmat(const SampleP<R>& S, R qx, R qy, R qz
   }
 }
 
-// eigenvalues of the symmetric 3x3 matrix (xx yy zz xy xz yz), ascending
+// Eigenpair of branch b (0, 1, 2 in ascending order of the eigenvalue) of the symmetric 3x3
+// matrix D (xx yy zz xy xz yz).  Cardano's trigonometric solution of the characteristic
+// cubic only estimates the eigenvalues -- its accuracy degrades where two of them nearly
+// coincide -- and tells which eigenvalue stands apart from the other two.  That one's
+// eigenvector is the largest cross product of two rows of D - lambda I and its eigenvalue
+// the Rayleigh quotient; the other two are the eigenpairs of D restricted to the plane
+// orthogonal to it (a 2x2 problem in closed form).  Eigenvalues come out accurate to a few
+// ulps of the largest, eigenvectors to that over the distance to the nearest other one.
 template <typename R>
-__device__ __forceinline__ void eig3_values(const R D[6], R l[3]) {
+__device__ __forceinline__ void eig3_branch(const R D[6], int b, R* lam, R* ex, R* ey, R* ez) {
   using M = Mth<R>;
   const R a00 = D[0], a11 = D[1], a22 = D[2], a01 = D[3], a02 = D[4], a12 = D[5];
   const R p1 = a01 * a01 + a02 * a02 + a12 * a12;
   if (p1 == R(0)) {
-    R x = a00, y = a11, z = a22, t;
-    if (x > y) { t = x; x = y; y = t; }
-    if (y > z) { t = y; y = z; z = t; }
-    if (x > y) { t = x; x = y; y = t; }
-    l[0] = x;
-    l[1] = y;
-    l[2] = z;
+    // diagonal: a stable sort of the three entries
+    R v0 = a00, v1 = a11, v2 = a22, t;
+    int i0 = 0, i1 = 1, i2 = 2, ti;
+    if (v0 > v1) { t = v0; v0 = v1; v1 = t; ti = i0; i0 = i1; i1 = ti; }
+    if (v1 > v2) { t = v1; v1 = v2; v2 = t; ti = i1; i1 = i2; i2 = ti; }
+    if (v0 > v1) { t = v0; v0 = v1; v1 = t; ti = i0; i0 = i1; i1 = ti; }
+    const int ib = b == 0 ? i0 : (b == 1 ? i1 : i2);
+    *lam = b == 0 ? v0 : (b == 1 ? v1 : v2);
+    *ex = ib == 0 ? R(1) : R(0);
+    *ey = ib == 1 ? R(1) : R(0);
+    *ez = ib == 2 ? R(1) : R(0);
     return;
   }
+  // Cardano estimates
   const R q = (a00 + a11 + a22) / R(3);
   const R p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + R(2) * p1;
   const R p = M::sqrt(p2 / R(6));
@@ -579,42 +595,114 @@ __device__ __forceinline__ void eig3_values(const R D[6], R l[3]) {
                   b02 * (b01 * b12 - b11 * b02));
   r = M::fmin(R(1), M::fmax(R(-1), r));
   const R phi = M::acos_(r) / R(3);
-  l[2] = q + R(2) * p * M::cos_(phi);
-  l[0] = q + R(2) * p * M::cos_(phi + R(2) * (R)kPi / R(3));
-  l[1] = R(3) * q - l[0] - l[2];
-}
-
-// unit eigenvector of eigenvalue lam: the largest cross product of two rows of D - lam I
-template <typename R>
-__device__ __forceinline__ void eig3_vector(const R D[6], R lam, R* ex, R* ey, R* ez) {
-  const R r0x = D[0] - lam, r0y = D[3], r0z = D[4];
-  const R r1x = D[3], r1y = D[1] - lam, r1z = D[5];
-  const R r2x = D[4], r2y = D[5], r2z = D[2] - lam;
+  const R l2 = q + R(2) * p * M::cos_(phi);
+  const R l0 = q + R(2) * p * M::cos_(phi + R(2) * (R)kPi / R(3));
+  const R l1 = R(3) * q - l0 - l2;
+  // the isolated eigenvalue's eigenvector: largest cross product of two rows of D - li I
+  const R li = (l1 - l0 >= l2 - l1) ? l0 : l2;
+  const R r0x = a00 - li, r0y = a01, r0z = a02;
+  const R r1x = a01, r1y = a11 - li, r1z = a12;
+  const R r2x = a02, r2y = a12, r2z = a22 - li;
   R cx[3], cy[3], cz[3];
   cx[0] = r0y * r1z - r0z * r1y; cy[0] = r0z * r1x - r0x * r1z; cz[0] = r0x * r1y - r0y * r1x;
   cx[1] = r0y * r2z - r0z * r2y; cy[1] = r0z * r2x - r0x * r2z; cz[1] = r0x * r2y - r0y * r2x;
   cx[2] = r1y * r2z - r1z * r2y; cy[2] = r1z * r2x - r1x * r2z; cz[2] = r1x * r2y - r1y * r2x;
-  R bx = cx[0], by = cy[0], bz = cz[0];
-  R nb = bx * bx + by * by + bz * bz;
+  R gx = cx[0], gy = cy[0], gz = cz[0];
+  R nb = gx * gx + gy * gy + gz * gz;
 #pragma unroll
   for (int i = 1; i < 3; ++i) {
     const R ni = cx[i] * cx[i] + cy[i] * cy[i] + cz[i] * cz[i];
     if (ni > nb) {
       nb = ni;
-      bx = cx[i];
-      by = cy[i];
-      bz = cz[i];
+      gx = cx[i];
+      gy = cy[i];
+      gz = cz[i];
     }
   }
   if (nb > R(0)) {
-    const R inv = R(1) / Mth<R>::sqrt(nb);
-    *ex = bx * inv;
-    *ey = by * inv;
-    *ez = bz * inv;
+    const R inv = R(1) / M::sqrt(nb);
+    gx = gx * inv;
+    gy = gy * inv;
+    gz = gz * inv;
   } else {
-    *ex = R(1);
-    *ey = R(0);
-    *ez = R(0);
+    gx = R(1);
+    gy = R(0);
+    gz = R(0);
+  }
+  const R dgx = a00 * gx + a01 * gy + a02 * gz;
+  const R dgy = a01 * gx + a11 * gy + a12 * gz;
+  const R dgz = a02 * gx + a12 * gy + a22 * gz;
+  const R lam_e = gx * dgx + gy * dgy + gz * dgz;
+  // orthonormal basis (u, w) of the plane orthogonal to it: u = e x (axis least along e)
+  const R ax = M::fabs(gx), ay = M::fabs(gy), az = M::fabs(gz);
+  const int axis = (ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2);
+  R ux, uy, uz;
+  if (axis == 0) {
+    ux = R(0);
+    uy = gz;
+    uz = -gy;
+  } else if (axis == 1) {
+    ux = -gz;
+    uy = R(0);
+    uz = gx;
+  } else {
+    ux = gy;
+    uy = -gx;
+    uz = R(0);
+  }
+  const R un = R(1) / M::sqrt(ux * ux + uy * uy + uz * uz);
+  ux = ux * un;
+  uy = uy * un;
+  uz = uz * un;
+  const R wx = gy * uz - gz * uy, wy = gz * ux - gx * uz, wz = gx * uy - gy * ux;
+  const R dux = a00 * ux + a01 * uy + a02 * uz;
+  const R duy = a01 * ux + a11 * uy + a12 * uz;
+  const R duz = a02 * ux + a12 * uy + a22 * uz;
+  const R dwx = a00 * wx + a01 * wy + a02 * wz;
+  const R dwy = a01 * wx + a11 * wy + a12 * wz;
+  const R dwz = a02 * wx + a12 * wy + a22 * wz;
+  const R A = ux * dux + uy * duy + uz * duz;
+  const R B = ux * dwx + uy * dwy + uz * dwz;
+  const R C = wx * dwx + wy * dwy + wz * dwz;
+  const R mid = R(0.5) * (A + C), h = R(0.5) * (A - C);
+  const R rr = M::hypot(h, B);
+  const R mu_hi = mid + rr, mu_lo = mid - rr;
+  // position of lam_e among the three (ties keep it first)
+  const int pos_e = !(lam_e > mu_lo) ? 0 : (!(lam_e > mu_hi) ? 1 : 2);
+  if (b == pos_e) {
+    *lam = lam_e;
+    *ex = gx;
+    *ey = gy;
+    *ez = gz;
+    return;
+  }
+  const bool want_hi = b > pos_e ? (b == 2) : (b == 1);
+  *lam = want_hi ? mu_hi : mu_lo;
+  // eigenvector of mu_hi in the (u, w) plane: (rr + h, B) or (B, rr - h), the longer one
+  R cu, cw;
+  if (h >= R(0)) {
+    cu = rr + h;
+    cw = B;
+  } else {
+    cu = B;
+    cw = rr - h;
+  }
+  const R cn = M::hypot(cu, cw);
+  if (cn > R(0)) {
+    cu = cu / cn;
+    cw = cw / cn;
+  } else {
+    cu = R(1);
+    cw = R(0);
+  }
+  if (want_hi) {
+    *ex = ux * cu + wx * cw;
+    *ey = uy * cu + wy * cw;
+    *ez = uz * cu + wz * cw;
+  } else {
+    *ex = ux * -cw + wx * cu;
+    *ey = uy * -cw + wy * cu;
+    *ez = uz * -cw + wz * cu;
   }
 }
 
@@ -630,8 +718,7 @@ __device__ __forceinline__ void to_crystal(R c, R s, R vx, R vy, R vz, R* ox, R*
 template <typename R>
 struct BvkPoint {
   R g, hw, qx, qy, qz;
-  R D[6];
-  R lam;
+  R lam, ex, ey, ez;  // eigenvalue and unit eigenvector of the branch
 };
 
 template <typename R>
@@ -642,10 +729,9 @@ __device__ __forceinline__ BvkPoint<R> bvk_point(const SampleP<R>& S, R c, R s, 
   const R kf = (R)kKPerV * Mth<R>::sqrt(Ef / (R)kMeVPerV2);
   const R Qx = dix * ki - dfx * kf, Qy = diy * ki - dfy * kf, Qz = diz * ki - dfz * kf;
   to_crystal<R>(c, s, Qx, Qy, Qz, &P.qx, &P.qy, &P.qz);
-  bvk_dynmat<R>(S, P.qx, P.qy, P.qz, P.D);
-  R l[3];
-  eig3_values<R>(P.D, l);
-  P.lam = b == 0 ? l[0] : (b == 1 ? l[1] : l[2]);
+  R D[6];
+  bvk_dynmat<R>(S, P.qx, P.qy, P.qz, D);
+  eig3_branch<R>(D, b, &P.lam, &P.ex, &P.ey, &P.ez);
   P.hw = S.bvk_hwu * Mth<R>::sqrt(Mth<R>::fmax(P.lam, R(0)));
   P.g = Ei - Ef - (R)sg * P.hw;
   return P;
@@ -706,8 +792,7 @@ __device__ __forceinline__ bool kernel_bvk(const SampleP<R>& S, R crot, R srot,
   const BvkPoint<R> P = bvk_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy, dfz,
                                      Ef, b, sg);
   if (!(P.hw >= R(1e-3))) return false;
-  R ex, ey, ez;
-  eig3_vector<R>(P.D, P.lam, &ex, &ey, &ez);
+  const R ex = P.ex, ey = P.ey, ez = P.ez;
   // d hw / d Ef through Q(Ef) (Hellmann-Feynman: d lambda = e^T dD e)
   const R kf = (R)kKPerV * M::sqrt(Ef / (R)kMeVPerV2);
   const R dkf = kf / (R(2) * Ef);
@@ -790,23 +875,24 @@ __device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>&
 // tof bin: FP64 mode as written; FP32 mode takes the offset from tof_min from the float
 // pair exactly (the two differences are exact or nearly so) and scales it in float
 template <typename R>
-__device__ __forceinline__ int64_t tof_bin(const DetP<R>& D, const Tof<R>& tof);
+__device__ __forceinline__ int64_t tof_bin(const TofWin& W, const Tof<R>& tof);
 template <>
-__device__ __forceinline__ int64_t tof_bin<double>(const DetP<double>& D, const Tof<double>& tof) {
-  const double fb = ::floor((tof.v - D.tof_min) / D.dt);
-  if (!(fb >= 0.0 && fb < (double)D.n_tof)) return -1;
+__device__ __forceinline__ int64_t tof_bin<double>(const TofWin& W, const Tof<double>& tof) {
+  const double fb = ::floor((tof.v - W.tof_min) / W.dt);
+  if (!(fb >= 0.0 && fb < (double)W.n_tof)) return -1;
   return (int64_t)fb;
 }
 template <>
-__device__ __forceinline__ int64_t tof_bin<float>(const DetP<float>& D, const Tof<float>& tof) {
-  const float off = (tof.hi - D.tmin_hi) + (tof.lo - D.tmin_lo);
-  const float fb = floorf(off * D.inv_dt);
-  if (!(fb >= 0.0f && fb < (float)D.n_tof)) return -1;
+__device__ __forceinline__ int64_t tof_bin<float>(const TofWin& W, const Tof<float>& tof) {
+  const float off = (tof.hi - W.tmin_hi) + (tof.lo - W.tmin_lo);
+  const float fb = floorf(off * W.inv_dt);
+  if (!(fb >= 0.0f && fb < (float)W.n_tof)) return -1;
   return (int64_t)fb;
 }
 
 template <typename R>
-__device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const Ray<R>& n) {
+__device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const TofWin& W,
+                                                 const Ray<R>& n) {
   using M = Mth<R>;
   Hit<R> h;
   h.bin = -1;
@@ -829,15 +915,16 @@ __device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const Ray<R>&
   h.tof.add(s / n.speed);
   h.w_det = n.w;
   h.pabs = R(1);
-  const int64_t tb = tof_bin<R>(D, h.tof);
-  h.bin = (tb < 0) ? -2 : (int64_t)h.pixel * D.n_tof + tb;
+  const int64_t tb = tof_bin<R>(W, h.tof);
+  h.bin = (tb < 0) ? -2 : (int64_t)h.pixel * W.n_tof + tb;
   return h;
 }
 
 // tube centre directions staged in shared memory: tu[2*i] = sin(phi_i), tu[2*i+1] = cos(phi_i)
 template <typename R>
-__device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const R* __restrict__ tu,
-                                               const Ray<R>& n, R u_det) {
+__device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const TofWin& W,
+                                               const R* __restrict__ tu, const Ray<R>& n,
+                                               R u_det) {
   using M = Mth<R>;
   Hit<R> h;
   h.bin = -1;
@@ -910,17 +997,17 @@ __device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const R* __rest
   h.tof.add(s_abs / n.speed);
   h.pabs = pabs;
   h.w_det = n.w * pabs;
-  const int64_t tb = tof_bin<R>(D, h.tof);
-  h.bin = (tb < 0) ? -2 : (int64_t)h.pixel * D.n_tof + tb;
+  const int64_t tb = tof_bin<R>(W, h.tof);
+  h.bin = (tb < 0) ? -2 : (int64_t)h.pixel * W.n_tof + tb;
   return h;
 }
 
 template <typename R, int DET>
-__device__ __forceinline__ Hit<R> detect(const DetP<R>& D, const R* tu, const NeutronRng& rng,
-                                         int order, const Ray<R>& n) {
-  if (DET == MCV_DET_SURFACE) return detect_surface<R>(D, n);
+__device__ __forceinline__ Hit<R> detect(const DetP<R>& D, const TofWin& W, const R* tu,
+                                         const NeutronRng& rng, int order, const Ray<R>& n) {
+  if (DET == MCV_DET_SURFACE) return detect_surface<R>(D, W, n);
   const R u = rng.first<R>(order, 3);
-  return detect_tubes<R>(D, tu, n, u);
+  return detect_tubes<R>(D, W, tu, n, u);
 }
 
 // ---- tallies ---------------------------------------------------------------------------

@@ -1,0 +1,48 @@
+// Host-side pieces of the C ABI shared by its translation units (mcv_api.cu, mcv_batch.cu):
+// the context, the error message, and the conversion of the public descriptions (mcv.h)
+// into the kernels' parameter blocks.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "mcv_launch.h"
+
+struct mcv_ctx {
+  int device;
+  int sm_count;
+  int* d_err;          // device error flag (kernels set it; mcv_sync reads and clears it)
+  unsigned long long* d_queue;  // spare device words next to the error flag
+  int occ[2][3][3][2]; // cached blocks per SM of the fused kernel: [fp][ns 1,2,4][det][bvk]
+  // batched launch chosen by mcv_batch_tune for a shape: neutrons per work item and blocks
+  // per SM (0: not tuned yet)
+  struct Tuned {
+    int64_t chunk;
+    int blocks_per_sm;
+  } tuned[2][3][3][2];
+};
+
+namespace mcv {
+namespace host {
+
+constexpr int64_t kMaxNeutrons = (int64_t)1 << 40;
+
+mcv_status fail(mcv_status st, const std::string& msg);
+mcv_status cuda_fail(cudaError_t e, const char* where);
+bool is_finite(double v);
+mcv_status check_ctx(mcv_ctx* ctx);
+int ns_index(int ns);
+
+mcv_status build_beam(const mcv_beam_params* b, BeamP<double>* B);
+mcv_status build_sample(const mcv_sample* s, SampleP<double>* S);
+mcv_status build_detector(const mcv_detector* d, DetP<double>* D);
+TofWin tof_window(double tof_min_s, double tof_max_s, int n_tof);
+void cast_beam(const BeamP<double>& d, BeamP<float>* f);
+void cast_sample(const SampleP<double>& d, SampleP<float>* f);
+void cast_detector(const DetP<double>& d, DetP<float>* f);
+void cast_all(TraceArgs* A);
+
+}  // namespace host
+}  // namespace mcv

@@ -43,6 +43,11 @@ struct Forward {
   Acc<R> a_bs, a_det, a_over;
   Counts cnt;
   int err = 0;
+  double* hist;     // the histogram and tallies of the simulation being traced
+  double* tallies;
+
+  __device__ __forceinline__ explicit Forward(const TraceArgs& A)
+      : hist(A.hist), tallies(A.tallies) {}
 
   __device__ __forceinline__ void start(const Lane<R>&) {}
 
@@ -58,7 +63,7 @@ struct Forward {
     if (DET == MCV_DET_NONE) return;
     Ray<R> pe = L.n;
     pe.w = we;
-    record(A, detect<R, DET>(Dof<R>(A), tu, rng, L.o, pe));
+    record(A, detect<R, DET>(Dof<R>(A), Dof<R>(A).win, tu, rng, L.o, pe));
   }
 
   // a packet's detector result into the histogram and the tallies
@@ -68,7 +73,7 @@ struct Forward {
         err = 1;
         return;
       }
-      if (A.hist) atomicAdd(A.hist + h.bin, (double)h.w_det);
+      if (hist) atomicAdd(hist + h.bin, (double)h.w_det);
       a_det.add(h.w_det);
       cnt.ndet++;
     } else if (h.bin == -2) {
@@ -91,8 +96,9 @@ struct Forward {
     }
   }
 
+  // the warp's tallies into `tallies`; the accumulators start again from zero
   __device__ __forceinline__ void flush(const TraceArgs& A, int lane) {
-    if (A.tallies) {
+    if (tallies) {
       const double v_bs = warp_sum(a_bs.value());
       const double v_det = warp_sum(a_det.value());
       const double v_over = warp_sum(a_over.value());
@@ -100,17 +106,21 @@ struct Forward {
       const uint32_t n_miss = warp_sum(cnt.nmiss), n_hit = warp_sum(cnt.nhit);
       const uint32_t n_emit = warp_sum(cnt.nemit);
       if (lane == 0) {
-        atomicAdd(A.tallies + MCV_T_BEAMSTOP, v_bs);
-        atomicAdd(A.tallies + MCV_T_WDET, v_det);
-        atomicAdd(A.tallies + MCV_T_WOVER, v_over);
-        atomicAdd(A.tallies + MCV_T_NDET, (double)n_det);
-        atomicAdd(A.tallies + MCV_T_NOVER, (double)n_over);
-        atomicAdd(A.tallies + MCV_T_NMISS, (double)n_miss);
-        atomicAdd(A.tallies + MCV_T_NHIT, (double)n_hit);
-        atomicAdd(A.tallies + MCV_T_NEMIT, (double)n_emit);
+        atomicAdd(tallies + MCV_T_BEAMSTOP, v_bs);
+        atomicAdd(tallies + MCV_T_WDET, v_det);
+        atomicAdd(tallies + MCV_T_WOVER, v_over);
+        atomicAdd(tallies + MCV_T_NDET, (double)n_det);
+        atomicAdd(tallies + MCV_T_NOVER, (double)n_over);
+        atomicAdd(tallies + MCV_T_NMISS, (double)n_miss);
+        atomicAdd(tallies + MCV_T_NHIT, (double)n_hit);
+        atomicAdd(tallies + MCV_T_NEMIT, (double)n_emit);
       }
     }
     if (__any_sync(0xffffffffu, err != 0) && lane == 0 && A.err) atomicOr(A.err, 1);
+    a_bs = Acc<R>();
+    a_det = Acc<R>();
+    a_over = Acc<R>();
+    cnt = Counts();
   }
 };
 
@@ -149,9 +159,13 @@ constexpr size_t wave_smem_bytes() {
 
 extern __shared__ __align__(16) unsigned char g_wave_smem[];
 
+// The waves of one warp over neutron ids first_id + [lo, hi) of one simulation (sample S,
+// beam B, time window W, random stream (seed, sim_id)).  Returns with both queues empty.
 template <typename R, int NS, int DET, int KS>
-__device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forward<R, DET>& pol) {
-  const SampleP<R>& S = Sof<R>(A);
+__device__ __forceinline__ void run_waves(const TraceArgs& A, const SampleP<R>& S,
+                                          const BeamP<R>& B, const TofWin& W, uint32_t seed,
+                                          uint32_t sim_id, int64_t first_id, int64_t lo,
+                                          int64_t hi, const R* tu, Forward<R, DET>& pol) {
   const DetP<R>& D = Dof<R>(A);
   const unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -160,9 +174,6 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
   QNeutron<R>* hq = reinterpret_cast<QNeutron<R>*>(g_wave_smem) + wib * kQueue;
   QPacket<R>* dq = reinterpret_cast<QPacket<R>*>(g_wave_smem + (size_t)kWarps * kQueue *
                                                    sizeof(QNeutron<R>)) + wib * kQueue;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
   int64_t next = lo;
   int hq_n = 0, dq_n = 0;
   Lane<R> L;
@@ -180,9 +191,9 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
       Ray<R> nr;
       int64_t nid = 0;
       if (i < hi) {
-        nid = A.first_id + i;
-        const NeutronRng rng(A.seed, A.sim_id, nid);
-        bool ok = make_beam<R>(Bof<R>(A), rng, &nr);
+        nid = first_id + i;
+        const NeutronRng rng(seed, sim_id, nid);
+        bool ok = make_beam<R>(B, rng, &nr);
         ok = ok && !(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0));
         if (ok) {
           Seg<R> seg[2 * NS];
@@ -264,7 +275,7 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
       if (L.o == S.max_orders || !(st.len_tot > R(0))) {
         L.active = false;
       } else {
-        const NeutronRng rng(A.seed, A.sim_id, L.nid);
+        const NeutronRng rng(seed, sim_id, L.nid);
         L.active = step_scatter<R, NS, KS, Forward<R, DET>>(A, S, rng, L, st, pol);
       }
     }
@@ -294,21 +305,20 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const R* tu, Forwa
       }
       __syncwarp();
       if (lane < take) {
-        const NeutronRng rng(A.seed, A.sim_id, nid);
-        pol.record(A, detect<R, DET>(D, tu, rng, order, pe));
+        const NeutronRng rng(seed, sim_id, nid);
+        pol.record(A, detect<R, DET>(D, W, tu, rng, order, pe));
       }
       dq_n -= take;
     }
     if (done) break;
   }
-  pol.flush(A, lane);
 }
 
 template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  Forward<R, DET> pol;
+  Forward<R, DET> pol(A);
   run_chain<R, NS, DET, KS, Forward<R, DET>>(A, tu, pol);
 }
 
@@ -329,8 +339,66 @@ __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     wave_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  Forward<R, DET> pol;
-  run_waves<R, NS, DET, KS>(A, tu, pol);
+  Forward<R, DET> pol(A);
+  // each warp owns one contiguous range of the launch's neutron ids
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
+  run_waves<R, NS, DET, KS>(A, Sof<R>(A), Bof<R>(A), Dof<R>(A).win, A.seed, A.sim_id,
+                            A.first_id, lo, hi, tu, pol);
+  pol.flush(A, threadIdx.x & 31);
+}
+
+// ---- batched launch (no counterpart in the paper) -------------------------------------------
+// Many simulations (sample orientations, incident energies, neutron counts) in one persistent
+// launch: every warp takes work items -- chunks of one simulation's neutron ids -- from a
+// device queue until it is empty, copies that simulation's parameter block into its slot of
+// shared memory, and runs the waves over the chunk into that simulation's histogram.  Each
+// neutron's arithmetic is the single-simulation kernel's.
+template <typename R>
+constexpr size_t batch_smem_bytes() {
+  return wave_smem_bytes<R>() + (size_t)kWarps * sizeof(SimP<R>);
+}
+
+template <typename R, int NS, int DET, int KS>
+__global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
+    batch_wave_kernel(const __grid_constant__ TraceArgs A, const __grid_constant__ BatchArgs Q) {
+  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  stage_tubes<R, DET>(A, tu);
+  const unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  SimP<R>* mine = reinterpret_cast<SimP<R>*>(g_wave_smem + wave_smem_bytes<R>()) +
+                  (threadIdx.x >> 5);
+  const SimP<R>* sims = static_cast<const SimP<R>*>(Q.sims);
+  Forward<R, DET> pol(A);
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(Q.next, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= (unsigned long long)Q.n_items) break;
+    const int64_t k = (int64_t)item;
+    // the simulation of item k: the last s with item0[s] <= k
+    int s_lo = 0, s_hi = Q.nsims - 1;
+    while (s_lo < s_hi) {
+      const int mid = (s_lo + s_hi + 1) >> 1;
+      if (Q.item0[mid] <= k)
+        s_lo = mid;
+      else
+        s_hi = mid - 1;
+    }
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(sims + s_lo);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(mine);
+    __syncwarp();
+    for (int w = lane; w < (int)(sizeof(SimP<R>) / 4); w += 32) dst[w] = src[w];
+    __syncwarp();
+    const SimP<R>& J = *mine;
+    const int64_t lo = (k - Q.item0[s_lo]) * Q.chunk;
+    const int64_t hi = min(lo + Q.chunk, J.n);
+    pol.hist = J.hist;
+    pol.tallies = J.tallies;
+    run_waves<R, NS, DET, KS>(A, J.S, J.B, J.win, J.seed, J.sim_id, J.first_id, lo, hi, tu, pol);
+    pol.flush(A, lane);
+  }
 }
 
 // the fused forward runs as waves (dynamic shared memory for the warp queues) unless it
@@ -392,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant_
     if (!load_input<R>(A, i, &n)) continue;
     cnt.nemit++;
     const NeutronRng rng(A.seed, A.sim_id, A.in_id[i]);
-    const Hit<R> h = detect<R, DET>(Dof<R>(A), tu, rng, o, n);
+    const Hit<R> h = detect<R, DET>(Dof<R>(A), Dof<R>(A).win, tu, rng, o, n);
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
@@ -466,7 +534,7 @@ struct Adjoint {
     if (L.o == 0) return;
     Ray<R> pe = L.n;
     pe.w = R(1);
-    const Hit<R> h = detect<R, DET>(Dof<R>(A), tu, rng, L.o, pe);
+    const Hit<R> h = detect<R, DET>(Dof<R>(A), Dof<R>(A).win, tu, rng, L.o, pe);
     if (h.bin < 0) return;
     if (h.bin >= Dof<R>(A).n_bins) {
       err = 1;
@@ -589,6 +657,39 @@ cudaError_t blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem);
 }
 
+// the batched kernel of a shape; its dynamic shared memory limit is set where its occupancy
+// is queried (batch_blocks_per_sm_t), once before the first launch, so that a launch is only
+// the launch (and can be captured in a CUDA graph)
+template <typename R, int NS, int KS>
+const void* batch_fn_nk(int det) {
+  if (det == MCV_DET_SURFACE) return (const void*)batch_wave_kernel<R, NS, MCV_DET_SURFACE, KS>;
+  return (const void*)batch_wave_kernel<R, NS, MCV_DET_TUBES, KS>;
+}
+
+template <typename R>
+const void* batch_fn_t(int ns, int det, int bvk) {
+  if (ns <= 1) return bvk ? batch_fn_nk<R, 1, kKernelsAll>(det) : batch_fn_nk<R, 1, kKernelsPowder>(det);
+  if (ns == 2) return bvk ? batch_fn_nk<R, 2, kKernelsAll>(det) : batch_fn_nk<R, 2, kKernelsPowder>(det);
+  return bvk ? batch_fn_nk<R, 4, kKernelsAll>(det) : batch_fn_nk<R, 4, kKernelsPowder>(det);
+}
+
+template <typename R>
+cudaError_t batch_blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
+  const void* fn = batch_fn_t<R>(ns, det, bvk);
+  const size_t smem = batch_smem_bytes<R>();
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem);
+}
+
+template <typename R>
+cudaError_t launch_batch_t(const TraceArgs& A, const BatchArgs& Q, int ns, int det, int bvk,
+                           int grid, cudaStream_t s) {
+  const void* fn = batch_fn_t<R>(ns, det, bvk);
+  void* args[] = {const_cast<TraceArgs*>(&A), const_cast<BatchArgs*>(&Q)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, batch_smem_bytes<R>(), s);
+}
+
 template <typename R>
 cudaError_t launch_beam_t(const TraceArgs& A, int grid, cudaStream_t s) {
   beam_kernel<R><<<grid, kThreads, 0, s>>>(A);
@@ -645,6 +746,13 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   cudaError_t launch_adjoint_##SUFFIX(const TraceArgs& A, int det, int grid,                \
                                       cudaStream_t s) {                                     \
     return launch_adjoint_t<R>(A, det, grid, s);                                            \
+  }                                                                                         \
+  cudaError_t batch_blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int* blocks) {         \
+    return batch_blocks_per_sm_t<R>(ns, det, bvk, blocks);                                  \
+  }                                                                                         \
+  cudaError_t launch_batch_##SUFFIX(const TraceArgs& A, const BatchArgs& Q, int ns, int det, \
+                                    int bvk, int grid, cudaStream_t s) {                    \
+    return launch_batch_t<R>(A, Q, ns, det, bvk, grid, s);                                  \
   }
 
 }  // namespace mcv

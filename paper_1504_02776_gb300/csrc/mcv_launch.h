@@ -1,4 +1,5 @@
-// Host-side entry points of the kernels (mcv_trace.cu, mcv_grad.cu), used by the C ABI.
+// Host-side entry points of the kernels (mcv_fp32.cu, mcv_fp64.cu, mcv_misc.cu), used by the
+// C ABI.
 #pragma once
 
 #include <string>
@@ -26,6 +27,11 @@ cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
                         double* g, double* loss, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
+// batched launch: blocks per SM of its kernel (also sets the kernel's shared-memory limit;
+// call before the first launch of a shape), and the launch itself
+cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks);
+cudaError_t launch_batch(const TraceArgs& A, const BatchArgs& Q, int fp_mode, int ns, int det,
+                         int bvk, int grid, cudaStream_t s);
 // sets the message mcv_last_error() returns to the calling thread
 void set_last_error(const std::string& msg);
 

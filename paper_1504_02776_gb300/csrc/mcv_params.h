@@ -63,6 +63,13 @@ struct SampleP {
   R bvk_hwu;       // hbar sqrt(phi/M) in meV: hbar omega = bvk_hwu sqrt(lambda')
 };
 
+// time-of-flight window of the histogram: n_tof bins of width dt from tof_min
+struct TofWin {
+  double tof_min, dt;
+  float tmin_hi, tmin_lo, inv_dt;  // FP32 binning: tof_min as a float pair, 1 / dt
+  int n_tof;
+};
+
 template <typename R>
 struct DetP {
   int kind;
@@ -72,14 +79,12 @@ struct DetP {
   int row_off[3];
   int tubes_per_pack, pixels_per_tube;
   int max_tubes_row;
-  int n_tof;
   int64_t n_bins;
   R radius, height, half_h;
   R row_y[3];
   R tube_r, half_len, pitch, period, phi0, pix_len;
   R mu_he_v;        // 100 n sigma 2200: mu(v) = mu_he_v / v (1/m)
-  double tof_min, dt;
-  float tmin_hi, tmin_lo, inv_dt;  // FP32 tof binning: tof_min as a float pair
+  TofWin win;
   R tube_u[2 * MCV_MAX_TUBES_PER_ROW];  // sin, cos of every tube centre angle of a row
 };
 
@@ -113,6 +118,30 @@ struct TraceArgs {
   const double* g;
   double* dsqe;
   double* dsig;
+};
+
+// One simulation of a batched launch: its own sample, beam, random stream, neutron range,
+// time window and histogram; the detector geometry is the batch's.
+template <typename R>
+struct SimP {
+  SampleP<R> S;
+  BeamP<R> B;
+  TofWin win;
+  uint32_t seed, sim_id;
+  int64_t first_id, n;
+  double* hist;
+  double* tallies;
+};
+
+// The work queue of a batched launch: item k covers neutrons [c chunk, (c + 1) chunk) of
+// the simulation s with item0[s] <= k < item0[s + 1], c = k - item0[s].
+struct BatchArgs {
+  const void* sims;          // SimP<R>[nsims], device
+  const int64_t* item0;      // nsims + 1 prefix sums of the items per simulation, device
+  int nsims;
+  int64_t n_items;
+  int64_t chunk;             // neutrons per work item
+  unsigned long long* next;  // the queue's counter (zero at launch), device
 };
 
 }  // namespace mcv

@@ -38,9 +38,9 @@ def test_binding_mirrors_struct_sizes():
     probe = r'''
 #include <stdio.h>
 #include "mcv.h"
-int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
+int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
  sizeof(mcv_scatterer), sizeof(mcv_sqe), sizeof(mcv_bvk), sizeof(mcv_sample),
- sizeof(mcv_detector), sizeof(mcv_neutrons), sizeof(mcv_events));return 0;}
+ sizeof(mcv_detector), sizeof(mcv_neutrons), sizeof(mcv_events), sizeof(mcv_sim));return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
@@ -50,7 +50,7 @@ int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
         sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
                                                 check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (B.BeamParams, B.Scatterer, B.Sqe, B.Bvk, B.Sample,
-                                        B.Detector, B.Neutrons, B.Events)]
+                                        B.Detector, B.Neutrons, B.Events, B.Sim)]
     assert sizes == mine
 
 
