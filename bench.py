@@ -197,6 +197,114 @@ def run_reference(args):
 
 
 # ---- our arm --------------------------------------------------------------------------------
+def _timed(fn, reps):
+    """Device time of reps calls of fn on the current stream (ms per call)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def batch_extras(ctx, args):
+    """The batched forms against one simulation per launch on the same GPU:
+    the 64-simulation incident-energy sweep (sample in an aluminium can, 1e5..1e8 neutrons
+    per simulation, one full histogram each) and the single crystal at 181 orientations x 2e6
+    neutrons (one full histogram each, 170 GB).  Histograms accumulate (cleared once)."""
+    import torch
+
+    import mcv_inputs as mi
+    from paper_1504_02776_gb300 import binding as B
+    out = {}
+
+    tables = {}
+
+    def per_launch(sims, hists, fp):
+        def f():
+            for wl, (c, t) in zip(sims, hists):
+                table = tables.get(id(wl.sqe.table)) if wl.sqe is not None else None
+                ctx.trace(wl, fp_mode=fp, table=table, counts=c, tallies=t, sync=False)
+        return f
+
+    # incident-energy sweep
+    sims = mi.config5()
+    n_tot = sum(w.n for w in sims)
+    hists = [ctx.new_hist(w.detector) for w in sims]
+    tables[id(sims[0].sqe.table)] = ctx.table(sims[0])
+    b = ctx.batch(sims, fp_mode=B.FP32, hists=hists)
+    shape = b.tune()
+    b.run()
+    ms_b = _timed(b.run, args.batch_reps)
+    ctx.sync()
+    det = sum(float(t[B.T_NDET].item()) for _, t in hists) / (args.batch_reps + 1)
+    ms_l32 = _timed(per_launch(sims, hists, B.FP32), 1)
+    ms_l64 = _timed(per_launch(sims, hists, B.FP64), 1)
+    ctx.sync()
+    b.close()
+    out["ei_sweep"] = {
+        "workload": "64 simulations, Ei log-spaced 10-500 meV, counts log-uniform 1e5-1e8 "
+                    "(seed 7; %d neutrons in total), powder S(Q,E) in a 1.5 mm Al can, up to "
+                    "5 orders, one 117,760 x 1000 FP64 histogram per simulation, time window "
+                    "scaled with 1/v" % n_tot,
+        "neutrons": n_tot,
+        "batched_fp32": {"value": n_tot / (ms_b / 1e3), "unit": "neutrons/s", "ms": ms_b,
+                         "shape": shape, "detected_events_per_s": det / (ms_b / 1e3)},
+        "per_launch_fp32": {"value": n_tot / (ms_l32 / 1e3), "unit": "neutrons/s",
+                            "ms": ms_l32, "launches": len(sims)},
+        "per_launch_fp64": {"value": n_tot / (ms_l64 / 1e3), "unit": "neutrons/s",
+                            "ms": ms_l64, "launches": len(sims)},
+        "speedup_batched_fp32_over_per_launch_fp64": ms_l64 / ms_b,
+    }
+    del hists, b
+    torch.cuda.empty_cache()
+
+    # single crystal, 181 orientations
+    sims = mi.config3_batch()
+    n_tot = sum(w.n for w in sims)
+    nb = sims[0].detector.n_bins
+    free, _ = torch.cuda.mem_get_info()
+    if free < (len(sims) + 4) * nb * 8:
+        out["crystal_181"] = {"skipped": "needs %.0f GB free" % ((len(sims) + 4) * nb * 8 / 1e9)}
+        return out
+    hists = [(torch.zeros(nb, dtype=torch.float64, device="cuda"),
+              torch.zeros(B.MCV_NTALLY, dtype=torch.float64, device="cuda")) for _ in sims]
+    b = ctx.batch(sims, fp_mode=B.FP32, hists=hists)
+    shape = b.tune()
+    b.run()
+    ms_b = _timed(b.run, max(1, args.batch_reps - 1))
+    ctx.sync()
+    b.close()
+    sample = sims[::args.crystal_fp64_stride]
+    ms_l64 = _timed(per_launch(sample, hists[::args.crystal_fp64_stride], B.FP64), 1)
+    ms_l32 = _timed(per_launch(sims, hists, B.FP32), 1)
+    ctx.sync()
+    n_s = sum(w.n for w in sample)
+    out["crystal_181"] = {
+        "workload": "fcc Born-von Karman single crystal, 2 cm cube, Ei=50 meV, 181 "
+                    "orientations (0-180 deg) x 2e6 neutrons, one 117,760 x 1000 FP64 "
+                    "histogram per orientation (%.0f GB)" % (len(sims) * nb * 8 / 1e9),
+        "neutrons": n_tot,
+        "batched_fp32": {"value": n_tot / (ms_b / 1e3), "unit": "neutrons/s", "ms": ms_b,
+                         "shape": shape},
+        "per_launch_fp32": {"value": n_tot / (ms_l32 / 1e3), "unit": "neutrons/s",
+                            "ms": ms_l32, "launches": len(sims)},
+        "per_launch_fp64": {"value": n_s / (ms_l64 / 1e3), "unit": "neutrons/s",
+                            "ms_sample": ms_l64, "launches": len(sample),
+                            "sample": "every %d-th orientation (%d of %d), rate applied to "
+                                      "the whole batch" % (args.crystal_fp64_stride,
+                                                           len(sample), len(sims))},
+        "speedup_batched_fp32_over_per_launch_fp64": (n_tot / (ms_b / 1e3)) /
+                                                     (n_s / (ms_l64 / 1e3)),
+    }
+    del hists
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -294,6 +402,11 @@ def run_ours(args):
     value64 = world * N * args.fp64_steps / (ms64 / 1e3)
     ctx.sync()
 
+    # ---- batched forms (rank 0 of a single-GPU run; they hold up to 170 GB of histograms)
+    batched = None
+    if not args.no_batch and world == 1:
+        batched = batch_extras(ctx, args)
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -362,6 +475,7 @@ def run_ours(args):
                          "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                          "speedup_fp32_over_fp64": value / value64},
         "roofline": roof,
+        "batched": batched,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,
@@ -388,6 +502,9 @@ def main():
     ap.add_argument("--ref-per-worker", type=int, default=400_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--crystal-fp64-stride", type=int, default=18)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

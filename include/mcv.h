@@ -237,9 +237,11 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
 /* ---- batched launches ------------------------------------------------------------------- */
 /* The paper has no counterpart to these calls.  A batch is many independent simulations
  * (sample orientations, incident energies, neutron counts of any mix) traced in ONE
- * persistent launch of the fused path (source -> sample -> detector -> histogram): every
- * warp takes work items, chunks of one simulation's neutron ids, from a device queue until
- * it is empty, so uneven simulations keep every SM busy to the end.  Each neutron's history
+ * persistent launch of the fused path (source -> sample -> detector -> histogram).  Each
+ * simulation's neutron ids are cut into work items handed out by its own device queue; every
+ * warp starts at a simulation of its own (warps spread in proportion to the neutron counts),
+ * takes that simulation's items until its queue is empty, then helps with the others, so
+ * uneven simulations keep every SM busy to the end.  Each neutron's history
  * and arithmetic are those of mcv_trace_sample with the same simulation's arguments; only
  * the order of the FP64 histogram additions differs.
  *
@@ -272,11 +274,13 @@ mcv_status mcv_batch_create(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
  * replayed; runs of one batch must not overlap on the GPU (they share the queue). */
 mcv_status mcv_batch_run(mcv_batch* b, void* stream);
 /* Autotuner: times the batch kernel on a proportional sample of about trial_neutrons
- * neutrons (<= 0: 2e7) of this batch for each candidate launch shape (work-item sizes
- * 1024..65536 neutrons, blocks per SM from the occupancy limit down), with histograms in
- * scratch memory (the simulations' own histograms are not touched), keeps the fastest for
- * this batch and records it on the context for later batches of the same kind (real type,
- * number of scatterers, detector kind, kernel set).  Synchronises `stream`; allocates. */
+ * neutrons (<= 0: 2e7) of this batch for each candidate launch shape -- work-item sizes of
+ * 512..8192 neutrons (scaled by the sample's fraction of the batch in the trial, which keeps
+ * the number of items per warp) and blocks per SM at and below the occupancy limit -- with
+ * histograms in scratch memory (the simulations' own histograms are not touched), keeps the
+ * fastest for this batch and records it on the context for later batches of the same kind
+ * (real type, number of scatterers, detector kind, kernel set).  Synchronises `stream`;
+ * allocates. */
 mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream);
 /* The batch's launch shape: neutrons per work item, blocks per SM, grid size, work items. */
 mcv_status mcv_batch_shape(const mcv_batch* b, int64_t* chunk, int* blocks_per_sm,

@@ -16,13 +16,14 @@ using namespace mcv::host;
 namespace {
 
 constexpr int kWarpsPerBlock = 4;  // the kernels' 128 threads
-constexpr int64_t kDefaultChunk = 16384;
+constexpr int64_t kDefaultChunk = 8192;
 constexpr int64_t kMinChunk = 256;
 
 // The simulations of a batch as the kernel reads them: host images of the parameter blocks
 // in the batch's real type, and the shape of the batch.
 struct BatchImage {
   int fp = 0, ns = 1, det = 0, bvk = 0;
+  int ss = 1;  // every simulation has the same sample (kept in kernel parameter space)
   int nsims = 0;
   int64_t total_n = 0;
   std::vector<unsigned char> sims;  // SimP<R>[nsims]
@@ -49,8 +50,9 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
   im->sim_bytes = fp_mode == MCV_FP32 ? sizeof(mcv::SimP<float>) : sizeof(mcv::SimP<double>);
   im->sims.assign((size_t)nsims * im->sim_bytes, 0);
   im->n.assign(nsims, 0);
-  int ns = 1, bvk = 0;
+  int ns = 1, bvk = 0, same = 1;
   int64_t total = 0;
+  mcv::SampleP<double> first;
   for (int k = 0; k < nsims; ++k) {
     const mcv_sim& s = sims[k];
     const std::string who = "simulation " + std::to_string(k) + ": ";
@@ -84,6 +86,10 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
     total += s.n;
     ns = std::max(ns, d.S.ns);
     if (d.S.has_bvk) bvk = 1;
+    if (k == 0)
+      first = d.S;
+    else if (std::memcmp(&first, &d.S, sizeof(first)) != 0)
+      same = 0;
     im->n[k] = s.n;
     if (fp_mode == MCV_FP32) {
       mcv::SimP<float> f;
@@ -104,47 +110,61 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
   }
   im->ns = ns <= 1 ? 1 : (ns == 2 ? 2 : 4);
   im->bvk = bvk;
+  im->ss = same;
   im->total_n = total;
+  if (same) {
+    // the shared sample goes into the kernel's parameter blocks
+    A->Sd = first;
+    cast_sample(first, &A->Sf);
+  }
   return MCV_OK;
 }
 
-// item prefix sums for a chunk size: item0[s] = number of items before simulation s
-std::vector<int64_t> item_prefix(const std::vector<int64_t>& n, int64_t chunk) {
-  std::vector<int64_t> p(n.size() + 1, 0);
-  for (size_t k = 0; k < n.size(); ++k) p[k + 1] = p[k] + (n[k] + chunk - 1) / chunk;
-  return p;
+// number of work items of a batch for a chunk size
+int64_t count_items(const std::vector<int64_t>& n, int64_t chunk) {
+  int64_t k = 0;
+  for (int64_t m : n) k += (m + chunk - 1) / chunk;
+  return k;
 }
 
-// Device layout of a batch: the queue counter (256 bytes), SimP[nsims], item0[nsims + 1].
+// Device layout of a batch: the item counters (nsims, padded to 256 bytes), SimP[nsims],
+// nstart[nsims + 1].
+size_t counters_bytes(const BatchImage& im) {
+  return ((im.n.size() * sizeof(unsigned long long) + 255) / 256) * 256;
+}
+
 size_t device_bytes(const BatchImage& im) {
-  return 256 + im.sims.size() + (im.n.size() + 1) * sizeof(int64_t);
+  return counters_bytes(im) + im.sims.size() + (im.n.size() + 1) * sizeof(int64_t);
 }
 
-void point_args(void* base, const BatchImage& im, int64_t chunk, int64_t n_items,
-                mcv::BatchArgs* Q) {
+void point_args(void* base, const BatchImage& im, int64_t chunk, mcv::BatchArgs* Q) {
   unsigned char* b = static_cast<unsigned char*>(base);
   Q->next = reinterpret_cast<unsigned long long*>(b);
-  Q->sims = b + 256;
-  Q->item0 = reinterpret_cast<const int64_t*>(b + 256 + im.sims.size());
+  Q->sims = b + counters_bytes(im);
+  Q->nstart = reinterpret_cast<const int64_t*>(b + counters_bytes(im) + im.sims.size());
   Q->nsims = im.nsims;
   Q->chunk = chunk;
-  Q->n_items = n_items;
+  Q->total = im.total_n;
 }
 
-// host image of the whole device block
-std::vector<unsigned char> device_image(const BatchImage& im, const std::vector<int64_t>& item0) {
+// host image of the whole device block (counters zero)
+std::vector<unsigned char> device_image(const BatchImage& im) {
   std::vector<unsigned char> out(device_bytes(im), 0);
-  std::memcpy(out.data() + 256, im.sims.data(), im.sims.size());
-  std::memcpy(out.data() + 256 + im.sims.size(), item0.data(), item0.size() * sizeof(int64_t));
+  std::vector<int64_t> nstart(im.n.size() + 1, 0);
+  for (size_t k = 0; k < im.n.size(); ++k) nstart[k + 1] = nstart[k] + im.n[k];
+  std::memcpy(out.data() + counters_bytes(im), im.sims.data(), im.sims.size());
+  std::memcpy(out.data() + counters_bytes(im) + im.sims.size(), nstart.data(),
+              nstart.size() * sizeof(int64_t));
   return out;
 }
 
-// default work-item size: about 8 items per resident warp, a power of two in [256, 16384]
+// default work-item size: about 16 items per resident warp, a multiple of 32 in
+// [kMinChunk, kDefaultChunk] (items of one simulation follow each other in a warp without a
+// drain, so small items cost little more than their queue counter update)
 int64_t default_chunk(int64_t total_n, int64_t warps) {
-  int64_t want = total_n / std::max<int64_t>(1, warps * 8);
-  int64_t c = kMinChunk;
-  while (c * 2 <= want && c < kDefaultChunk) c *= 2;
-  return c;
+  int64_t c = total_n / std::max<int64_t>(1, warps * 16);
+  c = std::min(std::max(c, kMinChunk), kDefaultChunk);
+  return (c / 32) * 32;
 }
 
 int grid_of(int sm_count, int blocks_per_sm, int64_t n_items) {
@@ -161,7 +181,7 @@ struct mcv_batch {
   BatchImage im;
   void* d_block = nullptr;
   mcv::BatchArgs Q;
-  int64_t chunk = 0;
+  int64_t chunk = 0, n_items = 0;
   int blocks_per_sm = 1, max_blocks_per_sm = 1;
   int grid = 1;
 };
@@ -174,31 +194,32 @@ mcv::TraceArgs& zeroed(mcv::TraceArgs& A) {
 }
 
 mcv_ctx::Tuned& tuned_slot(mcv_ctx* ctx, const BatchImage& im) {
-  return ctx->tuned[im.fp][ns_index(im.ns)][im.det][im.bvk];
+  return ctx->tuned[im.fp][ns_index(im.ns)][im.det][im.bvk][im.ss];
 }
 
-// uploads the batch's device block for the batch's current chunk
+// uploads the batch's device block and sets the launch arguments for its current chunk
 mcv_status upload(mcv_batch* b) {
-  const std::vector<int64_t> item0 = item_prefix(b->im.n, b->chunk);
-  const std::vector<unsigned char> img = device_image(b->im, item0);
+  const std::vector<unsigned char> img = device_image(b->im);
   cudaError_t e = cudaMemcpy(b->d_block, img.data(), img.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (batch parameters)");
-  point_args(b->d_block, b->im, b->chunk, item0.back(), &b->Q);
-  b->grid = grid_of(b->ctx->sm_count, b->blocks_per_sm, b->Q.n_items);
+  point_args(b->d_block, b->im, b->chunk, &b->Q);
+  b->n_items = count_items(b->im.n, b->chunk);
+  b->grid = grid_of(b->ctx->sm_count, b->blocks_per_sm, b->n_items);
   return MCV_OK;
 }
 
-mcv_status launch(mcv_batch* b, const mcv::BatchArgs& Q, int grid, cudaStream_t s) {
-  if (Q.n_items == 0) return MCV_OK;
-  cudaError_t e = cudaMemsetAsync(Q.next, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue counter)");
-  e = mcv::launch_batch(b->A, Q, b->im.fp, b->im.ns, b->im.det, b->im.bvk, grid, s);
+mcv_status launch(mcv_batch* b, const mcv::BatchArgs& Q, int64_t n_items, int grid,
+                  cudaStream_t s) {
+  if (n_items == 0) return MCV_OK;
+  cudaError_t e = cudaMemsetAsync(Q.next, 0, (size_t)Q.nsims * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue counters)");
+  e = mcv::launch_batch(b->A, Q, b->im.fp, b->im.ns, b->im.det, b->im.bvk, b->im.ss, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return MCV_OK;
 }
 
 mcv_status occupancy(mcv_ctx* ctx, const BatchImage& im, int* blocks) {
-  cudaError_t e = mcv::batch_blocks_per_sm(im.fp, im.ns, im.det, im.bvk, blocks);
+  cudaError_t e = mcv::batch_blocks_per_sm(im.fp, im.ns, im.det, im.bvk, im.ss, blocks);
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel occupancy");
   if (*blocks < 1) return fail(MCV_ECUDA, "the batch kernel does not fit on an SM");
   (void)ctx;
@@ -258,7 +279,7 @@ mcv_status mcv_batch_run(mcv_batch* b, void* stream) {
   if (!b) return fail(MCV_EINVAL, "batch is NULL");
   mcv_status st = check_ctx(b->ctx);
   if (st != MCV_OK) return st;
-  return launch(b, b->Q, b->grid, static_cast<cudaStream_t>(stream));
+  return launch(b, b->Q, b->n_items, b->grid, static_cast<cudaStream_t>(stream));
 }
 
 mcv_status mcv_batch_shape(const mcv_batch* b, int64_t* chunk, int* blocks_per_sm, int* grid,
@@ -267,7 +288,7 @@ mcv_status mcv_batch_shape(const mcv_batch* b, int64_t* chunk, int* blocks_per_s
   if (chunk) *chunk = b->chunk;
   if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
   if (grid) *grid = b->grid;
-  if (n_items) *n_items = b->Q.n_items;
+  if (n_items) *n_items = b->n_items;
   return MCV_OK;
 }
 
@@ -318,29 +339,34 @@ mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream) {
   }
   void* d_trial = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&d_trial, device_bytes(tr));
+  if (e == cudaSuccess) {
+    const std::vector<unsigned char> img = device_image(tr);
+    e = cudaMemcpyAsync(d_trial, img.data(), img.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ev1);
   float best_ms = -1.0f;
   int64_t best_chunk = b->chunk;
   int best_blocks = b->blocks_per_sm;
-  const int64_t chunks[] = {1024, 4096, 16384, 65536};
+  // candidate work-item sizes of the full batch; the trial uses them scaled by its fraction
+  // of the neutrons, which keeps the number of items per warp (the load balance at the end)
+  const double frac = (double)tr.total_n / (double)b->im.total_n;
+  const int64_t chunks[] = {512, 1024, 2048, 4096, 8192};
   st = MCV_OK;
   for (int64_t chunk : chunks) {
     if (e != cudaSuccess || st != MCV_OK) break;
-    const std::vector<int64_t> item0 = item_prefix(tr.n, chunk);
-    const std::vector<unsigned char> img = device_image(tr, item0);
-    e = cudaMemcpyAsync(d_trial, img.data(), img.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) break;
+    const int64_t tc = std::max<int64_t>(32, ((int64_t)(chunk * frac) / 32) * 32);
     mcv::BatchArgs Q;
-    point_args(d_trial, tr, chunk, item0.back(), &Q);
-    for (int bps = b->max_blocks_per_sm; bps >= std::max(1, b->max_blocks_per_sm - 2); --bps) {
-      const int grid = grid_of(b->ctx->sm_count, bps, Q.n_items);
-      st = launch(b, Q, grid, s);  // warm-up
+    point_args(d_trial, tr, tc, &Q);
+    const int64_t items = count_items(tr.n, tc);
+    for (int bps = b->max_blocks_per_sm; bps >= std::max(1, b->max_blocks_per_sm - 1); --bps) {
+      const int grid = grid_of(b->ctx->sm_count, bps, items);
+      st = launch(b, Q, items, grid, s);  // warm-up
       if (st != MCV_OK) break;
       e = cudaEventRecord(ev0, s);
-      if (e == cudaSuccess) st = launch(b, Q, grid, s);
+      if (e == cudaSuccess) st = launch(b, Q, items, grid, s);
       if (st != MCV_OK) break;
       if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
@@ -392,16 +418,16 @@ mcv_status mcv_trace_batch(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
     b.chunk = default_chunk(b.im.total_n, (int64_t)ctx->sm_count * b.blocks_per_sm * kWarpsPerBlock);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const std::vector<int64_t> item0 = item_prefix(b.im.n, b.chunk);
-  const std::vector<unsigned char> img = device_image(b.im, item0);
+  const std::vector<unsigned char> img = device_image(b.im);
   void* d = nullptr;
   cudaError_t e = cudaMallocAsync(&d, img.size(), s);
   if (e != cudaSuccess) return fail(MCV_ENOMEM, "cannot allocate the batch's parameter block");
   // pageable source: the copy has taken the host bytes when the call returns
   e = cudaMemcpyAsync(d, img.data(), img.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    point_args(d, b.im, b.chunk, item0.back(), &b.Q);
-    st = launch(&b, b.Q, grid_of(ctx->sm_count, b.blocks_per_sm, b.Q.n_items), s);
+    point_args(d, b.im, b.chunk, &b.Q);
+    const int64_t items = count_items(b.im.n, b.chunk);
+    st = launch(&b, b.Q, items, grid_of(ctx->sm_count, b.blocks_per_sm, items), s);
   }
   cudaError_t ef = cudaFreeAsync(d, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (batch parameters)");

@@ -35,19 +35,21 @@ __device__ __forceinline__ void store_slot(const TraceArgs& A, int64_t slot, con
   A.pk_order[slot] = order;
 }
 
+// Where the forward path's histogram and tallies are: the launch's (kernel parameters)
+struct LaunchOut {
+  static __device__ __forceinline__ double* hist(const TraceArgs& A) { return A.hist; }
+  static __device__ __forceinline__ double* tallies(const TraceArgs& A) { return A.tallies; }
+};
+
 // Forward policy: packets go to the packet slots and/or through the detector into the
-// histogram; order-0 packets go to the beam stop.
-template <typename R, int DET>
+// histogram; order-0 packets go to the beam stop.  Out: where the histogram and tallies of
+// the simulation being traced are (read where used, so they hold no registers).
+template <typename R, int DET, class Out = LaunchOut>
 struct Forward {
   static constexpr bool kWantsGs = false;
   Acc<R> a_bs, a_det, a_over;
   Counts cnt;
   int err = 0;
-  double* hist;     // the histogram and tallies of the simulation being traced
-  double* tallies;
-
-  __device__ __forceinline__ explicit Forward(const TraceArgs& A)
-      : hist(A.hist), tallies(A.tallies) {}
 
   __device__ __forceinline__ void start(const Lane<R>&) {}
 
@@ -73,6 +75,7 @@ struct Forward {
         err = 1;
         return;
       }
+      double* hist = Out::hist(A);
       if (hist) atomicAdd(hist + h.bin, (double)h.w_det);
       a_det.add(h.w_det);
       cnt.ndet++;
@@ -98,6 +101,7 @@ struct Forward {
 
   // the warp's tallies into `tallies`; the accumulators start again from zero
   __device__ __forceinline__ void flush(const TraceArgs& A, int lane) {
+    double* tallies = Out::tallies(A);
     if (tallies) {
       const double v_bs = warp_sum(a_bs.value());
       const double v_det = warp_sum(a_det.value());
@@ -159,13 +163,95 @@ constexpr size_t wave_smem_bytes() {
 
 extern __shared__ __align__(16) unsigned char g_wave_smem[];
 
-// The waves of one warp over neutron ids first_id + [lo, hi) of one simulation (sample S,
-// beam B, time window W, random stream (seed, sim_id)).  Returns with both queues empty.
-template <typename R, int NS, int DET, int KS>
-__device__ __forceinline__ void run_waves(const TraceArgs& A, const SampleP<R>& S,
-                                          const BeamP<R>& B, const TofWin& W, uint32_t seed,
-                                          uint32_t sim_id, int64_t first_id, int64_t lo,
-                                          int64_t hi, const R* tu, Forward<R, DET>& pol) {
+// Sources of neutron-id ranges for the waves: a single range, or further items of the same
+// simulation from its work queue (warp-collective: called by all 32 lanes together).
+struct NoMoreIds {
+  __device__ __forceinline__ bool more(int64_t*, int64_t*) { return false; }
+};
+
+// A warp's slot in the batched kernel's shared memory: the simulation it traces and that
+// simulation's work queue, and the warp's walk over the simulations.  Warp-uniform values
+// that are read where they are used rather than held in registers.
+struct QueueSlot {
+  unsigned long long* ctr;
+  int64_t n, chunk, items;
+};
+
+template <typename R>
+struct BatchWarp {
+  SimP<R> sim;
+  QueueSlot q;
+  int home, v;
+};
+
+template <typename R>
+constexpr size_t batch_smem_bytes() {
+  return wave_smem_bytes<R>() + (size_t)kWarps * sizeof(BatchWarp<R>);
+}
+
+template <typename R>
+__device__ __forceinline__ BatchWarp<R>& batch_warp() {
+  return reinterpret_cast<BatchWarp<R>*>(g_wave_smem + wave_smem_bytes<R>())[threadIdx.x >> 5];
+}
+
+// further items of the simulation in the warp's slot, from its work queue
+template <typename R>
+struct QueuedIds {
+  __device__ __forceinline__ bool more(int64_t* lo, int64_t* hi) {
+    const QueueSlot& q = batch_warp<R>().q;
+    unsigned long long k = 0;
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(q.ctr, 1ull);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= (unsigned long long)q.items) return false;
+    *lo = (int64_t)k * q.chunk;
+    *hi = min(*lo + q.chunk, q.n);
+    return true;
+  }
+};
+
+// the histogram and tallies of the simulation in the warp's slot
+template <typename R>
+struct SlotOut {
+  static __device__ __forceinline__ double* hist(const TraceArgs&) { return batch_warp<R>().sim.hist; }
+  static __device__ __forceinline__ double* tallies(const TraceArgs&) {
+    return batch_warp<R>().sim.tallies;
+  }
+};
+
+// The simulation the waves trace: its parameters from kernel parameter space (single launch)
+// or from the warp's slot of shared memory (batched launch), read where they are used.
+template <typename R>
+struct ParamJob {
+  const TraceArgs& A;
+  __device__ __forceinline__ const SampleP<R>& S() const { return Sof<R>(A); }
+  __device__ __forceinline__ const BeamP<R>& B() const { return Bof<R>(A); }
+  __device__ __forceinline__ const TofWin& W() const { return Dof<R>(A).win; }
+  __device__ __forceinline__ uint32_t seed() const { return A.seed; }
+  __device__ __forceinline__ uint32_t sim_id() const { return A.sim_id; }
+  __device__ __forceinline__ int64_t first_id() const { return A.first_id; }
+};
+
+// The batched launch's simulation: the one in the warp's slot.  SS: every simulation has the
+// launch's sample, which then stays in kernel parameter space.
+template <typename R, bool SS>
+struct SlotJob {
+  const TraceArgs& A;
+  __device__ __forceinline__ const SampleP<R>& S() const {
+    return SS ? Sof<R>(A) : batch_warp<R>().sim.S;
+  }
+  __device__ __forceinline__ const BeamP<R>& B() const { return batch_warp<R>().sim.B; }
+  __device__ __forceinline__ const TofWin& W() const { return batch_warp<R>().sim.win; }
+  __device__ __forceinline__ uint32_t seed() const { return batch_warp<R>().sim.seed; }
+  __device__ __forceinline__ uint32_t sim_id() const { return batch_warp<R>().sim.sim_id; }
+  __device__ __forceinline__ int64_t first_id() const { return batch_warp<R>().sim.first_id; }
+};
+
+// The waves of one warp over neutron ids first_id + [lo, hi) of one simulation, and over
+// every further range `src` hands out for it.  Returns with both queues empty.
+template <typename R, int NS, int DET, int KS, class Job, class Src, class P>
+__device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, int64_t lo,
+                                          int64_t hi, const R* tu, P& pol, Src& src) {
+  const SampleP<R>& S = job.S();
   const DetP<R>& D = Dof<R>(A);
   const unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -185,15 +271,15 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const SampleP<R>& 
     const unsigned idle = __ballot_sync(kFull, !L.active);
     const int n_idle = __popc(idle);
     // ---- source stage
-    while (hq_n < n_idle && next < hi) {
+    while (hq_n < n_idle && (next < hi || src.more(&next, &hi))) {
       const int64_t i = next + lane;
       bool hit = false;
       Ray<R> nr;
       int64_t nid = 0;
       if (i < hi) {
-        nid = first_id + i;
-        const NeutronRng rng(seed, sim_id, nid);
-        bool ok = make_beam<R>(B, rng, &nr);
+        nid = job.first_id() + i;
+        const NeutronRng rng(job.seed(), job.sim_id(), nid);
+        bool ok = make_beam<R>(job.B(), rng, &nr);
         ok = ok && !(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0));
         if (ok) {
           Seg<R> seg[2 * NS];
@@ -275,15 +361,16 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const SampleP<R>& 
       if (L.o == S.max_orders || !(st.len_tot > R(0))) {
         L.active = false;
       } else {
-        const NeutronRng rng(seed, sim_id, L.nid);
-        L.active = step_scatter<R, NS, KS, Forward<R, DET>>(A, S, rng, L, st, pol);
+        const NeutronRng rng(job.seed(), job.sim_id(), L.nid);
+        L.active = step_scatter<R, NS, KS, P>(A, S, rng, L, st, pol);
       }
     }
     __syncwarp();
     // ---- detector stage: full batches now, the remainder once the range is done.  This is
     // the only place packets are detected, so a packet's arithmetic does not depend on the
     // batch it falls in (or on the launch shape).
-    const bool done = !__any_sync(kFull, L.active) && next >= hi && hq_n == 0;
+    bool done = !__any_sync(kFull, L.active) && next >= hi && hq_n == 0;
+    if (done) done = !src.more(&next, &hi);
     while (dq_n >= 32 || (done && dq_n > 0)) {
       const int take = dq_n < 32 ? dq_n : 32;
       Ray<R> pe;
@@ -305,8 +392,8 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const SampleP<R>& 
       }
       __syncwarp();
       if (lane < take) {
-        const NeutronRng rng(seed, sim_id, nid);
-        pol.record(A, detect<R, DET>(D, W, tu, rng, order, pe));
+        const NeutronRng rng(job.seed(), job.sim_id(), nid);
+        pol.record(A, detect<R, DET>(D, job.W(), tu, rng, order, pe));
       }
       dq_n -= take;
     }
@@ -318,7 +405,7 @@ template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  Forward<R, DET> pol(A);
+  Forward<R, DET> pol;
   run_chain<R, NS, DET, KS, Forward<R, DET>>(A, tu, pol);
 }
 
@@ -339,64 +426,78 @@ __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     wave_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  Forward<R, DET> pol(A);
+  Forward<R, DET> pol;
   // each warp owns one contiguous range of the launch's neutron ids
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
-  run_waves<R, NS, DET, KS>(A, Sof<R>(A), Bof<R>(A), Dof<R>(A).win, A.seed, A.sim_id,
-                            A.first_id, lo, hi, tu, pol);
+  NoMoreIds src;
+  const ParamJob<R> job{A};
+  run_waves<R, NS, DET, KS>(A, job, lo, hi, tu, pol, src);
   pol.flush(A, threadIdx.x & 31);
 }
 
 // ---- batched launch (no counterpart in the paper) -------------------------------------------
 // Many simulations (sample orientations, incident energies, neutron counts) in one persistent
-// launch: every warp takes work items -- chunks of one simulation's neutron ids -- from a
-// device queue until it is empty, copies that simulation's parameter block into its slot of
-// shared memory, and runs the waves over the chunk into that simulation's histogram.  Each
-// neutron's arithmetic is the single-simulation kernel's.
-template <typename R>
-constexpr size_t batch_smem_bytes() {
-  return wave_smem_bytes<R>() + (size_t)kWarps * sizeof(SimP<R>);
-}
-
-template <typename R, int NS, int DET, int KS>
+// launch.  Each simulation's neutron ids are cut into work items handed out by its own
+// device counter.  A warp starts at its home simulation (warps are spread over the
+// simulations in proportion to their neutron counts), copies that simulation's parameter
+// block into its slot of shared memory, and keeps taking items of it -- without draining its
+// queues between items -- until that queue is empty; then it moves on to the next
+// simulation that still has items.  Each neutron's arithmetic is the single-simulation
+// kernel's.
+// SS: every simulation has the batch's sample (A.Sf / A.Sd), kept in parameter space
+template <typename R, int NS, int DET, int KS, bool SS>
 __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     batch_wave_kernel(const __grid_constant__ TraceArgs A, const __grid_constant__ BatchArgs Q) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  const unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  SimP<R>* mine = reinterpret_cast<SimP<R>*>(g_wave_smem + wave_smem_bytes<R>()) +
-                  (threadIdx.x >> 5);
-  const SimP<R>* sims = static_cast<const SimP<R>*>(Q.sims);
-  Forward<R, DET> pol(A);
-  for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(Q.next, 1ull);
-    item = __shfl_sync(kFull, item, 0);
-    if (item >= (unsigned long long)Q.n_items) break;
-    const int64_t k = (int64_t)item;
-    // the simulation of item k: the last s with item0[s] <= k
-    int s_lo = 0, s_hi = Q.nsims - 1;
-    while (s_lo < s_hi) {
-      const int mid = (s_lo + s_hi + 1) >> 1;
-      if (Q.item0[mid] <= k)
-        s_lo = mid;
+  {
+    // home simulation: the last s with nstart[s] <= total * warp / warps
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t target = (int64_t)(((double)Q.total * (double)wid) / (double)nw);
+    int home = 0, h_hi = Q.nsims - 1;
+    while (home < h_hi) {
+      const int mid = (home + h_hi + 1) >> 1;
+      if (Q.nstart[mid] <= target)
+        home = mid;
       else
-        s_hi = mid - 1;
+        h_hi = mid - 1;
     }
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(sims + s_lo);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(mine);
+    if (lane == 0) {
+      batch_warp<R>().home = home;
+      batch_warp<R>().v = 0;
+    }
     __syncwarp();
-    for (int w = lane; w < (int)(sizeof(SimP<R>) / 4); w += 32) dst[w] = src[w];
+  }
+  Forward<R, DET, SlotOut<R>> pol;
+  const SlotJob<R, SS> job{A};
+  QueuedIds<R> src;
+  for (;;) {
+    BatchWarp<R>& me = batch_warp<R>();
+    const int v = me.v;
+    if (v >= Q.nsims) break;
+    int s = me.home + v;
+    if (s >= Q.nsims) s -= Q.nsims;
+    const int64_t n = Q.nstart[s + 1] - Q.nstart[s];
     __syncwarp();
-    const SimP<R>& J = *mine;
-    const int64_t lo = (k - Q.item0[s_lo]) * Q.chunk;
-    const int64_t hi = min(lo + Q.chunk, J.n);
-    pol.hist = J.hist;
-    pol.tallies = J.tallies;
-    run_waves<R, NS, DET, KS>(A, J.S, J.B, J.win, J.seed, J.sim_id, J.first_id, lo, hi, tu, pol);
+    if (lane == 0) {
+      me.v = v + 1;
+      me.q.ctr = Q.next + s;
+      me.q.n = n;
+      me.q.chunk = Q.chunk;
+      me.q.items = (n + Q.chunk - 1) / Q.chunk;
+    }
+    __syncwarp();
+    int64_t lo = 0, hi = 0;
+    if (!src.more(&lo, &hi)) continue;
+    const uint32_t* from = reinterpret_cast<const uint32_t*>(static_cast<const SimP<R>*>(Q.sims) + s);
+    uint32_t* to = reinterpret_cast<uint32_t*>(&me.sim);
+    for (int w = lane; w < (int)(sizeof(SimP<R>) / 4); w += 32) to[w] = from[w];
+    __syncwarp();
+    run_waves<R, NS, DET, KS>(A, job, lo, hi, tu, pol, src);
     pol.flush(A, lane);
   }
 }
@@ -660,22 +761,30 @@ cudaError_t blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
 // the batched kernel of a shape; its dynamic shared memory limit is set where its occupancy
 // is queried (batch_blocks_per_sm_t), once before the first launch, so that a launch is only
 // the launch (and can be captured in a CUDA graph)
-template <typename R, int NS, int KS>
+template <typename R, int NS, int KS, bool SS>
 const void* batch_fn_nk(int det) {
-  if (det == MCV_DET_SURFACE) return (const void*)batch_wave_kernel<R, NS, MCV_DET_SURFACE, KS>;
-  return (const void*)batch_wave_kernel<R, NS, MCV_DET_TUBES, KS>;
+  if (det == MCV_DET_SURFACE)
+    return (const void*)batch_wave_kernel<R, NS, MCV_DET_SURFACE, KS, SS>;
+  return (const void*)batch_wave_kernel<R, NS, MCV_DET_TUBES, KS, SS>;
+}
+
+template <typename R, bool SS>
+const void* batch_fn_s(int ns, int det, int bvk) {
+  if (ns <= 1)
+    return bvk ? batch_fn_nk<R, 1, kKernelsAll, SS>(det) : batch_fn_nk<R, 1, kKernelsPowder, SS>(det);
+  if (ns == 2)
+    return bvk ? batch_fn_nk<R, 2, kKernelsAll, SS>(det) : batch_fn_nk<R, 2, kKernelsPowder, SS>(det);
+  return bvk ? batch_fn_nk<R, 4, kKernelsAll, SS>(det) : batch_fn_nk<R, 4, kKernelsPowder, SS>(det);
 }
 
 template <typename R>
-const void* batch_fn_t(int ns, int det, int bvk) {
-  if (ns <= 1) return bvk ? batch_fn_nk<R, 1, kKernelsAll>(det) : batch_fn_nk<R, 1, kKernelsPowder>(det);
-  if (ns == 2) return bvk ? batch_fn_nk<R, 2, kKernelsAll>(det) : batch_fn_nk<R, 2, kKernelsPowder>(det);
-  return bvk ? batch_fn_nk<R, 4, kKernelsAll>(det) : batch_fn_nk<R, 4, kKernelsPowder>(det);
+const void* batch_fn_t(int ns, int det, int bvk, int ss) {
+  return ss ? batch_fn_s<R, true>(ns, det, bvk) : batch_fn_s<R, false>(ns, det, bvk);
 }
 
 template <typename R>
-cudaError_t batch_blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
-  const void* fn = batch_fn_t<R>(ns, det, bvk);
+cudaError_t batch_blocks_per_sm_t(int ns, int det, int bvk, int ss, int* blocks) {
+  const void* fn = batch_fn_t<R>(ns, det, bvk, ss);
   const size_t smem = batch_smem_bytes<R>();
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -684,8 +793,8 @@ cudaError_t batch_blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
 
 template <typename R>
 cudaError_t launch_batch_t(const TraceArgs& A, const BatchArgs& Q, int ns, int det, int bvk,
-                           int grid, cudaStream_t s) {
-  const void* fn = batch_fn_t<R>(ns, det, bvk);
+                           int ss, int grid, cudaStream_t s) {
+  const void* fn = batch_fn_t<R>(ns, det, bvk, ss);
   void* args[] = {const_cast<TraceArgs*>(&A), const_cast<BatchArgs*>(&Q)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, batch_smem_bytes<R>(), s);
 }
@@ -746,13 +855,16 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   cudaError_t launch_adjoint_##SUFFIX(const TraceArgs& A, int det, int grid,                \
                                       cudaStream_t s) {                                     \
     return launch_adjoint_t<R>(A, det, grid, s);                                            \
-  }                                                                                         \
-  cudaError_t batch_blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int* blocks) {         \
-    return batch_blocks_per_sm_t<R>(ns, det, bvk, blocks);                                  \
+  }
+
+// defines the batched entry points of one real type (mcv_batch_fp32.cu / mcv_batch_fp64.cu)
+#define MCV_DEFINE_BATCH_ENTRY_POINTS(R, SUFFIX)                                            \
+  cudaError_t batch_blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int ss, int* blocks) { \
+    return batch_blocks_per_sm_t<R>(ns, det, bvk, ss, blocks);                              \
   }                                                                                         \
   cudaError_t launch_batch_##SUFFIX(const TraceArgs& A, const BatchArgs& Q, int ns, int det, \
-                                    int bvk, int grid, cudaStream_t s) {                    \
-    return launch_batch_t<R>(A, Q, ns, det, bvk, grid, s);                                  \
+                                    int bvk, int ss, int grid, cudaStream_t s) {            \
+    return launch_batch_t<R>(A, Q, ns, det, bvk, ss, grid, s);                              \
   }
 
 }  // namespace mcv

@@ -28,10 +28,11 @@ cudaError_t launch_chi2(const double* hist, const double* target, double c, int6
                         double* g, double* loss, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
 // batched launch: blocks per SM of its kernel (also sets the kernel's shared-memory limit;
-// call before the first launch of a shape), and the launch itself
-cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks);
+// call before the first launch of a shape), and the launch itself.  ss: every simulation
+// has the sample in A (kept in kernel parameter space).
+cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int ss, int* blocks);
 cudaError_t launch_batch(const TraceArgs& A, const BatchArgs& Q, int fp_mode, int ns, int det,
-                         int bvk, int grid, cudaStream_t s);
+                         int bvk, int ss, int grid, cudaStream_t s);
 // sets the message mcv_last_error() returns to the calling thread
 void set_last_error(const std::string& msg);
 

@@ -19,12 +19,12 @@ cudaError_t launch_detect_f64(const TraceArgs& A, const EventsArgs& E, int det, 
                               cudaStream_t s);
 cudaError_t launch_adjoint_f32(const TraceArgs& A, int det, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_f64(const TraceArgs& A, int det, int grid, cudaStream_t s);
-cudaError_t batch_blocks_per_sm_f32(int ns, int det, int bvk, int* blocks);
-cudaError_t batch_blocks_per_sm_f64(int ns, int det, int bvk, int* blocks);
+cudaError_t batch_blocks_per_sm_f32(int ns, int det, int bvk, int ss, int* blocks);
+cudaError_t batch_blocks_per_sm_f64(int ns, int det, int bvk, int ss, int* blocks);
 cudaError_t launch_batch_f32(const TraceArgs& A, const BatchArgs& Q, int ns, int det, int bvk,
-                             int grid, cudaStream_t s);
+                             int ss, int grid, cudaStream_t s);
 cudaError_t launch_batch_f64(const TraceArgs& A, const BatchArgs& Q, int ns, int det, int bvk,
-                             int grid, cudaStream_t s);
+                             int ss, int grid, cudaStream_t s);
 
 namespace {
 
@@ -96,15 +96,15 @@ cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, c
   return fp_mode == MCV_FP32 ? launch_adjoint_f32(A, det, grid, s) : launch_adjoint_f64(A, det, grid, s);
 }
 
-cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks) {
-  return fp_mode == MCV_FP32 ? batch_blocks_per_sm_f32(ns, det, bvk, blocks)
-                             : batch_blocks_per_sm_f64(ns, det, bvk, blocks);
+cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int ss, int* blocks) {
+  return fp_mode == MCV_FP32 ? batch_blocks_per_sm_f32(ns, det, bvk, ss, blocks)
+                             : batch_blocks_per_sm_f64(ns, det, bvk, ss, blocks);
 }
 
 cudaError_t launch_batch(const TraceArgs& A, const BatchArgs& Q, int fp_mode, int ns, int det,
-                         int bvk, int grid, cudaStream_t s) {
-  return fp_mode == MCV_FP32 ? launch_batch_f32(A, Q, ns, det, bvk, grid, s)
-                             : launch_batch_f64(A, Q, ns, det, bvk, grid, s);
+                         int bvk, int ss, int grid, cudaStream_t s) {
+  return fp_mode == MCV_FP32 ? launch_batch_f32(A, Q, ns, det, bvk, ss, grid, s)
+                             : launch_batch_f64(A, Q, ns, det, bvk, ss, grid, s);
 }
 
 cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s) {

@@ -133,15 +133,18 @@ struct SimP {
   double* tallies;
 };
 
-// The work queue of a batched launch: item k covers neutrons [c chunk, (c + 1) chunk) of
-// the simulation s with item0[s] <= k < item0[s + 1], c = k - item0[s].
+// The work queues of a batched launch: simulation s is cut into items of `chunk` neutron
+// ids, handed out in order by its own counter next[s].  A warp starts at its home
+// simulation -- the one holding neutron (total * warp / warps) of the batch in the order of
+// the nstart prefix sums -- and, when that queue is empty, moves on to the following
+// simulations (cyclically) until every queue is empty.
 struct BatchArgs {
   const void* sims;          // SimP<R>[nsims], device
-  const int64_t* item0;      // nsims + 1 prefix sums of the items per simulation, device
+  const int64_t* nstart;     // nsims + 1 prefix sums of the neutron counts, device
+  unsigned long long* next;  // nsims item counters, zero at launch, device
   int nsims;
-  int64_t n_items;
   int64_t chunk;             // neutrons per work item
-  unsigned long long* next;  // the queue's counter (zero at launch), device
+  int64_t total;             // nstart[nsims]
 };
 
 }  // namespace mcv

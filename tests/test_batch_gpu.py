@@ -44,6 +44,11 @@ def _same_sums(a, b, rtol=1e-12):
     return np.all(np.abs(a - b) <= rtol * np.abs(b))
 
 
+# FP32: the batched and the single-launch kernels are compiled separately, so an event's
+# last bits (and rarely its bin) may differ; at most 1e-4 of the events may change bin, each
+# change moving its weight out of one bin and into another
+FP32_MOVED = 2e-4
+
 COUNT_TALLIES = (B.T_NDET, B.T_NOVER, B.T_NMISS, B.T_NHIT, B.T_NEMIT)
 WEIGHT_TALLIES = (B.T_BEAMSTOP, B.T_WDET, B.T_WOVER)
 
@@ -78,8 +83,7 @@ def test_fp32_sweep_batch_matches_single_launches(ctx):
         total += hs.sum()
         moved += np.abs(hb - hs).sum()
         assert abs(tb[B.T_NDET] - ts[B.T_NDET]) <= max(1, 1e-4 * ts[B.T_NDET])
-    # the same kernel code: at most rounding-level moves of weight between bins
-    assert moved <= 1e-5 * total, (moved, total)
+    assert moved <= FP32_MOVED * total, (moved, total)
     b.close()
 
 
@@ -136,14 +140,14 @@ def test_tuner_keeps_histograms_and_picks_a_candidate(ctx):
     shape = b.tune(trial_neutrons=40000)
     for c, t in b.hists:
         assert not c.any() and not t.any()
-    assert shape["chunk"] in (1024, 4096, 16384, 65536)
+    assert shape["chunk"] in (512, 1024, 2048, 4096, 8192)
     assert 1 <= shape["blocks_per_sm"] <= 16
     b.run(sync=True)
     for wl, pair in zip(sims, b.hists):
         hb, tb = _np(pair)
         hs, ts = _np(ctx.trace(wl, fp_mode=B.FP32))
         assert abs(tb[B.T_NDET] - ts[B.T_NDET]) <= max(1, 1e-4 * ts[B.T_NDET])
-        assert np.abs(hb - hs).sum() <= 1e-5 * hs.sum()
+        assert np.abs(hb - hs).sum() <= FP32_MOVED * hs.sum()
     b.close()
 
 
@@ -197,7 +201,7 @@ def test_fullsize_crystal_batch_sampled_orientations(ctx):
         hb, tb = _np(hists[k])
         hs, ts = _np(ctx.trace(sims[k], fp_mode=B.FP32))
         assert abs(tb[B.T_NDET] - ts[B.T_NDET]) <= max(1, 1e-4 * ts[B.T_NDET])
-        assert np.abs(hb - hs).sum() <= 1e-5 * hs.sum()
+        assert np.abs(hb - hs).sum() <= FP32_MOVED * hs.sum()
         assert tb[B.T_NEMIT] == ts[B.T_NEMIT]
     b.close()
     del hists
@@ -218,6 +222,6 @@ def test_fullsize_sweep_batch_sampled_simulations(ctx):
         hb, tb = _np(b.hists[k])
         hs, ts = _np(ctx.trace(sims[k], fp_mode=B.FP32))
         assert abs(tb[B.T_NDET] - ts[B.T_NDET]) <= max(1, 1e-4 * ts[B.T_NDET])
-        assert np.abs(hb - hs).sum() <= 1e-5 * hs.sum()
+        assert np.abs(hb - hs).sum() <= FP32_MOVED * hs.sum()
     b.close()
     torch.cuda.empty_cache()
