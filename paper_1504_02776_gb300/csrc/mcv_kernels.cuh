@@ -41,27 +41,42 @@ struct LaunchOut {
   static __device__ __forceinline__ double* tallies(const TraceArgs& A) { return A.tallies; }
 };
 
+// one thread's running tallies: beam stop, detected and out-of-window weights, counts
+template <typename R>
+struct Tally {
+  Acc<R> bs, det, over;
+  Counts cnt;
+};
+
+// the tallies held in registers
+template <typename R>
+struct RegTally {
+  Tally<R> t;
+  __device__ __forceinline__ Tally<R>& get() { return t; }
+};
+
 // Forward policy: packets go to the packet slots and/or through the detector into the
 // histogram; order-0 packets go to the beam stop.  Out: where the histogram and tallies of
-// the simulation being traced are (read where used, so they hold no registers).
-template <typename R, int DET, class Out = LaunchOut>
+// the simulation being traced are (read where used, so they hold no registers).  Store:
+// where the thread's running tallies are kept.
+template <typename R, int DET, class Out = LaunchOut, class Store = RegTally<R>>
 struct Forward {
   static constexpr bool kWantsGs = false;
-  Acc<R> a_bs, a_det, a_over;
-  Counts cnt;
+  Store store;
   int err = 0;
 
   __device__ __forceinline__ void start(const Lane<R>&) {}
 
   __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const NeutronRng& rng,
                                        const Lane<R>& L, R we, R, R, R len_tot) {
-    if (L.o == 0 && len_tot > R(0)) cnt.nhit++;
+    Tally<R>& t = store.get();
+    if (L.o == 0 && len_tot > R(0)) t.cnt.nhit++;
     if (A.pk_order) store_slot<R>(A, L.idx * (Sof<R>(A).max_orders + 1) + L.o, L.n, we, L.nid, L.o);
     if (L.o == 0) {
-      a_bs.add(we);
+      t.bs.add(we);
       return;
     }
-    cnt.nemit++;
+    t.cnt.nemit++;
     if (DET == MCV_DET_NONE) return;
     Ray<R> pe = L.n;
     pe.w = we;
@@ -70,6 +85,7 @@ struct Forward {
 
   // a packet's detector result into the histogram and the tallies
   __device__ __forceinline__ void record(const TraceArgs& A, const Hit<R>& h) {
+    Tally<R>& t = store.get();
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
@@ -77,15 +93,20 @@ struct Forward {
       }
       double* hist = Out::hist(A);
       if (hist) atomicAdd(hist + h.bin, (double)h.w_det);
-      a_det.add(h.w_det);
-      cnt.ndet++;
+      t.det.add(h.w_det);
+      t.cnt.ndet++;
     } else if (h.bin == -2) {
-      a_over.add(h.w_det);
-      cnt.nover++;
+      t.over.add(h.w_det);
+      t.cnt.nover++;
     } else {
-      cnt.nmiss++;
+      t.cnt.nmiss++;
     }
   }
+
+  // the beam stop's share of a packet of order 0, and an incident neutron meeting the sample
+  __device__ __forceinline__ void beam_stop(R w) { store.get().bs.add(w); }
+  __device__ __forceinline__ void hit() { store.get().cnt.nhit++; }
+  __device__ __forceinline__ void emitted() { store.get().cnt.nemit++; }
 
   __device__ __forceinline__ void scatter(const TraceArgs&, const Lane<R>&, int, R,
                                           const Scatter<R>&, R, R) {}
@@ -102,13 +123,14 @@ struct Forward {
   // the warp's tallies into `tallies`; the accumulators start again from zero
   __device__ __forceinline__ void flush(const TraceArgs& A, int lane) {
     double* tallies = Out::tallies(A);
+    Tally<R>& t = store.get();
     if (tallies) {
-      const double v_bs = warp_sum(a_bs.value());
-      const double v_det = warp_sum(a_det.value());
-      const double v_over = warp_sum(a_over.value());
-      const uint32_t n_det = warp_sum(cnt.ndet), n_over = warp_sum(cnt.nover);
-      const uint32_t n_miss = warp_sum(cnt.nmiss), n_hit = warp_sum(cnt.nhit);
-      const uint32_t n_emit = warp_sum(cnt.nemit);
+      const double v_bs = warp_sum(t.bs.value());
+      const double v_det = warp_sum(t.det.value());
+      const double v_over = warp_sum(t.over.value());
+      const uint32_t n_det = warp_sum(t.cnt.ndet), n_over = warp_sum(t.cnt.nover);
+      const uint32_t n_miss = warp_sum(t.cnt.nmiss), n_hit = warp_sum(t.cnt.nhit);
+      const uint32_t n_emit = warp_sum(t.cnt.nemit);
       if (lane == 0) {
         atomicAdd(tallies + MCV_T_BEAMSTOP, v_bs);
         atomicAdd(tallies + MCV_T_WDET, v_det);
@@ -121,10 +143,7 @@ struct Forward {
       }
     }
     if (__any_sync(0xffffffffu, err != 0) && lane == 0 && A.err) atomicOr(A.err, 1);
-    a_bs = Acc<R>();
-    a_det = Acc<R>();
-    a_over = Acc<R>();
-    cnt = Counts();
+    t = Tally<R>();
   }
 };
 
@@ -184,9 +203,29 @@ struct BatchWarp {
   int home, v;
 };
 
+// Dynamic shared memory of the wave kernels: the warp queues, [the warps' batch slots,] and
+// every thread's running tallies (kept there rather than in registers).
+template <typename R>
+struct SmemTally {
+  size_t off;  // byte offset of the tallies in the dynamic shared memory
+  __device__ __forceinline__ Tally<R>& get() {
+    return reinterpret_cast<Tally<R>*>(g_wave_smem + off)[threadIdx.x];
+  }
+};
+
+template <typename R>
+constexpr size_t wave_kernel_smem_bytes() {
+  return wave_smem_bytes<R>() + (size_t)kThreads * sizeof(Tally<R>);
+}
+
+template <typename R>
+constexpr size_t batch_tally_offset() {
+  return wave_smem_bytes<R>() + (size_t)kWarps * sizeof(BatchWarp<R>);
+}
+
 template <typename R>
 constexpr size_t batch_smem_bytes() {
-  return wave_smem_bytes<R>() + (size_t)kWarps * sizeof(BatchWarp<R>);
+  return batch_tally_offset<R>() + (size_t)kThreads * sizeof(Tally<R>);
 }
 
 template <typename R>
@@ -286,7 +325,7 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
           if (assembly_segs<R, NS>(S, nr, seg) > 0)
             hit = true;
           else
-            pol.a_bs.add(nr.w * Mth<R>::exp(R(0)));  // order-0 packet, no material ahead
+            pol.beam_stop(nr.w * Mth<R>::exp(R(0)));  // order-0 packet, no material ahead
         }
       }
       const unsigned hm = __ballot_sync(kFull, hit);
@@ -334,11 +373,11 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
     if (L.active) {
       we = step_segments<R, NS, false>(A, S, L, st);
       if (L.o == 0) {
-        pol.a_bs.add(we);
-        if (st.len_tot > R(0)) pol.cnt.nhit++;
+        pol.beam_stop(we);
+        if (st.len_tot > R(0)) pol.hit();
       } else {
         to_det = true;
-        pol.cnt.nemit++;
+        pol.emitted();
       }
     }
     const unsigned dm = __ballot_sync(kFull, to_det);
@@ -426,7 +465,8 @@ __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     wave_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  Forward<R, DET> pol;
+  Forward<R, DET, LaunchOut, SmemTally<R>> pol{SmemTally<R>{wave_smem_bytes<R>()}};
+  pol.store.get() = Tally<R>();
   // each warp owns one contiguous range of the launch's neutron ids
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -472,7 +512,8 @@ __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     }
     __syncwarp();
   }
-  Forward<R, DET, SlotOut<R>> pol;
+  Forward<R, DET, SlotOut<R>, SmemTally<R>> pol{SmemTally<R>{batch_tally_offset<R>()}};
+  pol.store.get() = Tally<R>();
   const SlotJob<R, SS> job{A};
   QueuedIds<R> src;
   for (;;) {
@@ -697,7 +738,7 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const __grid_constant
 template <typename R, int NS, int DET, int KS>
 cudaError_t launch_trace_k(const TraceArgs& A, int grid, cudaStream_t s) {
   if (DET != MCV_DET_NONE && uses_waves(A, DET)) {
-    const size_t smem = wave_smem_bytes<R>();
+    const size_t smem = wave_kernel_smem_bytes<R>();
     cudaError_t e = cudaFuncSetAttribute(wave_kernel<R, NS, DET, KS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -750,7 +791,7 @@ template <typename R>
 cudaError_t blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
   const void* fn = ns <= 1 ? trace_fn_ns<R, 1>(det, bvk) : (ns == 2 ? trace_fn_ns<R, 2>(det, bvk)
                                                                     : trace_fn_ns<R, 4>(det, bvk));
-  const size_t smem = det != MCV_DET_NONE ? wave_smem_bytes<R>() : 0;
+  const size_t smem = det != MCV_DET_NONE ? wave_kernel_smem_bytes<R>() : 0;
   if (smem) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
