@@ -338,7 +338,8 @@ def run_ours(args):
     table = ctx.table(wl)
     counts, tallies = ctx.new_hist(wl.detector)
     stream = torch.cuda.current_stream()
-    first = rank * N
+    from paper_1504_02776_gb300.shards import shard
+    first, _ = shard(rank, world, N)
     sample32 = api.sample_struct(wl, B.FP32, table)
     det = api.detector_struct(wl.detector)
     beam = api.beam_struct(wl.beam)

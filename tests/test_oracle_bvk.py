@@ -161,3 +161,129 @@ def test_kernel_mean_weight_against_brute_force(seed):
     ref = _brute_force_direction(df, rot, ei)
     assert total > 0
     assert abs(total - ref) < 3e-3 * ref, (total, ref)
+
+
+# ---- accuracy near degenerate branches, against 40-digit arithmetic -------------------------
+def _mp_dynmat(mp, q):
+    coef = mp.mpf(10) / (27 * mp.mpf("1.66053906660e-27"))
+    D = mp.zeros(3, 3)
+    for n in BONDS:
+        qd = mp.mpf(A) / 2 * sum(mp.mpf(q[i]) * int(n[i]) for i in range(3))
+        c = coef * (1 - mp.cos(qd))
+        for i in range(3):
+            for j in range(3):
+                D[i, j] += c * int(n[i]) * int(n[j])
+    return D
+
+
+def _mp_modes(mp, q):
+    E, V = mp.eigsy(_mp_dynmat(mp, q))
+    order = sorted(range(3), key=lambda k: E[k])
+    lam = [E[k] for k in order]
+    vec = [[V[i, k] for i in range(3)] for k in order]
+    hbar, mev = mp.mpf("1.054571817e-34"), mp.mpf("1.602176634e-22")
+    return [hbar * mp.sqrt(max(x, 0)) / mev for x in lam], lam, vec
+
+
+def test_near_degenerate_branches_against_40_digit_reference():
+    """Along [100] the two transverse branches coincide; slightly off that axis they are
+    nearly degenerate (relative gaps 1e-2 .. 1e-7).  The eigenvalues must keep full relative
+    accuracy, and each eigenvector its accuracy over the gap (the trigonometric cubic alone
+    loses both there)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    base = np.array([2.1, 0.0, 0.0])
+    for tilt in (1e-1, 1e-2, 1e-3, 1e-4):
+        for direction in ([0, 1, 0], [0, 0.6, 0.8], [0, 1, 1]):
+            q = base + tilt * np.array(direction, float)
+            hw, ev = oracle.bvk_modes(WL, q)
+            hw_ref, lam, vec = _mp_modes(mp, q)
+            lmax = float(lam[2])
+            for b in range(3):
+                assert abs(hw[b] - float(hw_ref[b])) <= 1e-14 * float(hw_ref[2]) * float(hw_ref[2]) / max(float(hw_ref[b]), 1e-300) + 1e-15 * float(hw_ref[b]), (tilt, b)
+                gap = min([abs(float(lam[b] - lam[k])) for k in range(3) if k != b])
+                dot = abs(sum(ev[i, b] * float(vec[b][i]) for i in range(3)))
+                assert 1.0 - dot <= (8e-16 * lmax / gap) ** 2 + 1e-15, (tilt, b, 1.0 - dot)
+
+
+def _mp_factor(mp, speed, d, u, rot):
+    """The one-phonon factor of one event in 40-digit arithmetic: the same sampling (u), the
+    roots of g bracketed on the same 32 sub-intervals and solved to full precision."""
+    hbar, mn, e = mp.mpf("1.054571817e-34"), mp.mpf("1.67492749804e-27"), mp.mpf("1.602176634e-19")
+    kB, amu = mp.mpf("1.380649e-23"), mp.mpf("1.66053906660e-27")
+    mevv2 = mn / 2 / (e * mp.mpf("1e-3"))
+    kpv = mn / hbar * mp.mpf("1e-10")
+    mev_j = 1 / (e * mp.mpf("1e-3"))
+    M = 27 * amu
+    coef = mp.mpf(10) / M
+    c, sn = mp.cos(rot), mp.sin(rot)
+    u = [mp.mpf(x) for x in u]
+    d = [mp.mpf(x) for x in d]
+    speed = mp.mpf(speed)
+    ct = 2 * u[0] - 1
+    st = 2 * mp.sqrt(u[0] * (1 - u[0]))
+    ph = 2 * mp.pi * u[1]
+    df = (st * mp.cos(ph), st * mp.sin(ph), ct)
+    mode = min(max(int(mp.floor(6 * u[2])), 0), 5)
+    b, s = mode % 3, (1 if mode < 3 else -1)
+    Ei, ki = mevv2 * speed**2, kpv * speed
+
+    def at(E):
+        kf = kpv * mp.sqrt(E / mevv2)
+        Q = [ki * d[i] - kf * df[i] for i in range(3)]
+        bx, by, bz = c * Q[0] - sn * Q[2], Q[1], sn * Q[0] + c * Q[2]
+        Qc = (bz, bx, by)
+        Ev, V = mp.eigsy(_mp_dynmat(mp, Qc))
+        k = sorted(range(3), key=lambda j: Ev[j])[b]
+        hw = hbar * mp.sqrt(max(Ev[k], 0)) * mev_j
+        return Ei - E - s * hw, hw, Qc, [V[i, k] for i in range(3)], kf
+
+    wmax = hbar * mp.sqrt(24 * coef) * mev_j
+    lo = 0 if s > 0 else Ei
+    hi = Ei if s > 0 else Ei + wmax
+    step = (hi - lo) / 32
+    gk = [at(lo + k * step)[0] for k in range(33)]
+    br = [k for k in range(32) if (gk[k] > 0) != (gk[k + 1] > 0)]
+    pick = min(max(int(mp.floor(u[3] * len(br))), 0), len(br) - 1)
+    kb = br[pick]
+    Ef = mp.findroot(lambda E: at(E)[0], (lo + kb * step, lo + (kb + 1) * step),
+                     solver="anderson")
+    g, hw, Qc, ev, kf = at(Ef)
+    gp = mp.diff(lambda E: at(E)[0], Ef)
+    kT = kB * 300 * mev_j
+    nB = 1 / (mp.exp(hw / kT) - 1)
+    Ns = nB + 1 if s > 0 else nB
+    qe = sum(Qc[i] * ev[i] for i in range(3))
+    Q2 = sum(x * x for x in Qc)
+    dw = mp.exp(-Q2 * mp.mpf(mi.Bvk().msd_A2) / 3)
+    Rb = hbar**2 / (2 * M) * mp.mpf("1e20") * mev_j * qe * qe / hw
+    return 6 * len(br) * (kf / ki) * dw * Rb * Ns / abs(gp)
+
+
+def test_kernel_factor_against_40_digit_reference():
+    """Sampled events of the crystal run (multiple scattering, 30 degrees): the oracle's
+    factor agrees with the 40-digit evaluation within a few epsilon times the event's share
+    of the condition estimate."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    wl = mi.config3(rot_deg=30.0, n=400)
+    o = oracle.trace(wl, packets=True)
+    pk = o["packets"]
+    S = wl.max_orders + 1
+    rng = np.random.default_rng(5)
+    cand = [(i, k) for i in range(wl.n) for k in range(1, S) if pk["order"][i * S + k] >= 0]
+    checked = 0
+    for j in rng.choice(len(cand), 12, replace=False):
+        i, k = cand[j]
+        prev, cur = i * S + k - 1, i * S + k
+        v = np.array([pk["vx"][prev], pk["vy"][prev], pk["vz"][prev]])
+        sp = float(np.linalg.norm(v))
+        u = np.concatenate([oracle.uniforms(wl.seed, wl.sim_id, i, k - 1, 1),
+                            oracle.uniforms(wl.seed, wl.sim_id, i, k - 1, 2)])
+        got = oracle.kernel_scatter(wl, mi.K_BVK, sp, v / sp, u)
+        ref = _mp_factor(mp, sp, v / sp, u, mp.radians(30))
+        err = abs(got["factor"] / float(ref) - 1.0)
+        dk = pk["kappa"][cur] - pk["kappa"][prev]
+        assert err <= 4 * 2.2e-16 * dk + 1e-15, (i, k, err, dk)
+        checked += 1
+    assert checked == 12
