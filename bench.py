@@ -101,7 +101,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -453,11 +453,12 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
             "unit": "Tops/s", "frac": achieved / peak_ops,
             "traffic": None if traffic_per_n is None else traffic_per_n * N,
-            "kernel": "trace_kernel<float,1,TUBES>", "kernel_ms": trace_ms,
+            "kernel": "wave_kernel<float,1,TUBES,powder>", "kernel_ms": trace_ms,
             "ops_per_launch": ops,
             "peak_basis": "%d SMs x 128 FP32/INT32 lanes x %.0f MHz (max SM clock, "
                           "MEASURED_PEAKS.json)" % (props.multi_processor_count, sm_mhz),
-            "hbm_gbs_algorithmic": (N * 0 + t[B.T_NDET] * 16) / (trace_ms / 1e3) / 1e9,
+            # histogram read-modify-writes, one 8-byte word per detected event (read + write)
+            "hbm_gbs_algorithmic": t[B.T_NDET] * 16 / (trace_ms / 1e3) / 1e9,
             "hbm_peak_gbs_measured": peaks.get("hbm_gbs")}
 
     line = {
