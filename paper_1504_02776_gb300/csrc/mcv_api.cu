@@ -1,6 +1,7 @@
 // C ABI of libmcv.so (declared in include/mcv.h): argument checking, derived constants,
 // launch shapes.  No call here allocates device memory except mcv_create.  The batched
 // launches are in mcv_batch.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +49,9 @@ mcv_status build_beam(const mcv_beam_params* b, mcv::BeamP<double>* B) {
   B->t0 = (b->l1_m - b->z0_m) / B->speed0;
   B->t0_hi = (float)B->t0;
   B->t0_lo = (float)(B->t0 - (double)B->t0_hi);
+  B->energy_positive = b->ei_rel_sigma * 8.7 < 1.0 ? 1 : 0;
+  B->x_safe = INFINITY;
+  B->y_safe = INFINITY;
   return MCV_OK;
 }
 
@@ -213,6 +217,39 @@ mcv_status build_detector(const mcv_detector* d, mcv::DetP<double>* D) {
   return MCV_OK;
 }
 
+// Footprint bounds beyond which a neutron misses the sample for every divergence the
+// uniforms can give: the sample lies within radius r of the vertical axis and |y| <= hh; a
+// ray from the start plane z = -z0 with divergence angles |a| <= 8.66 div (Box-Muller
+// normals of uniforms >= 2^-54 stay within 8.65) moves sideways by at most
+// (z0 + r) tan(8.66 div) before it has passed the sample.  With a 1 % and 1 um margin.
+void set_miss_bounds(const mcv::SampleP<double>& S, mcv::BeamP<double>* B) {
+  B->x_safe = INFINITY;
+  B->y_safe = INFINITY;
+  if (!B->energy_positive) return;
+  double r = 0.0, hh = 0.0;
+  for (int j = 0; j < S.ns; ++j) {
+    const mcv::ScatP<double>& c = S.s[j];
+    double rj = 0.0, hj = 0.0;
+    if (c.shape == MCV_SHAPE_SOLID_CYL) {
+      rj = c.dim0;
+      hj = 0.5 * c.dim1;
+    } else if (c.shape == MCV_SHAPE_HOLLOW_CYL) {
+      rj = c.dim1;
+      hj = 0.5 * c.dim2;
+    } else {
+      rj = 0.5 * std::hypot(c.dim0, c.dim2);
+      hj = 0.5 * c.dim1;
+    }
+    r = std::max(r, rj);
+    hh = std::max(hh, hj);
+  }
+  const double a = 8.66 * B->div;
+  if (!(a < 1.0)) return;
+  const double shift = (B->z0 + r) * std::tan(a) * 1.01 + 1e-6;
+  B->x_safe = r + shift;
+  B->y_safe = hh + shift;
+}
+
 // float copies of the parameter blocks for the FP32 kernels
 void cast_beam(const mcv::BeamP<double>& d, mcv::BeamP<float>* f) {
   f->ei = (float)d.ei;
@@ -226,6 +263,12 @@ void cast_beam(const mcv::BeamP<double>& d, mcv::BeamP<float>* f) {
   f->t0 = d.t0;
   f->t0_hi = d.t0_hi;
   f->t0_lo = d.t0_lo;
+  f->energy_positive = d.energy_positive;
+  // rounded up: the float bounds stay on the safe side
+  f->x_safe = (float)d.x_safe;
+  if ((double)f->x_safe < d.x_safe) f->x_safe = std::nextafter(f->x_safe, INFINITY);
+  f->y_safe = (float)d.y_safe;
+  if ((double)f->y_safe < d.y_safe) f->y_safe = std::nextafter(f->y_safe, INFINITY);
 }
 
 void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
@@ -493,6 +536,7 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   } else {
     st = build_beam(beam, &A.Bd);
     if (st != MCV_OK) return st;
+    set_miss_bounds(A.Sd, &A.Bd);
   }
   const bool fused = det != nullptr;
   if (fused) {

@@ -64,6 +64,7 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
       return fail(MCV_EINVAL, who + "sample fp_mode differs from the batch's");
     st = build_beam(s.beam, &d.B);
     if (st != MCV_OK) return fail(st, who + mcv_last_error());
+    set_miss_bounds(d.S, &d.B);
     if (s.n < 0 || s.n > kMaxNeutrons || s.first_id < 0 ||
         s.first_id > (((int64_t)1 << 62) - s.n))
       return fail(MCV_EINVAL, who + "bad neutron range");

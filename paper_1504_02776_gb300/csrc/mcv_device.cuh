@@ -197,37 +197,65 @@ template <>
 __device__ __forceinline__ const BeamP<double>& Bof<double>(const TraceArgs& A) { return A.Bd; }
 
 // ---- source -----------------------------------------------------------------------------
-// Synthetic beam at the sample: Gaussian energy, uniform footprint, Gaussian divergence.
-// Returns false when the drawn energy is not positive (no packet).
+// Synthetic beam at the sample: Gaussian energy (random block 0), uniform footprint
+// (block 1), Gaussian divergence (block 2).  The position and direction come first: they
+// alone decide whether the neutron meets the sample, and a neutron that misses it needs no
+// energy when every energy draw is positive (BeamP::energy_positive).
+// aux: what the energy part needs from the direction part (FP32: tan^2 ax + tan^2 ay).
+// The footprint alone already settles most misses: a neutron whose footprint lies outside
+// (x_safe, y_safe) cannot reach the sample whatever its divergence (BeamP::x_safe).
 template <typename R>
-__device__ __forceinline__ bool make_beam(const BeamP<R>& B, const NeutronRng& rng, Ray<R>* n);
+__device__ __forceinline__ void beam_footprint(const BeamP<R>& B, const NeutronRng& rng,
+                                               Ray<R>* n);
+template <typename R>
+__device__ __forceinline__ void beam_divergence(const BeamP<R>& B, const NeutronRng& rng,
+                                                Ray<R>* n, R* aux);
+template <typename R>
+__device__ __forceinline__ bool beam_energy(const BeamP<R>& B, const NeutronRng& rng, R aux,
+                                            Ray<R>* n);
 
 template <>
-__device__ __forceinline__ bool make_beam<double>(const BeamP<double>& B, const NeutronRng& rng,
-                                                  Ray<double>* n) {
+__device__ __forceinline__ void beam_footprint<double>(const BeamP<double>& B,
+                                                       const NeutronRng& rng, Ray<double>* n) {
+  double u0, u1;
+  rng.pair<double>(-1, 1, &u0, &u1);
+  n->x = (u0 - 0.5) * B.width;
+  n->y = (u1 - 0.5) * B.height;
+  n->z = -B.z0;
+  n->w = 1.0;
+}
+
+template <>
+__device__ __forceinline__ void beam_divergence<double>(const BeamP<double>& B,
+                                                        const NeutronRng& rng, Ray<double>* n,
+                                                        double* aux) {
+  using M = Mth<double>;
+  double u0, u1, s, c;
+  rng.pair<double>(-1, 2, &u0, &u1);
+  M::sincos2pi(u1, &s, &c);
+  const double rr = M::sqrt(-2.0 * M::log(u0));
+  const double ax = B.div * (rr * c), ay = B.div * (rr * s);
+  const double tx = M::tan(ax), ty = M::tan(ay);
+  const double norm = M::sqrt(tx * tx + ty * ty + 1.0);
+  n->dx = tx / norm;
+  n->dy = ty / norm;
+  n->dz = 1.0 / norm;
+  *aux = 0.0;
+}
+
+template <>
+__device__ __forceinline__ bool beam_energy<double>(const BeamP<double>& B,
+                                                    const NeutronRng& rng, double,
+                                                    Ray<double>* n) {
   using M = Mth<double>;
   double u0, u1, s, c;
   rng.pair<double>(-1, 0, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const double zE = M::sqrt(-2.0 * M::log(u0)) * c;
   const double E = B.ei * (1.0 + B.rel * zE);
-  rng.pair<double>(-1, 1, &u0, &u1);
-  n->x = (u0 - 0.5) * B.width;
-  n->y = (u1 - 0.5) * B.height;
-  rng.pair<double>(-1, 2, &u0, &u1);
-  M::sincos2pi(u1, &s, &c);
-  const double rr = M::sqrt(-2.0 * M::log(u0));
-  const double ax = B.div * (rr * c), ay = B.div * (rr * s);
   if (!(E > 0.0)) return false;
-  const double tx = M::tan(ax), ty = M::tan(ay);
-  const double norm = M::sqrt(tx * tx + ty * ty + 1.0);
-  n->dx = tx / norm;
-  n->dy = ty / norm;
-  n->dz = 1.0 / norm;
   n->speed = M::sqrt(E / kMeVPerV2);
-  n->z = -B.z0;
   n->t.set((B.l1 - B.z0) / (n->speed * n->dz));
-  n->w = 1.0;
   return true;
 }
 
@@ -236,36 +264,68 @@ __device__ __forceinline__ bool make_beam<double>(const BeamP<double>& B, const 
 // keeps ~1e-12 s accuracy: speed = v0 (1 + eta), eta = d/(1 + sqrt(1 + d)), d = rel z;
 // path/speed = t0 (1 + xi)/(1 + eta), xi = e/(1 + sqrt(1 + e)), e = tan^2 ax + tan^2 ay.
 template <>
-__device__ __forceinline__ bool make_beam<float>(const BeamP<float>& B, const NeutronRng& rng,
-                                                 Ray<float>* n) {
-  using M = Mth<float>;
-  float u0, u1, s, c;
-  rng.pair<float>(-1, 0, &u0, &u1);
-  M::sincos2pi(u1, &s, &c);
-  const float zE = M::sqrt(-2.0f * M::log(u0)) * c;
-  const float dE = B.rel * zE;
+__device__ __forceinline__ void beam_footprint<float>(const BeamP<float>& B,
+                                                      const NeutronRng& rng, Ray<float>* n) {
+  float u0, u1;
   rng.pair<float>(-1, 1, &u0, &u1);
   n->x = (u0 - 0.5f) * B.width;
   n->y = (u1 - 0.5f) * B.height;
+  n->z = -B.z0;
+  n->w = 1.0f;
+}
+
+template <>
+__device__ __forceinline__ void beam_divergence<float>(const BeamP<float>& B,
+                                                       const NeutronRng& rng, Ray<float>* n,
+                                                       float* aux) {
+  using M = Mth<float>;
+  float u0, u1, s, c;
   rng.pair<float>(-1, 2, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const float rr = M::sqrt(-2.0f * M::log(u0));
   const float ax = B.div * (rr * c), ay = B.div * (rr * s);
-  if (!(1.0f + dE > 0.0f)) return false;
   const float tx = M::tan(ax), ty = M::tan(ay);
   const float e = tx * tx + ty * ty;
   const float sq = M::sqrt(1.0f + e);
   n->dx = tx / sq;
   n->dy = ty / sq;
   n->dz = 1.0f / sq;
+  *aux = e;
+}
+
+template <>
+__device__ __forceinline__ bool beam_energy<float>(const BeamP<float>& B,
+                                                   const NeutronRng& rng, float e,
+                                                   Ray<float>* n) {
+  using M = Mth<float>;
+  float u0, u1, s, c;
+  rng.pair<float>(-1, 0, &u0, &u1);
+  M::sincos2pi(u1, &s, &c);
+  const float zE = M::sqrt(-2.0f * M::log(u0)) * c;
+  const float dE = B.rel * zE;
+  if (!(1.0f + dE > 0.0f)) return false;
+  const float sq = M::sqrt(1.0f + e);
   const float eta = dE / (1.0f + M::sqrt(1.0f + dE));
   const float xi = e / (1.0f + sq);
   n->speed = B.speed0 * (1.0f + eta);
-  n->z = -B.z0;
   n->t.set2(B.t0_hi, B.t0_lo);
   n->t.add(B.t0_hi * ((xi - eta) / (1.0f + eta)));
-  n->w = 1.0f;
   return true;
+}
+
+// The whole source draw; returns false when the drawn energy is not positive (no packet).
+template <typename R>
+__device__ __forceinline__ bool make_beam(const BeamP<R>& B, const NeutronRng& rng, Ray<R>* n) {
+  R aux;
+  beam_footprint<R>(B, rng, n);
+  beam_divergence<R>(B, rng, n, &aux);
+  return beam_energy<R>(B, rng, aux, n);
+}
+
+// the footprint is far enough from the sample that the neutron misses it for any divergence
+template <typename R>
+__device__ __forceinline__ bool surely_misses(const BeamP<R>& B, const Ray<R>& n) {
+  return Mth<R>::fabs(n.x) > B.x_safe || Mth<R>::fabs(n.y) > B.y_safe;
 }
 
 // ---- geometry ----------------------------------------------------------------------------

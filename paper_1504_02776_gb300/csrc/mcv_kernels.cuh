@@ -176,8 +176,14 @@ struct QPacket {  // a transmitted packet of order >= 1 on its way to the detect
 };
 
 template <typename R>
+struct QFoot {  // a footprint that may lead into the sample
+  R x, y;
+  int64_t nid;
+};
+
+template <typename R>
 constexpr size_t wave_smem_bytes() {
-  return (size_t)kWarps * kQueue * (sizeof(QNeutron<R>) + sizeof(QPacket<R>));
+  return (size_t)kWarps * kQueue * (sizeof(QNeutron<R>) + sizeof(QPacket<R>) + sizeof(QFoot<R>));
 }
 
 extern __shared__ __align__(16) unsigned char g_wave_smem[];
@@ -299,8 +305,11 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
   QNeutron<R>* hq = reinterpret_cast<QNeutron<R>*>(g_wave_smem) + wib * kQueue;
   QPacket<R>* dq = reinterpret_cast<QPacket<R>*>(g_wave_smem + (size_t)kWarps * kQueue *
                                                    sizeof(QNeutron<R>)) + wib * kQueue;
+  QFoot<R>* fq = reinterpret_cast<QFoot<R>*>(
+                     g_wave_smem + (size_t)kWarps * kQueue * (sizeof(QNeutron<R>) + sizeof(QPacket<R>))) +
+                 wib * kQueue;
   int64_t next = lo;
-  int hq_n = 0, dq_n = 0;
+  int hq_n = 0, dq_n = 0, fq_n = 0;
   Lane<R> L;
   L.active = false;
   L.o = 0;
@@ -309,20 +318,64 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
   for (;;) {
     const unsigned idle = __ballot_sync(kFull, !L.active);
     const int n_idle = __popc(idle);
-    // ---- source stage
-    while (hq_n < n_idle && (next < hi || src.more(&next, &hi))) {
-      const int64_t i = next + lane;
+    // ---- source stage.  Footprints first, 32 new ids at a time: a neutron whose footprint
+    // cannot lead into the sample only adds its weight to the beam stop; the others are
+    // queued.  Then 32 queued footprints at a time get their divergence and, where they meet
+    // the sample, their energy: those are queued for the sample stage, the rest add to the
+    // beam stop.  (Misses need no energy: BeamP::x_safe is finite only when every energy
+    // draw is positive.)
+    while (hq_n < n_idle && (fq_n > 0 || next < hi || src.more(&next, &hi))) {
+      if (fq_n < 32 && (next < hi || src.more(&next, &hi))) {
+        const int64_t i = next + lane;
+        bool maybe = false;
+        Ray<R> nr;
+        int64_t nid = 0;
+        if (i < hi) {
+          nid = job.first_id() + i;
+          const NeutronRng rng(job.seed(), job.sim_id(), nid);
+          beam_footprint<R>(job.B(), rng, &nr);
+          if (!surely_misses<R>(job.B(), nr))
+            maybe = true;
+          else if (!(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0)))
+            pol.beam_stop(nr.w * Mth<R>::exp(R(0)));  // order-0 packet, no material ahead
+        }
+        const unsigned mm = __ballot_sync(kFull, maybe);
+        if (maybe) {
+          QFoot<R>& f = fq[fq_n + __popc(mm & lt_mask)];
+          f.x = nr.x;
+          f.y = nr.y;
+          f.nid = nid;
+        }
+        fq_n += __popc(mm);
+        next += 32;
+        __syncwarp();
+        continue;
+      }
+      const int take_f = fq_n < 32 ? fq_n : 32;
       bool hit = false;
       Ray<R> nr;
       int64_t nid = 0;
-      if (i < hi) {
-        nid = job.first_id() + i;
+      if (lane < take_f) {
+        const QFoot<R>& f = fq[fq_n - take_f + lane];
+        nid = f.nid;
+        nr.x = f.x;
+        nr.y = f.y;
+        nr.z = -job.B().z0;
+        nr.w = R(1);
+      }
+      fq_n -= take_f;
+      __syncwarp();
+      if (lane < take_f) {
         const NeutronRng rng(job.seed(), job.sim_id(), nid);
-        bool ok = make_beam<R>(job.B(), rng, &nr);
+        R aux;
+        beam_divergence<R>(job.B(), rng, &nr, &aux);
+        Seg<R> seg[2 * NS];
+        const bool meets = assembly_segs<R, NS>(S, nr, seg) > 0;
+        bool ok = (meets || !job.B().energy_positive) ? beam_energy<R>(job.B(), rng, aux, &nr)
+                                                      : true;
         ok = ok && !(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0));
         if (ok) {
-          Seg<R> seg[2 * NS];
-          if (assembly_segs<R, NS>(S, nr, seg) > 0)
+          if (meets)
             hit = true;
           else
             pol.beam_stop(nr.w * Mth<R>::exp(R(0)));  // order-0 packet, no material ahead
@@ -342,7 +395,6 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
         q.nid = nid;
       }
       hq_n += __popc(hm);
-      next += 32;
       __syncwarp();
     }
     const int take = min(n_idle, hq_n);
@@ -408,7 +460,7 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
     // ---- detector stage: full batches now, the remainder once the range is done.  This is
     // the only place packets are detected, so a packet's arithmetic does not depend on the
     // batch it falls in (or on the launch shape).
-    bool done = !__any_sync(kFull, L.active) && next >= hi && hq_n == 0;
+    bool done = !__any_sync(kFull, L.active) && next >= hi && hq_n == 0 && fq_n == 0;
     if (done) done = !src.more(&next, &hi);
     while (dq_n >= 32 || (done && dq_n > 0)) {
       const int take = dq_n < 32 ? dq_n : 32;

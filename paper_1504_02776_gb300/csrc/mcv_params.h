@@ -26,6 +26,12 @@ struct BeamP {
   R speed0;            // sqrt(ei / kMeVPerV2)
   double t0;           // (l1 - z0) / speed0
   float t0_hi, t0_lo;  // t0 as a float pair
+  // every energy draw is positive: rel z > -1 for every Box-Muller z the uniforms can give
+  // (|z| <= sqrt(-2 ln 2^-54) = 8.65 for uniforms >= 2^-54), checked as rel * 8.7 < 1
+  int energy_positive;
+  // footprints with |x| > x_safe or |y| > y_safe miss the sample for every divergence the
+  // uniforms can give (+inf: no such shortcut); set from the sample's bounding cylinder
+  R x_safe, y_safe;
 };
 
 template <typename R>
