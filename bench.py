@@ -32,11 +32,14 @@ WORKLOAD = ("powder S(Q,E), hollow cylinder r_out=1 cm wall 2 mm h=4 cm, Ei=100 
 N_DEFAULT = 100_000_000
 
 # Algorithmic cost model of the path (lane operations: FP32/INT32 arithmetic, each
-# transcendental counted as its instruction sequence), per event type.  Derivation in
-# DESIGN.md ("Roofline").  Event counts come from the run's own tallies.
+# transcendental counted as its instruction sequence, a Philox4x32-10 block as ~110), per
+# event type.  Derivation in DESIGN.md ("Roofline").  Event counts come from the run's own
+# tallies, and the share of footprints that can lead into the sample from the geometry.
 COST = {
-    "beam": 480,        # 3 Philox blocks, 2 Box-Muller pairs, 2 tan, direction, speed, time
-    "order": 85,        # segments ahead (hollow cylinder: 2 cylinder spans + slab), tau, exp
+    "footprint": 130,   # 1 Philox block, footprint, sure-miss test
+    "direction": 190,   # 1 Philox block, Box-Muller, 2 tan, normalisation
+    "segments": 85,     # segments ahead (hollow cylinder: 2 cylinder spans + slab), tau, exp
+    "energy": 170,      # 1 Philox block, Box-Muller, speed, time of flight to the sample
     "scatter": 465,     # scattering point (Philox, exp, move) + S(Q,E) kernel (2 Philox,
                         # kinematics, 2 sqrt, table lookup, rotation with sincos)
     "detect": 280,      # circle crossing, atan2, 3 tube chords, absorption (Philox, expm1,
@@ -45,12 +48,43 @@ COST = {
 }
 
 
-def ops_per_step(n, t):
-    """Lane operations of one step from its event counts (n incident neutrons; tallies t)."""
+def maybe_fraction(wl):
+    """Share of footprints inside the sure-miss bounds (uniform footprint): the bounds are
+    the sample's radius / half height plus the sideways move over (z0 + r) at the largest
+    divergence the uniforms can give (8.66 sigma), with a 1 % and 1 um margin."""
+    def radius(s):
+        if s.kind == 0:
+            return s.dims[0]
+        if s.kind == 1:
+            return s.dims[1]
+        return 0.5 * math.hypot(s.dims[0], s.dims[2])
+
+    def half_height(s):
+        return 0.5 * (s.dims[2] if s.kind == 1 else s.dims[1])
+
+    r = max(radius(s) for s in wl.scatterers)
+    hh = max(half_height(s) for s in wl.scatterers)
+    b = wl.beam
+    shift = (b.z0_m + r) * math.tan(8.66 * b.div_sigma_rad) * 1.01 + 1e-6
+    fx = 1.0 if b.width_m <= 0 else min(1.0, 2 * (r + shift) / b.width_m)
+    fy = 1.0 if b.height_m <= 0 else min(1.0, 2 * (hh + shift) / b.height_m)
+    return fx * fy
+
+
+def ops_per_step(n, t, wl):
+    """Lane operations of one step from its event counts (n incident neutrons; tallies t):
+    every incident neutron's footprint, the direction and first segments of the footprints
+    that may lead into the sample, the energy and order-0 step of those that meet it, and
+    per scattering the kernel, the next order's segments and the emitted packet's detector
+    trace; one histogram add per detected event."""
     from paper_1504_02776_gb300 import binding as B
     emitted = t[B.T_NEMIT]
-    return (n * (COST["beam"] + COST["order"]) + emitted * (COST["scatter"] + COST["order"]
-            + COST["detect"]) + t[B.T_NDET] * COST["hist"])
+    hits = t[B.T_NHIT]
+    maybe = n * maybe_fraction(wl)
+    return (n * COST["footprint"] + maybe * (COST["direction"] + COST["segments"])
+            + hits * (COST["energy"] + COST["segments"])
+            + emitted * (COST["scatter"] + COST["segments"] + COST["detect"])
+            + t[B.T_NDET] * COST["hist"])
 
 
 def csrc_hash():
@@ -447,7 +481,7 @@ def run_ours(args):
     peaks = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * sm_mhz * 1e6   # FP32/INT32 lanes x clock
-    ops = ops_per_step(N, t)
+    ops = ops_per_step(N, t, wl)
     achieved = ops / (trace_ms / 1e3)
     traffic_per_n = load_traffic()
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,

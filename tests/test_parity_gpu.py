@@ -82,6 +82,29 @@ def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     assert t[B.T_NEMIT] == to[oracle.T_NPACK0 + 1:oracle.T_NPACK0 + 8].sum()
 
 
+def _wide_divergent(n):
+    """A 12 x 12 cm beam with 60 mrad divergence on the powder cylinder: footprints just inside
+    the source stage's sure-miss bounds reach the sample only through the tails of the
+    divergence, so a bound that were too tight would lose hits."""
+    wl = _small_c2(n)
+    return wl.replace(beam=mi.Beam(ei_mev=100.0, ei_rel_sigma=0.01, div_sigma_rad=0.06,
+                                   width_m=0.12, height_m=0.12))
+
+
+@pytest.mark.parametrize("fp", [B.FP64, B.FP32])
+def test_sure_miss_bounds_keep_every_hit(ctx, fp):
+    wl = _wide_divergent(200000)
+    counts, tallies = ctx.trace(wl, fp_mode=fp)
+    to = oracle.trace(wl, packets=False, hist=False)["tallies"]
+    t = tallies.cpu().numpy()
+    if fp == B.FP64:
+        assert t[B.T_NHIT] == to[oracle.T_NHIT]
+        assert abs(t[B.T_BEAMSTOP] - to[oracle.T_BEAMSTOP]) <= 1e-12 * to[oracle.T_BEAMSTOP]
+    else:
+        assert abs(t[B.T_NHIT] - to[oracle.T_NHIT]) <= 2
+        assert abs(t[B.T_BEAMSTOP] - to[oracle.T_BEAMSTOP]) <= 1e-5 * to[oracle.T_BEAMSTOP]
+
+
 def test_fp64_stored_beam_path_matches_fused(ctx):
     wl = _small_c2(20000)
     beam = ctx.beam(wl, fp_mode=B.FP64)
