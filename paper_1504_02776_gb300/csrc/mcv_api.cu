@@ -376,6 +376,18 @@ int grid_for(mcv_ctx* ctx, int64_t items, int per_sm) {
   return (int)(g < 1 ? 1 : g);
 }
 
+PhiloxKeys philox_keys(uint32_t seed, uint32_t sim_id) {
+  PhiloxKeys K;
+  uint32_t k0 = seed, k1 = sim_id;
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = k0;
+    K.k1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+
 TofWin tof_window(double tof_min_s, double tof_max_s, int n_tof) {
   TofWin w;
   w.n_tof = n_tof;
@@ -501,6 +513,7 @@ mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint
   if (n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;
+  A.keys = philox_keys(seed, sim_id);
   A.first_id = first_id;
   A.n = n;
   A.pk_x = out->x;
@@ -554,6 +567,7 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   if (n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;
+  A.keys = philox_keys(seed, sim_id);
   A.first_id = first_id;
   A.n = n;
   A.stop_on_zero = 1;
@@ -614,6 +628,7 @@ mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
   if (packets->n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;
+  A.keys = philox_keys(seed, sim_id);
   A.n = packets->n;
   A.in_x = packets->x;
   A.in_y = packets->y;
@@ -674,6 +689,7 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
   if (e != cudaSuccess) return cuda_fail(e, "zero kernel launch");
   A.seed = seed;
   A.sim_id = sim_id;
+  A.keys = philox_keys(seed, sim_id);
   A.first_id = first_id;
   A.n = n;
   A.err = ctx->d_err;

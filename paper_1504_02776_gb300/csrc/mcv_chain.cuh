@@ -88,13 +88,13 @@ __device__ __forceinline__ R step_segments(const TraceArgs& A, const SampleP<R>&
 constexpr int kKernelsPowder = (1 << MCV_KERNEL_ISO) | (1 << MCV_KERNEL_SQE);
 constexpr int kKernelsAll = kKernelsPowder | (1 << MCV_KERNEL_BVK);
 
-template <typename R, int NS, int KS, class P>
+template <typename R, int NS, int KS, class P, class Rng>
 __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R>& S,
-                                             const NeutronRng& rng, Lane<R>& L,
+                                             const Rng& rng, Lane<R>& L,
                                              const StepState<R, NS>& st, P& pol) {
   using M = Mth<R>;
   R u_pt, u_k;
-  rng.pair<R>(L.o, 0, &u_pt, &u_k);
+  rng.template pair<R>(L.o, 0, &u_pt, &u_k);
   const R ell = u_pt * st.len_tot;
   R acc = R(0), tau_pt = R(0), s_pt = R(0), lg_pt = R(0);
   int j = 0;
@@ -156,7 +156,7 @@ __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R
 template <typename R, int NS, int DET, int KS, class P>
 __device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane<R>& L, P& pol) {
   const SampleP<R>& S = Sof<R>(A);
-  const NeutronRng rng(A.seed, A.sim_id, L.nid);
+  const NeutronRng rng(A.keys, L.nid);
   StepState<R, NS> st;
   const R we = step_segments<R, NS, P::kWantsGs>(A, S, L, st);
   pol.emit(A, tu, rng, L, we, st.atten, st.lg, st.len_tot);
@@ -197,7 +197,7 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
           if (from_input) {
             ok = load_input<R>(A, i, &L.n);
           } else {
-            const NeutronRng rng(A.seed, A.sim_id, L.nid);
+            const NeutronRng rng(A.keys, L.nid);
             ok = make_beam<R>(Bof<R>(A), rng, &L.n);
           }
           ok = ok && !(L.n.w < Sof<R>(A).min_prob) && !(A.stop_on_zero && L.n.w == R(0));

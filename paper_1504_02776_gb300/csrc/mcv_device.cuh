@@ -70,20 +70,35 @@ struct Words {
   uint32_t a, b, c, d;
 };
 
+// Round keys of the ten rounds: from a table computed on the host (PhiloxKeys, kept in
+// kernel parameter space, where the kernel reads them as constants), or computed from the
+// key (seed, sim) as they are used (one add per round, for keys that vary between warps).
+struct KeysTable {
+  const PhiloxKeys* p;
+  __device__ __forceinline__ KeysTable(const PhiloxKeys& k) : p(&k) {}
+  __device__ __forceinline__ uint32_t key0(int r) const { return p->k0[r]; }
+  __device__ __forceinline__ uint32_t key1(int r) const { return p->k1[r]; }
+};
+
+struct KeysOnTheFly {
+  uint32_t s0, s1;
+  __device__ __forceinline__ uint32_t key0(int r) const { return s0 + (uint32_t)r * 0x9E3779B9u; }
+  __device__ __forceinline__ uint32_t key1(int r) const { return s1 + (uint32_t)r * 0xBB67AE85u; }
+};
+
+template <class KS>
 __device__ __forceinline__ Words philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                          uint32_t k0, uint32_t k1) {
+                                          const KS& ks) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
     const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
     const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    const uint32_t n0 = hi1 ^ c1 ^ ks.key0(round);
+    const uint32_t n2 = hi0 ^ c3 ^ ks.key1(round);
     c0 = n0;
     c1 = lo1;
     c2 = n2;
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return Words{c0, c1, c2, c3};
 }
@@ -111,24 +126,28 @@ __device__ __forceinline__ float to_unit<float>(uint32_t hi, uint32_t lo) {
   return fminf(__fmaf_rn(h, 0x1p-32f, c), 0x1.fffffep-1f);
 }
 
-// The stream of one neutron: key (seed, sim), counter (id lo, id hi, 4*(event+1)+block, 0).
-struct NeutronRng {
-  uint32_t k0, k1, n0, n1;
-  __device__ __forceinline__ NeutronRng(uint32_t seed, uint32_t sim, int64_t nid)
-      : k0(seed), k1(sim), n0((uint32_t)((uint64_t)nid & 0xffffffffu)),
+// The stream of one neutron: key (seed, sim) given by its round keys, counter
+// (id lo, id hi, 4*(event+1)+block, 0).
+template <class KS>
+struct NeutronRngT {
+  KS ks;
+  uint32_t n0, n1;
+  __device__ __forceinline__ NeutronRngT(KS keys, int64_t nid)
+      : ks(keys), n0((uint32_t)((uint64_t)nid & 0xffffffffu)),
         n1((uint32_t)((uint64_t)nid >> 32)) {}
   template <typename R>
   __device__ __forceinline__ void pair(int event, int block, R* u0, R* u1) const {
-    const Words w = philox10(n0, n1, (uint32_t)(4 * (event + 1) + block), 0u, k0, k1);
+    const Words w = philox10(n0, n1, (uint32_t)(4 * (event + 1) + block), 0u, ks);
     *u0 = to_unit<R>(w.a, w.b);
     *u1 = to_unit<R>(w.c, w.d);
   }
   template <typename R>
   __device__ __forceinline__ R first(int event, int block) const {
-    const Words w = philox10(n0, n1, (uint32_t)(4 * (event + 1) + block), 0u, k0, k1);
+    const Words w = philox10(n0, n1, (uint32_t)(4 * (event + 1) + block), 0u, ks);
     return to_unit<R>(w.a, w.b);
   }
 };
+using NeutronRng = NeutronRngT<KeysTable>;
 
 // ---- time of flight ---------------------------------------------------------------------
 // FP64 mode: a double.  FP32 mode: an unevaluated sum of two floats (48 significant bits,
@@ -204,34 +223,24 @@ __device__ __forceinline__ const BeamP<double>& Bof<double>(const TraceArgs& A) 
 // aux: what the energy part needs from the direction part (FP32: tan^2 ax + tan^2 ay).
 // The footprint alone already settles most misses: a neutron whose footprint lies outside
 // (x_safe, y_safe) cannot reach the sample whatever its divergence (BeamP::x_safe).
-template <typename R>
-__device__ __forceinline__ void beam_footprint(const BeamP<R>& B, const NeutronRng& rng,
-                                               Ray<R>* n);
-template <typename R>
-__device__ __forceinline__ void beam_divergence(const BeamP<R>& B, const NeutronRng& rng,
-                                                Ray<R>* n, R* aux);
-template <typename R>
-__device__ __forceinline__ bool beam_energy(const BeamP<R>& B, const NeutronRng& rng, R aux,
-                                            Ray<R>* n);
-
-template <>
-__device__ __forceinline__ void beam_footprint<double>(const BeamP<double>& B,
-                                                       const NeutronRng& rng, Ray<double>* n) {
+template <class Rng>
+__device__ __forceinline__ void beam_footprint(const BeamP<double>& B,
+                                                       const Rng& rng, Ray<double>* n) {
   double u0, u1;
-  rng.pair<double>(-1, 1, &u0, &u1);
+  rng.template pair<double>(-1, 1, &u0, &u1);
   n->x = (u0 - 0.5) * B.width;
   n->y = (u1 - 0.5) * B.height;
   n->z = -B.z0;
   n->w = 1.0;
 }
 
-template <>
-__device__ __forceinline__ void beam_divergence<double>(const BeamP<double>& B,
-                                                        const NeutronRng& rng, Ray<double>* n,
+template <class Rng>
+__device__ __forceinline__ void beam_divergence(const BeamP<double>& B,
+                                                        const Rng& rng, Ray<double>* n,
                                                         double* aux) {
   using M = Mth<double>;
   double u0, u1, s, c;
-  rng.pair<double>(-1, 2, &u0, &u1);
+  rng.template pair<double>(-1, 2, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const double rr = M::sqrt(-2.0 * M::log(u0));
   const double ax = B.div * (rr * c), ay = B.div * (rr * s);
@@ -243,13 +252,13 @@ __device__ __forceinline__ void beam_divergence<double>(const BeamP<double>& B,
   *aux = 0.0;
 }
 
-template <>
-__device__ __forceinline__ bool beam_energy<double>(const BeamP<double>& B,
-                                                    const NeutronRng& rng, double,
+template <class Rng>
+__device__ __forceinline__ bool beam_energy(const BeamP<double>& B,
+                                                    const Rng& rng, double,
                                                     Ray<double>* n) {
   using M = Mth<double>;
   double u0, u1, s, c;
-  rng.pair<double>(-1, 0, &u0, &u1);
+  rng.template pair<double>(-1, 0, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const double zE = M::sqrt(-2.0 * M::log(u0)) * c;
   const double E = B.ei * (1.0 + B.rel * zE);
@@ -263,24 +272,24 @@ __device__ __forceinline__ bool beam_energy<double>(const BeamP<double>& B,
 // (computed once in FP64 on the host) times small FP32 corrections, so that the FP64 time
 // keeps ~1e-12 s accuracy: speed = v0 (1 + eta), eta = d/(1 + sqrt(1 + d)), d = rel z;
 // path/speed = t0 (1 + xi)/(1 + eta), xi = e/(1 + sqrt(1 + e)), e = tan^2 ax + tan^2 ay.
-template <>
-__device__ __forceinline__ void beam_footprint<float>(const BeamP<float>& B,
-                                                      const NeutronRng& rng, Ray<float>* n) {
+template <class Rng>
+__device__ __forceinline__ void beam_footprint(const BeamP<float>& B,
+                                                      const Rng& rng, Ray<float>* n) {
   float u0, u1;
-  rng.pair<float>(-1, 1, &u0, &u1);
+  rng.template pair<float>(-1, 1, &u0, &u1);
   n->x = (u0 - 0.5f) * B.width;
   n->y = (u1 - 0.5f) * B.height;
   n->z = -B.z0;
   n->w = 1.0f;
 }
 
-template <>
-__device__ __forceinline__ void beam_divergence<float>(const BeamP<float>& B,
-                                                       const NeutronRng& rng, Ray<float>* n,
+template <class Rng>
+__device__ __forceinline__ void beam_divergence(const BeamP<float>& B,
+                                                       const Rng& rng, Ray<float>* n,
                                                        float* aux) {
   using M = Mth<float>;
   float u0, u1, s, c;
-  rng.pair<float>(-1, 2, &u0, &u1);
+  rng.template pair<float>(-1, 2, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const float rr = M::sqrt(-2.0f * M::log(u0));
   const float ax = B.div * (rr * c), ay = B.div * (rr * s);
@@ -293,13 +302,13 @@ __device__ __forceinline__ void beam_divergence<float>(const BeamP<float>& B,
   *aux = e;
 }
 
-template <>
-__device__ __forceinline__ bool beam_energy<float>(const BeamP<float>& B,
-                                                   const NeutronRng& rng, float e,
+template <class Rng>
+__device__ __forceinline__ bool beam_energy(const BeamP<float>& B,
+                                                   const Rng& rng, float e,
                                                    Ray<float>* n) {
   using M = Mth<float>;
   float u0, u1, s, c;
-  rng.pair<float>(-1, 0, &u0, &u1);
+  rng.template pair<float>(-1, 0, &u0, &u1);
   M::sincos2pi(u1, &s, &c);
   const float zE = M::sqrt(-2.0f * M::log(u0)) * c;
   const float dE = B.rel * zE;
@@ -314,12 +323,12 @@ __device__ __forceinline__ bool beam_energy<float>(const BeamP<float>& B,
 }
 
 // The whole source draw; returns false when the drawn energy is not positive (no packet).
-template <typename R>
-__device__ __forceinline__ bool make_beam(const BeamP<R>& B, const NeutronRng& rng, Ray<R>* n) {
+template <typename R, class Rng>
+__device__ __forceinline__ bool make_beam(const BeamP<R>& B, const Rng& rng, Ray<R>* n) {
   R aux;
-  beam_footprint<R>(B, rng, n);
-  beam_divergence<R>(B, rng, n, &aux);
-  return beam_energy<R>(B, rng, aux, n);
+  beam_footprint(B, rng, n);
+  beam_divergence(B, rng, n, &aux);
+  return beam_energy(B, rng, aux, n);
 }
 
 // the footprint is far enough from the sample that the neutron misses it for any divergence
@@ -512,11 +521,11 @@ __device__ __forceinline__ void turn(R c, R s, R u, R* dx, R* dy, R* dz) {
 }
 
 // incoherent elastic: isotropic, speed unchanged (Debye-Waller factor taken as 1)
-template <typename R>
-__device__ __forceinline__ void kernel_iso(const NeutronRng& rng, int o, Ray<R>* n, Scatter<R>* sc) {
+template <typename R, class Rng>
+__device__ __forceinline__ void kernel_iso(const Rng& rng, int o, Ray<R>* n, Scatter<R>* sc) {
   using M = Mth<R>;
   R u0, u1, sp, cp;
-  rng.pair<R>(o, 1, &u0, &u1);
+  rng.template pair<R>(o, 1, &u0, &u1);
   const R ct = R(2) * u0 - R(1);
   const R st = R(2) * M::sqrt(u0 * (R(1) - u0));
   M::sincos2pi(u1, &sp, &cp);
@@ -534,8 +543,8 @@ __device__ __forceinline__ void kernel_iso(const NeutronRng& rng, int o, Ray<R>*
 // tabulated isotropic S(Q,E): E uniform on [e_min, min(e_max, Ei)], Q uniform on
 // [|ki - kf|, min(ki + kf, q_max)], azimuth uniform; weight S Q dE dQ / (2 ki^2); nearest bin.
 // Returns false when the kernel cannot scatter (empty range or outside the table).
-template <typename R>
-__device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng& rng, int o,
+template <typename R, class Rng>
+__device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const Rng& rng, int o,
                                            Ray<R>* n, Scatter<R>* sc, int* err) {
   using M = Mth<R>;
   const R Ei = (R)kMeVPerV2 * n->speed * n->speed;
@@ -544,7 +553,7 @@ __device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng
   if (!(e_hi > e_lo)) return false;
   const R dE = e_hi - e_lo;
   R u0, u1;
-  rng.pair<R>(o, 1, &u0, &u1);
+  rng.template pair<R>(o, 1, &u0, &u1);
   const R E = e_lo + u0 * dE;
   // Ef = Ei - E; when the range ends at Ei it is the sampled offset from that end
   const R Ef = (e_hi == Ei) ? (R(1) - u0) * dE : Ei - E;
@@ -573,7 +582,7 @@ __device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const NeutronRng
     return false;
   }
   const R Sv = (R)__ldg(S.sqe + entry);
-  const R u2 = rng.first<R>(o, 2);
+  const R u2 = rng.template first<R>(o, 2);
   turn<R>(c2t, s2t, u2, &n->dx, &n->dy, &n->dz);
   n->speed = speed_f;
   sc->rest = Q * dE * dQ / (R(2) * ki * ki);
@@ -797,14 +806,14 @@ __device__ __forceinline__ BvkPoint<R> bvk_point(const SampleP<R>& S, R c, R s, 
   return P;
 }
 
-template <typename R>
+template <typename R, class Rng>
 __device__ __forceinline__ bool kernel_bvk(const SampleP<R>& S, R crot, R srot,
-                                           const NeutronRng& rng, int o, Ray<R>* n,
+                                           const Rng& rng, int o, Ray<R>* n,
                                            Scatter<R>* sc) {
   using M = Mth<R>;
   R u0, u1, u2, u3;
-  rng.pair<R>(o, 1, &u0, &u1);
-  rng.pair<R>(o, 2, &u2, &u3);
+  rng.template pair<R>(o, 1, &u0, &u1);
+  rng.template pair<R>(o, 2, &u2, &u3);
   const R ct = R(2) * u0 - R(1);
   const R st = R(2) * M::sqrt(u0 * (R(1) - u0));
   R sp, cp;
@@ -981,10 +990,47 @@ __device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const TofWin&
 }
 
 // tube centre directions staged in shared memory: tu[2*i] = sin(phi_i), tu[2*i+1] = cos(phi_i)
+// Where a packet meets the tube rows: the row at its crossing of the tube-centre circle and
+// the tube g nearest to that crossing (candidates g - 1, g, g + 1).  False: it meets no row
+// or lies outside the rows' arc (no candidate tube), i.e. it misses the detector.
 template <typename R>
-__device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const TofWin& W,
+__device__ __forceinline__ bool tubes_locate(const DetP<R>& D, const Ray<R>& n, int* row_out,
+                                             int* g_out) {
+  using M = Mth<R>;
+  const R Rad = (R)D.radius;
+  R sR;
+  if (!exit_cyl<R>(Rad, n, &sR)) return false;
+  const R Px = n.x + sR * n.dx, Py = n.y + sR * n.dy, Pz = n.z + sR * n.dz;
+  int row = -1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (row < 0 && i < D.n_rows && M::fabs(Py - (R)D.row_y[i]) <= (R)D.half_len) row = i;
+  }
+  if (row < 0) return false;
+  const int tpp = D.tubes_per_pack;
+  const R period = (R)D.period, pitch = (R)D.pitch;
+  const R arc = (M::atan2(Px, Pz) - (R)D.phi0) * Rad;
+  const R p = M::floor(arc / period);
+  const R within = arc - p * period;
+  R k = M::floor(within / pitch);
+  if (k > (R)(tpp - 1)) k = (R)(tpp - 1);
+  // more than one tube outside the rows' arc: no candidate (the range check on the float
+  // also keeps its conversion to int in range)
+  if (!(p >= R(-1) && p <= (R)D.packs[row])) return false;
+  const int g = (int)p * tpp + (int)k;
+  if (g + 1 < 0 || g - 1 >= D.packs[row] * tpp) return false;
+  *row_out = row;
+  *g_out = g;
+  return true;
+}
+
+// The rest of the tube detector for a located packet: the first of the candidate tubes the
+// ray enters, the absorption point drawn from the truncated exponential of the 3He path
+// (u_det), pixel, time of flight and bin.
+template <typename R>
+__device__ __forceinline__ Hit<R> tubes_absorb(const DetP<R>& D, const TofWin& W,
                                                const R* __restrict__ tu, const Ray<R>& n,
-                                               R u_det) {
+                                               R u_det, int row, int g) {
   using M = Mth<R>;
   Hit<R> h;
   h.bin = -1;
@@ -993,26 +1039,8 @@ __device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const TofWin& W
   h.w_det = R(0);
   h.pabs = R(0);
   const R Rad = (R)D.radius;
-  R sR;
-  if (!exit_cyl<R>(Rad, n, &sR)) return h;
-  const R Px = n.x + sR * n.dx, Py = n.y + sR * n.dy, Pz = n.z + sR * n.dz;
-  int row = -1, row_off = 0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (row < 0 && i < D.n_rows && M::fabs(Py - (R)D.row_y[i]) <= (R)D.half_len) {
-      row = i;
-      row_off = D.row_off[i];
-    }
-  }
-  if (row < 0) return h;
   const int tpp = D.tubes_per_pack;
-  const R period = (R)D.period, pitch = (R)D.pitch;
-  const R arc = (M::atan2(Px, Pz) - (R)D.phi0) * Rad;
-  const R p = M::floor(arc / period);
-  const R within = arc - p * period;
-  R k = M::floor(within / pitch);
-  if (k > (R)(tpp - 1)) k = (R)(tpp - 1);
-  const int g = (int)p * tpp + (int)k;
+  const int row_off = D.row_off[row];
   const int n_tubes_row = D.packs[row] * tpp;
   const R y_lo = (R)D.row_y[row] - (R)D.half_len;
   const R y_hi = (R)D.row_y[row] + (R)D.half_len;
@@ -1062,11 +1090,31 @@ __device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const TofWin& W
   return h;
 }
 
-template <typename R, int DET>
+// Tube detector system (section 2.4.3, "Ray tracing in a detector system"): the packet's
+// crossing of the tube-centre circle picks the row and three candidate tubes; the first
+// tube the ray enters absorbs it.
+template <typename R>
+__device__ __forceinline__ Hit<R> detect_tubes(const DetP<R>& D, const TofWin& W,
+                                               const R* __restrict__ tu, const Ray<R>& n,
+                                               R u_det) {
+  int row = 0, g = 0;
+  if (!tubes_locate<R>(D, n, &row, &g)) {
+    Hit<R> h;
+    h.bin = -1;
+    h.pixel = -1;
+    h.tof = n.t;
+    h.w_det = R(0);
+    h.pabs = R(0);
+    return h;
+  }
+  return tubes_absorb<R>(D, W, tu, n, u_det, row, g);
+}
+
+template <typename R, int DET, class Rng>
 __device__ __forceinline__ Hit<R> detect(const DetP<R>& D, const TofWin& W, const R* tu,
-                                         const NeutronRng& rng, int order, const Ray<R>& n) {
+                                         const Rng& rng, int order, const Ray<R>& n) {
   if (DET == MCV_DET_SURFACE) return detect_surface<R>(D, W, n);
-  const R u = rng.first<R>(order, 3);
+  const R u = rng.template first<R>(order, 3);
   return detect_tubes<R>(D, W, tu, n, u);
 }
 

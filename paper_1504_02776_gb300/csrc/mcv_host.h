@@ -39,6 +39,7 @@ mcv_status build_beam(const mcv_beam_params* b, BeamP<double>* B);
 mcv_status build_sample(const mcv_sample* s, SampleP<double>* S);
 mcv_status build_detector(const mcv_detector* d, DetP<double>* D);
 TofWin tof_window(double tof_min_s, double tof_max_s, int n_tof);
+PhiloxKeys philox_keys(uint32_t seed, uint32_t sim_id);
 void set_miss_bounds(const SampleP<double>& S, BeamP<double>* B);
 void cast_beam(const BeamP<double>& d, BeamP<float>* f);
 void cast_sample(const SampleP<double>& d, SampleP<float>* f);

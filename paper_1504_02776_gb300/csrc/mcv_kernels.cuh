@@ -67,7 +67,8 @@ struct Forward {
 
   __device__ __forceinline__ void start(const Lane<R>&) {}
 
-  __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const NeutronRng& rng,
+  template <class Rng>
+  __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const Rng& rng,
                                        const Lane<R>& L, R we, R, R, R len_tot) {
     Tally<R>& t = store.get();
     if (L.o == 0 && len_tot > R(0)) t.cnt.nhit++;
@@ -105,6 +106,8 @@ struct Forward {
 
   // the beam stop's share of a packet of order 0, and an incident neutron meeting the sample
   __device__ __forceinline__ void beam_stop(R w) { store.get().bs.add(w); }
+  // a packet that misses the detector system
+  __device__ __forceinline__ void missed() { store.get().cnt.nmiss++; }
   __device__ __forceinline__ void hit() { store.get().cnt.nhit++; }
   __device__ __forceinline__ void emitted() { store.get().cnt.nemit++; }
 
@@ -173,6 +176,7 @@ struct QPacket {  // a transmitted packet of order >= 1 on its way to the detect
   Tof<R> t;
   int64_t nid;
   int order;
+  int16_t row, g;  // located packets (FP64 tube detector): row, tube nearest to the crossing
 };
 
 template <typename R>
@@ -271,8 +275,7 @@ struct ParamJob {
   __device__ __forceinline__ const SampleP<R>& S() const { return Sof<R>(A); }
   __device__ __forceinline__ const BeamP<R>& B() const { return Bof<R>(A); }
   __device__ __forceinline__ const TofWin& W() const { return Dof<R>(A).win; }
-  __device__ __forceinline__ uint32_t seed() const { return A.seed; }
-  __device__ __forceinline__ uint32_t sim_id() const { return A.sim_id; }
+  __device__ __forceinline__ NeutronRng rng(int64_t nid) const { return NeutronRng(A.keys, nid); }
   __device__ __forceinline__ int64_t first_id() const { return A.first_id; }
 };
 
@@ -286,8 +289,11 @@ struct SlotJob {
   }
   __device__ __forceinline__ const BeamP<R>& B() const { return batch_warp<R>().sim.B; }
   __device__ __forceinline__ const TofWin& W() const { return batch_warp<R>().sim.win; }
-  __device__ __forceinline__ uint32_t seed() const { return batch_warp<R>().sim.seed; }
-  __device__ __forceinline__ uint32_t sim_id() const { return batch_warp<R>().sim.sim_id; }
+  // keys computed as used: a table in shared memory would cost a load per round
+  __device__ __forceinline__ NeutronRngT<KeysOnTheFly> rng(int64_t nid) const {
+    const SimP<R>& J = batch_warp<R>().sim;
+    return NeutronRngT<KeysOnTheFly>(KeysOnTheFly{J.seed, J.sim_id}, nid);
+  }
   __device__ __forceinline__ int64_t first_id() const { return batch_warp<R>().sim.first_id; }
 };
 
@@ -332,8 +338,8 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
         int64_t nid = 0;
         if (i < hi) {
           nid = job.first_id() + i;
-          const NeutronRng rng(job.seed(), job.sim_id(), nid);
-          beam_footprint<R>(job.B(), rng, &nr);
+          const auto rng = job.rng(nid);
+          beam_footprint(job.B(), rng, &nr);
           if (!surely_misses<R>(job.B(), nr))
             maybe = true;
           else if (!(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0)))
@@ -366,12 +372,12 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
       fq_n -= take_f;
       __syncwarp();
       if (lane < take_f) {
-        const NeutronRng rng(job.seed(), job.sim_id(), nid);
+        const auto rng = job.rng(nid);
         R aux;
-        beam_divergence<R>(job.B(), rng, &nr, &aux);
+        beam_divergence(job.B(), rng, &nr, &aux);
         Seg<R> seg[2 * NS];
         const bool meets = assembly_segs<R, NS>(S, nr, seg) > 0;
-        bool ok = (meets || !job.B().energy_positive) ? beam_energy<R>(job.B(), rng, aux, &nr)
+        bool ok = (meets || !job.B().energy_positive) ? beam_energy(job.B(), rng, aux, &nr)
                                                       : true;
         ok = ok && !(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0));
         if (ok) {
@@ -418,23 +424,34 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
     }
     hq_n -= take;
     __syncwarp();
-    // ---- sample stage
+    // ---- sample stage.  FP64: a transmitted packet of order >= 1 is first located on the
+    // tube rows (row and candidate tubes) and only packets that can reach a tube are queued
+    // for the detector stage (the FP64 detector arithmetic is costly enough that skipping it
+    // for the ~3/4 of packets that miss pays for the idle order-0 lanes here); FP32: all of
+    // them are queued and the detector stage locates them, with every lane busy.
+    constexpr bool kLocateEarly = DET == MCV_DET_TUBES && sizeof(R) == 8;
     StepState<R, NS> st;
     R we = R(0);
     bool to_det = false;
+    int row = 0, g = 0;
     if (L.active) {
       we = step_segments<R, NS, false>(A, S, L, st);
       if (L.o == 0) {
         pol.beam_stop(we);
         if (st.len_tot > R(0)) pol.hit();
       } else {
-        to_det = true;
         pol.emitted();
+        if (!kLocateEarly || tubes_locate<R>(D, L.n, &row, &g))
+          to_det = true;
+        else
+          pol.missed();
       }
     }
     const unsigned dm = __ballot_sync(kFull, to_det);
     if (to_det) {
       QPacket<R>& p = dq[dq_n + __popc(dm & lt_mask)];
+      p.row = (int16_t)row;
+      p.g = (int16_t)g;
       p.x = L.n.x;
       p.y = L.n.y;
       p.z = L.n.z;
@@ -452,7 +469,7 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
       if (L.o == S.max_orders || !(st.len_tot > R(0))) {
         L.active = false;
       } else {
-        const NeutronRng rng(job.seed(), job.sim_id(), L.nid);
+        const auto rng = job.rng(L.nid);
         L.active = step_scatter<R, NS, KS, P>(A, S, rng, L, st, pol);
       }
     }
@@ -465,10 +482,12 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
     while (dq_n >= 32 || (done && dq_n > 0)) {
       const int take = dq_n < 32 ? dq_n : 32;
       Ray<R> pe;
-      int order = 0;
+      int order = 0, row = 0, g = 0;
       int64_t nid = 0;
       if (lane < take) {
         const QPacket<R>& p = dq[dq_n - take + lane];
+        row = p.row;
+        g = p.g;
         pe.x = p.x;
         pe.y = p.y;
         pe.z = p.z;
@@ -483,8 +502,13 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
       }
       __syncwarp();
       if (lane < take) {
-        const NeutronRng rng(job.seed(), job.sim_id(), nid);
-        pol.record(A, detect<R, DET>(D, job.W(), tu, rng, order, pe));
+        const auto rng = job.rng(nid);
+        if (kLocateEarly) {
+          const R u = rng.template first<R>(order, 3);
+          pol.record(A, tubes_absorb<R>(D, job.W(), tu, pe, u, row, g));
+        } else {
+          pol.record(A, detect<R, DET>(D, job.W(), tu, rng, order, pe));
+        }
       }
       dq_n -= take;
     }
@@ -606,7 +630,7 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const __grid_constant__ 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t nid = A.first_id + i;
-    const NeutronRng rng(A.seed, A.sim_id, nid);
+    const NeutronRng rng(A.keys, nid);
     Ray<R> n;
     const bool ok = make_beam<R>(Bof<R>(A), rng, &n);
     if (!ok) {
@@ -653,7 +677,7 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant_
     Ray<R> n;
     if (!load_input<R>(A, i, &n)) continue;
     cnt.nemit++;
-    const NeutronRng rng(A.seed, A.sim_id, A.in_id[i]);
+    const NeutronRng rng(A.keys, A.in_id[i]);
     const Hit<R> h = detect<R, DET>(Dof<R>(A), Dof<R>(A).win, tu, rng, o, n);
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
@@ -723,7 +747,8 @@ struct Adjoint {
     cum_ds = 0.0;
   }
 
-  __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const NeutronRng& rng,
+  template <class Rng>
+  __device__ __forceinline__ void emit(const TraceArgs& A, const R* tu, const Rng& rng,
                                        const Lane<R>& L, R we, R atten, R lg, R) {
     if (L.o == 0) return;
     Ray<R> pe = L.n;

@@ -12,7 +12,7 @@
 
 #include <cuda_runtime.h>
 
-#include "mcv_launch.h"
+#include "mcv_host.h"
 
 namespace {
 
@@ -98,6 +98,7 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
   if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
   A.seed = seed;
   A.sim_id = sim_id;
+  A.keys = mcv::host::philox_keys(seed, sim_id);
   A.first_id = first_id;
   A.n = n;
   A.err = reinterpret_cast<int*>(scratch);

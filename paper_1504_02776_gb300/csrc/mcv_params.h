@@ -69,6 +69,13 @@ struct SampleP {
   R bvk_hwu;       // hbar sqrt(phi/M) in meV: hbar omega = bvk_hwu sqrt(lambda')
 };
 
+// Round keys of a Philox4x32-10 stream keyed by (seed, sim): round r uses
+// (seed + r 0x9E3779B9, sim + r 0xBB67AE85).  They depend on the key only, so the host
+// computes them once per launch and the kernels read them as constants.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
 // time-of-flight window of the histogram: n_tof bins of width dt from tof_min
 struct TofWin {
   double tof_min, dt;
@@ -102,6 +109,7 @@ struct TraceArgs {
   BeamP<float> Bf;
   BeamP<double> Bd;
   uint32_t seed, sim_id;
+  PhiloxKeys keys;  // round keys of (seed, sim_id)
   int64_t first_id, n;
   // fused outputs
   double* hist;
