@@ -339,6 +339,44 @@ def batch_extras(ctx, args):
     return out
 
 
+def grad_extras(ctx, value64):
+    """The differentiable form (config 4): chi-squared loss of the 1e7-neutron powder run
+    against a seeded target and its adjoint gradient w.r.t. the 200 x 400 S(Q,E) table and
+    the cross sections -- one mcv_grad call (forward trace, loss, adjoint trace; FP32 trace,
+    FP64 accumulation) -- against the plain FP64 forward of the same neutrons."""
+    import torch
+
+    import mcv_inputs as mi
+    from paper_1504_02776_gb300 import api, binding as B
+    wl = mi.config4()
+    table = ctx.table(wl)
+    # target: the run with omega scaled by 1.05 (seed 1), Poisson noise, c = n / sum(I)
+    tw = mi.config2(n=wl.n, omega_scale=1.05).replace(seed=1)
+    counts, _ = ctx.trace(tw, fp_mode=B.FP32, table=ctx.table(tw))
+    scale_c = wl.n / float(counts.sum().item())
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2)
+    target = torch.poisson(scale_c * counts, generator=gen)
+    hist = torch.empty_like(counts)
+    g_work = torch.empty_like(counts)
+
+    def step():
+        api._grad_call(ctx, wl, target, scale_c, B.FP32, wl.n, 0, table, None, None, 0, hist,
+                       g_work)
+
+    for _ in range(2):
+        step()
+    ms = _timed(step, 3)
+    ctx.sync()
+    ms64 = wl.n / value64 * 1e3
+    return {"workload": "config 4: chi2 of the 1e7-neutron powder run vs a seeded target "
+                        "(omega x 1.05, Poisson), gradient w.r.t. 200 x 400 S(Q,E) entries and "
+                        "sigma_abs, sigma_s; forward + loss + adjoint in one mcv_grad call",
+            "value": wl.n / (ms / 1e3), "unit": "neutrons/s", "ms": ms,
+            "plain_fp64_forward_ms_same_neutrons": ms64,
+            "speedup_over_plain_fp64_forward": ms64 / ms}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -438,9 +476,12 @@ def run_ours(args):
     ctx.sync()
 
     # ---- batched forms (rank 0 of a single-GPU run; they hold up to 170 GB of histograms)
+    # and the differentiable form
     batched = None
+    differentiable = None
     if not args.no_batch and world == 1:
         batched = batch_extras(ctx, args)
+        differentiable = grad_extras(ctx, value64)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -512,6 +553,7 @@ def run_ours(args):
                          "speedup_fp32_over_fp64": value / value64},
         "roofline": roof,
         "batched": batched,
+        "differentiable": differentiable,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,

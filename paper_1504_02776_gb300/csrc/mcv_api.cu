@@ -454,6 +454,7 @@ mcv_status mcv_create(int device, mcv_ctx** out) {
     return cuda_fail(e, "cudaMemset");
   }
   std::memset(c->occ, 0, sizeof(c->occ));
+  std::memset(c->occ_adj, 0, sizeof(c->occ_adj));
   std::memset(c->tuned, 0, sizeof(c->tuned));
   *out = c;
   return MCV_OK;
@@ -719,7 +720,12 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
     A.g = g_work;
     A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
     A.dsig = dsig;
-    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_for(ctx, n, 2), s);
+    int& occ_a = ctx->occ_adj[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.has_bvk ? 1 : 0];
+    if (occ_a == 0) {
+      e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ_a);
+      if (e != cudaSuccess || occ_a < 1) occ_a = 1;
+    }
+    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_for(ctx, n, occ_a), s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
   }
   return MCV_OK;

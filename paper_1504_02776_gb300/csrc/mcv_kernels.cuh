@@ -942,6 +942,25 @@ cudaError_t launch_adjoint_nk(const TraceArgs& A, int det, int grid, cudaStream_
   return cudaGetLastError();
 }
 
+// resident blocks per SM of the adjoint kernel of a shape
+template <typename R, int NS, int KS>
+const void* adjoint_fn_nk(int det) {
+  if (det == MCV_DET_SURFACE) return (const void*)adjoint_kernel<R, NS, MCV_DET_SURFACE, KS>;
+  return (const void*)adjoint_kernel<R, NS, MCV_DET_TUBES, KS>;
+}
+
+template <typename R>
+cudaError_t adjoint_blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
+  const void* fn;
+  if (ns <= 1)
+    fn = bvk ? adjoint_fn_nk<R, 1, kKernelsAll>(det) : adjoint_fn_nk<R, 1, kKernelsPowder>(det);
+  else if (ns == 2)
+    fn = bvk ? adjoint_fn_nk<R, 2, kKernelsAll>(det) : adjoint_fn_nk<R, 2, kKernelsPowder>(det);
+  else
+    fn = bvk ? adjoint_fn_nk<R, 4, kKernelsAll>(det) : adjoint_fn_nk<R, 4, kKernelsPowder>(det);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, 0);
+}
+
 template <typename R, int NS>
 cudaError_t launch_adjoint_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
   if (A.Sd.has_bvk) return launch_adjoint_nk<R, NS, kKernelsAll>(A, det, grid, s);
@@ -973,6 +992,9 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   cudaError_t launch_adjoint_##SUFFIX(const TraceArgs& A, int det, int grid,                \
                                       cudaStream_t s) {                                     \
     return launch_adjoint_t<R>(A, det, grid, s);                                            \
+  }                                                                                         \
+  cudaError_t adjoint_blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int* blocks) {       \
+    return adjoint_blocks_per_sm_t<R>(ns, det, bvk, blocks);                                \
   }
 
 // defines the batched entry points of one real type (mcv_batch_fp32.cu / mcv_batch_fp64.cu)

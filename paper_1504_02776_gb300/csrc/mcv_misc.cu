@@ -19,6 +19,8 @@ cudaError_t launch_detect_f64(const TraceArgs& A, const EventsArgs& E, int det, 
                               cudaStream_t s);
 cudaError_t launch_adjoint_f32(const TraceArgs& A, int det, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_f64(const TraceArgs& A, int det, int grid, cudaStream_t s);
+cudaError_t adjoint_blocks_per_sm_f32(int ns, int det, int bvk, int* blocks);
+cudaError_t adjoint_blocks_per_sm_f64(int ns, int det, int bvk, int* blocks);
 cudaError_t batch_blocks_per_sm_f32(int ns, int det, int bvk, int ss, int* blocks);
 cudaError_t batch_blocks_per_sm_f64(int ns, int det, int bvk, int ss, int* blocks);
 cudaError_t launch_batch_f32(const TraceArgs& A, const BatchArgs& Q, int ns, int det, int bvk,
@@ -43,6 +45,18 @@ __global__ void zero_kernel(double* __restrict__ p, int64_t n) {
   }
 }
 
+// 1/d for d >= 1 without an FP64 division (GB300's FP64 rate is about 1/64 of its FP32
+// rate, and a division is a long FP64 sequence): the FP32 reciprocal as the seed, then two
+// Newton-Raphson steps x <- x + x (1 - d x) in FP64, each of which squares the relative
+// error (2^-23 -> 2^-46 -> below FP64 rounding).  Very large d take the division.
+__device__ __forceinline__ double recip_ge1(double d) {
+  if (!(d < 1e30)) return 1.0 / d;
+  double x = (double)__frcp_rn((float)d);
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
+}
+
 // chi2 = sum_b (c I_b - T_b)^2 / max(T_b, 1);  g_b = 2 c (c I_b - T_b) / max(T_b, 1)
 __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hist,
                                                    const double* __restrict__ target, double c,
@@ -52,10 +66,11 @@ __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hi
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
     const double T = target[b];
-    const double den = fmax(T, 1.0);
+    const double inv = recip_ge1(fmax(T, 1.0));
     const double r = c * hist[b] - T;
-    part += r * r / den;
-    g[b] = 2.0 * c * r / den;
+    const double ri = r * inv;
+    part += r * ri;
+    g[b] = 2.0 * c * ri;
   }
   part = warp_sum(part);
   __shared__ double red[8];
@@ -94,6 +109,11 @@ cudaError_t launch_detect(const TraceArgs& A, const EventsArgs& E, int fp_mode, 
 
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s) {
   return fp_mode == MCV_FP32 ? launch_adjoint_f32(A, det, grid, s) : launch_adjoint_f64(A, det, grid, s);
+}
+
+cudaError_t adjoint_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks) {
+  return fp_mode == MCV_FP32 ? adjoint_blocks_per_sm_f32(ns, det, bvk, blocks)
+                             : adjoint_blocks_per_sm_f64(ns, det, bvk, blocks);
 }
 
 cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int ss, int* blocks) {

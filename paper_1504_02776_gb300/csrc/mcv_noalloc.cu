@@ -130,7 +130,10 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
     A.g = g;
     A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
     A.dsig = dsig;
-    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_of(2), s);
+    int occ_a = 0;
+    e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ_a);
+    if (e != cudaSuccess || occ_a < 1) occ_a = 1;
+    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_of(occ_a), s);
     if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
   }
   return MCV_OK;
