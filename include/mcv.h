@@ -172,7 +172,7 @@ typedef struct {
 } mcv_events;
 
 /* ---- context ------------------------------------------------------------------------- */
-/* Creates a context on `device` (allocates a small device block: error flag, work queue).
+/* Creates a context on `device` (allocates a 256-byte device block for the error flag).
  * Returns MCV_EINVAL for a bad device or out pointer, MCV_ECUDA/MCV_ENOMEM on failure. */
 mcv_status mcv_create(int device, mcv_ctx** out);
 /* Frees the context and its device memory; NULL is ignored. */

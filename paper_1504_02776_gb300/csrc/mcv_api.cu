@@ -446,7 +446,6 @@ mcv_status mcv_create(int device, mcv_ctx** out) {
     delete c;
     return fail(MCV_ENOMEM, "cannot allocate the context's device block");
   }
-  c->d_queue = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->d_err) + 128);
   e = cudaMemset(c->d_err, 0, 256);
   if (e != cudaSuccess) {
     cudaFree(c->d_err);

@@ -14,7 +14,6 @@ struct mcv_ctx {
   int device;
   int sm_count;
   int* d_err;          // device error flag (kernels set it; mcv_sync reads and clears it)
-  unsigned long long* d_queue;  // spare device words next to the error flag
   int occ[2][3][3][2]; // cached blocks per SM of the fused kernel: [fp][ns 1,2,4][det][bvk]
   int occ_adj[2][3][3][2];  // the same for the adjoint kernel
   // batched launch chosen by mcv_batch_tune for a kind of batch: neutrons per work item and

@@ -1,5 +1,5 @@
-// Host-side entry points of the kernels (mcv_fp32.cu, mcv_fp64.cu, mcv_misc.cu), used by the
-// C ABI.
+// Host-side entry points of the kernels (mcv_fp32.cu, mcv_fp64.cu, mcv_batch_fp32.cu,
+// mcv_batch_fp64.cu, mcv_misc.cu), used by the C ABI.
 #pragma once
 
 #include <string>
