@@ -17,8 +17,9 @@
  *     number densities in 1/A^3, cross sections in barn (absorption quoted at 2200 m/s and
  *     scaled as 1/v).
  *   - All array arguments are DEVICE pointers owned by the caller, on the device the
- *     context was created for.  The library allocates device memory only inside the
- *     context (mcv_create) and never frees caller memory.
+ *     context was created for.  The library allocates device memory only for its own
+ *     bookkeeping (the context, a batch's parameter block, the autotuner's scratch; each
+ *     call that does says so) and never frees caller memory.
  *   - Calls are asynchronous on the caller's CUDA stream (`stream`, a cudaStream_t; NULL is
  *     the legacy default stream).  Argument errors are reported before anything is
  *     launched (MCV_EINVAL, nothing written).  Launch failures return MCV_ECUDA.  Errors
