@@ -732,19 +732,23 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant_
 // scatter-adds into dS (FP64 atomics, the table is L2-resident) and dsig (warp-reduced).
 constexpr int kMaxOrders = 7;
 
+// The path sums (cum_*) and the per-thread accumulators are kept in the real type of the
+// trace: FP64 in FP64 mode, compensated FP32 sums in FP32 mode (the FP64 pipe of GB300 runs
+// at about 1/64 of the FP32 rate, so FP64 arithmetic per packet would dominate the FP32
+// adjoint); the table-gradient atomics are FP64 in both.
 template <typename R, int DET>
 struct Adjoint {
   static constexpr bool kWantsGs = true;
   R a[kMaxOrders];   // scattering factor without the table value
   R s[kMaxOrders];   // table value (1 for kernels without a table)
   int e[kMaxOrders]; // table entry or -1
-  double cum_dabs = 0.0, cum_ds = 0.0;
-  double acc_abs = 0.0, acc_s = 0.0;
+  R cum_dabs = R(0), cum_ds = R(0);
+  Acc<R> acc_abs, acc_s;
   int err = 0;
 
   __device__ __forceinline__ void start(const Lane<R>&) {
-    cum_dabs = 0.0;
-    cum_ds = 0.0;
+    cum_dabs = R(0);
+    cum_ds = R(0);
   }
 
   template <class Rng>
@@ -759,14 +763,15 @@ struct Adjoint {
       err = 1;
       return;
     }
-    const double gb = A.g[h.bin];
-    if (gb == 0.0) return;
-    const ScatP<double>& g = A.Sd.s[A.gs];
-    const double w_det = (double)(we * h.pabs);
-    const double dabs = cum_dabs - g.n100 * (2200.0 / (double)L.n.speed) * (double)lg;
-    const double ds = cum_ds - g.n100 * (double)lg;
-    acc_abs += gb * w_det * dabs;
-    acc_s += gb * w_det * ds;
+    const double g64 = A.g[h.bin];
+    if (g64 == 0.0) return;
+    const R gb = (R)g64;
+    const ScatP<R>& g = Sof<R>(A).s[A.gs];
+    const R w_det = we * h.pabs;
+    const R dabs = cum_dabs - g.n100 * (R(2200) / L.n.speed) * lg;
+    const R ds = cum_ds - g.n100 * lg;
+    acc_abs.add(gb * w_det * dabs);
+    acc_s.add(gb * w_det * ds);
     if (!A.dsqe) return;
     R base = atten * h.pabs;
     for (int m = 0; m < L.o; ++m) base *= a[m];
@@ -775,7 +780,7 @@ struct Adjoint {
       R prod = base;
       for (int m = 0; m < L.o; ++m)
         if (m != k) prod *= s[m];
-      atomicAdd(A.dsqe + e[k], gb * (double)prod);
+      atomicAdd(A.dsqe + e[k], g64 * (double)prod);
     }
   }
 
@@ -785,16 +790,16 @@ struct Adjoint {
     a[k] = a_fac * out.rest;
     s[k] = out.s_value;
     e[k] = out.entry;
-    const ScatP<double>& g = A.Sd.s[A.gs];
-    cum_dabs -= g.n100 * (2200.0 / (double)speed_in) * (double)lg_pt;
-    cum_ds -= g.n100 * (double)lg_pt;
-    if (j == A.gs) cum_ds += 1.0 / g.sig_s;
+    const ScatP<R>& g = Sof<R>(A).s[A.gs];
+    cum_dabs -= g.n100 * (R(2200) / speed_in) * lg_pt;
+    cum_ds -= g.n100 * lg_pt;
+    if (j == A.gs) cum_ds += R(1) / g.sig_s;
   }
 
   __device__ __forceinline__ void clear(const TraceArgs&, int64_t, int) {}
 
   __device__ __forceinline__ void flush(const TraceArgs& A, int lane) {
-    const double s_abs = warp_sum(acc_abs), s_s = warp_sum(acc_s);
+    const double s_abs = warp_sum(acc_abs.value()), s_s = warp_sum(acc_s.value());
     if (lane == 0) {
       atomicAdd(A.dsig + 0, s_abs);
       atomicAdd(A.dsig + 1, s_s);
