@@ -66,9 +66,12 @@ __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hi
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
     const double T = target[b];
-    const double inv = recip_ge1(fmax(T, 1.0));
     const double r = c * hist[b] - T;
-    const double ri = r * inv;
+    if (r == 0.0) {  // most bins: nothing simulated, nothing measured
+      g[b] = 0.0;
+      continue;
+    }
+    const double ri = r * recip_ge1(fmax(T, 1.0));
     part += r * ri;
     g[b] = 2.0 * c * ri;
   }
