@@ -225,7 +225,8 @@ mcv_status build_detector(const mcv_detector* d, mcv::DetP<double>* D) {
 void set_miss_bounds(const mcv::SampleP<double>& S, mcv::BeamP<double>* B) {
   B->x_safe = INFINITY;
   B->y_safe = INFINITY;
-  if (!B->energy_positive) return;
+  // only for a start plane upstream of the sample centre and energies that are all positive
+  if (!B->energy_positive || !(B->z0 >= 0.0)) return;
   double r = 0.0, hh = 0.0;
   for (int j = 0; j < S.ns; ++j) {
     const mcv::ScatP<double>& c = S.s[j];
