@@ -221,6 +221,16 @@ def can_scatterer() -> Scatterer:
                      sig_abs_b=0.23, kernels=[(K_ISO, 1.5)])
 
 
+def powder_in_can(n=100_000, ei=100.0) -> Workload:
+    """One simulation of the sweep's sample environment: the powder S(Q,E) sample inside the
+    aluminium can, incident energy `ei` with its own time window, on the full tube system."""
+    w = config2(n=n)
+    t0, t1 = tof_window_for(ei)
+    det = dataclasses.replace(w.detector, tof_min_s=t0, tof_max_s=t1)
+    return w.replace(name="powder-in-can-%gmeV" % ei, beam=powder_beam(ei=ei), detector=det,
+                     scatterers=[powder_sample(), can_scatterer()])
+
+
 def config3_batch(n=2_000_000, orientations=None, detector=None) -> List[Workload]:
     """The single crystal at 181 orientations (0..180 degrees in 1 degree steps), one
     simulation (random stream sim_id = the angle) and one histogram each."""

@@ -56,18 +56,40 @@ thread_local double g_kappa = 0.0;
 // relative-error budget of the current speed (units of the FP64 epsilon), carried from
 // kernel to kernel for the condition estimate
 thread_local double g_kappa_v = 0.0;
+// error scales (units of the FP64 epsilon) of the current point and direction, for the
+// chords computed from them: g_err_r (metres) from the roundings of the point's own
+// coordinates, taken in any direction; g_err_a (metres) from the error of the distance
+// along the previous ray (g_dprev) that placed the point, which moves a later surface
+// crossing only by its component along that surface's normal; g_err_d (dimensionless) of
+// the direction, carried while directions are built on each other.  An older error of the
+// start point moves the surfaces the ray met with the point, so it is not carried on.
+thread_local double g_err_r = 0.0;
+thread_local double g_err_a = 0.0;
+thread_local Vec3 g_dprev = {0.0, 0.0, 0.0};
+thread_local double g_err_d = 0.0;
 
 // ---- geometry -------------------------------------------------------------------------
+// One end of a ray interval: its distance s and two absolute error scales (units of the
+// FP64 epsilon, metres): er from the roundings of its own computation, ep from the errors
+// of the start point and direction (g_err_r, g_err_d).
+struct End {
+  double s, er, ep;
+};
+
 // Interval of s in which the line r + s d lies inside the infinite cylinder x^2+z^2 < R^2
 // (axis along y through the origin).  Written with the point of closest approach: its
 // squared distance to the axis is (r x d)^2 / a in the xz-plane, which stays accurate when
-// the start point is far from the axis compared with R.
-bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2) {
+// the start point is far from the axis compared with R.  e (optional) receives both ends
+// with their error scales: the roundings of tc +- half (and of g, R^2 / (half a) after the
+// square root), and the shift of a root under a change of the start point or direction,
+// whose derivative is R / (half a) (the surface point p obeys p.d = half a, |p| = R).
+bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2, End* e = nullptr) {
   double a = d.x * d.x + d.z * d.z;
   if (a == 0.0) {
     if (r.x * r.x + r.z * r.z < R * R) {
       *s1 = -kInf;
       *s2 = kInf;
+      if (e) e[0] = {-kInf, 0.0, 0.0}, e[1] = {kInf, 0.0, 0.0};
       return true;
     }
     return false;
@@ -80,6 +102,19 @@ bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2) {
   double half = std::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
+  if (e) {
+    double lever = R / (half * a);
+    double er = std::fabs(tc) + half + lever * R;
+    double ss[2] = {*s1, *s2};
+    for (int i = 0; i < 2; ++i) {
+      // the crossing point p (|p| = R); a shift of the start along g_dprev moves the root
+      // by its component along p over p.d = half a
+      double px = r.x + ss[i] * d.x, pz = r.z + ss[i] * d.z;
+      double along = std::fabs(px * g_dprev.x + pz * g_dprev.z) / (half * a);
+      e[i] = {ss[i], er,
+              lever * (g_err_r + std::fabs(ss[i]) * g_err_d) + along * g_err_a};
+    }
+  }
   return true;
 }
 
@@ -100,19 +135,27 @@ bool tube_interval(double R, double ux, double uz, double rt, Vec3 r, Vec3 d, do
   if (!(g > 0.0)) return false;
   // the chord is sensitive to the tube radius (rt^2/g) and, through the lever arm, to the
   // direction of the ray (closest-approach distance h, distance |tc| sqrt(a))
-  g_kappa += rt * rt / g + std::fabs(tc) * std::fabs(cr) / g;
+  // and to the error of the start point (|cr| |dr| / (sqrt(a) g))
+  g_kappa += rt * rt / g + std::fabs(tc) * std::fabs(cr) / g +
+             std::fabs(cr) * (g_err_r + g_err_a) / (std::sqrt(a) * g);
   double half = std::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
   return true;
 }
 
-// Interval of s in which |p + s dp| < half.
-bool slab_interval(double half, double p, double dp, double* s1, double* s2) {
+// Interval of s in which |p + s dp| < half.  e (optional): both ends with their error
+// scales, (|p| + half) / |dp| from the roundings (p_rounding: roundings already in p and dp,
+// as multiples of |p| and 1) and (p_err + |s| d_err) / |dp| from the start point and
+// direction (dprev_p: the slab-normal component of the previous ray, along which the start
+// point's distance error lies).
+bool slab_interval(double half, double p, double dp, double* s1, double* s2, End* e = nullptr,
+                   double p_rounding = 0.0, double dprev_p = 1.0) {
   if (dp == 0.0) {
     if (std::fabs(p) < half) {
       *s1 = -kInf;
       *s2 = kInf;
+      if (e) e[0] = {-kInf, 0.0, 0.0}, e[1] = {kInf, 0.0, 0.0};
       return true;
     }
     return false;
@@ -121,66 +164,98 @@ bool slab_interval(double half, double p, double dp, double* s1, double* s2) {
   double b = (half - p) / dp;
   *s1 = std::min(a, b);
   *s2 = std::max(a, b);
+  if (e) {
+    double ad = std::fabs(dp);
+    double er = ((1.0 + p_rounding) * std::fabs(p) + half) / ad;
+    double ea = g_err_r + std::fabs(dprev_p) * g_err_a;
+    e[0] = {*s1, er + p_rounding * std::fabs(*s1) / ad, (ea + std::fabs(*s1) * g_err_d) / ad};
+    e[1] = {*s2, er + p_rounding * std::fabs(*s2) / ad, (ea + std::fabs(*s2) * g_err_d) / ad};
+  }
   return true;
 }
 
 // Keep [a,b] clipped to s >= 0 if it has positive length.  Its length b - lo loses the
-// relative precision |a| + |b| over b - lo (a point close to the exit surface).
-int push_segment(double a, double b, double* sa, double* sb, int n) {
-  double lo = std::max(a, 0.0);
-  if (b > lo) {
-    g_kappa += (std::fabs(a) + std::fabs(b)) / (b - lo);
+// relative precision |a| + |b| over b - lo (a point close to the exit surface), and the
+// error scales of the ends over b - lo (a clipped start, lo = 0, is exact).  ra, rb
+// (optional) receive the error scales of the kept ends, ra0 the start's rounding scale
+// alone (an error of the start point or direction moves the point placed beyond the start
+// surface with that surface).
+int push_segment(End a, End b, double* sa, double* sb, double* ra, double* rb, double* ra0,
+                 int n) {
+  double lo = std::max(a.s, 0.0);
+  if (b.s > lo) {
+    double e_lo = a.s > 0.0 ? a.er + a.ep : 0.0;
+    g_kappa += (std::fabs(a.s) + std::fabs(b.s) + e_lo + b.er + b.ep) / (b.s - lo);
     sa[n] = lo;
-    sb[n] = b;
+    sb[n] = b.s;
+    if (ra) {
+      ra[n] = e_lo;
+      rb[n] = b.er + b.ep;
+      ra0[n] = a.s > 0.0 ? a.er : 0.0;
+    }
     return n + 1;
   }
   return n;
 }
 
-int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double sb[2]) {
+// the later of two interval starts, and the earlier of two ends
+End later(End u, End v) { return v.s > u.s ? v : u; }
+End earlier(End u, End v) { return v.s < u.s ? v : u; }
+
+int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double sb[2],
+                   double ra[2] = nullptr, double rb[2] = nullptr, double ra0[2] = nullptr) {
   // Shapes and their combination (the hollow cylinder is a difference of two cylinders),
-  // paper section 2.4.2 ("Shapes" and constructive solid geometry).
+  // paper section 2.4.2 ("Shapes" and constructive solid geometry).  ra, rb (optional)
+  // receive the error scales of the segment ends, ra0 the starts' rounding scales.
   double y1, y2, c1, c2;
+  End ec[2], ey[2];
   if (sc.kind == ORC_SOLID_CYL) {
-    if (!cylinder_interval(sc.dims[0], r, d, &c1, &c2)) return 0;
-    if (!slab_interval(0.5 * sc.dims[1], r.y, d.y, &y1, &y2)) return 0;
-    return push_segment(std::max(c1, y1), std::min(c2, y2), sa, sb, 0);
+    if (!cylinder_interval(sc.dims[0], r, d, &c1, &c2, ec)) return 0;
+    if (!slab_interval(0.5 * sc.dims[1], r.y, d.y, &y1, &y2, ey, 0.0, g_dprev.y)) return 0;
+    return push_segment(later(ec[0], ey[0]), earlier(ec[1], ey[1]), sa, sb, ra, rb, ra0, 0);
   }
   if (sc.kind == ORC_HOLLOW_CYL) {
-    if (!cylinder_interval(sc.dims[1], r, d, &c1, &c2)) return 0;
-    if (!slab_interval(0.5 * sc.dims[2], r.y, d.y, &y1, &y2)) return 0;
-    double lo = std::max(c1, y1), hi = std::min(c2, y2);
-    if (!(hi > lo)) return 0;
+    if (!cylinder_interval(sc.dims[1], r, d, &c1, &c2, ec)) return 0;
+    if (!slab_interval(0.5 * sc.dims[2], r.y, d.y, &y1, &y2, ey, 0.0, g_dprev.y)) return 0;
+    End lo = later(ec[0], ey[0]), hi = earlier(ec[1], ey[1]);
+    if (!(hi.s > lo.s)) return 0;
     double i1, i2;
-    if (!cylinder_interval(sc.dims[0], r, d, &i1, &i2)) return push_segment(lo, hi, sa, sb, 0);
+    End ei[2];
+    if (!cylinder_interval(sc.dims[0], r, d, &i1, &i2, ei))
+      return push_segment(lo, hi, sa, sb, ra, rb, ra0, 0);
     int n = 0;
-    n = push_segment(lo, std::min(hi, i1), sa, sb, n);
-    n = push_segment(std::max(lo, i2), hi, sa, sb, n);
+    n = push_segment(lo, earlier(hi, ei[0]), sa, sb, ra, rb, ra0, n);
+    n = push_segment(later(lo, ei[1]), hi, sa, sb, ra, rb, ra0, n);
     return n;
   }
   if (sc.kind == ORC_BLOCK) {
     // body frame: the block is rotated by rot_y about +y, so body = R^T lab
     double c = std::cos(sc.rot_y), s = std::sin(sc.rot_y);
-    Vec3 rb = {c * r.x - s * r.z, r.y, s * r.x + c * r.z};
+    Vec3 rb_ = {c * r.x - s * r.z, r.y, s * r.x + c * r.z};
     Vec3 db = {c * d.x - s * d.z, d.y, s * d.x + c * d.z};
-    double lo = -kInf, hi = kInf, a, b;
-    if (!slab_interval(0.5 * sc.dims[0], rb.x, db.x, &a, &b)) return 0;
-    lo = std::max(lo, a);
-    hi = std::min(hi, b);
-    if (!slab_interval(0.5 * sc.dims[1], rb.y, db.y, &a, &b)) return 0;
-    lo = std::max(lo, a);
-    hi = std::min(hi, b);
-    if (!slab_interval(0.5 * sc.dims[2], rb.z, db.z, &a, &b)) return 0;
-    lo = std::max(lo, a);
-    hi = std::min(hi, b);
-    return push_segment(lo, hi, sa, sb, 0);
+    End lo = {-kInf, 0.0, 0.0}, hi = {kInf, 0.0, 0.0}, e[2];
+    double a, b;
+    // the rotated coordinates carry a few more roundings of |r| and |d|
+    double px = c * g_dprev.x - s * g_dprev.z, pz = s * g_dprev.x + c * g_dprev.z;
+    if (!slab_interval(0.5 * sc.dims[0], rb_.x, db.x, &a, &b, e, 3.0, px)) return 0;
+    lo = later(lo, e[0]);
+    hi = earlier(hi, e[1]);
+    if (!slab_interval(0.5 * sc.dims[1], rb_.y, db.y, &a, &b, e, 0.0, g_dprev.y)) return 0;
+    lo = later(lo, e[0]);
+    hi = earlier(hi, e[1]);
+    if (!slab_interval(0.5 * sc.dims[2], rb_.z, db.z, &a, &b, e, 3.0, pz)) return 0;
+    lo = later(lo, e[0]);
+    hi = earlier(hi, e[1]);
+    return push_segment(lo, hi, sa, sb, ra, rb, ra0, 0);
   }
   return 0;
 }
 
 struct Segment {
   double sa, sb;
-  int j;  // scatterer index
+  int j;         // scatterer index
+  double ra, rb;  // error scales of the ends (units of the FP64 epsilon, metres)
+  double ra0;     // rounding scale of the start alone
 };
 
 // All material segments ahead of the ray, sorted by entry distance (ray tracing in a
@@ -188,9 +263,9 @@ struct Segment {
 int assembly_segments(const orc_config& cfg, Vec3 r, Vec3 d, Segment* out) {
   int n = 0;
   for (int j = 0; j < cfg.n_scat; ++j) {
-    double sa[2], sb[2];
-    int m = shape_segments(cfg.scat[j], r, d, sa, sb);
-    for (int i = 0; i < m; ++i) out[n++] = {sa[i], sb[i], j};
+    double sa[2], sb[2], ra[2], rb[2], ra0[2];
+    int m = shape_segments(cfg.scat[j], r, d, sa, sb, ra, rb, ra0);
+    for (int i = 0; i < m; ++i) out[n++] = {sa[i], sb[i], j, ra[i], rb[i], ra0[i]};
   }
   for (int i = 1; i < n; ++i) {  // insertion sort by entry
     Segment key = out[i];
@@ -900,6 +975,11 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
   g_kappa = 1.0;
   g_kappa_v = 2.0;
   if (!make_beam(cfg, nid, &n)) return;
+  // the start point's transverse coordinates are rounded once; the direction a few times
+  g_err_r = std::fabs(n.r.x) + std::fabs(n.r.y);
+  g_err_a = 0.0;
+  g_dprev = n.d;
+  g_err_d = 4.0;
   for (int o = 0;; ++o) {
     if (n.w < cfg.min_prob) break;
     if (stop_on_zero && n.w == 0.0) break;
@@ -933,6 +1013,10 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     // scattering point, uniform over the material length ahead
     double ell = u[0] * L;
     double acc = 0.0, tau_pt = 0.0, s_pt = 0.0, lg_pt = 0.0;
+    // error scale of the scattering distance: the rounding of the chosen segment's start,
+    // the lengths summed into acc and (times u) into L, and the roundings of ell and s_pt
+    double e_pt = std::fabs(ell);
+    for (int i = 0; i < ns; ++i) e_pt += u[0] * (seg[i].ra + seg[i].rb);
     int j = seg[ns - 1].j;
     for (int i = 0; i < ns; ++i) {
       double len = seg[i].sb - seg[i].sa;
@@ -940,6 +1024,8 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
       if (ell < acc + len || i == ns - 1) {
         double part = ell - acc;
         s_pt = seg[i].sa + part;
+        e_pt += seg[i].ra0 + std::fabs(s_pt);
+        for (int m = 0; m < i; ++m) e_pt += seg[m].ra + seg[m].rb;
         tau_pt += mu * part;
         if (seg[i].j == gs) lg_pt += part;
         j = seg[i].j;
@@ -961,6 +1047,10 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     }
     n.r = add(n.r, scale(n.d, s_pt));
     n.t = n.t + s_pt / n.speed;
+    // the new point: the error of s_pt along the ray, and the roundings of its coordinates
+    g_err_a = e_pt;
+    g_dprev = n.d;
+    g_err_r = std::sqrt(dot(n.r, n.r)) + std::fabs(s_pt);
     // kernel choice with probability sigma_k / sigma_s (weight unchanged)
     int k = 0;
     if (sc.nk == 2 && !(u[1] * (sc.ksig_b[0] + sc.ksig_b[1]) < sc.ksig_b[0])) k = 1;
@@ -974,6 +1064,8 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     rec.a_factor = rec.a_factor * ko.rest;
     n.d = ko.d;
     n.speed = ko.speed;
+    // an isotropic direction is drawn afresh; the others are built on the incoming one
+    g_err_d = sc.ktype[k] == ORC_K_ISO ? 4.0 : g_err_d + 8.0;
     on_scatter(o + 1, sc.ktype[k], j, ko, rec, n.w);
   }
 }
