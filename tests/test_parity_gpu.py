@@ -38,8 +38,22 @@ def _small_c2(n):
     return mi.config2(n=n)
 
 
+def _powder_in_can(n):
+    return mi.powder_in_can(n)
+
+
+def _can_10mev(n):
+    return mi.powder_in_can(n, ei=10.0)
+
+
+def _can_500mev(n):
+    return mi.powder_in_can(n, ei=500.0)
+
+
 # ---------------------------------------------------------------- FP64 per packet
-@pytest.mark.parametrize("make,n", [(mi.config1, 20000), (_small_c2, 20000)])
+@pytest.mark.parametrize("make,n", [(mi.config1, 20000), (_small_c2, 20000),
+                                    (_powder_in_can, 20000), (_can_10mev, 20000),
+                                    (_can_500mev, 20000)])
 def test_fp64_packets_match_oracle(ctx, make, n):
     wl = make(n)
     pk, g = H.packets(ctx, wl, B.FP64)
@@ -247,7 +261,8 @@ def rate_bound(rate, n):
     return mu + 4.0 * np.sqrt(mu) + 1.0
 
 
-@pytest.mark.parametrize("make,n", [(mi.config1, 200000), (_small_c2, 200000)])
+@pytest.mark.parametrize("make,n", [(mi.config1, 200000), (_small_c2, 200000),
+                                    (_powder_in_can, 200000)])
 def test_fp32_fast_mode_within_bounds(ctx, make, n):
     wl = make(n)
     st = fp32_stats(ctx, wl)
