@@ -287,3 +287,65 @@ def test_kernel_factor_against_40_digit_reference():
         assert err <= 4 * 2.2e-16 * dk + 1e-15, (i, k, err, dk)
         checked += 1
     assert checked == 12
+
+
+# ---- root bracketing against a dense scan ----------------------------------------------------
+def _g_dense(ef, df, rot, ei, b, s):
+    """g(Ef) = Ei - Ef - s hw_b(Q(Ef)) at many Ef (numpy eigh, branches ascending)."""
+    speed = math.sqrt(ei / C_EV)
+    ki = C_KV * speed
+    kf = C_KV * np.sqrt(np.maximum(ef, 0.0) / C_EV)
+    Q = ki * np.array([0, 0, 1.0])[None] - kf[:, None] * df[None]
+    lam = np.linalg.eigvalsh(dynmat(_lab_to_crystal(Q, rot)))
+    return ei - ef - s * hw_of(lam[:, b])
+
+
+def test_roots_against_dense_scan():
+    """The 32-sub-interval bracketing of g (section S4 single-crystal kernel, our reading):
+    every root the oracle solves is a root of g found independently (dense scan with numpy's
+    eigen-solver, refined by Brent's method) in the same sub-interval; a sub-interval holds
+    an odd number of dense roots exactly when the oracle brackets one there; and the roots the
+    bracketing cannot see (pairs inside one sub-interval) are rare."""
+    brentq = pytest.importorskip("scipy.optimize").brentq
+    rng = np.random.default_rng(21)
+    ei = 50.0
+    speed = math.sqrt(ei / C_EV)
+    w_max = HBAR * math.sqrt(24 * 10.0 / (27 * AMU)) / (QE * 1e-3)
+    n_dense, n_missed, n_checked = 0, 0, 0
+    for _ in range(60):
+        rot = math.radians(rng.uniform(0, 180))
+        u0, u1 = rng.random(2)
+        ct, st = 2 * u0 - 1, 2 * math.sqrt(u0 * (1 - u0))
+        df = np.array([st * math.cos(2 * math.pi * u1), st * math.sin(2 * math.pi * u1), ct])
+        for m in range(6):
+            b, s = m % 3, (1 if m < 3 else -1)
+            lo, hi = (0.0, ei) if s > 0 else (ei, ei + w_max)
+            step = (hi - lo) / 32
+            u2 = (m + 0.5) / 6
+            nr = int(oracle.kernel_bvk(WL, rot, speed, [0, 0, 1], [u0, u1, u2, 0.5])
+                     ["event"]["nroots"])
+            # dense scan: 128 points per sub-interval, sub-interval ends included
+            ef = lo + step * np.arange(32 * 128 + 1) / 128
+            g = _g_dense(ef, df, rot, ei, b, s)
+            roots = []
+            for k in np.flatnonzero((g[:-1] > 0) != (g[1:] > 0)):
+                f = lambda e: _g_dense(np.array([e]), df, rot, ei, b, s)[0]  # noqa: E731
+                roots.append(brentq(f, ef[k], ef[k + 1], xtol=1e-13, rtol=1e-15))
+            roots = np.array(roots)
+            sub = np.minimum(((roots - lo) / step).astype(int), 31)
+            bracketed = [k for k in range(32) if (g[128 * k] > 0) != (g[128 * (k + 1)] > 0)]
+            assert len(bracketed) == nr, (rot, u0, u1, m, bracketed, nr)
+            for k in range(32):
+                assert (np.sum(sub == k) % 2 == 1) == (k in bracketed)
+            n_dense += len(roots)
+            n_missed += len(roots) - nr
+            for r in range(nr):
+                out = oracle.kernel_bvk(WL, rot, speed, [0, 0, 1], [u0, u1, u2, (r + 0.5) / nr])
+                if not out["ok"]:
+                    continue
+                e_f = C_EV * out["speed"] ** 2
+                cand = roots[sub == bracketed[r]]
+                assert np.min(np.abs(cand - e_f)) < 1e-7, (e_f, cand)
+                n_checked += 1
+    assert n_checked > 200
+    assert n_missed <= 0.01 * n_dense, (n_missed, n_dense)
