@@ -537,7 +537,7 @@ def run_ours(args):
         e2e = {"value": world * N * args.e2e_steps / (gms / 1e3), "unit": "neutrons/s",
                "h2d_bytes_per_step": int(host_table.numel() * 4),
                "d2h_bytes_per_step": int((counts.numel() + tallies.numel()) * 8),
-               "ms_per_step": gms / args.e2e_steps,
+               "ms_per_step": gms / args.e2e_steps, "steps": args.e2e_steps,
                "pipelining": "two histogram buffers; step k's read-back overlaps step k+1's "
                              "trace on a second stream"}
         del dev_bufs, host_bufs
@@ -601,7 +601,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    # default: as many steps as the device-timed region (the last read-back, which nothing
+    # overlaps, is spread over the same number of steps)
+    ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--cpu-per-worker", type=int, default=1_000_000)
     ap.add_argument("--ref-per-worker", type=int, default=400_000)
     ap.add_argument("--no-e2e", action="store_true")
@@ -612,6 +614,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
