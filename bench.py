@@ -479,8 +479,10 @@ def run_ours(args):
     # and the differentiable form
     batched = None
     differentiable = None
-    if not args.no_batch and world == 1:
+    extras = "none" if args.no_batch else args.extras
+    if world == 1 and extras in ("all", "batch"):
         batched = batch_extras(ctx, args)
+    if world == 1 and extras in ("all", "grad"):
         differentiable = grad_extras(ctx, value64)
 
     # ---- end to end through the public API with host buffers: every step copies the
@@ -608,7 +610,10 @@ def main():
     ap.add_argument("--ref-per-worker", type=int, default=400_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched and the differentiable forms (same as --extras none)")
+    ap.add_argument("--extras", default="all", choices=["all", "batch", "grad", "none"],
+                    help="which of the batched and differentiable forms to run")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--crystal-fp64-stride", type=int, default=18)
     args = ap.parse_args()

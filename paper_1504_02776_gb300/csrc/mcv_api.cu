@@ -415,6 +415,7 @@ mcv_status build_trace_args_for_grad(const mcv_sample* sample, const mcv_beam_pa
   if (st != MCV_OK) return st;
   st = build_beam(beam, &A->Bd);
   if (st != MCV_OK) return st;
+  set_miss_bounds(A->Sd, &A->Bd);
   st = build_detector(det, &A->Dd);
   if (st != MCV_OK) return st;
   cast_all(A);
@@ -668,6 +669,7 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
   if (st != MCV_OK) return st;
   st = build_beam(beam, &A.Bd);
   if (st != MCV_OK) return st;
+  set_miss_bounds(A.Sd, &A.Bd);
   st = build_detector(det, &A.Dd);
   if (st != MCV_OK) return st;
   if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))

@@ -5,6 +5,8 @@
 //
 // Policy interface (device, per lane):
 //   kWantsGs                        compile-time: path lengths in scatterer A.gs are needed
+//   kMeetingOnly                    compile-time: only neutrons that meet the sample matter
+//                                   (their other packets carry nothing the policy uses)
 //   start(L)                        a new neutron begins
 //   emit(A, tu, rng, L, we, atten, lg)   packet of order L.o with weight we = w e^{-tau}
 //   scatter(A, L, j, a_fac, out, lg_pt, speed_in)  after the kernel of order L.o scattered
@@ -151,6 +153,21 @@ __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R
   return true;
 }
 
+// The source draw of a neutron that matters only if it meets the sample: false as soon as
+// the footprint (host-derived sure-miss bounds) or the direction shows that it misses, which
+// skips the later draws; otherwise the same packet as make_beam.
+template <typename R, int NS, class Rng>
+__device__ __forceinline__ bool make_beam_meeting(const BeamP<R>& B, const SampleP<R>& S,
+                                                  const Rng& rng, Ray<R>* n) {
+  R aux;
+  beam_footprint(B, rng, n);
+  if (surely_misses<R>(B, *n)) return false;
+  beam_divergence(B, rng, n, &aux);
+  Seg<R> seg[2 * NS];
+  if (assembly_segs<R, NS>(S, *n, seg) == 0) return false;
+  return beam_energy(B, rng, aux, n);
+}
+
 // One order of one neutron: segments ahead, emission of the transmitted packet, then the
 // scattered packet continues.  Returns whether the neutron is still alive.
 template <typename R, int NS, int DET, int KS, class P>
@@ -198,7 +215,8 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
             ok = load_input<R>(A, i, &L.n);
           } else {
             const NeutronRng rng(A.keys, L.nid);
-            ok = make_beam<R>(Bof<R>(A), rng, &L.n);
+            ok = P::kMeetingOnly ? make_beam_meeting<R, NS>(Bof<R>(A), Sof<R>(A), rng, &L.n)
+                                 : make_beam<R>(Bof<R>(A), rng, &L.n);
           }
           ok = ok && !(L.n.w < Sof<R>(A).min_prob) && !(A.stop_on_zero && L.n.w == R(0));
           if (!ok) pol.clear(A, i, 0);

@@ -62,6 +62,7 @@ struct RegTally {
 template <typename R, int DET, class Out = LaunchOut, class Store = RegTally<R>>
 struct Forward {
   static constexpr bool kWantsGs = false;
+  static constexpr bool kMeetingOnly = false;
   Store store;
   int err = 0;
 
@@ -739,6 +740,9 @@ constexpr int kMaxOrders = 7;
 template <typename R, int DET>
 struct Adjoint {
   static constexpr bool kWantsGs = true;
+  // a neutron that does not meet the sample only reaches the beam stop, which carries no
+  // gradient: its divergence and energy are not drawn
+  static constexpr bool kMeetingOnly = true;
   R a[kMaxOrders];   // scattering factor without the table value
   R s[kMaxOrders];   // table value (1 for kernels without a table)
   int e[kMaxOrders]; // table entry or -1
