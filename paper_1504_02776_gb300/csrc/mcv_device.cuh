@@ -849,9 +849,6 @@ __device__ __forceinline__ bool kernel_bvk(const SampleP<R>& S, R crot, R srot,
   const int iters = sizeof(R) == 8 ? 50 : 24;
   for (int it = 0; it < iters; ++it) {
     const R mid = R(0.5) * (ea + eb);
-    // adjacent ends: mid is one of them, whose side is known, so this and every later
-    // step would leave (ea, eb) unchanged
-    if (mid == ea || mid == eb) break;
     const BvkPoint<R> P = bvk_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy, dfz,
                                        mid, b, sg);
     if ((P.g > R(0)) == ga_pos)
