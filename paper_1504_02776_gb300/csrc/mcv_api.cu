@@ -214,6 +214,7 @@ mcv_status build_detector(const mcv_detector* d, mcv::DetP<double>* D) {
   }
   if (npix > ((int64_t)1 << 31) - 1) return fail(MCV_EINVAL, "too many pixels");
   D->n_bins = npix * d->n_tof;
+  set_det_miss_bounds(-1.0, D);  // off until the packets are known to start in a sample
   return MCV_OK;
 }
 
@@ -249,6 +250,57 @@ void set_miss_bounds(const mcv::SampleP<double>& S, mcv::BeamP<double>* B) {
   const double shift = (B->z0 + r) * std::tan(a) * 1.01 + 1e-6;
   B->x_safe = r + shift;
   B->y_safe = hh + shift;
+}
+
+// radius of a cylinder about the y axis that holds every scatterer of the sample
+double sample_radius(const mcv::SampleP<double>& S) {
+  double r = 0.0;
+  for (int j = 0; j < S.ns; ++j) {
+    const mcv::ScatP<double>& c = S.s[j];
+    if (c.shape == MCV_SHAPE_SOLID_CYL)
+      r = std::max(r, c.dim0);
+    else if (c.shape == MCV_SHAPE_HOLLOW_CYL)
+      r = std::max(r, c.dim1);
+    else
+      r = std::max(r, 0.5 * std::hypot(c.dim0, c.dim2));
+  }
+  return r;
+}
+
+// Sure-miss bounds of the tube system for packets that start inside a sample of radius
+// r_s (every scattered packet does).  Height: the tubes' vertical extent, 1 mm margin; the
+// horizontal path to the tube ring is at least R - r_t - 1 mm minus the start's |x| + |z|.
+// Direction: the arc of tube centres widened by the tube radius, by the angle the sample's
+// extent subtends at the ring (asin(r_s / (R - r_t))) and by 1 mrad; off when it reaches
+// half a turn.  The bounds only skip packets the detector trace would find missing.
+void set_det_miss_bounds(double r_s, mcv::DetP<double>* D) {
+  D->miss_r_in = 0.0;
+  D->miss_y_top = INFINITY;
+  D->miss_y_bot = -INFINITY;
+  D->miss_phi = 0;
+  if (D->kind != MCV_DET_TUBES || !(r_s >= 0.0)) return;
+  const double r_in = D->radius - D->tube_r - 1e-3;
+  if (!(r_in > 2.0 * r_s)) return;
+  double top = -INFINITY, bot = INFINITY;
+  int packs = 0;
+  for (int i = 0; i < D->n_rows; ++i) {
+    top = std::max(top, D->row_y[i] + D->half_len);
+    bot = std::min(bot, D->row_y[i] - D->half_len);
+    packs = std::max(packs, D->packs[i]);
+  }
+  D->miss_r_in = r_in;
+  D->miss_y_top = top + 1e-3;
+  D->miss_y_bot = bot - 1e-3;
+  const double widen = std::asin(std::min(1.0, r_s / r_in)) +
+                       std::asin(std::min(1.0, D->tube_r / r_in)) + 1e-3;
+  const double lo = D->phi0 - widen;
+  const double hi = D->phi0 + packs * D->period / D->radius + widen;
+  if (!(hi - lo < 0.95 * mcv::kPi)) return;
+  D->miss_phi = 1;
+  D->miss_a_x = std::sin(lo);
+  D->miss_a_z = std::cos(lo);
+  D->miss_b_x = std::sin(hi);
+  D->miss_b_z = std::cos(hi);
 }
 
 // float copies of the parameter blocks for the FP32 kernels
@@ -340,6 +392,14 @@ void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
   f->pix_len = (float)d.pix_len;
   f->mu_he_v = (float)d.mu_he_v;
   f->win = d.win;
+  f->miss_r_in = (float)d.miss_r_in;
+  f->miss_y_top = (float)d.miss_y_top;
+  f->miss_y_bot = (float)d.miss_y_bot;
+  f->miss_phi = d.miss_phi;
+  f->miss_a_x = (float)d.miss_a_x;
+  f->miss_a_z = (float)d.miss_a_z;
+  f->miss_b_x = (float)d.miss_b_x;
+  f->miss_b_z = (float)d.miss_b_z;
   for (int i = 0; i < 2 * MCV_MAX_TUBES_PER_ROW; ++i) f->tube_u[i] = (float)d.tube_u[i];
 }
 
@@ -418,6 +478,7 @@ mcv_status build_trace_args_for_grad(const mcv_sample* sample, const mcv_beam_pa
   set_miss_bounds(A->Sd, &A->Bd);
   st = build_detector(det, &A->Dd);
   if (st != MCV_OK) return st;
+  set_det_miss_bounds(sample_radius(A->Sd), &A->Dd);
   cast_all(A);
   return MCV_OK;
 }
@@ -557,6 +618,8 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   if (fused) {
     st = build_detector(det, &A.Dd);
     if (st != MCV_OK) return st;
+    // generated neutrons: every detected packet starts at a scattering point in the sample
+    if (!in) set_det_miss_bounds(sample_radius(A.Sd), &A.Dd);
     if (!hist || (!hist->counts && !hist->tallies))
       return fail(MCV_EINVAL, "a detector needs a histogram or tallies");
   }
@@ -672,6 +735,7 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
   set_miss_bounds(A.Sd, &A.Bd);
   st = build_detector(det, &A.Dd);
   if (st != MCV_OK) return st;
+  set_det_miss_bounds(sample_radius(A.Sd), &A.Dd);
   if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
     return fail(MCV_EINVAL, "bad neutron range");
   if (!target || !g_work || !loss || !dsig || !hist || !hist->counts)

@@ -43,7 +43,6 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
   if (fp_mode != MCV_FP64 && fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
   mcv_status st = build_detector(det, &A->Dd);
   if (st != MCV_OK) return st;
-  cast_detector(A->Dd, &A->Df);
   im->fp = fp_mode;
   im->det = A->Dd.kind;
   im->nsims = nsims;
@@ -52,6 +51,7 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
   im->n.assign(nsims, 0);
   int ns = 1, bvk = 0, same = 1;
   int64_t total = 0;
+  double r_s = 0.0;  // radius holding every simulation's sample
   mcv::SampleP<double> first;
   for (int k = 0; k < nsims; ++k) {
     const mcv_sim& s = sims[k];
@@ -65,6 +65,7 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
     st = build_beam(s.beam, &d.B);
     if (st != MCV_OK) return fail(st, who + mcv_last_error());
     set_miss_bounds(d.S, &d.B);
+    r_s = std::max(r_s, sample_radius(d.S));
     if (s.n < 0 || s.n > kMaxNeutrons || s.first_id < 0 ||
         s.first_id > (((int64_t)1 << 62) - s.n))
       return fail(MCV_EINVAL, who + "bad neutron range");
@@ -109,6 +110,9 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
       put_sim(im, k, d);
     }
   }
+  // every detected packet starts at a scattering point in one of the samples
+  set_det_miss_bounds(r_s, &A->Dd);
+  cast_detector(A->Dd, &A->Df);
   im->ns = ns <= 1 ? 1 : (ns == 2 ? 2 : 4);
   im->bvk = bvk;
   im->ss = same;

@@ -990,6 +990,26 @@ __device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const TofWin&
 }
 
 // tube centre directions staged in shared memory: tu[2*i] = sin(phi_i), tu[2*i+1] = cos(phi_i)
+// A packet that surely misses every tube (DetP::miss_*: set for packets that start inside the
+// sample): on its way out to the tube ring its height only moves further beyond the rows,
+// or its horizontal direction points away from the arc of tubes.  A few operations, no
+// square root; the detector trace would find the same packets missing.
+template <typename R>
+__device__ __forceinline__ bool det_surely_misses(const DetP<R>& D, const Ray<R>& n) {
+  using M = Mth<R>;
+  // horizontal path to the ring >= miss_r_in - (|x| + |z|); along it y moves by at least
+  // |dy| times that length (|d_h| <= 1)
+  const R lmin = D.miss_r_in - (M::fabs(n.x) + M::fabs(n.z));
+  if (lmin > R(0)) {
+    const R y_far = n.y + n.dy * lmin;
+    if ((n.dy >= R(0) && y_far > D.miss_y_top) || (n.dy <= R(0) && y_far < D.miss_y_bot))
+      return true;
+  }
+  // sin of the angle from each end of the arc to the direction (phi = atan2(x, z))
+  return D.miss_phi && (n.dx * D.miss_a_z - n.dz * D.miss_a_x < R(0) ||
+                        n.dz * D.miss_b_x - n.dx * D.miss_b_z < R(0));
+}
+
 // Where a packet meets the tube rows: the row at its crossing of the tube-centre circle and
 // the tube g nearest to that crossing (candidates g - 1, g, g + 1).  False: it meets no row
 // or lies outside the rows' arc (no candidate tube), i.e. it misses the detector.

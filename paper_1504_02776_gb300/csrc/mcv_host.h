@@ -41,6 +41,8 @@ mcv_status build_detector(const mcv_detector* d, DetP<double>* D);
 TofWin tof_window(double tof_min_s, double tof_max_s, int n_tof);
 PhiloxKeys philox_keys(uint32_t seed, uint32_t sim_id);
 void set_miss_bounds(const SampleP<double>& S, BeamP<double>* B);
+double sample_radius(const SampleP<double>& S);
+void set_det_miss_bounds(double r_s, DetP<double>* D);
 void cast_beam(const BeamP<double>& d, BeamP<float>* f);
 void cast_sample(const SampleP<double>& d, SampleP<float>* f);
 void cast_detector(const DetP<double>& d, DetP<float>* f);

@@ -442,7 +442,9 @@ __device__ __forceinline__ void run_waves(const TraceArgs& A, const Job& job, in
         if (st.len_tot > R(0)) pol.hit();
       } else {
         pol.emitted();
-        if (!kLocateEarly || tubes_locate<R>(D, L.n, &row, &g))
+        if (DET == MCV_DET_TUBES && det_surely_misses<R>(D, L.n))
+          pol.missed();
+        else if (!kLocateEarly || tubes_locate<R>(D, L.n, &row, &g))
           to_det = true;
         else
           pol.missed();

@@ -98,6 +98,14 @@ struct DetP {
   R tube_r, half_len, pitch, period, phi0, pix_len;
   R mu_he_v;        // 100 n sigma 2200: mu(v) = mu_he_v / v (1/m)
   TofWin win;
+  // packets that surely miss every tube (tube system; set when the packets start inside a
+  // known sample, else off): a packet whose horizontal path to the tube ring is at least
+  // miss_r_in - (|x| + |z|) and whose height there lies above miss_y_top or below
+  // miss_y_bot, or (miss_phi) whose horizontal direction lies outside the arc from
+  // (miss_a_x, miss_a_z) to (miss_b_x, miss_b_z) that holds every tube seen from the sample
+  R miss_r_in, miss_y_top, miss_y_bot;
+  int miss_phi;
+  R miss_a_x, miss_a_z, miss_b_x, miss_b_z;
   R tube_u[2 * MCV_MAX_TUBES_PER_ROW];  // sin, cos of every tube centre angle of a row
 };
 
