@@ -33,8 +33,10 @@ N_DEFAULT = 100_000_000
 
 # Algorithmic cost model of the path (lane operations: FP32/INT32 arithmetic, each
 # transcendental counted as its instruction sequence, a Philox4x32-10 block as ~110), per
-# event type.  Derivation in DESIGN.md ("Roofline").  Event counts come from the run's own
-# tallies, and the share of footprints that can lead into the sample from the geometry.
+# event type.  Event counts come from the run's own tallies, and the share of footprints
+# that can lead into the sample from the geometry.  A packet that misses the detector is
+# counted at the cost of the cheapest test that can tell (the height/direction bounds):
+# the model counts the least work the path needs, not the work the kernel happens to do.
 COST = {
     "footprint": 130,   # 1 Philox block, footprint, sure-miss test
     "direction": 190,   # 1 Philox block, Box-Muller, 2 tan, normalisation
@@ -43,7 +45,8 @@ COST = {
     "scatter": 465,     # scattering point (Philox, exp, move) + S(Q,E) kernel (2 Philox,
                         # kinematics, 2 sqrt, table lookup, rotation with sincos)
     "detect": 280,      # circle crossing, atan2, 3 tube chords, absorption (Philox, expm1,
-                        # log1p), pixel, tof
+                        # log1p), pixel, tof -- a detected packet (in or outside the window)
+    "miss": 15,         # a missed packet: height and direction bounds
     "hist": 6,          # bin index and one FP64 atomic add
 }
 
@@ -75,15 +78,17 @@ def ops_per_step(n, t, wl):
     """Lane operations of one step from its event counts (n incident neutrons; tallies t):
     every incident neutron's footprint, the direction and first segments of the footprints
     that may lead into the sample, the energy and order-0 step of those that meet it, and
-    per scattering the kernel, the next order's segments and the emitted packet's detector
-    trace; one histogram add per detected event."""
+    per scattering the kernel and the next order's segments; per emitted packet its detector
+    trace (a missed packet: the bounds test that finds it missing); one histogram add per
+    detected event."""
     from paper_1504_02776_gb300 import binding as B
     emitted = t[B.T_NEMIT]
     hits = t[B.T_NHIT]
     maybe = n * maybe_fraction(wl)
     return (n * COST["footprint"] + maybe * (COST["direction"] + COST["segments"])
             + hits * (COST["energy"] + COST["segments"])
-            + emitted * (COST["scatter"] + COST["segments"] + COST["detect"])
+            + emitted * (COST["scatter"] + COST["segments"])
+            + (t[B.T_NDET] + t[B.T_NOVER]) * COST["detect"] + t[B.T_NMISS] * COST["miss"]
             + t[B.T_NDET] * COST["hist"])
 
 
