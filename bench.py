@@ -502,27 +502,35 @@ def run_ours(args):
                       torch.empty(tallies.numel(), dtype=torch.float64).pin_memory())
                      for _ in range(2)]
         hists = [B.Hist(c.data_ptr(), tl.data_ptr()) for c, tl in dev_bufs]
-        copy_stream = torch.cuda.Stream()
+        # the read-back is split over several copy streams (one copy engine each)
+        n_copy = 4
+        copy_streams = [torch.cuda.Stream() for _ in range(n_copy)]
         ready = [torch.cuda.Event() for _ in range(2)]
-        copied = [torch.cuda.Event() for _ in range(2)]
-        for ev in copied:
-            ev.record(copy_stream)
+        copied = [[torch.cuda.Event() for _ in range(n_copy)] for _ in range(2)]
+        for evs_j in copied:
+            for ev, cs in zip(evs_j, copy_streams):
+                ev.record(cs)
+        cuts = [counts.numel() * q // n_copy for q in range(n_copy + 1)]
 
         def e2e_step(k):
             j = k % 2
             c_j, t_j = dev_bufs[j]
-            stream.wait_event(copied[j])  # the previous read-back of this buffer is done
+            for ev in copied[j]:  # the previous read-back of this buffer is done
+                stream.wait_event(ev)
             table.copy_(host_table.view(-1).view_as(table), non_blocking=True)
             B.mcv_zero(ctx.handle, c_j.data_ptr(), c_j.numel(), sptr)
             B.mcv_zero(ctx.handle, t_j.data_ptr(), t_j.numel(), sptr)
             B.mcv_trace_sample(ctx.handle, sample32, beam, None, wl.seed, wl.sim_id, first, N,
                                det, hists[j], None, sptr)
             ready[j].record(stream)
-            copy_stream.wait_event(ready[j])
-            with torch.cuda.stream(copy_stream):
-                host_bufs[j][0].copy_(c_j, non_blocking=True)
-                host_bufs[j][1].copy_(t_j, non_blocking=True)
-            copied[j].record(copy_stream)
+            for q, cs in enumerate(copy_streams):
+                cs.wait_event(ready[j])
+                with torch.cuda.stream(cs):
+                    a, b = cuts[q], cuts[q + 1]
+                    host_bufs[j][0][a:b].copy_(c_j[a:b], non_blocking=True)
+                    if q == 0:
+                        host_bufs[j][1].copy_(t_j, non_blocking=True)
+                copied[j][q].record(cs)
 
         for k in range(2):
             e2e_step(k)
@@ -532,8 +540,9 @@ def run_ours(args):
         g0.record(stream)
         for k in range(args.e2e_steps):
             e2e_step(k)
-        for ev in copied:
-            stream.wait_event(ev)
+        for evs_j in copied:
+            for ev in evs_j:
+                stream.wait_event(ev)
         g1.record(stream)
         torch.cuda.synchronize()
         gms = g0.elapsed_time(g1)
@@ -545,8 +554,8 @@ def run_ours(args):
                "h2d_bytes_per_step": int(host_table.numel() * 4),
                "d2h_bytes_per_step": int((counts.numel() + tallies.numel()) * 8),
                "ms_per_step": gms / args.e2e_steps, "steps": args.e2e_steps,
-               "pipelining": "two histogram buffers; step k's read-back overlaps step k+1's "
-                             "trace on a second stream"}
+               "pipelining": "two histogram buffers; step k's read-back (split over %d copy "
+                             "streams) overlaps step k+1's trace" % n_copy}
         del dev_bufs, host_bufs
         ctx.sync()
 
