@@ -503,7 +503,7 @@ def run_ours(args):
                      for _ in range(2)]
         hists = [B.Hist(c.data_ptr(), tl.data_ptr()) for c, tl in dev_bufs]
         # the read-back is split over several copy streams (one copy engine each)
-        n_copy = 4
+        n_copy = 8
         copy_streams = [torch.cuda.Stream() for _ in range(n_copy)]
         ready = [torch.cuda.Event() for _ in range(2)]
         copied = [[torch.cuda.Event() for _ in range(n_copy)] for _ in range(2)]

@@ -76,7 +76,10 @@ def test_fp64_packets_match_oracle(ctx, make, n):
     assert np.all(np.abs(hc - ho) <= tol + 1e-15 * np.abs(ho))
 
 
-@pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 50000)])
+# the fused tube-system runs also cover the detector sure-miss bounds of the sample stage:
+# the detected, missed and out-of-window counts must equal the oracle's, which has no bounds
+@pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 400000),
+                                    (_powder_in_can, 200000), (_can_10mev, 100000)])
 def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     wl = make(n)
     counts, tallies = ctx.trace(wl, fp_mode=B.FP64)
