@@ -271,8 +271,8 @@ double sample_radius(const mcv::SampleP<double>& S) {
 // r_s (every scattered packet does).  Height: the tubes' vertical extent, 1 mm margin; the
 // horizontal path to the tube ring is at least R - r_t - 1 mm minus the start's |x| + |z|.
 // Direction: the arc of tube centres widened by the tube radius, by the angle the sample's
-// extent subtends at the ring (asin(r_s / (R - r_t))) and by 1 mrad; off when it reaches
-// half a turn.  The bounds only skip packets the detector trace would find missing.
+// extent subtends at the ring (asin(r_s / (R - r_t))) and by 1 mrad; off when it comes
+// within 10 mrad of half a turn.  The bounds only skip packets the detector trace would find missing.
 void set_det_miss_bounds(double r_s, mcv::DetP<double>* D) {
   D->miss_r_in = 0.0;
   D->miss_y_top = INFINITY;
@@ -295,7 +295,7 @@ void set_det_miss_bounds(double r_s, mcv::DetP<double>* D) {
                        std::asin(std::min(1.0, D->tube_r / r_in)) + 1e-3;
   const double lo = D->phi0 - widen;
   const double hi = D->phi0 + packs * D->period / D->radius + widen;
-  if (!(hi - lo < 0.95 * mcv::kPi)) return;
+  if (!(hi - lo < mcv::kPi - 0.01)) return;  // the two-sided test holds for arcs under a half turn
   D->miss_phi = 1;
   D->miss_a_x = std::sin(lo);
   D->miss_a_z = std::cos(lo);

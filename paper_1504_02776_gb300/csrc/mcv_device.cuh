@@ -997,13 +997,15 @@ __device__ __forceinline__ Hit<R> detect_surface(const DetP<R>& D, const TofWin&
 template <typename R>
 __device__ __forceinline__ bool det_surely_misses(const DetP<R>& D, const Ray<R>& n) {
   using M = Mth<R>;
-  // horizontal path to the ring >= miss_r_in - (|x| + |z|); along it y moves by at least
-  // |dy| times that length (|d_h| <= 1)
+  // horizontal path to the ring >= lmin = miss_r_in - (|x| + |z|); along it y moves by
+  // |dy| lmin / |d_h| at least: beyond the rows when the room left above (below) the start,
+  // a, is below that, a |d_h| < |dy| lmin, compared squared (no square root)
   const R lmin = D.miss_r_in - (M::fabs(n.x) + M::fabs(n.z));
   if (lmin > R(0)) {
-    const R y_far = n.y + n.dy * lmin;
-    if ((n.dy >= R(0) && y_far > D.miss_y_top) || (n.dy <= R(0) && y_far < D.miss_y_bot))
-      return true;
+    const R a = n.dy >= R(0) ? D.miss_y_top - n.y : n.y - D.miss_y_bot;
+    const R h2 = n.dx * n.dx + n.dz * n.dz;
+    const R m = n.dy * lmin;
+    if (a <= R(0) || a * a * h2 < m * m) return true;
   }
   // sin of the angle from each end of the arc to the direction (phi = atan2(x, z))
   return D.miss_phi && (n.dx * D.miss_a_z - n.dz * D.miss_a_x < R(0) ||

@@ -28,7 +28,7 @@ def _bounds(det, r_s):
     widen = math.asin(r_s / r_in) + math.asin(det.tube_r_m / r_in) + 1e-3
     lo = det.phi0_rad - widen
     hi = det.phi0_rad + max(det.packs) * period / det.radius_m + widen
-    if not hi - lo < 0.95 * math.pi:  # the direction test is off for arcs near half a turn
+    if not hi - lo < math.pi - 0.01:  # the direction test is off for arcs near half a turn
         lo = hi = None
     return r_in, top, bot, lo, hi
 
@@ -37,8 +37,9 @@ def _surely_misses(b, r, d):
     r_in, top, bot, lo, hi = b
     lmin = r_in - (abs(r[0]) + abs(r[2]))
     assert lmin > 0
-    y_far = r[1] + d[1] * lmin
-    if (d[1] >= 0 and y_far > top) or (d[1] <= 0 and y_far < bot):
+    # room left above (below) the start against the rise over the shortest path out
+    a = top - r[1] if d[1] >= 0 else r[1] - bot
+    if a <= 0 or a * a * (d[0] ** 2 + d[2] ** 2) < (d[1] * lmin) ** 2:
         return True
     if lo is None:
         return False
@@ -88,9 +89,8 @@ def test_rule_never_skips_a_detection(packs):
             skipped += 1
             assert h["bin"] == -1, (r, d, h)
     assert detected > 300
-    assert skipped > 0.2 * n
-    if b[3] is not None:  # the direction test is on for the shorter arc
-        assert skipped > 0.5 * n
+    assert b[3] is not None  # both arcs are under half a turn: the direction test is on
+    assert skipped > 0.4 * n
 
 
 def dataclass_with_wide_window(det, packs):
