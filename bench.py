@@ -93,11 +93,14 @@ def ops_per_step(n, t, wl):
 
 
 def csrc_hash():
+    """Hash of the kernel sources and of the build script (its per-file compiler flags)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1504_02776_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    files = [os.path.join(d, f) for f in sorted(os.listdir(d))]
+    files.append(os.path.join(ROOT, "paper_1504_02776_gb300", "build.py"))
+    for p in files:
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -584,8 +587,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "neutrons_per_gpu_per_step": N,
-                   "precision": "FP32 geometry and kernel sampling; FP64 time of flight, "
-                                "tallies and histogram",
+                   "precision": "FP32 geometry and kernel sampling (division and square "
+                                "root to 2 ulp); FP64 time of flight, tallies and histogram",
                    "l2": "inputs larger than L2: the 942 MB histogram is cleared and "
                          "rewritten every step",
                    "parallelism": "neutron-id shards per GPU" if world > 1 else "1 GPU"},
