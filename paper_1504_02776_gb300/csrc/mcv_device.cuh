@@ -24,7 +24,13 @@ struct Mth<float> {
   static __device__ __forceinline__ float log(float x) { return logf(x); }
   static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
   static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
-  static __device__ __forceinline__ float tan(float x) { return tanf(x); }
+  // tan, sin and cos through sincospif: its argument reduction is exact, so these keep
+  // their relative accuracy when the FP32 units are built with fast math
+  static __device__ __forceinline__ float tan(float x) {
+    float s, c;
+    sincospif(x * 0.318309886f, &s, &c);
+    return s / c;
+  }
   static __device__ __forceinline__ float atan2(float y, float x) { return atan2f(y, x); }
   static __device__ __forceinline__ float floor(float x) { return floorf(x); }
   static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
@@ -36,8 +42,8 @@ struct Mth<float> {
     sincospif(2.0f * u, s, c);
   }
   static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
-  static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
-  static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
+  static __device__ __forceinline__ float cos_(float x) { return cospif(x * 0.318309886f); }
+  static __device__ __forceinline__ float sin_(float x) { return sinpif(x * 0.318309886f); }
   static __device__ __forceinline__ float acos_(float x) { return acosf(x); }
 };
 
