@@ -587,9 +587,9 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "neutrons_per_gpu_per_step": N,
-                   "precision": "FP32 geometry and kernel sampling (fast-math division, "
-                                "square root, exp and log; tan, sin, cos through sincospi); "
-                                "FP64 time of flight, tallies and histogram",
+                   "precision": "FP32 geometry and kernel sampling (division and square "
+                                "root to 2 ulp, hardware exp and log, subnormals kept); FP64 "
+                                "time of flight, tallies and histogram",
                    "l2": "inputs larger than L2: the 942 MB histogram is cleared and "
                          "rewritten every step",
                    "parallelism": "neutron-id shards per GPU" if world > 1 else "1 GPU"},

@@ -18,8 +18,8 @@ SOURCES = ["mcv_fp32.cu", "mcv_fp64.cu", "mcv_batch_fp32.cu", "mcv_batch_fp64.cu
            "mcv_api.cu", "mcv_batch.cu", "mcv_noalloc.cu"]
 # per-file flags: the FP64 kernels round every operation separately (no FMA contraction)
 FILE_FLAGS = {"mcv_fp64.cu": ["-fmad=false"], "mcv_batch_fp64.cu": ["-fmad=false"],
-              "mcv_fp32.cu": ["-use_fast_math"],
-              "mcv_batch_fp32.cu": ["-use_fast_math"]}
+              "mcv_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"],
+              "mcv_batch_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

@@ -20,12 +20,14 @@ struct Mth;
 template <>
 struct Mth<float> {
   static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
-  static __device__ __forceinline__ float exp(float x) { return expf(x); }
-  static __device__ __forceinline__ float log(float x) { return logf(x); }
+  // exp and log from the hardware approximations (a few ulp; subnormals kept, so a tiny
+  // table value or weight is not flushed to zero)
+  static __device__ __forceinline__ float exp(float x) { return __expf(x); }
+  static __device__ __forceinline__ float log(float x) { return __logf(x); }
   static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
   static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
-  // tan, sin and cos through sincospif: its argument reduction is exact, so these keep
-  // their relative accuracy when the FP32 units are built with fast math
+  // tan, sin and cos through sincospif: its argument reduction is exact and it has no long
+  // slow path, and these keep their relative accuracy for small arguments
   static __device__ __forceinline__ float tan(float x) {
     float s, c;
     sincospif(x * 0.318309886f, &s, &c);
