@@ -9,7 +9,8 @@ that clears the histogram).  Prints one JSON line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 For N > 1 it is launched by torch.distributed.run; each rank simulates its own neutron-id
-range (weak scaling, no collective in the timed region).
+range (weak scaling, no collective in the timed region); after the timed region the ranks'
+histograms and tallies are summed over NCCL (the run's result), timed on its own.
 """
 import argparse
 import hashlib
@@ -366,11 +367,9 @@ def grad_extras(ctx, value64):
     gen.manual_seed(2)
     target = torch.poisson(scale_c * counts, generator=gen)
     hist = torch.empty_like(counts)
-    g_work = torch.empty_like(counts)
 
     def step():
-        api._grad_call(ctx, wl, target, scale_c, B.FP32, wl.n, 0, table, None, None, 0, hist,
-                       g_work)
+        api._grad_call(ctx, wl, target, scale_c, B.FP32, wl.n, 0, table, None, None, 0, hist)
 
     for _ in range(2):
         step()
@@ -456,13 +455,27 @@ def run_ours(args):
     ctx.sync()
     ms = e0.elapsed_time(e1)
     trace_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    t = tallies.cpu().numpy()
     tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    collective = None
+    t_local = tallies.cpu().numpy()  # this rank's tallies of the last step
     if world > 1:
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        # the run's result: the ranks' histograms and tallies summed (the path's one exchange
+        # step), after the timed region and timed on its own
+        from paper_1504_02776_gb300.shards import reduce_sum
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        r0.record(stream)
+        reduce_sum([counts, tallies])
+        r1.record(stream)
+        torch.cuda.synchronize()
+        collective = {"op": "all_reduce(SUM) over NCCL of the FP64 histogram and tallies",
+                      "bytes": int((counts.numel() + tallies.numel()) * 8),
+                      "ms": r0.elapsed_time(r1), "in_timed_region": False}
+    t = tallies.cpu().numpy()  # the whole run's tallies of the last step
     ms = float(tm.item())
     value = world * N * args.steps / (ms / 1e3)
-    det_per_s = world * t[B.T_NDET] * args.steps / (ms / 1e3)
+    det_per_s = t[B.T_NDET] * args.steps / (ms / 1e3)
 
     # ---- plain FP64 forward, one simulation per launch, same workload and histogram
     sample64 = api.sample_struct(wl, B.FP64, table)
@@ -567,7 +580,7 @@ def run_ours(args):
     peaks = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * sm_mhz * 1e6   # FP32/INT32 lanes x clock
-    ops = ops_per_step(N, t, wl)
+    ops = ops_per_step(N, t_local, wl)
     achieved = ops / (trace_ms / 1e3)
     traffic_per_n = load_traffic()
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -578,7 +591,7 @@ def run_ours(args):
             "peak_basis": "%d SMs x 128 FP32/INT32 lanes x %.0f MHz (max SM clock, "
                           "MEASURED_PEAKS.json)" % (props.multi_processor_count, sm_mhz),
             # histogram read-modify-writes, one 8-byte word per detected event (read + write)
-            "hbm_gbs_algorithmic": t[B.T_NDET] * 16 / (trace_ms / 1e3) / 1e9,
+            "hbm_gbs_algorithmic": t_local[B.T_NDET] * 16 / (trace_ms / 1e3) / 1e9,
             "hbm_peak_gbs_measured": peaks.get("hbm_gbs")}
 
     line = {
@@ -602,6 +615,7 @@ def run_ours(args):
         "differentiable": differentiable,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
+        "collective": collective,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }

@@ -23,8 +23,8 @@
  *   - Calls are asynchronous on the caller's CUDA stream (`stream`, a cudaStream_t; NULL is
  *     the legacy default stream).  Argument errors are reported before anything is
  *     launched (MCV_EINVAL, nothing written).  Launch failures return MCV_ECUDA.  Errors
- *     found by the kernels themselves (index out of range) set a flag in the context that
- *     mcv_sync reports as MCV_EDEVICE.
+ *     found by the kernels themselves (an index out of range, invalid data in a caller's
+ *     device buffer) set a flag in the context that mcv_sync reports as MCV_EDEVICE.
  *   - Histograms and tallies are ACCUMULATED into; callers zero them (cudaMemset or
  *     mcv_zero) before the first call, and split runs over neutron-id ranges add up.
  *   - Random numbers: Philox4x32-10 with key (seed, sim_id) and counter (neutron id low
@@ -49,7 +49,9 @@ typedef enum {
   MCV_ENOMEM = 2,    /* the context could not allocate its own device memory */
   MCV_ECUDA = 3,     /* a CUDA call failed (message in mcv_last_error) */
   MCV_ETIMEOUT = 4,  /* a bounded device wait ran out */
-  MCV_EDEVICE = 5    /* a kernel found an out-of-range index (reported by mcv_sync) */
+  MCV_EDEVICE = 5    /* a kernel found invalid device data: an out-of-range index, a packet
+                        order above 7, a target bin that is negative or not finite
+                        (reported by mcv_sync) */
 } mcv_status;
 
 enum { MCV_MAX_SCATTERERS = 4, MCV_MAX_TUBES_PER_ROW = 512, MCV_NTALLY = 8 };
@@ -180,7 +182,8 @@ mcv_status mcv_create(int device, mcv_ctx** out);
 mcv_status mcv_destroy(mcv_ctx* ctx);
 /* Message of the last error returned to the calling thread ("" if none). */
 const char* mcv_last_error(void);
-/* Waits for `stream`, then reports and clears the device error flag (MCV_EDEVICE). */
+/* Waits for `stream`, then reports and clears the device error flag (MCV_EDEVICE).  With
+ * ctx == NULL it reads the error word of mcv_grad_noalloc on the current device instead. */
 mcv_status mcv_sync(mcv_ctx* ctx, void* stream);
 /* Number of pixels of a detector description (0 if invalid). */
 int64_t mcv_detector_pixels(const mcv_detector* det);
@@ -216,8 +219,10 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample,
  * with order >= 1 is traced to the first tube (or the surface) it meets; the absorption
  * point is drawn from the truncated exponential of the 3He path, the weight is multiplied
  * by the absorption probability, and (pixel, tof) is histogrammed.  Slots with order 0
- * add their weight to MCV_T_BEAMSTOP; order -1 slots are skipped.  packets->id and
- * packets->order are required (the detector draw uses them).  fp_mode as the packets. */
+ * add their weight to MCV_T_BEAMSTOP; order -1 slots are skipped; a slot with an order
+ * above 7 (no packet of the library has one) is skipped and sets the device error flag
+ * (MCV_EDEVICE at mcv_sync).  packets->id and packets->order are required (the detector
+ * draw uses them).  fp_mode as the packets. */
 mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
                       const mcv_neutrons* packets, uint32_t seed, uint32_t sim_id,
                       mcv_hist* hist, mcv_events* events, void* stream);
@@ -226,14 +231,29 @@ mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
  * histogram of neutrons first_id..first_id+n-1, and its gradient with respect to the S(Q,E)
  * table entries and the absorption and scattering cross sections of scatterer
  * grad_scatterer, differentiating packet weights along the fixed random paths.
- * hist->counts (n_bins) receives I (cleared first), g_work (n_bins) receives dchi2/dI,
- * loss (1), dsqe (nq*ne) and dsig (2: d/dsig_abs, d/dsig_s) are FP64 device outputs and
- * are overwritten. */
+ * hist->counts (n_bins) receives I (cleared first); loss (1), dsqe (nq*ne) and dsig (2:
+ * d/dsig_abs, d/dsig_s) are FP64 device outputs and are overwritten.  g_work (n_bins, may
+ * be NULL) receives dchi2/dI of every bin; without it the adjoint evaluates dchi2/dI only
+ * for the bins its packets reach (no per-bin buffer is written: the faster form).  target
+ * bins must be finite and >= 0; others set the device error flag (MCV_EDEVICE at mcv_sync). */
 mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
                     const mcv_detector* det, uint32_t seed, uint32_t sim_id,
                     int64_t first_id, int64_t n, const double* target, double scale_c,
                     int grad_scatterer, mcv_hist* hist, double* g_work, double* loss,
                     double* dsqe, double* dsig, void* stream);
+
+/* The loss and the adjoint without the forward step, for a run whose neutrons are split
+ * over several calls or devices (no counterpart in the paper): hist (n_bins, device, read
+ * only) is the histogram of the WHOLE run -- the sum of every part's forward histogram --
+ * and this call adds the gradient of the neutrons first_id..first_id+n-1 only.  loss
+ * receives chi2 of hist (the same on every part), dsqe and dsig this part's share (all
+ * overwritten; summed over the parts they give mcv_grad's gradient of the whole run).
+ * g_work as mcv_grad.  Errors as mcv_grad. */
+mcv_status mcv_adjoint(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
+                       const mcv_detector* det, uint32_t seed, uint32_t sim_id,
+                       int64_t first_id, int64_t n, const double* hist, const double* target,
+                       double scale_c, int grad_scatterer, double* g_work, double* loss,
+                       double* dsqe, double* dsig, void* stream);
 
 /* ---- batched launches ------------------------------------------------------------------- */
 /* The paper has no counterpart to these calls.  A batch is many independent simulations
@@ -306,11 +326,17 @@ mcv_status mcv_trace_batch(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
  *     than MCV_NOALLOC_MAX_BINS bins are rejected with MCV_EINVAL and a message.
  *   - It runs on the current CUDA device.  The first call on a device looks up the array's
  *     device address (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  No call allocates or frees memory.
- *   - Every call shares the array: the error word is cleared at the start of each call and
- *     the work buffer is overwritten, so consecutive calls on one stream are independent, but
- *     calls that overlap on the GPU (other streams, other host threads) race on it.
- *   - Errors: as mcv_grad; the message is returned by mcv_last_error(). */
+ *     before any stream capture.  Later calls made outside capture look it up again (the
+ *     address of a context created anew, e.g. after cudaDeviceReset); calls made during
+ *     capture use the address of the last lookup.  No call allocates or frees memory.
+ *   - Every call shares the array: the work buffer is overwritten by each call, so
+ *     consecutive calls on one stream are independent, but calls that overlap on the GPU
+ *     (other streams, other host threads) race on it.
+ *   - Errors: argument and launch errors as mcv_grad, returned at once.  Errors the kernels
+ *     find on the device (as mcv_grad: an index out of range, a target bin that is negative
+ *     or not finite) set the array's error word, which keeps them across calls until
+ *     mcv_sync(NULL, stream) waits for `stream` and reports them (MCV_EDEVICE, word cleared).
+ *     The message is returned by mcv_last_error(). */
 #define MCV_NOALLOC_MAX_BINS (1 << 20)
 mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* beam,
                             const mcv_detector* det, uint32_t seed, uint32_t sim_id,

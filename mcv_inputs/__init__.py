@@ -231,6 +231,16 @@ def powder_in_can(n=100_000, ei=100.0) -> Workload:
                      scatterers=[powder_sample(), can_scatterer()])
 
 
+def powder_two_kernels(n=100_000, sig_iso=1.5, sig_sqe=5.0, ei=100.0) -> Workload:
+    """The powder cylinder of the benchmark with a kernel composite (the paper's section
+    2.4.2): incoherent elastic (isotropic, sig_iso) next to the tabulated S(Q,E) (sig_sqe),
+    the scattering kernel picked per event in proportion to the cross sections."""
+    w = config2(n=n)
+    s = powder_sample()
+    s = Scatterer(s.kind, s.dims, s.n_per_A3, s.sig_abs_b, [(K_ISO, sig_iso), (K_SQE, sig_sqe)])
+    return w.replace(name="powder-two-kernels-%gmeV" % ei, scatterers=[s], beam=powder_beam(ei=ei))
+
+
 def config3_batch(n=2_000_000, orientations=None, detector=None) -> List[Workload]:
     """The single crystal at 181 orientations (0..180 degrees in 1 degree steps), one
     simulation (random stream sim_id = the angle) and one histogram each."""

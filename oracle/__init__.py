@@ -84,6 +84,8 @@ def lib():
         L.orc_n_pixels.restype = C.c_int64
         L.orc_grad.argtypes = [P, C.c_int64, C.c_int64, P, C.c_double, C.c_int, P, P, P, P]
         L.orc_grad.restype = C.c_int
+        L.orc_adjoint.argtypes = [P, C.c_int64, C.c_int64, P, P, C.c_double, C.c_int, P, P, P]
+        L.orc_adjoint.restype = C.c_int
         L.orc_loss.argtypes = [P, C.c_int64, C.c_int64, P, C.c_double, P, P]
         L.orc_loss.restype = C.c_int
         L.orc_bvk_modes.argtypes = [P, P, P, P]
@@ -237,6 +239,24 @@ def grad(wl, target, scale_c, first_id=0, n=None, gs=0):
         raise ValueError("oracle rejected the configuration")
     shape = wl.sqe.table.shape if wl.sqe is not None else (1,)
     return {"hist": h, "loss": loss.value, "dsqe": dsqe.reshape(shape), "dsig": dsig}
+
+
+def adjoint(wl, hist, target, scale_c, first_id=0, n=None, gs=0):
+    """Loss of the whole run's histogram `hist` and the gradient of neutrons
+    first_id..first_id+n-1 (the share of one part of a split run)."""
+    n = wl.n if n is None else n
+    cfg = make_config(wl)
+    hist = np.ascontiguousarray(hist, dtype=np.float64)
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    out = C.c_double()
+    dsqe = np.zeros(wl.sqe.table.size if wl.sqe is not None else 1)
+    dsig = np.zeros(2)
+    rc = lib().orc_adjoint(C.byref(cfg), first_id, n, _ptr(hist), _ptr(target), scale_c, gs,
+                           C.byref(out), _ptr(dsqe), _ptr(dsig))
+    if rc:
+        raise ValueError("oracle rejected the configuration")
+    shape = wl.sqe.table.shape if wl.sqe is not None else (1,)
+    return {"loss": out.value, "dsqe": dsqe.reshape(shape), "dsig": dsig}
 
 
 def loss(wl, target, scale_c, first_id=0, n=None):

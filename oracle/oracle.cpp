@@ -1496,17 +1496,18 @@ int orc_loss(const orc_config* cfg, int64_t first_id, int64_t n, const double* t
 }
 
 // Adjoint of the chi-squared loss along fixed random paths: every packet weight is a
-// product of factors, so d w / d theta follows from the factors' derivatives.
-int orc_grad(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
-             double scale_c, int gs, double* hist_out, double* loss, double* dsqe,
-             double* dsig) {
+// product of factors, so d w / d theta follows from the factors' derivatives.  The loss and
+// dchi2/dI are those of `hist` (the whole run's histogram); the gradient sums over the
+// neutrons first_id..first_id+n-1 only, so the gradients of the parts of a split run add up
+// to that of the whole run.
+int orc_adjoint(const orc_config* cfg, int64_t first_id, int64_t n, const double* hist,
+                const double* target, double scale_c, int gs, double* loss, double* dsqe,
+                double* dsig) {
   if (!config_ok(cfg) || n < 0 || cfg->det_kind == ORC_DET_NONE) return 1;
   if (gs < 0 || gs >= cfg->n_scat) return 1;
   int64_t nb = n_pixels(*cfg) * cfg->n_tof;
-  std::fill(hist_out, hist_out + nb, 0.0);
-  orc_trace(cfg, first_id, n, nullptr, nullptr, hist_out, nullptr);
   std::vector<double> g(nb);
-  *loss = chi2_and_grad(*cfg, hist_out, target, scale_c, g.data());
+  *loss = chi2_and_grad(*cfg, hist, target, scale_c, g.data());
   if (cfg->sqe) std::fill(dsqe, dsqe + (int64_t)cfg->nq * cfg->ne, 0.0);
   dsig[0] = 0.0;
   dsig[1] = 0.0;
@@ -1551,6 +1552,19 @@ int orc_grad(const orc_config* cfg, int64_t first_id, int64_t n, const double* t
     chain_one(*cfg, nid, false, gs, emit, on_scatter, nullptr);
   }
   return 0;
+}
+
+// The forward histogram of the neutrons first_id..first_id+n-1, then the adjoint of the
+// same neutrons.
+int orc_grad(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
+             double scale_c, int gs, double* hist_out, double* loss, double* dsqe,
+             double* dsig) {
+  if (!config_ok(cfg) || n < 0 || cfg->det_kind == ORC_DET_NONE) return 1;
+  if (gs < 0 || gs >= cfg->n_scat) return 1;
+  int64_t nb = n_pixels(*cfg) * cfg->n_tof;
+  std::fill(hist_out, hist_out + nb, 0.0);
+  orc_trace(cfg, first_id, n, nullptr, nullptr, hist_out, nullptr);
+  return orc_adjoint(cfg, first_id, n, hist_out, target, scale_c, gs, loss, dsqe, dsig);
 }
 
 }  // extern "C"

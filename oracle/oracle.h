@@ -142,6 +142,13 @@ int orc_grad(const orc_config* cfg, int64_t first_id, int64_t n, const double* t
              double scale_c, int gs, double* hist_out, double* loss, double* dsqe,
              double* dsig);
 
+/* the loss of `hist` (the whole run's histogram, n_pixels*n_tof) and the adjoint gradient of
+   the neutrons first_id..first_id+n-1 only (dsqe, dsig overwritten): the parts of a split run
+   add up to orc_grad of the whole run */
+int orc_adjoint(const orc_config* cfg, int64_t first_id, int64_t n, const double* hist,
+                const double* target, double scale_c, int gs, double* loss, double* dsqe,
+                double* dsig);
+
 /* loss only (for finite differences) */
 int orc_loss(const orc_config* cfg, int64_t first_id, int64_t n, const double* target,
              double scale_c, double* hist_work, double* loss);

@@ -285,7 +285,9 @@ Context.batch = lambda self, workloads, fp_mode=B.FP32, hists=None, first_ids=No
 def _grad_call(c, wl, target, scale_c, fp_mode, n, first_id, table, sig_abs, sig_s,
                grad_scatterer, counts=None, g_work=None):
     """mcv_grad with the cross sections of `grad_scatterer` replaced by sig_abs, sig_s (the
-    kernels' cross sections scaled together)."""
+    kernels' cross sections scaled together).  g_work (optional): a tensor of n_bins doubles
+    that receives dchi2/dI of every bin; without it the adjoint evaluates dchi2/dI only where
+    its packets land."""
     sample = sample_struct(wl, fp_mode, table)
     sc = sample.scat[grad_scatterer]
     if sig_abs is not None:
@@ -297,8 +299,6 @@ def _grad_call(c, wl, target, scale_c, fp_mode, n, first_id, table, sig_abs, sig
     nb = wl.detector.n_bins
     if counts is None:
         counts = torch.empty(nb, dtype=torch.float64, device="cuda")
-    if g_work is None:
-        g_work = torch.empty(nb, dtype=torch.float64, device="cuda")
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     dsqe = torch.empty(wl.sqe.table.size if wl.sqe is not None else 1, dtype=torch.float64,
                        device="cuda")
@@ -353,3 +353,45 @@ def chi2_loss(ctx, wl, table, sig_abs, sig_s, target, scale_c, fp_mode=B.FP32, n
     n = wl.n if n is None else n
     run = (ctx, wl, target, scale_c, fp_mode, n, first_id, grad_scatterer)
     return Chi2Loss.apply(table, sig_abs, sig_s, run)
+
+
+def _adjoint_call(c, wl, hist, target, scale_c, fp_mode, n, first_id, table, grad_scatterer):
+    """mcv_adjoint: loss of the whole run's histogram `hist`, gradient of this id range."""
+    sample = sample_struct(wl, fp_mode, table)
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    dsqe = torch.empty(wl.sqe.table.size if wl.sqe is not None else 1, dtype=torch.float64,
+                       device="cuda")
+    dsig = torch.empty(2, dtype=torch.float64, device="cuda")
+    B.mcv_adjoint(c.handle, sample, beam_struct(wl.beam), detector_struct(wl.detector), wl.seed,
+                  wl.sim_id, first_id, n, _ptr(hist), _ptr(target), float(scale_c),
+                  grad_scatterer, None, _ptr(loss), _ptr(dsqe), _ptr(dsig), _stream())
+    return {"loss": loss, "dsqe": dsqe, "dsig": dsig}
+
+
+def _grad_sharded(self, wl, target, scale_c, rank, world, fp_mode=B.FP32, n_total=None,
+                  table=None, grad_scatterer=0, group=None, sync=True):
+    """The chi-squared loss and gradient of a run of n_total neutrons (default wl.n) split
+    over the ranks of `group` (one GPU each, NCCL): this rank traces its share of the ids,
+    the histograms are summed over the ranks, this rank's adjoint runs on the summed
+    histogram, and the gradients are summed (shards.sharded_gradient)."""
+    from . import shards
+    n_total = wl.n if n_total is None else n_total
+    if table is None:
+        table = self.table(wl)
+    hist = torch.zeros(wl.detector.n_bins, dtype=torch.float64, device="cuda")
+
+    def forward(first, n, h):
+        self.trace(wl, fp_mode=fp_mode, n=n, first_id=first, table=table, counts=h,
+                   tallies=None, sync=False)
+
+    def adjoint(first, n, h):
+        return _adjoint_call(self, wl, h, target, scale_c, fp_mode, n, first, table,
+                             grad_scatterer)
+
+    out = shards.sharded_gradient(forward, adjoint, hist, rank, world, n_total, group=group)
+    if sync:
+        self.sync()
+    return out
+
+
+Context.grad_sharded = _grad_sharded

@@ -113,6 +113,8 @@ def _load():
     L.mcv_detect.argtypes = [P, P, C.c_int, P, C.c_uint32, C.c_uint32, P, P, P]
     L.mcv_grad.argtypes = [P, P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
                            C.c_double, C.c_int, P, P, P, P, P, P]
+    L.mcv_adjoint.argtypes = [P, P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P, P,
+                              C.c_double, C.c_int, P, P, P, P, P]
     L.mcv_grad_noalloc.argtypes = [P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
                                    C.c_double, C.c_int, P, P, P, P, P]
     L.mcv_batch_create.argtypes = [P, P, C.c_int, P, C.c_int, C.POINTER(C.c_void_p)]
@@ -123,7 +125,7 @@ def _load():
     L.mcv_batch_destroy.argtypes = [P]
     L.mcv_trace_batch.argtypes = [P, P, C.c_int, P, C.c_int, P]
     for name in ("mcv_create", "mcv_destroy", "mcv_sync", "mcv_zero", "mcv_beam",
-                 "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_grad_noalloc",
+                 "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_adjoint", "mcv_grad_noalloc",
                  "mcv_batch_create", "mcv_batch_run", "mcv_batch_tune", "mcv_batch_shape",
                  "mcv_batch_destroy", "mcv_trace_batch"):
         getattr(L, name).restype = st
@@ -186,6 +188,13 @@ def mcv_grad(ctx, sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
     _check(lib.mcv_grad(ctx, C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
                         first_id, n, target, scale_c, grad_scatterer, C.byref(hist), g_work,
                         loss, dsqe, dsig, stream))
+
+
+def mcv_adjoint(ctx, sample, beam, det, seed, sim_id, first_id, n, hist, target, scale_c,
+                grad_scatterer, g_work, loss, dsqe, dsig, stream=None):
+    _check(lib.mcv_adjoint(ctx, C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
+                           first_id, n, hist, target, scale_c, grad_scatterer, g_work, loss,
+                           dsqe, dsig, stream))
 
 
 def mcv_grad_noalloc(sample, beam, det, seed, sim_id, first_id, n, target, scale_c,

@@ -531,6 +531,7 @@ mcv_status mcv_destroy(mcv_ctx* ctx) {
 }
 
 mcv_status mcv_sync(mcv_ctx* ctx, void* stream) {
+  if (!ctx) return mcv::noalloc_sync(static_cast<cudaStream_t>(stream));
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -540,7 +541,9 @@ mcv_status mcv_sync(mcv_ctx* ctx, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
   if (flag) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
-    return fail(MCV_EDEVICE, "a kernel found an out-of-range index");
+    return fail(MCV_EDEVICE,
+                "a kernel found an out-of-range index, a packet order above 7 or a target bin "
+                "that is negative or not finite");
   }
   return MCV_OK;
 }
@@ -719,49 +722,101 @@ mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
   return MCV_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// What mcv_grad and mcv_adjoint share: the parameter blocks and the checks of the gradient
+// outputs.
+mcv_status grad_args(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
+                     const mcv_detector* det, uint32_t seed, uint32_t sim_id, int64_t first_id,
+                     int64_t n, const double* target, double scale_c, int grad_scatterer,
+                     const double* hist, double* loss, double* dsqe, double* dsig,
+                     mcv::TraceArgs* A) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  std::memset(A, 0, sizeof(*A));
+  st = build_sample(sample, &A->Sd);
+  if (st != MCV_OK) return st;
+  st = build_beam(beam, &A->Bd);
+  if (st != MCV_OK) return st;
+  set_miss_bounds(A->Sd, &A->Bd);
+  st = build_detector(det, &A->Dd);
+  if (st != MCV_OK) return st;
+  set_det_miss_bounds(sample_radius(A->Sd), &A->Dd);
+  if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
+    return fail(MCV_EINVAL, "bad neutron range");
+  if (!target || !loss || !dsig || !hist)
+    return fail(MCV_EINVAL, "the gradient needs target, the histogram, loss and dsig");
+  if (A->Sd.has_sqe && !dsqe) return fail(MCV_EINVAL, "the gradient needs dsqe for an S(Q,E) sample");
+  if (grad_scatterer < 0 || grad_scatterer >= A->Sd.ns)
+    return fail(MCV_EINVAL, "grad_scatterer out of range");
+  if (!(A->Sd.s[grad_scatterer].sig_s > 0.0))
+    return fail(MCV_EINVAL, "the differentiated scatterer needs a positive cross section");
+  if (!is_finite(scale_c)) return fail(MCV_EINVAL, "scale_c is not finite");
+  A->seed = seed;
+  A->sim_id = sim_id;
+  A->keys = philox_keys(seed, sim_id);
+  A->first_id = first_id;
+  A->n = n;
+  A->err = ctx->d_err;
+  A->gs = grad_scatterer;
+  cast_all(A);
+  return MCV_OK;
+}
+
+// The loss of the histogram `hist` and the adjoint of the neutron range of A: clears loss,
+// dsig and dsqe, then the chi-squared kernel and the adjoint kernel.
+mcv_status loss_and_adjoint(mcv_ctx* ctx, mcv::TraceArgs& A, int fp, const double* hist,
+                            const double* target, double scale_c, double* g_work, double* loss,
+                            double* dsqe, double* dsig, cudaStream_t s) {
+  const int zgrid = ctx->sm_count * 8;
+  cudaError_t e = mcv::launch_zero(loss, 1, 1, s);
+  if (e == cudaSuccess) e = mcv::launch_zero(dsig, 2, 1, s);
+  if (e == cudaSuccess && A.Sd.has_sqe) e = mcv::launch_zero(dsqe, (int64_t)A.Sd.nq * A.Sd.ne, zgrid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "zero kernel launch");
+  e = mcv::launch_chi2(hist, target, scale_c, A.Dd.n_bins, g_work, loss, ctx->d_err, zgrid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "chi2 kernel launch");
+  if (A.n > 0) {
+    // adjoint: the same paths, traced through zero weights
+    A.hist = nullptr;
+    A.tallies = nullptr;
+    A.stop_on_zero = 0;
+    A.g = g_work;
+    A.hist_in = hist;
+    A.target = target;
+    A.scale_c = scale_c;
+    A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
+    A.dsig = dsig;
+    int& occ_a = ctx->occ_adj[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.has_bvk ? 1 : 0];
+    if (occ_a == 0) {
+      e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ_a);
+      if (e != cudaSuccess || occ_a < 1) occ_a = 1;
+    }
+    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_for(ctx, A.n, occ_a), s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+  }
+  return MCV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
                     const mcv_detector* det, uint32_t seed, uint32_t sim_id, int64_t first_id,
                     int64_t n, const double* target, double scale_c, int grad_scatterer,
                     mcv_hist* hist, double* g_work, double* loss, double* dsqe, double* dsig,
                     void* stream) {
-  mcv_status st = check_ctx(ctx);
-  if (st != MCV_OK) return st;
   mcv::TraceArgs A;
-  std::memset(&A, 0, sizeof(A));
-  st = build_sample(sample, &A.Sd);
+  mcv_status st = grad_args(ctx, sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
+                            grad_scatterer, hist ? hist->counts : nullptr, loss, dsqe, dsig, &A);
   if (st != MCV_OK) return st;
-  st = build_beam(beam, &A.Bd);
-  if (st != MCV_OK) return st;
-  set_miss_bounds(A.Sd, &A.Bd);
-  st = build_detector(det, &A.Dd);
-  if (st != MCV_OK) return st;
-  set_det_miss_bounds(sample_radius(A.Sd), &A.Dd);
-  if (n < 0 || n > kMaxNeutrons || first_id < 0 || first_id > (((int64_t)1 << 62) - n))
-    return fail(MCV_EINVAL, "bad neutron range");
-  if (!target || !g_work || !loss || !dsig || !hist || !hist->counts)
-    return fail(MCV_EINVAL, "mcv_grad needs target, hist->counts, g_work, loss and dsig");
-  if (A.Sd.has_sqe && !dsqe) return fail(MCV_EINVAL, "mcv_grad needs dsqe for an S(Q,E) sample");
-  if (grad_scatterer < 0 || grad_scatterer >= A.Sd.ns)
-    return fail(MCV_EINVAL, "grad_scatterer out of range");
-  if (!(A.Sd.s[grad_scatterer].sig_s > 0.0))
-    return fail(MCV_EINVAL, "the differentiated scatterer needs a positive cross section");
-  if (!is_finite(scale_c)) return fail(MCV_EINVAL, "scale_c is not finite");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int zgrid = ctx->sm_count * 8;
   cudaError_t e = mcv::launch_zero(hist->counts, A.Dd.n_bins, zgrid, s);
   if (e == cudaSuccess && hist->tallies) e = mcv::launch_zero(hist->tallies, MCV_NTALLY, 1, s);
-  if (e == cudaSuccess) e = mcv::launch_zero(loss, 1, 1, s);
-  if (e == cudaSuccess) e = mcv::launch_zero(dsig, 2, 1, s);
-  if (e == cudaSuccess && A.Sd.has_sqe) e = mcv::launch_zero(dsqe, (int64_t)A.Sd.nq * A.Sd.ne, zgrid, s);
   if (e != cudaSuccess) return cuda_fail(e, "zero kernel launch");
-  A.seed = seed;
-  A.sim_id = sim_id;
-  A.keys = philox_keys(seed, sim_id);
-  A.first_id = first_id;
-  A.n = n;
-  A.err = ctx->d_err;
-  A.gs = grad_scatterer;
-  cast_all(&A);
   const int fp = sample->fp_mode;
   if (n > 0) {
     // forward: the histogram of this neutron range
@@ -776,25 +831,20 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
     e = mcv::launch_trace(A, fp, A.Dd.kind, grid_for(ctx, n, occ), s);
     if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
   }
-  e = mcv::launch_chi2(hist->counts, target, scale_c, A.Dd.n_bins, g_work, loss, ctx->sm_count * 8, s);
-  if (e != cudaSuccess) return cuda_fail(e, "chi2 kernel launch");
-  if (n > 0) {
-    // adjoint: the same paths, traced through zero weights
-    A.hist = nullptr;
-    A.tallies = nullptr;
-    A.stop_on_zero = 0;
-    A.g = g_work;
-    A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
-    A.dsig = dsig;
-    int& occ_a = ctx->occ_adj[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.has_bvk ? 1 : 0];
-    if (occ_a == 0) {
-      e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ_a);
-      if (e != cudaSuccess || occ_a < 1) occ_a = 1;
-    }
-    e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_for(ctx, n, occ_a), s);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
-  }
-  return MCV_OK;
+  return loss_and_adjoint(ctx, A, fp, hist->counts, target, scale_c, g_work, loss, dsqe, dsig, s);
+}
+
+mcv_status mcv_adjoint(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_params* beam,
+                       const mcv_detector* det, uint32_t seed, uint32_t sim_id,
+                       int64_t first_id, int64_t n, const double* hist, const double* target,
+                       double scale_c, int grad_scatterer, double* g_work, double* loss,
+                       double* dsqe, double* dsig, void* stream) {
+  mcv::TraceArgs A;
+  mcv_status st = grad_args(ctx, sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
+                            grad_scatterer, hist, loss, dsqe, dsig, &A);
+  if (st != MCV_OK) return st;
+  return loss_and_adjoint(ctx, A, sample->fp_mode, hist, target, scale_c, g_work, loss, dsqe,
+                          dsig, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

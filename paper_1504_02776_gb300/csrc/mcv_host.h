@@ -49,4 +49,9 @@ void cast_detector(const DetP<double>& d, DetP<float>* f);
 void cast_all(TraceArgs* A);
 
 }  // namespace host
+
+// mcv_sync without a context: waits for `stream`, then reports and clears the device error
+// word of mcv_grad_noalloc on the current device (mcv_noalloc.cu)
+mcv_status noalloc_sync(cudaStream_t stream);
+
 }  // namespace mcv

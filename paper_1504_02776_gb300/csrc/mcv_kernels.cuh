@@ -12,9 +12,13 @@
 #include <cuda_runtime.h>
 
 #include "mcv_chain.cuh"
+#include "mcv_chi2.cuh"
 #include "mcv_launch.h"
 
 namespace mcv {
+
+// largest number of scattering orders of a packet (mcv_sample::max_orders <= 7)
+constexpr int kMaxOrders = 7;
 
 constexpr int kThreads = 128;
 
@@ -668,6 +672,10 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant_
        i += (int64_t)gridDim.x * blockDim.x) {
     const int o = A.in_order[i];
     if (o < 0) continue;
+    if (o > kMaxOrders) {  // no packet of the library has such an order: flag it, skip it
+      err = 1;
+      continue;
+    }
     const R w = static_cast<const R*>(A.in_w)[i];
     if (o == 0) {
       a_bs.add(w);
@@ -733,7 +741,6 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant_
 // The adjoint kernel recomputes each neutron's path with the forward arithmetic (the shared
 // chain step) instead of storing it, keeps the per-scattering records in the thread, and
 // scatter-adds into dS (FP64 atomics, the table is L2-resident) and dsig (warp-reduced).
-constexpr int kMaxOrders = 7;
 
 // The path sums (cum_*) and the per-thread accumulators are kept in the real type of the
 // trace: FP64 in FP64 mode, compensated FP32 sums in FP32 mode (the FP64 pipe of GB300 runs
@@ -769,7 +776,8 @@ struct Adjoint {
       err = 1;
       return;
     }
-    const double g64 = A.g[h.bin];
+    const double g64 = A.g ? A.g[h.bin]
+                           : chi2_grad_bin(A.hist_in[h.bin], A.target[h.bin], A.scale_c);
     if (g64 == 0.0) return;
     const R gb = (R)g64;
     const ScatP<R>& g = Sof<R>(A).s[A.gs];

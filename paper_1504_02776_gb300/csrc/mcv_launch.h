@@ -24,8 +24,10 @@ cudaError_t launch_beam(const TraceArgs& A, int fp_mode, int grid, cudaStream_t 
 cudaError_t launch_detect(const TraceArgs& A, const EventsArgs& E, int fp_mode, int det, int grid,
                           cudaStream_t s);
 cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s);
+// chi-squared loss into *loss (accumulated); g (optional) receives dchi2/dI per bin; err
+// (optional) is set when a target bin is negative or not finite
 cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
-                        double* g, double* loss, int grid, cudaStream_t s);
+                        double* g, double* loss, int* err, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
 cudaError_t adjoint_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks);
 // batched launch: blocks per SM of its kernel (also sets the kernel's shared-memory limit;

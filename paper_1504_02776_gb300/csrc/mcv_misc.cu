@@ -2,6 +2,7 @@
 // dispatch of the per-type entry points.
 #include <cuda_runtime.h>
 
+#include "mcv_chi2.cuh"
 #include "mcv_device.cuh"
 #include "mcv_launch.h"
 
@@ -45,40 +46,20 @@ __global__ void zero_kernel(double* __restrict__ p, int64_t n) {
   }
 }
 
-// 1/d for d >= 1 without an FP64 division (GB300's FP64 rate is about 1/64 of its FP32
-// rate, and a division is a long FP64 sequence): the FP32 reciprocal as the seed, then two
-// Newton-Raphson steps x <- x + x (1 - d x) in FP64, each of which squares the relative
-// error (2^-23 -> 2^-46 -> below FP64 rounding).  Very large d take the division.
-__device__ __forceinline__ double recip_ge1(double d) {
-  if (!(d < 1e30)) return 1.0 / d;
-  double x = (double)__frcp_rn((float)d);
-  x = fma(x, fma(-d, x, 1.0), x);
-  x = fma(x, fma(-d, x, 1.0), x);
-  return x;
-}
-
-// chi2 = sum_b (c I_b - T_b)^2 / max(T_b, 1);  g_b = 2 c (c I_b - T_b) / max(T_b, 1)
-// One bin: its gradient entry, its loss term added to part.  A bin with nothing simulated
-// and nothing measured (both values +0: almost all of the 117,760,000) is recognised from
-// the bits with integer operations and costs no FP64 work (c is finite: r would be 0).
-__device__ __forceinline__ double chi2_bin(double h, double T, double c, double* part) {
-  if ((__double_as_longlong(h) | __double_as_longlong(T)) == 0) return 0.0;
-  const double r = c * h - T;
-  if (r == 0.0) return 0.0;
-  const double ri = r * recip_ge1(fmax(T, 1.0));
-  *part += r * ri;
-  return 2.0 * c * ri;
-}
-
+// chi2 = sum_b (c I_b - T_b)^2 / max(T_b, 1) into *loss; g (optional) receives
+// g_b = dchi2/dI_b for every bin.  Without g the kernel only reads (16 bytes per bin): the
+// adjoint evaluates g_b itself for the bins its packets reach.  A measured bin that is
+// negative or not finite sets the error flag (err, optional).
 __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hist,
                                                    const double* __restrict__ target, double c,
                                                    int64_t nb, double* __restrict__ g,
-                                                   double* __restrict__ loss) {
+                                                   double* __restrict__ loss, int* err) {
   double part = 0.0;
+  bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // four grid-strided bins per pass, their loads issued together (the kernel streams
-  // 24 bytes per bin); the bins of a thread are summed in the same order as one at a time
+  // four grid-strided bins per pass, their loads issued together; the bins of a thread are
+  // summed in the same order as one at a time
   for (; b + 3 * stride < nb; b += 4 * stride) {
     double h[4], T[4];
 #pragma unroll
@@ -87,9 +68,19 @@ __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hi
       T[k] = target[b + k * stride];
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) g[b + k * stride] = chi2_bin(h[k], T[k], c, &part);
+    for (int k = 0; k < 4; ++k) {
+      bad |= !target_ok(T[k]);
+      const double gb = chi2_bin(h[k], T[k], c, &part);
+      if (g) g[b + k * stride] = gb;
+    }
   }
-  for (; b < nb; b += stride) g[b] = chi2_bin(hist[b], target[b], c, &part);
+  for (; b < nb; b += stride) {
+    const double T = target[b];
+    bad |= !target_ok(T);
+    const double gb = chi2_bin(hist[b], T, c, &part);
+    if (g) g[b] = gb;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && err) atomicOr(err, 1);
   part = warp_sum(part);
   __shared__ double red[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -152,8 +143,8 @@ cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
-                        double* g, double* loss, int grid, cudaStream_t s) {
-  chi2_kernel<<<grid, 256, 0, s>>>(hist, target, c, nb, g, loss);
+                        double* g, double* loss, int* err, int grid, cudaStream_t s) {
+  chi2_kernel<<<grid, 256, 0, s>>>(hist, target, c, nb, g, loss, err);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 // its context or from the caller (the device error word and dchi2/dI per histogram bin)
 // live here instead, in one file-scope device array that every GPU loading the library
 // holds until the process exits.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -26,21 +27,30 @@ mcv_status noalloc_fail(mcv_status st, const std::string& msg) {
   return st;
 }
 
-// device address of the array, looked up once per device with that device current
+// Device address of the array on each device.  The address belongs to the module loaded in
+// the device's current context; it is looked up again on every call made outside stream
+// capture (a context created anew, after cudaDeviceReset, may hold the module elsewhere) and
+// kept for calls made during capture, where no lookup is done.
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+std::atomic<double*> g_scratch_addr[kMaxDevices];
 
-mcv_status scratch_of(int device, double** out) {
+mcv_status scratch_of(int device, cudaStream_t stream, double** out) {
   if (device < 0 || device >= kMaxDevices)
     return noalloc_fail(MCV_EINVAL, "device index out of range");
-  if (!g_scratch_addr[device]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess)
+    return noalloc_fail(MCV_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  double* addr = g_scratch_addr[device].load();
+  if (cap == cudaStreamCaptureStatusNone || !addr) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess)
       return noalloc_fail(MCV_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[device] = static_cast<double*>(p);
+    addr = static_cast<double*>(p);
+    g_scratch_addr[device].store(addr);
   }
-  *out = g_scratch_addr[device];
+  *out = addr;
   return MCV_OK;
 }
 
@@ -80,17 +90,17 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* scratch = nullptr;
-  st = scratch_of(device, &scratch);
+  st = scratch_of(device, s, &scratch);
   if (st != MCV_OK) return st;
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* g = scratch + kHeader;
-  // the error word and the outputs start at zero; the dchi2/dI bins are all overwritten
-  e = mcv::launch_zero(scratch, kHeader, 1, s);
-  if (e == cudaSuccess) e = mcv::launch_zero(hist->counts, A.Dd.n_bins, sms * 8, s);
+  // the outputs start at zero; the dchi2/dI bins are all overwritten; the error word keeps
+  // what earlier calls found until mcv_sync(NULL, stream) reads and clears it
+  e = mcv::launch_zero(hist->counts, A.Dd.n_bins, sms * 8, s);
   if (e == cudaSuccess && hist->tallies) e = mcv::launch_zero(hist->tallies, MCV_NTALLY, 1, s);
   if (e == cudaSuccess) e = mcv::launch_zero(loss, 1, 1, s);
   if (e == cudaSuccess) e = mcv::launch_zero(dsig, 2, 1, s);
@@ -121,7 +131,8 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
     e = mcv::launch_trace(A, fp, A.Dd.kind, grid_of(occ), s);
     if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
   }
-  e = mcv::launch_chi2(hist->counts, target, scale_c, A.Dd.n_bins, g, loss, sms * 8, s);
+  e = mcv::launch_chi2(hist->counts, target, scale_c, A.Dd.n_bins, g, loss,
+                       reinterpret_cast<int*>(scratch), sms * 8, s);
   if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
   if (n > 0) {
     A.hist = nullptr;
@@ -140,3 +151,32 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
 }
 
 }  // extern "C"
+
+namespace mcv {
+
+mcv_status noalloc_sync(cudaStream_t stream) {
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess)
+    return noalloc_fail(MCV_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  int device = 0;
+  e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
+  double* scratch = nullptr;
+  mcv_status st = scratch_of(device, stream, &scratch);
+  if (st != MCV_OK) return st;
+  int flag = 0;
+  e = cudaMemcpy(&flag, scratch, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess)
+    return noalloc_fail(MCV_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  if (flag) {
+    e = cudaMemset(scratch, 0, sizeof(int));
+    if (e != cudaSuccess)
+      return noalloc_fail(MCV_ECUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    return noalloc_fail(MCV_EDEVICE,
+                        "mcv_grad_noalloc: a kernel found an out-of-range index or a target "
+                        "bin that is negative or not finite");
+  }
+  return MCV_OK;
+}
+
+}  // namespace mcv

@@ -134,10 +134,14 @@ struct TraceArgs {
   int32_t* pk_order;
   int* err;
   int stop_on_zero;
-  // adjoint: the scatterer whose cross sections are differentiated, dchi2/dI per bin,
-  // and the FP64 gradient outputs
+  // adjoint: the scatterer whose cross sections are differentiated, dchi2/dI per bin (g;
+  // when null, g_b is evaluated from the forward histogram hist_in, the target and scale_c
+  // for the bins the packets reach), and the FP64 gradient outputs
   int gs;
   const double* g;
+  const double* hist_in;
+  const double* target;
+  double scale_c;
   double* dsqe;
   double* dsig;
 };

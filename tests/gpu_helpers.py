@@ -69,3 +69,48 @@ def check_fp64_packets(gpu, orc):
     bad = {f: int((dev[f] > RT64).sum()) for f in ("r", "v", "t")}
     bad["w"] = int((dev["w"] > fp64_weight_tol(k)).sum())
     return dev, bad
+
+
+def flat_excess(dev_w, kappa, flat=RT64):
+    """Packets whose weight deviation exceeds the flat bar: count, share, and the largest
+    deviation over the condition-scaled bar (<= 1 when every one of them is explained by the
+    rounding amplification of its history)."""
+    beyond = dev_w > flat
+    worst = float((dev_w[beyond] / fp64_weight_tol(kappa[beyond])).max()) if beyond.any() else 0.0
+    return int(beyond.sum()), float(beyond.mean()) if dev_w.size else 0.0, worst
+
+
+def oracle_sparse_hist(wl, n=None, chunk=200_000):
+    """The oracle's detected events of a run, traced in chunks of neutron ids: per bin the
+    summed detected weight, the summed weight * max(1e-5, 1e-6 kappa_det) (the FP32 bar of
+    its events), the summed weight * 1e-5 (the flat FP32 bar) and the event count."""
+    import oracle
+    n = wl.n if n is None else n
+    bins, w, kd = [], [], []
+    for first in range(0, n, chunk):
+        m = min(chunk, n - first)
+        pk = oracle.trace(wl, first_id=first, n=m, packets=True, hist=False)["packets"]
+        hit = (pk["order"] >= 1) & (pk["bin"] >= 0)
+        bins.append(pk["bin"][hit])
+        w.append(pk["w_det"][hit])
+        kd.append(pk["kappa_det"][hit])
+    b = np.concatenate(bins)
+    w = np.concatenate(w)
+    kd = np.concatenate(kd)
+    ub, inv = np.unique(b, return_inverse=True)
+    return {"bins": ub,
+            "I": np.bincount(inv, weights=w, minlength=ub.size),
+            "tol_k": np.bincount(inv, weights=w * np.maximum(1e-5, 1e-6 * kd), minlength=ub.size),
+            "tol_flat": np.bincount(inv, weights=w * 1e-5, minlength=ub.size),
+            "n": np.bincount(inv, minlength=ub.size),
+            "events": int(b.size)}
+
+
+def gpu_sparse(counts, bins):
+    """Values of a device histogram at `bins` and its own non-zero bins outside them."""
+    import torch
+    idx = torch.from_numpy(bins).to(counts.device)
+    at = counts[idx].cpu().numpy() if bins.size else np.zeros(0)
+    nz = torch.nonzero(counts).flatten().cpu().numpy()
+    extra = np.setdiff1d(nz, bins, assume_unique=False)
+    return at, extra, counts[torch.from_numpy(extra).to(counts.device)].cpu().numpy() if extra.size else np.zeros(0)

@@ -53,7 +53,7 @@ def _can_500mev(n):
 # ---------------------------------------------------------------- FP64 per packet
 @pytest.mark.parametrize("make,n", [(mi.config1, 20000), (_small_c2, 20000),
                                     (_powder_in_can, 20000), (_can_10mev, 20000),
-                                    (_can_500mev, 20000)])
+                                    (_can_500mev, 20000), (mi.powder_two_kernels, 20000)])
 def test_fp64_packets_match_oracle(ctx, make, n):
     wl = make(n)
     pk, g = H.packets(ctx, wl, B.FP64)
@@ -79,7 +79,8 @@ def test_fp64_packets_match_oracle(ctx, make, n):
 # the fused tube-system runs also cover the detector sure-miss bounds of the sample stage:
 # the detected, missed and out-of-window counts must equal the oracle's, which has no bounds
 @pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 400000),
-                                    (_powder_in_can, 200000), (_can_10mev, 100000)])
+                                    (_powder_in_can, 200000), (_can_10mev, 100000),
+                                    (mi.powder_two_kernels, 200000)])
 def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     wl = make(n)
     counts, tallies = ctx.trace(wl, fp_mode=B.FP64)
@@ -224,7 +225,9 @@ def test_invalid_arguments_are_rejected(ctx):
 
 
 # ---------------------------------------------------------------- FP32 fast mode
-W_FLOOR = 1e-30   # weights below this are outside the FP32 normal range
+# Weights below this are beyond FP32: its normal range ends at 1.2e-38, and a weight within
+# two orders of that end may have passed through subnormal intermediate products.
+W_FLOOR = 1e-36
 
 
 def fp32_stats(ctx, wl):
@@ -252,9 +255,15 @@ def fp32_stats(ctx, wl):
     flips = int((events & (ev["bin"] != op["bin"])).sum())
     both = det & (op["bin"] >= 0) & (ev["bin"] >= 0) & (op["w_det"] >= W_FLOOR)
     wd = np.abs(ev["w_det"][both] - op["w_det"][both]) / op["w_det"][both]
+    # every detected event of a neutron whose FP32 history took another discrete decision
+    # counts as an event that may have moved (it is charged to the same 1e-4 budget)
+    diff_n = np.repeat(~same, slots)
+    detected_any = (op["order"] >= 1) & ((op["bin"] >= 0) | (ev["bin"] >= 0)) & sig
+    moved = int((diff_n & detected_any).sum())
     return {"neutrons": wl.n, "structure_diff": int((~same).sum()), "dev": dev,
             "kappa": sub_o["kappa"], "kappa_det": op["kappa_det"][both],
             "flips": flips, "events": int(events.sum()), "wdet_dev": wd,
+            "moved": moved, "events_all": int(detected_any.sum()),
             "hist_gpu": counts.cpu().numpy(), "hist_orc": orc["hist"]}
 
 
@@ -265,12 +274,16 @@ def rate_bound(rate, n):
 
 
 @pytest.mark.parametrize("make,n", [(mi.config1, 200000), (_small_c2, 200000),
-                                    (_powder_in_can, 200000)])
+                                    (_powder_in_can, 200000), (mi.powder_two_kernels, 200000)])
 def test_fp32_fast_mode_within_bounds(ctx, make, n):
     wl = make(n)
     st = fp32_stats(ctx, wl)
-    # discrete decisions taken differently in FP32 (S(Q,E) bin edges, kinematic cuts)
-    assert st["structure_diff"] <= rate_bound(1e-3, n), st["structure_diff"]
+    print("\n%s: %d neutrons with another discrete decision in FP32 (%d detected events), "
+          "%d events in another bin, of %d detected events" % (
+              wl.name, st["structure_diff"], st["moved"], st["flips"], st["events_all"]))
+    # discrete decisions taken differently in FP32 (S(Q,E) bin edges, kinematic cuts) and
+    # events in another pixel or tof bin: together at most 1e-4 of the detected events
+    assert st["moved"] + st["flips"] <= rate_bound(1e-4, st["events_all"])
     # packet states within 1e-5 relative, or within the rounding amplification of the
     # history (1e-6 kappa: ~16 FP32 unit roundoffs per unit of the condition estimate)
     # where that is larger; at most 1e-4 of the packets beyond
@@ -279,7 +292,6 @@ def test_fp32_fast_mode_within_bounds(ctx, make, n):
         d = st["dev"][f]
         assert (d > tol).sum() <= rate_bound(1e-4, d.size), (f, float(np.quantile(d / tol, 0.9999)))
     # detector: at most 1e-4 of the events change pixel or tof bin
-    assert st["flips"] <= rate_bound(1e-4, st["events"]), (st["flips"], st["events"])
     tol_d = np.maximum(1e-5, 1e-6 * st["kappa_det"])
     assert (st["wdet_dev"] > tol_d).sum() <= rate_bound(1e-4, st["wdet_dev"].size)
     # histogram: total detected weight agrees within the flips
@@ -332,9 +344,11 @@ def test_fp64_crystal_packets_match_oracle(ctx, rot):
 def test_fp32_crystal_within_bounds(ctx):
     wl = _crystal(20000, 45.0)
     st = fp32_stats(ctx, wl)
-    assert st["structure_diff"] <= rate_bound(1e-3, wl.n), st["structure_diff"]
+    print("\n%s: %d neutrons with another discrete decision in FP32 (%d detected events), "
+          "%d events in another bin, of %d detected events" % (
+              wl.name, st["structure_diff"], st["moved"], st["flips"], st["events_all"]))
     tol = np.maximum(1e-5, 1e-6 * st["kappa"])
     for f in ("r", "v", "t", "w"):
         d = st["dev"][f]
-        assert (d > tol).sum() <= rate_bound(1e-3, d.size), (f, float(np.quantile(d / tol, 0.999)))
-    assert st["flips"] <= rate_bound(1e-3, st["events"]), (st["flips"], st["events"])
+        assert (d > tol).sum() <= rate_bound(1e-4, d.size), (f, float(np.quantile(d / tol, 0.9999)))
+    assert st["moved"] + st["flips"] <= rate_bound(1e-4, st["events_all"])

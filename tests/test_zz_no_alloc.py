@@ -64,6 +64,56 @@ def test_noalloc_gradient_matches_mcv_grad_twice(fp_mode):
     ctx.close()
 
 
+def test_noalloc_allocates_nothing():
+    """After a first call (which loads the kernels), further calls leave both torch's
+    allocator and the device's free memory exactly as they were."""
+    wl, target, c = _case(n=2000)
+    tg = torch.from_numpy(target).cuda()
+    table = torch.from_numpy(wl.sqe.table).cuda()
+    _noalloc(wl, table, tg, c, B.FP32)
+    torch.cuda.synchronize()
+    outs = [_noalloc(wl, table, tg, c, B.FP32) for _ in range(2)]  # output buffers first
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+    sample = api.sample_struct(wl, B.FP32, table)
+    det = api.detector_struct(wl.detector)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for o in outs:
+        hist = B.Hist(o["hist"].data_ptr(), None)
+        B.mcv_grad_noalloc(sample, api.beam_struct(wl.beam), det, wl.seed, wl.sim_id, 0, wl.n,
+                           C.c_void_p(tg.data_ptr()), c, 0, hist,
+                           C.c_void_p(o["loss"].data_ptr()), C.c_void_p(o["dsqe"].data_ptr()),
+                           C.c_void_p(o["dsig"].data_ptr()), stream)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+    assert after == before, (before, after)
+    B.mcv_sync(None, stream)
+
+
+def test_noalloc_reports_device_errors_at_sync():
+    """A target bin that is not a finite count >= 0 is found by the loss kernel on the device;
+    the error word keeps it until mcv_sync(NULL, stream) reports it, and is clear afterwards."""
+    wl, target, c = _case(n=1000)
+    bad = target.copy()
+    bad[7] = -1.0
+    table = torch.from_numpy(wl.sqe.table).cuda()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    B.mcv_sync(None, stream)  # nothing pending
+    _noalloc(wl, table, torch.from_numpy(bad).cuda(), c, B.FP64)
+    # a later valid call does not hide the earlier error
+    _noalloc(wl, table, torch.from_numpy(target).cuda(), c, B.FP64)
+    with pytest.raises(B.McvError) as e:
+        B.mcv_sync(None, stream)
+    assert e.value.status == B.MCV_EDEVICE
+    B.mcv_sync(None, stream)  # cleared
+    bad[7] = float("nan")
+    _noalloc(wl, table, torch.from_numpy(bad).cuda(), c, B.FP64)
+    with pytest.raises(B.McvError) as e:
+        B.mcv_sync(None, stream)
+    assert e.value.status == B.MCV_EDEVICE
+    B.mcv_sync(None, stream)
+
+
 def test_noalloc_rejects_histograms_beyond_its_buffer():
     wl = mi.config2(n=10)  # 117,760 x 1000 bins, more than the fixed buffer holds
     table = torch.from_numpy(wl.sqe.table).cuda()
