@@ -930,9 +930,10 @@ __device__ __forceinline__ bool exit_cyl(R rad, const Ray<R>& n, R* s) {
 }
 
 // Chord of a vertical tube (axis through R (ux, uz)) in coordinates along / across the
-// tube direction, so the large distance R cancels once.
+// tube direction, so the large distance R cancels once.  hl: the half chord.
 template <typename R>
-__device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>& n, R* s1, R* s2) {
+__device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>& n, R* s1, R* s2,
+                                          R* hl) {
   const R a = n.dx * n.dx + n.dz * n.dz;
   if (a == R(0)) return false;
   const R o_rad = n.x * ux + n.z * uz - Rad;
@@ -946,6 +947,7 @@ __device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>&
   const R half = Mth<R>::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
+  *hl = half;
   return true;
 }
 
@@ -1075,13 +1077,13 @@ __device__ __forceinline__ Hit<R> tubes_absorb(const DetP<R>& D, const TofWin& W
   const R y_lo = (R)D.row_y[row] - (R)D.half_len;
   const R y_hi = (R)D.row_y[row] + (R)D.half_len;
   int best = -1;
-  R best_in = M::inf(), best_out = R(0);
+  R best_in = M::inf(), best_out = R(0), best_len = R(0);
 #pragma unroll
   for (int dc = -1; dc <= 1; ++dc) {
     const int c = g + dc;
     if (c < 0 || c >= n_tubes_row) continue;
-    R s1, s2;
-    if (!tube_span<R>(Rad, tu[2 * c], tu[2 * c + 1], (R)D.tube_r, n, &s1, &s2)) continue;
+    R s1, s2, hl;
+    if (!tube_span<R>(Rad, tu[2 * c], tu[2 * c + 1], (R)D.tube_r, n, &s1, &s2, &hl)) continue;
     R ys1, ys2;
     if (n.dy == R(0)) {
       if (!(n.y >= y_lo && n.y <= y_hi)) continue;
@@ -1099,10 +1101,14 @@ __device__ __forceinline__ Hit<R> tubes_absorb(const DetP<R>& D, const TofWin& W
       best = c;
       best_in = s_in;
       best_out = s_out;
+      // FP32: the ends of the chord lie ~3 m from the sample, where floats are spaced
+      // 2.4e-7 m apart, so their difference would lose ~1e-5 of a 1-2 cm chord; an uncut
+      // chord is taken as twice the half chord instead.  FP64 keeps the difference.
+      best_len = (sizeof(R) == 4 && s_in == s1 && s_out == s2) ? hl + hl : s_out - s_in;
     }
   }
   if (best < 0) return h;
-  const R L = best_out - best_in;
+  const R L = best_len;
   const R mu = (R)D.mu_he_v / n.speed;
   const R pabs = -M::expm1(-mu * L);
   const R x = -M::log1p(-u_det * pabs) / mu;

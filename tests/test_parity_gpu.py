@@ -288,6 +288,8 @@ def test_fp32_fast_mode_within_bounds(ctx, make, n):
     # history (1e-6 kappa: ~16 FP32 unit roundoffs per unit of the condition estimate)
     # where that is larger; at most 1e-4 of the packets beyond
     tol = np.maximum(1e-5, 1e-6 * st["kappa"])
+    print("  share of packets beyond a flat 1e-5: " + ", ".join(
+        "%s %.2e" % (f, float((st["dev"][f] > 1e-5).mean())) for f in ("r", "v", "t", "w")))
     for f in ("r", "v", "t", "w"):
         d = st["dev"][f]
         assert (d > tol).sum() <= rate_bound(1e-4, d.size), (f, float(np.quantile(d / tol, 0.9999)))
