@@ -24,7 +24,7 @@ BOLTZMANN_MEV_PER_K = 1.380649e-23 / 1.602176634e-22
 ATM_PA = 101325.0
 
 SOLID_CYL, HOLLOW_CYL, BLOCK = 0, 1, 2
-K_ISO, K_SQE, K_BVK = 0, 1, 2
+K_ISO, K_SQE, K_BVK, K_PHONON = 0, 1, 2, 3
 DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
 
 
@@ -117,6 +117,20 @@ class Bvk:
 
 
 @dataclass
+class PhononDos:
+    """Incoherent scattering from a phonon density of states: z[j-1] is the density of modes
+    of the energy bin at j de (meV), j = 1..len(z) (none at 0); mass_u the atomic mass; the
+    multi-phonon channel runs to order nmax; p the probabilities with which the kernel picks
+    its elastic, one-phonon and multi-phonon channels."""
+    z: np.ndarray
+    de: float = 0.25
+    mass_u: float = 50.9415
+    nmax: int = 5
+    p: tuple = (0.25, 0.375, 0.375)
+    temperature_K: float = 300.0
+
+
+@dataclass
 class Workload:
     name: str
     beam: Beam
@@ -127,6 +141,7 @@ class Workload:
     min_prob: float = 0.0
     sqe: Optional[SqeGrid] = None
     bvk: Optional[Bvk] = None
+    phonon: Optional[PhononDos] = None
     seed: int = 0
     sim_id: int = 0
 
@@ -154,6 +169,18 @@ def sqe_table(nq=200, ne=400, q_max=12.0, e_min=-90.0, e_max=90.0, omega_amp=40.
         f = np.where(x == 0.0, 1.0, x / -np.expm1(-x))
     s = 0.5 * (g(E - w) + g(E + w)) * f
     return s.astype(np.float32)
+
+
+# ---- synthetic phonon density of states ---------------------------------------------------
+def phonon_dos(de=0.25, e_max=40.0) -> np.ndarray:
+    """A vanadium-like density of states on E_j = j de (j = 1.. up to e_max): a Debye E^2 rise
+    rounded off above ~20 meV plus transverse and longitudinal peaks near 22 and 35 meV,
+    zero at e_max.  Unnormalised (the kernel normalises it)."""
+    E = de * np.arange(1, int(round(e_max / de)) + 1)
+    g = lambda c, s: np.exp(-0.5 * ((E - c) / s) ** 2)
+    z = (E / 20.0) ** 2 * np.exp(-(E / 24.0) ** 4) + 0.9 * g(22.0, 2.5) + 1.2 * g(35.0, 1.8)
+    z *= np.clip((e_max - E) / 2.0, 0.0, 1.0)
+    return z
 
 
 # ---- workloads --------------------------------------------------------------------------
@@ -239,6 +266,23 @@ def powder_two_kernels(n=100_000, sig_iso=1.5, sig_sqe=5.0, ei=100.0) -> Workloa
     s = powder_sample()
     s = Scatterer(s.kind, s.dims, s.n_per_A3, s.sig_abs_b, [(K_ISO, sig_iso), (K_SQE, sig_sqe)])
     return w.replace(name="powder-two-kernels-%gmeV" % ei, scatterers=[s], beam=powder_beam(ei=ei))
+
+
+def vanadium_sample() -> Scatterer:
+    """Vanadium-like incoherent scatterer (n 0.0722 A^-3, sigma_inc 5.08 b, sigma_abs 5.08 b at
+    2200 m/s) in the hollow cylinder of the benchmark, scattering through the incoherent
+    phonon expansion of phonon_dos()."""
+    return Scatterer(kind=HOLLOW_CYL, dims=(0.008, 0.010, 0.04), n_per_A3=0.0722,
+                     sig_abs_b=5.08, kernels=[(K_PHONON, 5.08)])
+
+
+def vanadium_powder(n=100_000, ei=100.0, nmax=5) -> Workload:
+    """Incoherent phonon scattering of a vanadium-like sample (elastic with Debye-Waller,
+    one-phonon and multi-phonon channels from a synthetic density of states), up to 5
+    scattering orders, on the 117,760-pixel tube system."""
+    return Workload(name="vanadium-phonon-%gmeV" % ei, beam=powder_beam(ei=ei),
+                    scatterers=[vanadium_sample()], detector=tube_detector(), n=n, max_orders=5,
+                    phonon=PhononDos(z=phonon_dos(), nmax=nmax))
 
 
 def config3_batch(n=2_000_000, orientations=None, detector=None) -> List[Workload]:

@@ -52,6 +52,8 @@ class Config(C.Structure):
         ("q_max", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double),
         ("bvk_phi_Nm", C.c_double), ("bvk_mass_u", C.c_double), ("bvk_a_A", C.c_double),
         ("bvk_msd_A2", C.c_double), ("temperature_K", C.c_double),
+        ("dos_z", C.POINTER(C.c_double)), ("dos_n", C.c_int), ("dos_de", C.c_double),
+        ("phonon_mass_u", C.c_double), ("phonon_nmax", C.c_int), ("phonon_p", C.c_double * 3),
         ("det_kind", C.c_int), ("det_radius_m", C.c_double), ("det_height_m", C.c_double),
         ("n_phi", C.c_int), ("n_y", C.c_int), ("n_rows", C.c_int), ("packs", C.c_int * 3),
         ("row_y_m", C.c_double * 3), ("tubes_per_pack", C.c_int),
@@ -88,6 +90,8 @@ def lib():
         L.orc_adjoint.restype = C.c_int
         L.orc_loss.argtypes = [P, C.c_int64, C.c_int64, P, C.c_double, P, P]
         L.orc_loss.restype = C.c_int
+        L.orc_phonon_tables.argtypes = [P, P, P, P, C.c_int64]
+        L.orc_phonon_tables.restype = C.c_int
         L.orc_bvk_modes.argtypes = [P, P, P, P]
         L.orc_kernel_bvk.argtypes = [P, C.c_double, C.c_double, P, P, P, P, P, P]
         L.orc_kernel_bvk.restype = C.c_int
@@ -128,6 +132,17 @@ def make_config(wl):
         v = wl.bvk
         c.bvk_phi_Nm, c.bvk_mass_u, c.bvk_a_A = v.phi_Nm, v.mass_u, v.a_A
         c.bvk_msd_A2, c.temperature_K = v.msd_A2, v.temperature_K
+    ph = getattr(wl, "phonon", None)
+    if ph is not None:
+        if wl.bvk is not None and wl.bvk.temperature_K != ph.temperature_K:
+            raise ValueError("one temperature per sample")
+        z = np.ascontiguousarray(ph.z, dtype=np.float64)
+        c._dos_keep = z
+        c.dos_z = z.ctypes.data_as(C.POINTER(C.c_double))
+        c.dos_n, c.dos_de = z.size, ph.de
+        c.phonon_mass_u, c.phonon_nmax = ph.mass_u, ph.nmax
+        c.phonon_p[:] = list(ph.p)
+        c.temperature_K = ph.temperature_K
     det = wl.detector
     if det is not None:
         c.det_kind = det.kind
@@ -291,3 +306,18 @@ def kernel_bvk(wl, rot_y, speed, d, u):
     ok = lib().orc_kernel_bvk(C.byref(cfg), rot_y, speed, _ptr(d), _ptr(u), C.byref(sp),
                               _ptr(d_out), C.byref(fac), _ptr(ev))
     return {"ok": bool(ok), "speed": sp.value, "d": d_out, "factor": fac.value, "event": ev[0]}
+
+
+def phonon_tables(wl):
+    """gamma_0 (1/meV), c_w (2W = c_w Q^2, A^2) and A_n (n = 1..n_max) as masses on the grid
+    E = i de, i = -n_max J..n_max J (rows n - 1) of the workload's phonon kernel."""
+    cfg = make_config(wl)
+    g0, cw = C.c_double(), C.c_double()
+    N, J = wl.phonon.nmax, wl.phonon.z.size
+    M = 2 * N * J + 1
+    a = np.zeros(N * M)
+    m = lib().orc_phonon_tables(C.byref(cfg), C.byref(g0), C.byref(cw), _ptr(a), a.size)
+    if m != M:
+        raise ValueError("oracle rejected the phonon kernel")
+    return {"gamma0": g0.value, "c_w": cw.value, "A": a.reshape(N, M),
+            "E": np.arange(-N * J, N * J + 1) * wl.phonon.de}

@@ -920,6 +920,201 @@ bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const
   return true;
 }
 
+// ---- incoherent scattering from a phonon density of states (supplement S4) ------------
+// The incoherent scattering function of a harmonic cubic crystal as a phonon expansion:
+//   S(Q,E) = e^{-2W} [ delta(E) + sum_{n=1}^{N} (2W)^n / n! A_n(E) ],
+//   A_1(E) = Z(|E|) / (|E| gamma_0) [n(|E|) + 1 if E > 0 (phonon created), n(|E|) if E < 0],
+//   A_n = A_1 * A_{n-1} (convolution),  gamma_0 = int coth(E / 2kT) Z(E) / E dE,
+//   2W = hbar^2 Q^2 gamma_0 / (2M),  n the Bose factor,  E = Ei - Ef.
+// Its n = 0 term is the incoherent elastic kernel with the Debye-Waller factor, its n = 1
+// term the incoherent inelastic single-phonon form (hbar^2 Q^2/2M e^{-2W} Z(E)/E
+// {coth(E/2kT) +- 1}/2), its n >= 2 terms the multi-phonon form S_n(Q) A_n(E).  The density
+// of states is a histogram of mode energies: dos_z[j-1] holds the modes of the bin at
+// E_j = j de, normalised here to weights w_j summing to 1, so A_1 is a set of masses on the
+// grid E = i de and every A_n is an exact discrete convolution on that grid.  A sampled
+// energy is spread uniformly over its bin (E = i de + (u - 1/2) de).
+// Sampling: channel c = elastic / one-phonon / multi-phonon with probabilities phonon_p; the
+// elastic channel draws an isotropic direction (weight e^{-2W} / p_0); the others draw the
+// grid point from A_1 (one-phonon) or from B = (A_2 + ... + A_N) / (N - 1) (multi-phonon),
+// then Q uniform over [|ki - kf|, ki + kf] and the azimuth uniform, weight
+//   (term of S at (Q, E)) / (sampling mass of E) * Q dQ / (2 ki^2) / p_c
+// (the same change of variables as the tabulated S(Q,E) kernel, with the mass of the energy
+// bin in place of dE / (e_max - e_min)).
+struct PhononModel {
+  const double* z = nullptr;
+  int J = 0, N = 0, M = 0;
+  double de = 0.0, kT = 0.0, mass = 0.0;
+  double gamma0 = 0.0, cw = 0.0;
+  double p[3] = {0.0, 0.0, 0.0};
+  std::vector<double> a1;             // A_1 masses on i = -J..J (index i + J)
+  std::vector<double> cdf1;           // cumulative sums of a1
+  std::vector<std::vector<double>> an;  // A_n masses on i = -N J..N J (index i + N J), n = 1..N
+  std::vector<double> b, cdfb;        // B and its cumulative sums on the same grid
+};
+
+double bose(double e, double kT) { return 1.0 / std::expm1(e / kT); }
+
+const PhononModel& phonon_model(const orc_config& cfg) {
+  thread_local PhononModel m;
+  const double kT = kBoltzmann * cfg.temperature_K * kMeVPerJ;
+  if (m.z == cfg.dos_z && m.J == cfg.dos_n && m.de == cfg.dos_de && m.kT == kT &&
+      m.mass == cfg.phonon_mass_u && m.N == cfg.phonon_nmax && m.p[0] == cfg.phonon_p[0] &&
+      m.p[1] == cfg.phonon_p[1] && m.p[2] == cfg.phonon_p[2])
+    return m;
+  m = PhononModel();
+  m.z = cfg.dos_z;
+  m.J = cfg.dos_n;
+  m.N = cfg.phonon_nmax;
+  m.de = cfg.dos_de;
+  m.kT = kT;
+  m.mass = cfg.phonon_mass_u;
+  for (int c = 0; c < 3; ++c) m.p[c] = cfg.phonon_p[c];
+  const int J = m.J, N = m.N;
+  m.M = 2 * N * J + 1;
+  // mode weights, gamma_0 and the Debye-Waller coefficient
+  double zsum = 0.0;
+  for (int j = 1; j <= J; ++j) zsum += cfg.dos_z[j - 1];
+  m.gamma0 = 0.0;
+  for (int j = 1; j <= J; ++j) {
+    const double e = j * m.de;
+    m.gamma0 += (cfg.dos_z[j - 1] / zsum) / (e * std::tanh(e / (2.0 * kT)));
+  }
+  // hbar^2 / 2M in meV A^2
+  const double hb2m = kHbar * kHbar / (2.0 * m.mass * kAtomicMass) * 1e20 * kMeVPerJ;
+  m.cw = hb2m * m.gamma0;
+  // A_1 masses
+  m.a1.assign(2 * J + 1, 0.0);
+  for (int j = 1; j <= J; ++j) {
+    const double e = j * m.de, w = cfg.dos_z[j - 1] / zsum;
+    const double nb = bose(e, kT);
+    m.a1[J + j] = w * (nb + 1.0) / (e * m.gamma0);
+    m.a1[J - j] = w * nb / (e * m.gamma0);
+  }
+  m.cdf1.assign(2 * J + 1, 0.0);
+  double acc = 0.0;
+  for (int i = 0; i < 2 * J + 1; ++i) m.cdf1[i] = (acc += m.a1[i]);
+  // A_n = A_1 * A_{n-1} on the grid i = -N J..N J
+  m.an.assign(N + 1, std::vector<double>(m.M, 0.0));
+  for (int i = -J; i <= J; ++i) m.an[1][i + N * J] = m.a1[i + J];
+  for (int n = 2; n <= N; ++n) {
+    for (int i = -n * J; i <= n * J; ++i) {
+      double v = 0.0;
+      for (int k = -J; k <= J; ++k) {
+        const int r = i - k;
+        if (r < -(n - 1) * J || r > (n - 1) * J) continue;
+        v += m.a1[k + J] * m.an[n - 1][r + N * J];
+      }
+      m.an[n][i + N * J] = v;
+    }
+  }
+  m.b.assign(m.M, 0.0);
+  m.cdfb.assign(m.M, 0.0);
+  acc = 0.0;
+  for (int i = 0; i < m.M; ++i) {
+    for (int n = 2; n <= N; ++n) m.b[i] += m.an[n][i] / (N - 1);
+    m.cdfb[i] = (acc += m.b[i]);
+  }
+  return m;
+}
+
+// index of the first cumulative sum above u * total (a draw from the masses)
+int draw_index(const std::vector<double>& cdf, double u) {
+  const double x = u * cdf.back();
+  int i = (int)(std::upper_bound(cdf.begin(), cdf.end(), x) - cdf.begin());
+  return std::min(i, (int)cdf.size() - 1);
+}
+
+bool kernel_phonon(const orc_config& cfg, double speed, Vec3 d, const double u[4], KernelOut* o) {
+  const PhononModel& m = phonon_model(cfg);
+  const double Ei = kMeVPerV2 * speed * speed;
+  const double ki = kKPerV * speed;
+  o->entry = -1;
+  o->s_value = 1.0;
+  o->ki = ki;
+  // channel, and the rescaled uniform of the energy draw
+  int ch = 2;
+  double lo = m.p[0] + m.p[1];
+  if (u[0] < m.p[0]) {
+    ch = 0;
+    lo = 0.0;
+  } else if (u[0] < m.p[0] + m.p[1]) {
+    ch = 1;
+    lo = m.p[0];
+  }
+  o->mode = ch;
+  if (ch == 0) {
+    // elastic: isotropic, weight e^{-2W}
+    const double ct = 2.0 * u[2] - 1.0;
+    const double st = 2.0 * std::sqrt(u[2] * (1.0 - u[2]));
+    const double phi = 2.0 * kPi * u[3];
+    o->d = {st * std::cos(phi), st * std::sin(phi), ct};
+    o->speed = speed;
+    o->kf = ki;
+    o->e = 0.0;
+    o->qvec = add(scale(d, ki), scale(o->d, -ki));
+    o->q = std::sqrt(dot(o->qvec, o->qvec));
+    o->rest = std::exp(-m.cw * o->q * o->q) / m.p[0];
+    o->factor = o->rest;
+    return true;
+  }
+  const double ue = (u[0] - lo) / m.p[ch];
+  int i;
+  double mass;
+  if (ch == 1) {
+    const int k = draw_index(m.cdf1, ue);
+    i = k - m.J;
+    mass = m.a1[k];
+  } else {
+    const int k = draw_index(m.cdfb, ue);
+    i = k - m.N * m.J;
+    mass = m.b[k];
+  }
+  const double E = (i + (u[1] - 0.5)) * m.de;
+  const double Ef = Ei - E;
+  if (!(Ef > 0.0)) return false;
+  const double speed_f = std::sqrt(Ef / kMeVPerV2);
+  const double kf = kKPerV * speed_f;
+  const double q_lo = std::fabs(ki - kf), q_hi = ki + kf;
+  const double dQ = q_hi - q_lo;
+  // condition estimate: the width of the Q range and the final speed, as for S(Q,E)
+  g_kappa += (ki + kf) / dQ + 2.0 * g_kappa_v * (1.0 + (ki + kf) / dQ);
+  g_kappa_v = 1.0 + 0.5 * ((Ei + std::fabs(E)) / Ef + 2.0 * (Ei / Ef) * g_kappa_v);
+  const double Q = q_lo + u[2] * dQ;
+  // scattering angle from 1 -/+ cos as products of the offsets from the ends of the range
+  const double den = 2.0 * ki * kf;
+  const double one_m = (u[2] * dQ) * (Q + q_lo) / den;
+  const double one_p = ((1.0 - u[2]) * dQ) * (ki + kf + Q) / den;
+  double c2t = (one_m <= one_p) ? 1.0 - one_m : one_p - 1.0;
+  c2t = std::min(1.0, std::max(-1.0, c2t));
+  const double s2t = std::sqrt(std::max(0.0, one_m * one_p));
+  const double phi = 2.0 * kPi * u[3];
+  // the term of S at (Q, E) over the sampling mass of E
+  const double w2 = m.cw * Q * Q;
+  double ratio;
+  if (ch == 1) {
+    ratio = w2 * std::exp(-w2);  // 2W e^{-2W} A_1 / A_1
+  } else {
+    const int g = i + m.N * m.J;
+    double sum = 0.0, pw = w2;
+    double fact = 1.0;
+    for (int n = 2; n <= m.N; ++n) {
+      pw *= w2;
+      fact *= n;
+      sum += pw / fact * m.an[n][g];
+    }
+    ratio = std::exp(-w2) * sum / mass;
+  }
+  o->d = rotate_about(d, c2t, s2t, phi);
+  o->speed = speed_f;
+  o->kf = kf;
+  o->q = Q;
+  o->e = E;
+  o->rest = ratio * Q * dQ / (2.0 * ki * ki) / m.p[ch];
+  o->factor = o->rest;
+  o->qvec = add(scale(d, ki), scale(o->d, -kf));
+  return true;
+}
+
 bool kernel_scatter(const orc_config& cfg, int ktype, double speed, Vec3 d, const double u[4],
                     KernelOut* o, double rot_y = 0.0) {
   if (ktype == ORC_K_ISO) {
@@ -928,6 +1123,7 @@ bool kernel_scatter(const orc_config& cfg, int ktype, double speed, Vec3 d, cons
   }
   if (ktype == ORC_K_SQE) return kernel_sqe(cfg, speed, d, u, o);
   if (ktype == ORC_K_BVK) return kernel_bvk(cfg, rot_y, speed, d, u, o);
+  if (ktype == ORC_K_PHONON) return kernel_phonon(cfg, speed, d, u, o);
   return false;
 }
 
@@ -1139,6 +1335,21 @@ bool config_ok(const orc_config* cfg) {
       if (s.ktype[k] == ORC_K_BVK && !(cfg->bvk_phi_Nm > 0 && cfg->bvk_mass_u > 0 &&
                                       cfg->bvk_a_A > 0 && cfg->temperature_K > 0))
         return false;
+      if (s.ktype[k] == ORC_K_PHONON) {
+        if (!cfg->dos_z || cfg->dos_n < 1 || !(cfg->dos_de > 0) || !(cfg->phonon_mass_u > 0) ||
+            cfg->phonon_nmax < 2 || !(cfg->temperature_K > 0))
+          return false;
+        double zs = 0.0, ps = 0.0;
+        for (int j = 0; j < cfg->dos_n; ++j) {
+          if (!(cfg->dos_z[j] >= 0)) return false;
+          zs += cfg->dos_z[j];
+        }
+        for (int c = 0; c < 3; ++c) {
+          if (!(cfg->phonon_p[c] > 0)) return false;
+          ps += cfg->phonon_p[c];
+        }
+        if (!(zs > 0) || std::fabs(ps - 1.0) > 1e-12) return false;
+      }
     }
   }
   if (cfg->det_kind != ORC_DET_NONE && cfg->n_tof <= 0) return false;
@@ -1351,6 +1562,8 @@ int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const dou
   if (ev) {
     ev->kernel = ktype;
     ev->entry = ko.entry;
+    ev->mode = ko.mode;
+    ev->nroots = ko.nroots;
     ev->q = ko.q;
     ev->e = ko.e;
     ev->ki = ko.ki;
@@ -1408,6 +1621,19 @@ int orc_kernel_bvk(const orc_config* cfg, double rot_y, double speed, const doub
     ev->qvec[2] = ko.qvec.z;
   }
   return 1;
+}
+
+int orc_phonon_tables(const orc_config* cfg, double* gamma0, double* c_w, double* a, int64_t cap) {
+  if (!cfg || !cfg->dos_z || cfg->dos_n < 1 || cfg->phonon_nmax < 2 || !(cfg->dos_de > 0) ||
+      !(cfg->temperature_K > 0) || !(cfg->phonon_mass_u > 0))
+    return 0;
+  const PhononModel& m = phonon_model(*cfg);
+  *gamma0 = m.gamma0;
+  *c_w = m.cw;
+  if (a && cap >= (int64_t)m.N * m.M)
+    for (int n = 1; n <= m.N; ++n)
+      for (int i = 0; i < m.M; ++i) a[(int64_t)(n - 1) * m.M + i] = m.an[n][i];
+  return m.M;
 }
 
 int orc_trace(const orc_config* cfg, int64_t first_id, int64_t n, orc_packet* packets,

@@ -25,7 +25,7 @@ extern "C" {
 /* shape kinds (all centred at the origin, axis or rotation axis along +y) */
 enum { ORC_SOLID_CYL = 0, ORC_HOLLOW_CYL = 1, ORC_BLOCK = 2 };
 /* kernel kinds */
-enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2 };
+enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2, ORC_K_PHONON = 3 };
 /* detector kinds */
 enum { ORC_DET_NONE = 0, ORC_DET_SURFACE = 1, ORC_DET_TUBES = 2 };
 
@@ -54,6 +54,15 @@ typedef struct {
   double q_max, e_min, e_max;
   /* single-crystal Born-von Karman kernel (fcc, nearest-neighbour central force) */
   double bvk_phi_Nm, bvk_mass_u, bvk_a_A, bvk_msd_A2, temperature_K;
+  /* incoherent scattering from a phonon density of states (temperature_K as above):
+     dos_z[j-1] = Z(j dos_de), j = 1..dos_n, the modes of the energy bin j dos_de (meV);
+     phonon_nmax >= 2 the largest order of the multi-phonon channel; phonon_p the
+     probabilities of the elastic, one-phonon and multi-phonon channels */
+  const double* dos_z;
+  int dos_n;
+  double dos_de, phonon_mass_u;
+  int phonon_nmax;
+  double phonon_p[3];
   /* detector */
   int det_kind;
   double det_radius_m, det_height_m; /* SURFACE */
@@ -161,6 +170,11 @@ void orc_bvk_modes(const orc_config* cfg, const double q[3], double hw[3], doubl
 int orc_kernel_bvk(const orc_config* cfg, double rot_y, double speed, const double d[3],
                    const double u[4], double* speed_out, double d_out[3], double* factor,
                    orc_event* ev);
+
+/* the tables of the phonon kernel (for the pins): gamma_0 (1/meV), c_w (2W = c_w Q^2, A^2)
+   and the masses of A_n on the grid E = i dos_de, i = -n_max*dos_n..n_max*dos_n
+   (a[(n-1)*M + i + n_max*dos_n], n = 1..n_max, M = 2*n_max*dos_n + 1); returns M, or 0 */
+int orc_phonon_tables(const orc_config* cfg, double* gamma0, double* c_w, double* a, int64_t cap);
 
 #ifdef __cplusplus
 }
