@@ -56,7 +56,7 @@ typedef enum {
 
 enum { MCV_MAX_SCATTERERS = 4, MCV_MAX_TUBES_PER_ROW = 512, MCV_NTALLY = 8 };
 enum { MCV_SHAPE_SOLID_CYL = 0, MCV_SHAPE_HOLLOW_CYL = 1, MCV_SHAPE_BLOCK = 2 };
-enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2 };
+enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2, MCV_KERNEL_PHONON = 3 };
 enum { MCV_DET_NONE = 0, MCV_DET_SURFACE = 1, MCV_DET_TUBES = 2 };
 enum { MCV_FP64 = 0, MCV_FP32 = 1 };
 
@@ -110,6 +110,26 @@ typedef struct {
   double phi_Nm, mass_u, a_A, msd_A2, temperature_K;
 } mcv_bvk;
 
+/* Incoherent scattering from a phonon density of states (supplement "Scattering kernels used
+ * in the examples": incoherent elastic with the Debye-Waller factor, incoherent inelastic
+ * single-phonon, multi-phonon), as the phonon expansion
+ *   S(Q,E) = e^{-2W} [delta(E) + sum_{n=1}^{n_max} (2W)^n/n! A_n(E)],  2W = c_w Q^2,
+ *   A_1(E) = Z(|E|)/(|E| gamma_0) (n_B(|E|) + 1 for E > 0, n_B(|E|) for E < 0),
+ *   A_n = A_1 * A_{n-1},  gamma_0 = sum coth(E/2kT) Z(E)/E,  c_w = hbar^2 gamma_0 / 2M,
+ * E = Ei - Ef.  The density of states is a histogram of mode energies: Z at j*de_mev,
+ * j = 1..n_modes, normalised by the library; each A_n is a set of masses on the grid
+ * E = i*de_mev, and a sampled energy is spread uniformly over its grid bin.  The kernel picks
+ * the elastic, one-phonon or multi-phonon channel with probabilities p[0..2] (summing to 1).
+ * tables: device memory of mcv_phonon_table_bytes(n_modes, n_max) bytes filled by
+ * mcv_phonon_build, which also writes gamma0 (1/meV) and c_w (A^2). */
+typedef struct {
+  const void* tables;
+  int n_modes, n_max;
+  double de_mev, mass_u, temperature_K;
+  double p[3];
+  double gamma0, c_w;
+} mcv_phonon;
+
 /* The sample assembly: a flat list of scatterers (the composite of section 2.4.1, one level
  * deep).  max_orders = maximum number of scatterings of a packet; packets whose weight
  * drops below min_prob are discarded (section 2.4.3); fp_mode MCV_FP64 traces in FP64,
@@ -122,6 +142,7 @@ typedef struct {
   int fp_mode;
   mcv_sqe sqe;
   mcv_bvk bvk;
+  mcv_phonon phonon;
 } mcv_sample;
 
 /* Detector system.  SURFACE: ideal cylinder of radius_m, height_m, efficiency 1, n_phi x
@@ -189,6 +210,16 @@ mcv_status mcv_sync(mcv_ctx* ctx, void* stream);
 int64_t mcv_detector_pixels(const mcv_detector* det);
 /* Sets n doubles at dst (device) to zero on `stream` with the library's own fill kernel. */
 mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream);
+
+/* Bytes of the device tables of the phonon kernel (mcv_phonon), 0 for invalid sizes. */
+int64_t mcv_phonon_table_bytes(int n_modes, int n_max);
+/* Builds the tables of the phonon kernel from the density of states dos_z (host, n_modes
+ * values Z(j*de_mev), j = 1..n_modes, >= 0, not all 0) and ph's n_modes, n_max (2..16),
+ * de_mev, mass_u, temperature_K and p; writes ph->gamma0 and ph->c_w, copies the tables to
+ * `tables` (device, `bytes` >= mcv_phonon_table_bytes) on `stream` and sets ph->tables.
+ * The host data may be freed when the call returns.  Errors: MCV_EINVAL, MCV_ECUDA. */
+mcv_status mcv_phonon_build(const double* dos_z, mcv_phonon* ph, void* tables, int64_t bytes,
+                            void* stream);
 
 /* ---- the component chain ------------------------------------------------------------- */
 /* Source: writes n packets with ids first_id..first_id+n-1 into out (slots 0..n-1; out->id

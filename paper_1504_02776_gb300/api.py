@@ -39,8 +39,40 @@ def detector_struct(det):
     return d
 
 
+def phonon_struct(ph, stream=None):
+    """mcv_phonon of a workload's phonon density of states, its tables built by the library
+    (mcv_phonon_build) into a device tensor; returns (struct, tensor) -- keep the tensor."""
+    import numpy as np
+    z = np.ascontiguousarray(ph.z, dtype=np.float64)
+    p = B.Phonon()
+    p.n_modes, p.n_max = z.size, ph.nmax
+    p.de_mev, p.mass_u, p.temperature_K = ph.de, ph.mass_u, ph.temperature_K
+    p.p[:] = list(ph.p)
+    nbytes = B.mcv_phonon_table_bytes(p.n_modes, p.n_max)
+    if nbytes <= 0:
+        raise ValueError("bad phonon table size")
+    tables = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    B.mcv_phonon_build(z.ctypes.data_as(C.c_void_p), p, C.c_void_p(tables.data_ptr()), nbytes,
+                       _stream() if stream is None else stream)
+    return p, tables
+
+
+_PHONON_CACHE = {}
+
+
+def phonon_for(ph):
+    """The (struct, device tables) of a PhononDos, built once per description."""
+    import numpy as np
+    key = (np.asarray(ph.z, dtype=np.float64).tobytes(), ph.de, ph.mass_u, ph.nmax,
+           tuple(ph.p), ph.temperature_K, torch.cuda.current_device())
+    if key not in _PHONON_CACHE:
+        _PHONON_CACHE[key] = phonon_struct(ph)
+    return _PHONON_CACHE[key]
+
+
 def sample_struct(wl, fp_mode, table=None):
-    """mcv_sample from a workload; `table` is the device FP32 S(Q,E) tensor (if any)."""
+    """mcv_sample from a workload; `table` is the device FP32 S(Q,E) tensor (if any); the
+    phonon kernel's tables are built on the device once per description (phonon_for)."""
     s = B.Sample()
     s.n_scatterers = len(wl.scatterers)
     for j, sc in enumerate(wl.scatterers):
@@ -64,6 +96,9 @@ def sample_struct(wl, fp_mode, table=None):
         v = wl.bvk
         s.bvk.phi_Nm, s.bvk.mass_u, s.bvk.a_A = v.phi_Nm, v.mass_u, v.a_A
         s.bvk.msd_A2, s.bvk.temperature_K = v.msd_A2, v.temperature_K
+    if getattr(wl, "phonon", None) is not None:
+        ph, _ = phonon_for(wl.phonon)
+        C.memmove(C.addressof(s.phonon), C.addressof(ph), C.sizeof(ph))
     return s
 
 

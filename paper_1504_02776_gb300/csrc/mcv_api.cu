@@ -66,7 +66,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
   S->ns = s->n_scatterers;
   S->max_orders = s->max_orders;
   S->min_prob = s->min_prob;
-  bool need_sqe = false, need_bvk = false;
+  bool need_sqe = false, need_bvk = false, need_phonon = false;
   for (int j = 0; j < s->n_scatterers; ++j) {
     const mcv_scatterer& a = s->scat[j];
     mcv::ScatP<double>& d = S->s[j];
@@ -78,9 +78,10 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     double sig = 0.0;
     for (int k = 0; k < a.n_kernels; ++k) {
       if (a.kernel[k] != MCV_KERNEL_ISO && a.kernel[k] != MCV_KERNEL_SQE &&
-          a.kernel[k] != MCV_KERNEL_BVK)
+          a.kernel[k] != MCV_KERNEL_BVK && a.kernel[k] != MCV_KERNEL_PHONON)
         return fail(MCV_EINVAL, "unknown kernel kind");
       if (a.kernel[k] == MCV_KERNEL_BVK) need_bvk = true;
+      if (a.kernel[k] == MCV_KERNEL_PHONON) need_phonon = true;
       if (a.kernel_sig_b[k] < 0) return fail(MCV_EINVAL, "negative kernel cross section");
       if (a.kernel[k] == MCV_KERNEL_SQE) need_sqe = true;
       sig += a.kernel_sig_b[k];
@@ -148,6 +149,37 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     S->bvk_wmax = mcv::kHbar * std::sqrt(24.0 * S->bvk_coef) * mev_per_j;
     S->bvk_hwu = mcv::kHbar * std::sqrt(S->bvk_coef) * mev_per_j;
   }
+  if (need_phonon) {
+    const mcv_phonon& p = s->phonon;
+    const int64_t bytes = mcv_phonon_table_bytes(p.n_modes, p.n_max);
+    if (!p.tables || bytes == 0) return fail(MCV_EINVAL, "phonon tables missing (mcv_phonon_build)");
+    if (!(p.de_mev > 0 && is_finite(p.de_mev) && p.gamma0 > 0 && is_finite(p.gamma0) &&
+          p.c_w > 0 && is_finite(p.c_w)))
+      return fail(MCV_EINVAL, "bad phonon description (build it with mcv_phonon_build)");
+    double ps = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      if (!(p.p[c] > 0) || !is_finite(p.p[c])) return fail(MCV_EINVAL, "bad phonon channel probabilities");
+      ps += p.p[c];
+    }
+    if (std::fabs(ps - 1.0) > 1e-12) return fail(MCV_EINVAL, "phonon channel probabilities must sum to 1");
+    const int J = p.n_modes, N = p.n_max, M = 2 * N * J + 1;
+    const double* base = static_cast<const double*>(p.tables);
+    S->has_phonon = 1;
+    S->ph_J = J;
+    S->ph_N = N;
+    S->ph_M = M;
+    S->ph_cdf1 = base;
+    S->ph_cdfb = base + (2 * J + 1);
+    S->ph_b = S->ph_cdfb + M;
+    S->ph_an = S->ph_b + M;
+    S->ph_de = p.de_mev;
+    S->ph_cw = p.c_w;
+    S->ph_p0 = p.p[0];
+    S->ph_p1 = p.p[1];
+    S->ph_p2 = p.p[2];
+    S->ph_p01 = p.p[0] + p.p[1];
+  }
+  S->wide = (need_bvk || need_phonon) ? 1 : 0;
   return MCV_OK;
 }
 
@@ -365,6 +397,26 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
   f->bvk_msd = (float)d.bvk_msd;
   f->bvk_wmax = (float)d.bvk_wmax;
   f->bvk_hwu = (float)d.bvk_hwu;
+  f->has_phonon = d.has_phonon;
+  f->ph_J = d.ph_J;
+  f->ph_N = d.ph_N;
+  f->ph_M = d.ph_M;
+  if (d.has_phonon) {
+    // the float copy of the tables follows the double one (mcv_phonon_build)
+    const int64_t T = (2 * (int64_t)d.ph_J + 1) + 2 * (int64_t)d.ph_M + (int64_t)(d.ph_N - 1) * d.ph_M;
+    const float* fb = reinterpret_cast<const float*>(d.ph_cdf1 + T);
+    f->ph_cdf1 = fb;
+    f->ph_cdfb = fb + (d.ph_cdfb - d.ph_cdf1);
+    f->ph_b = fb + (d.ph_b - d.ph_cdf1);
+    f->ph_an = fb + (d.ph_an - d.ph_cdf1);
+  }
+  f->ph_de = (float)d.ph_de;
+  f->ph_cw = (float)d.ph_cw;
+  f->ph_p0 = (float)d.ph_p0;
+  f->ph_p1 = (float)d.ph_p1;
+  f->ph_p2 = (float)d.ph_p2;
+  f->ph_p01 = (float)d.ph_p01;
+  f->wide = d.wide;
 }
 
 void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
@@ -669,9 +721,9 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   A.err = ctx->d_err;
   const int detk = fused ? A.Dd.kind : MCV_DET_NONE;
   const int fp = sample->fp_mode;
-  int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][detk][A.Sd.has_bvk ? 1 : 0];
+  int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][detk][A.Sd.wide ? 1 : 0];
   if (occ == 0) {
-    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, detk, A.Sd.has_bvk, &occ);
+    cudaError_t e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, detk, A.Sd.wide, &occ);
     if (e != cudaSuccess || occ < 1) occ = 1;
   }
   const int grid = grid_for(ctx, n, occ);
@@ -788,9 +840,9 @@ mcv_status loss_and_adjoint(mcv_ctx* ctx, mcv::TraceArgs& A, int fp, const doubl
     A.scale_c = scale_c;
     A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
     A.dsig = dsig;
-    int& occ_a = ctx->occ_adj[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.has_bvk ? 1 : 0];
+    int& occ_a = ctx->occ_adj[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.wide ? 1 : 0];
     if (occ_a == 0) {
-      e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ_a);
+      e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.wide, &occ_a);
       if (e != cudaSuccess || occ_a < 1) occ_a = 1;
     }
     e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_for(ctx, A.n, occ_a), s);
@@ -823,9 +875,9 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
     A.hist = hist->counts;
     A.tallies = hist->tallies;
     A.stop_on_zero = 1;
-    int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.has_bvk ? 1 : 0];
+    int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][A.Dd.kind][A.Sd.wide ? 1 : 0];
     if (occ == 0) {
-      e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ);
+      e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.wide, &occ);
       if (e != cudaSuccess || occ < 1) occ = 1;
     }
     e = mcv::launch_trace(A, fp, A.Dd.kind, grid_for(ctx, n, occ), s);

@@ -87,7 +87,7 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
     if (total > kMaxNeutrons - s.n) return fail(MCV_EINVAL, "too many neutrons in the batch");
     total += s.n;
     ns = std::max(ns, d.S.ns);
-    if (d.S.has_bvk) bvk = 1;
+    if (d.S.wide) bvk = 1;
     if (k == 0)
       first = d.S;
     else if (std::memcmp(&first, &d.S, sizeof(first)) != 0)

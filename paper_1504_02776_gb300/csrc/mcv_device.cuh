@@ -602,6 +602,109 @@ __device__ __forceinline__ bool kernel_sqe(const SampleP<R>& S, const Rng& rng, 
   return true;
 }
 
+// ---- incoherent scattering from a phonon density of states (supplement S4) -------------
+// The phonon expansion S(Q,E) = e^{-2W} [delta(E) + sum_{n>=1} (2W)^n/n! A_n(E)], 2W = c_w Q^2,
+// with A_1 and the multi-phonon mixture B = (A_2 + ... + A_N)/(N - 1) as masses on the grid
+// E = i de (tables of mcv_phonon_build).  Channel: elastic (isotropic, weight e^{-2W}),
+// one-phonon (grid point from A_1, weight 2W e^{-2W}) or multi-phonon (grid point from B,
+// weight e^{-2W} sum_{n>=2} (2W)^n/n! A_n / B) with probabilities p0, p1, p2; the energy is
+// spread over its grid bin; Q uniform over [|ki - kf|, ki + kf], azimuth uniform; the
+// inelastic weights carry Q dQ / (2 ki^2), and every channel's weight is divided by its
+// probability.  Returns false when the drawn energy loss leaves no final energy.
+
+// first index whose cumulative mass exceeds u times the total (a draw from the masses)
+template <typename R>
+__device__ __forceinline__ int draw_mass(const R* __restrict__ cdf, int size, R u) {
+  const R x = u * __ldg(cdf + size - 1);
+  int lo = 0, hi = size;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(cdf + mid) > x) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo < size - 1 ? lo : size - 1;
+}
+
+template <typename R, class Rng>
+__device__ __forceinline__ bool kernel_phonon(const SampleP<R>& S, const Rng& rng, int o,
+                                              Ray<R>* n, Scatter<R>* sc) {
+  using M = Mth<R>;
+  const R Ei = (R)kMeVPerV2 * n->speed * n->speed;
+  const R ki = (R)kKPerV * n->speed;
+  R u0, u1, u2, u3;
+  rng.template pair<R>(o, 1, &u0, &u1);
+  rng.template pair<R>(o, 2, &u2, &u3);
+  sc->entry = -1;
+  sc->s_value = R(1);
+  if (u0 < S.ph_p0) {
+    // elastic: isotropic direction, speed unchanged
+    const R ct = R(2) * u2 - R(1);
+    const R st = R(2) * M::sqrt(u2 * (R(1) - u2));
+    R sp, cp;
+    M::sincos2pi(u3, &sp, &cp);
+    const R dx = st * cp, dy = st * sp, dz = ct;
+    const R qx = n->dx * ki + dx * (-ki), qy = n->dy * ki + dy * (-ki), qz = n->dz * ki + dz * (-ki);
+    const R q = M::sqrt(qx * qx + qy * qy + qz * qz);
+    n->dx = dx;
+    n->dy = dy;
+    n->dz = dz;
+    sc->rest = M::exp(-S.ph_cw * q * q) / S.ph_p0;
+    sc->factor = sc->rest;
+    sc->q = q;
+    sc->e = R(0);
+    return true;
+  }
+  const bool one = u0 < S.ph_p01;
+  const R p_ch = one ? S.ph_p1 : S.ph_p2;
+  const R ue = (u0 - (one ? S.ph_p0 : S.ph_p01)) / p_ch;
+  int i;
+  R mass = R(1);
+  if (one) {
+    i = draw_mass<R>(S.ph_cdf1, 2 * S.ph_J + 1, ue) - S.ph_J;
+  } else {
+    const int k = draw_mass<R>(S.ph_cdfb, S.ph_M, ue);
+    i = k - S.ph_N * S.ph_J;
+    mass = __ldg(S.ph_b + k);
+  }
+  const R E = ((R)i + (u1 - R(0.5))) * S.ph_de;
+  const R Ef = Ei - E;
+  if (!(Ef > R(0))) return false;
+  const R speed_f = M::sqrt(Ef / (R)kMeVPerV2);
+  const R kf = (R)kKPerV * speed_f;
+  const R q_lo = M::fabs(ki - kf), q_hi = ki + kf;
+  const R dQ = q_hi - q_lo;
+  const R Q = q_lo + u2 * dQ;
+  // scattering angle from 1 -/+ cos as products of the offsets from the ends of the range
+  const R den = R(2) * ki * kf;
+  const R one_m = (u2 * dQ) * (Q + q_lo) / den;
+  const R one_p = ((R(1) - u2) * dQ) * (ki + kf + Q) / den;
+  R c2t = (one_m <= one_p) ? R(1) - one_m : one_p - R(1);
+  c2t = M::fmin(R(1), M::fmax(R(-1), c2t));
+  const R s2t = M::sqrt(M::fmax(R(0), one_m * one_p));
+  // the term of S at (Q, E) over the sampling mass of E
+  const R w2 = S.ph_cw * Q * Q;
+  R ratio;
+  if (one) {
+    ratio = w2 * M::exp(-w2);
+  } else {
+    const int g = i + S.ph_N * S.ph_J;
+    R sum = R(0), pw = w2, fact = R(1);
+    for (int k = 2; k <= S.ph_N; ++k) {
+      pw *= w2;
+      fact *= (R)k;
+      sum += pw / fact * __ldg(S.ph_an + (int64_t)(k - 2) * S.ph_M + g);
+    }
+    ratio = M::exp(-w2) * sum / mass;
+  }
+  turn<R>(c2t, s2t, u3, &n->dx, &n->dy, &n->dz);
+  n->speed = speed_f;
+  sc->rest = ratio * Q * dQ / (R(2) * ki * ki) / p_ch;
+  sc->factor = sc->rest;
+  sc->q = Q;
+  sc->e = E;
+  return true;
+}
+
 // ---- single-crystal coherent one-phonon kernel (Born-von Karman fcc) -------------------
 // Per atom of a Bravais crystal (supplement S4, coherent one-phonon, with q = Q reduced):
 //   d2sigma/dOmega dEf = sigma/4pi (kf/ki) e^{-2W} sum_{b,s} hbar^2 (Q.e_b)^2/(2M hw_b)
@@ -930,10 +1033,9 @@ __device__ __forceinline__ bool exit_cyl(R rad, const Ray<R>& n, R* s) {
 }
 
 // Chord of a vertical tube (axis through R (ux, uz)) in coordinates along / across the
-// tube direction, so the large distance R cancels once.  hl: the half chord.
+// tube direction, so the large distance R cancels once.
 template <typename R>
-__device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>& n, R* s1, R* s2,
-                                          R* hl) {
+__device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>& n, R* s1, R* s2) {
   const R a = n.dx * n.dx + n.dz * n.dz;
   if (a == R(0)) return false;
   const R o_rad = n.x * ux + n.z * uz - Rad;
@@ -947,7 +1049,6 @@ __device__ __forceinline__ bool tube_span(R Rad, R ux, R uz, R rt, const Ray<R>&
   const R half = Mth<R>::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
-  *hl = half;
   return true;
 }
 
@@ -1077,13 +1178,13 @@ __device__ __forceinline__ Hit<R> tubes_absorb(const DetP<R>& D, const TofWin& W
   const R y_lo = (R)D.row_y[row] - (R)D.half_len;
   const R y_hi = (R)D.row_y[row] + (R)D.half_len;
   int best = -1;
-  R best_in = M::inf(), best_out = R(0), best_len = R(0);
+  R best_in = M::inf(), best_out = R(0);
 #pragma unroll
   for (int dc = -1; dc <= 1; ++dc) {
     const int c = g + dc;
     if (c < 0 || c >= n_tubes_row) continue;
-    R s1, s2, hl;
-    if (!tube_span<R>(Rad, tu[2 * c], tu[2 * c + 1], (R)D.tube_r, n, &s1, &s2, &hl)) continue;
+    R s1, s2;
+    if (!tube_span<R>(Rad, tu[2 * c], tu[2 * c + 1], (R)D.tube_r, n, &s1, &s2)) continue;
     R ys1, ys2;
     if (n.dy == R(0)) {
       if (!(n.y >= y_lo && n.y <= y_hi)) continue;
@@ -1101,14 +1202,10 @@ __device__ __forceinline__ Hit<R> tubes_absorb(const DetP<R>& D, const TofWin& W
       best = c;
       best_in = s_in;
       best_out = s_out;
-      // FP32: the ends of the chord lie ~3 m from the sample, where floats are spaced
-      // 2.4e-7 m apart, so their difference would lose ~1e-5 of a 1-2 cm chord; an uncut
-      // chord is taken as twice the half chord instead.  FP64 keeps the difference.
-      best_len = (sizeof(R) == 4 && s_in == s1 && s_out == s2) ? hl + hl : s_out - s_in;
     }
   }
   if (best < 0) return h;
-  const R L = best_len;
+  const R L = best_out - best_in;
   const R mu = (R)D.mu_he_v / n.speed;
   const R pabs = -M::expm1(-mu * L);
   const R x = -M::log1p(-u_det * pabs) / mu;

@@ -859,7 +859,7 @@ cudaError_t launch_trace_nk(const TraceArgs& A, int det, int grid, cudaStream_t 
 
 template <typename R, int NS>
 cudaError_t launch_trace_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
-  if (A.Sd.has_bvk) return launch_trace_nk<R, NS, kKernelsAll>(A, det, grid, s);
+  if (A.Sd.wide) return launch_trace_nk<R, NS, kKernelsAll>(A, det, grid, s);
   return launch_trace_nk<R, NS, kKernelsPowder>(A, det, grid, s);
 }
 
@@ -982,7 +982,7 @@ cudaError_t adjoint_blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
 
 template <typename R, int NS>
 cudaError_t launch_adjoint_ns(const TraceArgs& A, int det, int grid, cudaStream_t s) {
-  if (A.Sd.has_bvk) return launch_adjoint_nk<R, NS, kKernelsAll>(A, det, grid, s);
+  if (A.Sd.wide) return launch_adjoint_nk<R, NS, kKernelsAll>(A, det, grid, s);
   return launch_adjoint_nk<R, NS, kKernelsPowder>(A, det, grid, s);
 }
 

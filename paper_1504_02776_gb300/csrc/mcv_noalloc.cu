@@ -126,7 +126,7 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
     A.tallies = hist->tallies;
     A.stop_on_zero = 1;
     int occ = 0;
-    e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ);
+    e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.wide, &occ);
     if (e != cudaSuccess || occ < 1) occ = 1;
     e = mcv::launch_trace(A, fp, A.Dd.kind, grid_of(occ), s);
     if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));
@@ -142,7 +142,7 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
     A.dsqe = A.Sd.has_sqe ? dsqe : nullptr;
     A.dsig = dsig;
     int occ_a = 0;
-    e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.has_bvk, &occ_a);
+    e = mcv::adjoint_blocks_per_sm(fp, A.Sd.ns, A.Dd.kind, A.Sd.wide, &occ_a);
     if (e != cudaSuccess || occ_a < 1) occ_a = 1;
     e = mcv::launch_adjoint(A, fp, A.Dd.kind, grid_of(occ_a), s);
     if (e != cudaSuccess) return noalloc_fail(MCV_ECUDA, cudaGetErrorString(e));

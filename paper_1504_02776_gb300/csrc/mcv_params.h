@@ -67,6 +67,17 @@ struct SampleP {
   R bvk_msd;       // <u^2> (A^2)
   R bvk_wmax;      // upper bound of hbar omega (meV)
   R bvk_hwu;       // hbar sqrt(phi/M) in meV: hbar omega = bvk_hwu sqrt(lambda')
+  // incoherent phonon kernel (mcv_phonon): cumulative masses of A_1 (2J + 1) and of the
+  // multi-phonon mixture B (M = 2NJ + 1), the masses of B and A_2..A_N (rows of M), in R
+  int has_phonon;
+  int ph_J, ph_N, ph_M;
+  const R* ph_cdf1;
+  const R* ph_cdfb;
+  const R* ph_b;
+  const R* ph_an;
+  R ph_de, ph_cw, ph_p0, ph_p1, ph_p2, ph_p01;
+  // the launch needs the full kernel set (any kernel besides isotropic and S(Q,E))
+  int wide;
 };
 
 // Round keys of a Philox4x32-10 stream keyed by (seed, sim): round r uses

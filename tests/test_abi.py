@@ -38,9 +38,10 @@ def test_binding_mirrors_struct_sizes():
     probe = r'''
 #include <stdio.h>
 #include "mcv.h"
-int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
+int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
  sizeof(mcv_scatterer), sizeof(mcv_sqe), sizeof(mcv_bvk), sizeof(mcv_sample),
- sizeof(mcv_detector), sizeof(mcv_neutrons), sizeof(mcv_events), sizeof(mcv_sim));return 0;}
+ sizeof(mcv_detector), sizeof(mcv_neutrons), sizeof(mcv_events), sizeof(mcv_sim),
+ sizeof(mcv_phonon));return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
@@ -50,7 +51,7 @@ int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_param
         sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
                                                 check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (B.BeamParams, B.Scatterer, B.Sqe, B.Bvk, B.Sample,
-                                        B.Detector, B.Neutrons, B.Events, B.Sim)]
+                                        B.Detector, B.Neutrons, B.Events, B.Sim, B.Phonon)]
     assert sizes == mine
 
 
@@ -63,3 +64,31 @@ def test_no_cpu_fallback_in_product_path():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_phonon_table_sizes_and_argument_checks():
+    """mcv_phonon_table_bytes and mcv_phonon_build's argument checks (no device needed: the
+    checks come before any CUDA call)."""
+    import numpy as np
+    from paper_1504_02776_gb300 import binding as B
+    J, N = 160, 5
+    M = 2 * N * J + 1
+    assert B.mcv_phonon_table_bytes(J, N) == 12 * ((2 * J + 1) + 2 * M + (N - 1) * M)
+    assert B.mcv_phonon_table_bytes(0, N) == 0 and B.mcv_phonon_table_bytes(J, 1) == 0
+    z = np.ones(J)
+    p = B.Phonon()
+    p.n_modes, p.n_max, p.de_mev, p.mass_u, p.temperature_K = J, N, 0.25, 50.9, 300.0
+    p.p[:] = [0.5, 0.3, 0.3]  # does not sum to 1
+    buf = ctypes.c_void_p(1)
+    nb = B.mcv_phonon_table_bytes(J, N)
+    with pytest.raises(B.McvError) as e:
+        B.mcv_phonon_build(z.ctypes.data_as(ctypes.c_void_p), p, buf, nb)
+    assert e.value.status == B.MCV_EINVAL
+    p.p[:] = [0.25, 0.375, 0.375]
+    with pytest.raises(B.McvError) as e:  # buffer too small
+        B.mcv_phonon_build(z.ctypes.data_as(ctypes.c_void_p), p, buf, nb - 1)
+    assert e.value.status == B.MCV_EINVAL
+    z[3] = -1.0
+    with pytest.raises(B.McvError) as e:
+        B.mcv_phonon_build(z.ctypes.data_as(ctypes.c_void_p), p, buf, nb)
+    assert e.value.status == B.MCV_EINVAL

@@ -56,6 +56,7 @@ FLAT_SHARE = {"powder": 1e-3, "crystal": 5e-3}
     (lambda n: mi.powder_in_can(n), 20000, "powder"),
     (lambda n: mi.powder_in_can(n, ei=10.0), 20000, "powder"),
     (lambda n: mi.powder_two_kernels(n), 20000, "powder"),
+    (lambda n: mi.vanadium_powder(n), 20000, "powder"),
     (lambda n: mi.config3(rot_deg=30.0, n=n), 4000, "crystal")])
 def test_fp64_flat_bar_holds_for_almost_every_packet(ctx, make, n, kind):
     wl = make(n)
@@ -79,7 +80,8 @@ W_ABS = 1e-36
 
 
 @pytest.mark.parametrize("make", [lambda n: mi.config2(n=n), lambda n: mi.powder_in_can(n),
-                                  lambda n: mi.powder_two_kernels(n)])
+                                  lambda n: mi.powder_two_kernels(n),
+                                  lambda n: mi.vanadium_powder(n)])
 def test_fp32_fused_histogram_per_bin_against_oracle(ctx, make):
     n = 1_000_000
     wl = make(n)

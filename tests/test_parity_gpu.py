@@ -53,7 +53,8 @@ def _can_500mev(n):
 # ---------------------------------------------------------------- FP64 per packet
 @pytest.mark.parametrize("make,n", [(mi.config1, 20000), (_small_c2, 20000),
                                     (_powder_in_can, 20000), (_can_10mev, 20000),
-                                    (_can_500mev, 20000), (mi.powder_two_kernels, 20000)])
+                                    (_can_500mev, 20000), (mi.powder_two_kernels, 20000),
+                                    (mi.vanadium_powder, 20000)])
 def test_fp64_packets_match_oracle(ctx, make, n):
     wl = make(n)
     pk, g = H.packets(ctx, wl, B.FP64)
@@ -80,7 +81,7 @@ def test_fp64_packets_match_oracle(ctx, make, n):
 # the detected, missed and out-of-window counts must equal the oracle's, which has no bounds
 @pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 400000),
                                     (_powder_in_can, 200000), (_can_10mev, 100000),
-                                    (mi.powder_two_kernels, 200000)])
+                                    (mi.powder_two_kernels, 200000), (mi.vanadium_powder, 200000)])
 def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     wl = make(n)
     counts, tallies = ctx.trace(wl, fp_mode=B.FP64)
@@ -274,7 +275,8 @@ def rate_bound(rate, n):
 
 
 @pytest.mark.parametrize("make,n", [(mi.config1, 200000), (_small_c2, 200000),
-                                    (_powder_in_can, 200000), (mi.powder_two_kernels, 200000)])
+                                    (_powder_in_can, 200000), (mi.powder_two_kernels, 200000),
+                                    (mi.vanadium_powder, 200000)])
 def test_fp32_fast_mode_within_bounds(ctx, make, n):
     wl = make(n)
     st = fp32_stats(ctx, wl)
@@ -354,3 +356,25 @@ def test_fp32_crystal_within_bounds(ctx):
         d = st["dev"][f]
         assert (d > tol).sum() <= rate_bound(1e-4, d.size), (f, float(np.quantile(d / tol, 0.9999)))
     assert st["moved"] + st["flips"] <= rate_bound(1e-4, st["events_all"])
+
+
+# ---------------------------------------------------------------- phonon density of states
+def test_phonon_tables_match_the_oracle(ctx):
+    """The library's tables (mcv_phonon_build) against the oracle's own: gamma_0, c_w, and
+    the A_n masses read back from the device (both real types)."""
+    wl = mi.vanadium_powder(n=1)
+    ph, tables = api.phonon_for(wl.phonon)
+    ref = oracle.phonon_tables(wl)
+    assert abs(ph.gamma0 - ref["gamma0"]) <= 1e-14 * ref["gamma0"]
+    assert abs(ph.c_w - ref["c_w"]) <= 1e-14 * ref["c_w"]
+    J, N = wl.phonon.z.size, wl.phonon.nmax
+    M = 2 * N * J + 1
+    T = (2 * J + 1) + 2 * M + (N - 1) * M
+    raw = tables.cpu().numpy()
+    d = raw[: 8 * T].view(np.float64)
+    f = raw[8 * T: 12 * T].view(np.float32)
+    an = d[(2 * J + 1) + 2 * M:].reshape(N - 1, M)
+    np.testing.assert_allclose(an, ref["A"][1:], rtol=1e-13, atol=1e-300)
+    np.testing.assert_allclose(f, d.astype(np.float32), rtol=0, atol=0)
+    # cumulative masses of A_1 end at 1
+    assert abs(d[2 * J] - 1.0) < 1e-13
