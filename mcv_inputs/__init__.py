@@ -24,7 +24,7 @@ BOLTZMANN_MEV_PER_K = 1.380649e-23 / 1.602176634e-22
 ATM_PA = 101325.0
 
 SOLID_CYL, HOLLOW_CYL, BLOCK = 0, 1, 2
-K_ISO, K_SQE, K_BVK, K_PHONON = 0, 1, 2, 3
+K_ISO, K_SQE, K_BVK, K_PHONON, K_BRAGG = 0, 1, 2, 3, 4
 DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
 
 
@@ -131,6 +131,15 @@ class PhononDos:
 
 
 @dataclass
+class BraggList:
+    """Reflections of a powder for coherent elastic scattering: lattice spacing d (A) and
+    per-atom strength w = multiplicity |F|^2 / (v0 atoms per cell) (barn / A^3), F the
+    structure factor of the cell in sqrt(barn) including its Debye-Waller factor."""
+    d: np.ndarray
+    w: np.ndarray
+
+
+@dataclass
 class Workload:
     name: str
     beam: Beam
@@ -142,6 +151,7 @@ class Workload:
     sqe: Optional[SqeGrid] = None
     bvk: Optional[Bvk] = None
     phonon: Optional[PhononDos] = None
+    bragg: Optional[BraggList] = None
     seed: int = 0
     sim_id: int = 0
 
@@ -181,6 +191,32 @@ def phonon_dos(de=0.25, e_max=40.0) -> np.ndarray:
     z = (E / 20.0) ** 2 * np.exp(-(E / 24.0) ** 4) + 0.9 * g(22.0, 2.5) + 1.2 * g(35.0, 1.8)
     z *= np.clip((e_max - E) / 2.0, 0.0, 1.0)
     return z
+
+
+# ---- synthetic powder diffraction --------------------------------------------------------
+def fcc_reflections(a=4.05, b_fm=3.449, msd_A2=0.053334, d_min=0.5) -> BraggList:
+    """Reflections of an fcc lattice (aluminium-like: a = 4.05 A, coherent length 3.449 fm,
+    <u^2> of the force-constant model at 300 K): h, k, l all even or all odd, d = a/|hkl|,
+    multiplicity = the number of (h, k, l) with the same h^2 + k^2 + l^2, F = 4 b, the
+    Debye-Waller factor exp(-Q^2 <u^2>/3) on |F|^2, down to d_min."""
+    v0 = a ** 3
+    b2 = (b_fm * 1e-13) ** 2 / 1e-24       # b^2 in barn (1 fm^2 = 0.01 barn)
+    nmax = int(math.ceil(a / d_min)) + 1
+    mult = {}
+    for h in range(-nmax, nmax + 1):
+        for k in range(-nmax, nmax + 1):
+            for l in range(-nmax, nmax + 1):
+                if (h, k, l) == (0, 0, 0) or len({h % 2, k % 2, l % 2}) != 1:
+                    continue
+                s2 = h * h + k * k + l * l
+                if a / math.sqrt(s2) >= d_min:
+                    mult[s2] = mult.get(s2, 0) + 1
+    s2 = np.array(sorted(mult))
+    d = a / np.sqrt(s2)
+    q = 2 * math.pi / d
+    f2 = 16.0 * b2 * np.exp(-q * q * msd_A2 / 3.0)
+    w = np.array([mult[int(x)] for x in s2]) * f2 / (v0 * 4.0)
+    return BraggList(d=d, w=w)
 
 
 # ---- workloads --------------------------------------------------------------------------
@@ -283,6 +319,17 @@ def vanadium_powder(n=100_000, ei=100.0, nmax=5) -> Workload:
     return Workload(name="vanadium-phonon-%gmeV" % ei, beam=powder_beam(ei=ei),
                     scatterers=[vanadium_sample()], detector=tube_detector(), n=n, max_orders=5,
                     phonon=PhononDos(z=phonon_dos(), nmax=nmax))
+
+
+def aluminium_powder(n=100_000, ei=100.0, sig_bragg=1.495, sig_inc=0.0082) -> Workload:
+    """Aluminium-like powder in the benchmark's hollow cylinder: coherent elastic (Bragg)
+    scattering from the fcc reflections next to a weak incoherent elastic term, n = 4/a^3,
+    sigma_abs 0.231 b at 2200 m/s; up to 5 orders on the 117,760-pixel tube system."""
+    a = 4.05
+    s = Scatterer(kind=HOLLOW_CYL, dims=(0.008, 0.010, 0.04), n_per_A3=4.0 / a ** 3,
+                  sig_abs_b=0.231, kernels=[(K_BRAGG, sig_bragg), (K_ISO, sig_inc)])
+    return Workload(name="aluminium-bragg-%gmeV" % ei, beam=powder_beam(ei=ei), scatterers=[s],
+                    detector=tube_detector(), n=n, max_orders=5, bragg=fcc_reflections(a=a))
 
 
 def config3_batch(n=2_000_000, orientations=None, detector=None) -> List[Workload]:

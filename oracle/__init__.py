@@ -54,6 +54,7 @@ class Config(C.Structure):
         ("bvk_msd_A2", C.c_double), ("temperature_K", C.c_double),
         ("dos_z", C.POINTER(C.c_double)), ("dos_n", C.c_int), ("dos_de", C.c_double),
         ("phonon_mass_u", C.c_double), ("phonon_nmax", C.c_int), ("phonon_p", C.c_double * 3),
+        ("refl_d", C.POINTER(C.c_double)), ("refl_w", C.POINTER(C.c_double)), ("n_refl", C.c_int),
         ("det_kind", C.c_int), ("det_radius_m", C.c_double), ("det_height_m", C.c_double),
         ("n_phi", C.c_int), ("n_y", C.c_int), ("n_rows", C.c_int), ("packs", C.c_int * 3),
         ("row_y_m", C.c_double * 3), ("tubes_per_pack", C.c_int),
@@ -143,6 +144,14 @@ def make_config(wl):
         c.phonon_mass_u, c.phonon_nmax = ph.mass_u, ph.nmax
         c.phonon_p[:] = list(ph.p)
         c.temperature_K = ph.temperature_K
+    br = getattr(wl, "bragg", None)
+    if br is not None:
+        d = np.ascontiguousarray(br.d, dtype=np.float64)
+        w = np.ascontiguousarray(br.w, dtype=np.float64)
+        c._refl_keep = (d, w)
+        c.refl_d = d.ctypes.data_as(C.POINTER(C.c_double))
+        c.refl_w = w.ctypes.data_as(C.POINTER(C.c_double))
+        c.n_refl = d.size
     det = wl.detector
     if det is not None:
         c.det_kind = det.kind

@@ -1115,8 +1115,84 @@ bool kernel_phonon(const orc_config& cfg, double speed, Vec3 d, const double u[4
   return true;
 }
 
+// ---- coherent elastic scattering from a powder (supplement S4) ------------------------
+// The cross section for scattering into the Debye-Scherrer cone of reflection tau is, per
+// atom, sigma_tau = lambda^3 / (4 sin theta_B) m |F_tau|^2 / (v0 n_cell) (the paper's form,
+// with theta_B half the scattering angle and lambda = 2 pi / ki), for every reflection with
+// lambda < 2 d_tau.  The reflections are taken in order of decreasing d; one is picked with
+// probability sigma_tau / sum sigma, the outgoing direction lies on its cone (sin theta_B =
+// lambda / 2d, azimuth uniform) with the speed unchanged, and the weight is
+// sum sigma / sigma_kernel: the Bragg cross section at this wavelength over the kernel's
+// nominal cross section, which sets its share of the attenuation and of the kernel choice.
+struct BraggList {
+  const double* d = nullptr;
+  const double* w = nullptr;
+  int n = -1;
+  std::vector<int> order;  // by decreasing d, ties in input order
+};
+
+const BraggList& bragg_list(const orc_config& cfg) {
+  thread_local BraggList L;
+  if (L.d == cfg.refl_d && L.w == cfg.refl_w && L.n == cfg.n_refl) return L;
+  L = BraggList();
+  L.d = cfg.refl_d;
+  L.w = cfg.refl_w;
+  L.n = cfg.n_refl;
+  L.order.resize(cfg.n_refl);
+  for (int i = 0; i < cfg.n_refl; ++i) L.order[i] = i;
+  std::stable_sort(L.order.begin(), L.order.end(),
+                   [&](int a, int b) { return cfg.refl_d[a] > cfg.refl_d[b]; });
+  return L;
+}
+
+bool kernel_bragg(const orc_config& cfg, double sig_kernel, double speed, Vec3 d,
+                  const double u[4], KernelOut* o) {
+  const BraggList& L = bragg_list(cfg);
+  const double ki = kKPerV * speed;
+  const double lam = 2.0 * kPi / ki;
+  double total = 0.0;
+  int allowed = 0;
+  for (int r = 0; r < L.n; ++r) {
+    const int t = L.order[r];
+    if (!(lam < 2.0 * cfg.refl_d[t])) break;
+    const double s = lam / (2.0 * cfg.refl_d[t]);
+    total += lam * lam * lam * cfg.refl_w[t] / (4.0 * s);
+    ++allowed;
+  }
+  if (allowed == 0 || !(total > 0.0)) return false;
+  const double x = u[0] * total;
+  double acc = 0.0;
+  int pick = L.order[allowed - 1];
+  for (int r = 0; r < allowed; ++r) {
+    const int t = L.order[r];
+    const double s = lam / (2.0 * cfg.refl_d[t]);
+    acc += lam * lam * lam * cfg.refl_w[t] / (4.0 * s);
+    if (x < acc) {
+      pick = t;
+      break;
+    }
+  }
+  const double s = lam / (2.0 * cfg.refl_d[pick]);
+  const double c2t = 1.0 - 2.0 * s * s;
+  const double s2t = 2.0 * s * std::sqrt((1.0 - s) * (1.0 + s));
+  o->d = rotate_about(d, c2t, s2t, 2.0 * kPi * u[1]);
+  o->speed = speed;
+  o->rest = total / sig_kernel;
+  o->factor = o->rest;
+  o->s_value = 1.0;
+  o->entry = -1;
+  o->mode = pick;
+  o->ki = ki;
+  o->kf = ki;
+  o->e = 0.0;
+  o->qvec = add(scale(d, ki), scale(o->d, -ki));
+  o->q = std::sqrt(dot(o->qvec, o->qvec));
+  return true;
+}
+
 bool kernel_scatter(const orc_config& cfg, int ktype, double speed, Vec3 d, const double u[4],
-                    KernelOut* o, double rot_y = 0.0) {
+                    KernelOut* o, double rot_y = 0.0, double sig_kernel = 1.0) {
+  if (ktype == ORC_K_BRAGG) return kernel_bragg(cfg, sig_kernel, speed, d, u, o);
   if (ktype == ORC_K_ISO) {
     kernel_iso(speed, d, u, o);
     return true;
@@ -1253,7 +1329,7 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     double uk[4];
     draw_kernel_uniforms(cfg, nid, o, uk);
     KernelOut ko;
-    if (!kernel_scatter(cfg, sc.ktype[k], n.speed, n.d, uk, &ko, sc.rot_y)) break;
+    if (!kernel_scatter(cfg, sc.ktype[k], n.speed, n.d, uk, &ko, sc.rot_y, sc.ksig_b[k])) break;
     rec.s_value = ko.s_value;
     rec.entry = ko.entry;
     n.w = n.w * rec.a_factor * ko.factor;
@@ -1335,6 +1411,11 @@ bool config_ok(const orc_config* cfg) {
       if (s.ktype[k] == ORC_K_BVK && !(cfg->bvk_phi_Nm > 0 && cfg->bvk_mass_u > 0 &&
                                       cfg->bvk_a_A > 0 && cfg->temperature_K > 0))
         return false;
+      if (s.ktype[k] == ORC_K_BRAGG) {
+        if (!cfg->refl_d || !cfg->refl_w || cfg->n_refl < 1 || !(s.ksig_b[k] > 0)) return false;
+        for (int r = 0; r < cfg->n_refl; ++r)
+          if (!(cfg->refl_d[r] > 0) || !(cfg->refl_w[r] >= 0)) return false;
+      }
       if (s.ktype[k] == ORC_K_PHONON) {
         if (!cfg->dos_z || cfg->dos_n < 1 || !(cfg->dos_de > 0) || !(cfg->phonon_mass_u > 0) ||
             cfg->phonon_nmax < 2 || !(cfg->temperature_K > 0))
@@ -1428,7 +1509,8 @@ bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* tr
   pr.event++;
   double uk[4] = {a[0], a[1], b[0], b[1]};
   KernelOut ko;
-  if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko, sc.rot_y)) return true;
+  if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko, sc.rot_y, sc.ksig_b[k]))
+    return true;
   p.n.w = p.n.w * ko.factor;
   p.n.d = ko.d;
   p.n.speed = ko.speed;
@@ -1553,7 +1635,12 @@ int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const dou
                        orc_event* ev) {
   KernelOut ko;
   const double rot = cfg->n_scat > 0 ? cfg->scat[0].rot_y : 0.0;
-  if (!kernel_scatter(*cfg, ktype, speed, Vec3{d[0], d[1], d[2]}, u, &ko, rot)) return 0;
+  // the nominal cross section of that kernel in scatterer 0 (the Bragg kernel's weight)
+  double sig = 1.0;
+  if (cfg->n_scat > 0)
+    for (int k = 0; k < cfg->scat[0].nk; ++k)
+      if (cfg->scat[0].ktype[k] == ktype) sig = cfg->scat[0].ksig_b[k];
+  if (!kernel_scatter(*cfg, ktype, speed, Vec3{d[0], d[1], d[2]}, u, &ko, rot, sig)) return 0;
   *speed_out = ko.speed;
   d_out[0] = ko.d.x;
   d_out[1] = ko.d.y;

@@ -25,7 +25,7 @@ extern "C" {
 /* shape kinds (all centred at the origin, axis or rotation axis along +y) */
 enum { ORC_SOLID_CYL = 0, ORC_HOLLOW_CYL = 1, ORC_BLOCK = 2 };
 /* kernel kinds */
-enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2, ORC_K_PHONON = 3 };
+enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2, ORC_K_PHONON = 3, ORC_K_BRAGG = 4 };
 /* detector kinds */
 enum { ORC_DET_NONE = 0, ORC_DET_SURFACE = 1, ORC_DET_TUBES = 2 };
 
@@ -63,6 +63,11 @@ typedef struct {
   double dos_de, phonon_mass_u;
   int phonon_nmax;
   double phonon_p[3];
+  /* coherent elastic powder diffraction: n_refl reflections, spacing refl_d (A) and
+     per-atom strength refl_w = multiplicity |F|^2 / (v0 atoms per cell) (barn / A^3) */
+  const double* refl_d;
+  const double* refl_w;
+  int n_refl;
   /* detector */
   int det_kind;
   double det_radius_m, det_height_m; /* SURFACE */
