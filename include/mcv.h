@@ -56,7 +56,8 @@ typedef enum {
 
 enum { MCV_MAX_SCATTERERS = 4, MCV_MAX_TUBES_PER_ROW = 512, MCV_NTALLY = 8 };
 enum { MCV_SHAPE_SOLID_CYL = 0, MCV_SHAPE_HOLLOW_CYL = 1, MCV_SHAPE_BLOCK = 2 };
-enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2, MCV_KERNEL_PHONON = 3 };
+enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2, MCV_KERNEL_PHONON = 3,
+       MCV_KERNEL_BRAGG = 4 };
 enum { MCV_DET_NONE = 0, MCV_DET_SURFACE = 1, MCV_DET_TUBES = 2 };
 enum { MCV_FP64 = 0, MCV_FP32 = 1 };
 
@@ -130,6 +131,21 @@ typedef struct {
   double gamma0, c_w;
 } mcv_phonon;
 
+/* Coherent elastic scattering from a powder (supplement "Scattering kernels used in the
+ * examples", the Debye-Scherrer cone): per atom, reflection tau scatters
+ *   sigma_tau = lambda^3 / (4 sin theta_B) w_tau,  w_tau = m |F_tau|^2 / (v0 atoms per cell)
+ * for lambda < 2 d_tau (theta_B: lambda = 2 d sin theta_B).  Reflections are taken in order
+ * of decreasing d; one is picked with probability sigma_tau / sum sigma, the packet leaves on
+ * its cone with an azimuth uniform about its direction, its speed unchanged, and its weight
+ * multiplied by sum sigma / sigma_k, sigma_k the kernel's nominal cross section
+ * (mcv_scatterer::kernel_sig_b, which sets its share of the attenuation and of the kernel
+ * choice).  No allowed reflection (lambda beyond twice the largest d): no scattering.
+ * tables: device memory of mcv_bragg_table_bytes(n) bytes filled by mcv_bragg_build. */
+typedef struct {
+  const void* tables;
+  int n;
+} mcv_bragg;
+
 /* The sample assembly: a flat list of scatterers (the composite of section 2.4.1, one level
  * deep).  max_orders = maximum number of scatterings of a packet; packets whose weight
  * drops below min_prob are discarded (section 2.4.3); fp_mode MCV_FP64 traces in FP64,
@@ -143,6 +159,7 @@ typedef struct {
   mcv_sqe sqe;
   mcv_bvk bvk;
   mcv_phonon phonon;
+  mcv_bragg bragg;
 } mcv_sample;
 
 /* Detector system.  SURFACE: ideal cylinder of radius_m, height_m, efficiency 1, n_phi x
@@ -179,11 +196,29 @@ typedef struct {
   int64_t n;
 } mcv_neutrons;
 
-/* Histogram I[pixel][tof bin] (FP64, n_pixels*n_tof) and MCV_NTALLY FP64 tallies; either
- * pointer may be NULL. */
+/* Event-mode output (section 3: the detector system records every neutron event, the
+ * alternative to a dense histogram): every detected packet, inside the time window or not,
+ * is appended as one record (pixel, sim tag = the simulation's sim_id, time of flight in s,
+ * detected weight).  Device arrays of `capacity` entries owned by the caller; `count` is a
+ * device counter the caller zeroes before the first call; each record takes the next index
+ * (atomically, in no particular order) and is written when the index is below capacity, so
+ * after a run min(*count, capacity) records are valid and *count > capacity means records
+ * were dropped. */
+typedef struct {
+  int32_t* pixel;
+  uint32_t* sim;
+  double* tof;
+  double* w;
+  int64_t capacity;
+  unsigned long long* count;
+} mcv_event_list;
+
+/* Histogram I[pixel][tof bin] (FP64, n_pixels*n_tof) and MCV_NTALLY FP64 tallies, and an
+ * optional event list (host struct pointing at device arrays); any pointer may be NULL. */
 typedef struct {
   double* counts;
   double* tallies;
+  mcv_event_list* events;
 } mcv_hist;
 
 /* Per-packet detector results (device, one entry per packet slot); any pointer may be
@@ -210,6 +245,16 @@ mcv_status mcv_sync(mcv_ctx* ctx, void* stream);
 int64_t mcv_detector_pixels(const mcv_detector* det);
 /* Sets n doubles at dst (device) to zero on `stream` with the library's own fill kernel. */
 mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream);
+
+/* Bytes of the device tables of the Bragg kernel (mcv_bragg) for n reflections (0 if n is not
+ * 1..65536). */
+int64_t mcv_bragg_table_bytes(int n);
+/* Builds the Bragg kernel's tables from n reflections (host arrays: d_A spacings > 0 in A,
+ * w >= 0 per-atom strengths in barn/A^3, see mcv_bragg), sorted by decreasing d (ties kept in
+ * input order), into `tables` (device, `bytes` >= mcv_bragg_table_bytes(n)) on `stream`; sets
+ * out->tables and out->n.  Errors: MCV_EINVAL, MCV_ECUDA. */
+mcv_status mcv_bragg_build(const double* d_A, const double* w, int n, mcv_bragg* out,
+                           void* tables, int64_t bytes, void* stream);
 
 /* Bytes of the device tables of the phonon kernel (mcv_phonon), 0 for invalid sizes. */
 int64_t mcv_phonon_table_bytes(int n_modes, int n_max);

@@ -70,6 +70,53 @@ def phonon_for(ph):
     return _PHONON_CACHE[key]
 
 
+_BRAGG_CACHE = {}
+
+
+def bragg_for(br):
+    """(mcv_bragg struct, device tables) of a reflection list, built once per description."""
+    import numpy as np
+    d = np.ascontiguousarray(br.d, dtype=np.float64)
+    w = np.ascontiguousarray(br.w, dtype=np.float64)
+    key = (d.tobytes(), w.tobytes(), torch.cuda.current_device())
+    if key not in _BRAGG_CACHE:
+        b = B.Bragg()
+        nbytes = B.mcv_bragg_table_bytes(d.size)
+        if nbytes <= 0:
+            raise ValueError("bad reflection count")
+        tables = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        B.mcv_bragg_build(d.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p), d.size, b,
+                          C.c_void_p(tables.data_ptr()), nbytes, _stream())
+        _BRAGG_CACHE[key] = (b, tables)
+    return _BRAGG_CACHE[key]
+
+
+class EventBuffers:
+    """Caller-owned device arrays of an event list (mcv_event_list) with `capacity` records."""
+
+    def __init__(self, capacity, device="cuda"):
+        self.capacity = capacity
+        self.pixel = torch.empty(capacity, dtype=torch.int32, device=device)
+        self.sim = torch.empty(capacity, dtype=torch.int32, device=device)
+        self.tof = torch.empty(capacity, dtype=torch.float64, device=device)
+        self.w = torch.empty(capacity, dtype=torch.float64, device=device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        self._struct = B.EventList(self.pixel.data_ptr(), self.sim.data_ptr(), self.tof.data_ptr(),
+                                   self.w.data_ptr(), capacity, self.count.data_ptr())
+
+    def struct(self):
+        return self._struct
+
+    def n(self):
+        return int(self.count.item())
+
+    def to_dict(self):
+        m = min(self.n(), self.capacity)
+        return {"pixel": self.pixel[:m].cpu().numpy(), "sim": self.sim[:m].cpu().numpy(),
+                "tof": self.tof[:m].cpu().numpy(), "w": self.w[:m].cpu().numpy(),
+                "count": self.n()}
+
+
 def sample_struct(wl, fp_mode, table=None):
     """mcv_sample from a workload; `table` is the device FP32 S(Q,E) tensor (if any); the
     phonon kernel's tables are built on the device once per description (phonon_for)."""
@@ -99,6 +146,9 @@ def sample_struct(wl, fp_mode, table=None):
     if getattr(wl, "phonon", None) is not None:
         ph, _ = phonon_for(wl.phonon)
         C.memmove(C.addressof(s.phonon), C.addressof(ph), C.sizeof(ph))
+    if getattr(wl, "bragg", None) is not None:
+        br, _ = bragg_for(wl.bragg)
+        C.memmove(C.addressof(s.bragg), C.addressof(br), C.sizeof(br))
     return s
 
 
@@ -159,16 +209,22 @@ class Context:
         return counts, tallies
 
     def trace(self, wl, fp_mode=B.FP64, n=None, first_id=0, table=None, counts=None,
-              tallies=None, beam_in=None, sync=True):
-        """Fused path: source -> sample -> detector -> histogram; returns (counts, tallies)."""
+              tallies=None, beam_in=None, sync=True, events=None, hist=True):
+        """Fused path: source -> sample -> detector -> histogram; returns (counts, tallies).
+        events: an EventBuffers that receives every detected packet as well (event mode);
+        hist=False with events: no histogram, only the tallies and the event list."""
         n = wl.n if n is None else n
         if table is None:
             table = self.table(wl)
         if counts is None and tallies is None:
-            counts, tallies = self.new_hist(wl.detector)
+            if hist:
+                counts, tallies = self.new_hist(wl.detector)
+            else:
+                tallies = torch.zeros(B.MCV_NTALLY, dtype=torch.float64, device="cuda")
         sample = sample_struct(wl, fp_mode, table)
         det = detector_struct(wl.detector)
-        hist = B.Hist(_ptr(counts), _ptr(tallies))
+        hist = B.Hist(_ptr(counts), _ptr(tallies),
+                      C.pointer(events.struct()) if events is not None else None)
         inp = beam_in.struct() if beam_in is not None else None
         B.mcv_trace_sample(self.handle, sample, beam_struct(wl.beam), inp, wl.seed, wl.sim_id,
                            first_id, n, det, hist, None, _stream())
@@ -201,8 +257,10 @@ class Context:
             self.sync()
         return out
 
-    def detect(self, wl, packets, counts=None, tallies=None, events=True, sync=True):
-        """Detector step on stored packets; returns (counts, tallies, events dict)."""
+    def detect(self, wl, packets, counts=None, tallies=None, events=True, sync=True,
+               event_list=None):
+        """Detector step on stored packets; returns (counts, tallies, events dict).
+        event_list: an EventBuffers that receives every detected packet (event mode)."""
         det = detector_struct(wl.detector)
         if counts is None and tallies is None:
             counts, tallies = self.new_hist(wl.detector)
@@ -215,7 +273,8 @@ class Context:
                   "w_det": torch.empty(n, dtype=torch.float64, device="cuda"),
                   "bin": torch.empty(n, dtype=torch.int64, device="cuda")}
             evs = B.Events(*(ev[k].data_ptr() for k in ("pixel", "tof", "w_det", "bin")))
-        hist = B.Hist(_ptr(counts), _ptr(tallies))
+        hist = B.Hist(_ptr(counts), _ptr(tallies),
+                      C.pointer(event_list.struct()) if event_list is not None else None)
         B.mcv_detect(self.handle, det, packets.fp_mode, packets.struct(), wl.seed, wl.sim_id,
                      hist, evs, _stream())
         if sync:
@@ -236,7 +295,7 @@ def _batch_detector(workloads):
     return d0
 
 
-def _batch_sims(ctx, workloads, fp_mode, hists, first_ids, tables):
+def _batch_sims(ctx, workloads, fp_mode, hists, first_ids, tables, event_lists=None):
     """mcv_sim entries for the workloads; returns (sims, structs kept alive, hists)."""
     keep = []
     sims = []
@@ -254,9 +313,13 @@ def _batch_sims(ctx, workloads, fp_mode, hists, first_ids, tables):
         keep += [sample, beam]
         counts, tallies = hists[k]
         first = 0 if first_ids is None else first_ids[k]
+        ev = None
+        if event_lists is not None and event_lists[k] is not None:
+            ev = C.pointer(event_lists[k].struct())
+            keep.append(ev)
         sims.append(B.Sim(C.pointer(sample), C.pointer(beam), wl.seed, wl.sim_id, first, wl.n,
                           wl.detector.tof_min_s, wl.detector.tof_max_s,
-                          B.Hist(_ptr(counts), _ptr(tallies))))
+                          B.Hist(_ptr(counts), _ptr(tallies), ev)))
     return sims, keep, hists
 
 
@@ -300,11 +363,14 @@ class Batch:
             pass
 
 
-def _trace_batch(self, workloads, fp_mode=B.FP32, hists=None, first_ids=None, sync=True):
-    """One-shot batched launch (mcv_trace_batch); returns the (counts, tallies) pairs."""
+def _trace_batch(self, workloads, fp_mode=B.FP32, hists=None, first_ids=None, sync=True,
+                 event_lists=None):
+    """One-shot batched launch (mcv_trace_batch); returns the (counts, tallies) pairs.
+    event_lists: one EventBuffers (or None) per workload; several may be the same object."""
     det = detector_struct(_batch_detector(workloads))
     tables = {}
-    sims, keep, hists = _batch_sims(self, workloads, fp_mode, hists, first_ids, tables)
+    sims, keep, hists = _batch_sims(self, workloads, fp_mode, hists, first_ids, tables,
+                                    event_lists)
     B.mcv_trace_batch(self.handle, sims, det, fp_mode, _stream())
     if sync:
         self.sync()

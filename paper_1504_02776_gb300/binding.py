@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libmcv.so")
 MCV_OK, MCV_EINVAL, MCV_ENOMEM, MCV_ECUDA, MCV_ETIMEOUT, MCV_EDEVICE = range(6)
 MCV_MAX_SCATTERERS, MCV_MAX_TUBES_PER_ROW, MCV_NTALLY = 4, 512, 8
 SHAPE_SOLID_CYL, SHAPE_HOLLOW_CYL, SHAPE_BLOCK = 0, 1, 2
-KERNEL_ISO, KERNEL_SQE, KERNEL_BVK, KERNEL_PHONON = 0, 1, 2, 3
+KERNEL_ISO, KERNEL_SQE, KERNEL_BVK, KERNEL_PHONON, KERNEL_BRAGG = 0, 1, 2, 3, 4
 DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
 FP64, FP32 = 0, 1
 (T_BEAMSTOP, T_WDET, T_WOVER, T_NDET, T_NOVER, T_NMISS, T_NHIT, T_NEMIT) = range(8)
@@ -59,10 +59,14 @@ class Phonon(C.Structure):
                 ("p", C.c_double * 3), ("gamma0", C.c_double), ("c_w", C.c_double)]
 
 
+class Bragg(C.Structure):
+    _fields_ = [("tables", C.c_void_p), ("n", C.c_int)]
+
+
 class Sample(C.Structure):
     _fields_ = [("n_scatterers", C.c_int), ("scat", Scatterer * MCV_MAX_SCATTERERS),
                 ("max_orders", C.c_int), ("min_prob", C.c_double), ("fp_mode", C.c_int),
-                ("sqe", Sqe), ("bvk", Bvk), ("phonon", Phonon)]
+                ("sqe", Sqe), ("bvk", Bvk), ("phonon", Phonon), ("bragg", Bragg)]
 
 
 class Detector(C.Structure):
@@ -84,8 +88,14 @@ class Neutrons(C.Structure):
                 ("order", C.c_void_p), ("n", C.c_int64)]
 
 
+class EventList(C.Structure):
+    _fields_ = [("pixel", C.c_void_p), ("sim", C.c_void_p), ("tof", C.c_void_p),
+                ("w", C.c_void_p), ("capacity", C.c_int64), ("count", C.c_void_p)]
+
+
 class Hist(C.Structure):
-    _fields_ = [("counts", C.c_void_p), ("tallies", C.c_void_p)]
+    _fields_ = [("counts", C.c_void_p), ("tallies", C.c_void_p),
+                ("events", C.POINTER(EventList))]
 
 
 class Events(C.Structure):
@@ -123,6 +133,9 @@ def _load():
                               C.c_double, C.c_int, P, P, P, P, P]
     L.mcv_grad_noalloc.argtypes = [P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
                                    C.c_double, C.c_int, P, P, P, P, P]
+    L.mcv_bragg_table_bytes.argtypes = [C.c_int]
+    L.mcv_bragg_table_bytes.restype = C.c_int64
+    L.mcv_bragg_build.argtypes = [P, P, C.c_int, P, P, C.c_int64, P]
     L.mcv_phonon_table_bytes.argtypes = [C.c_int, C.c_int]
     L.mcv_phonon_table_bytes.restype = C.c_int64
     L.mcv_phonon_build.argtypes = [P, P, P, C.c_int64, P]
@@ -135,7 +148,7 @@ def _load():
     L.mcv_trace_batch.argtypes = [P, P, C.c_int, P, C.c_int, P]
     for name in ("mcv_create", "mcv_destroy", "mcv_sync", "mcv_zero", "mcv_beam",
                  "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_adjoint", "mcv_grad_noalloc",
-                 "mcv_phonon_build",
+                 "mcv_phonon_build", "mcv_bragg_build",
                  "mcv_batch_create", "mcv_batch_run", "mcv_batch_tune", "mcv_batch_shape",
                  "mcv_batch_destroy", "mcv_trace_batch"):
         getattr(L, name).restype = st
@@ -214,6 +227,15 @@ def mcv_grad_noalloc(sample, beam, det, seed, sim_id, first_id, n, target, scale
     _check(lib.mcv_grad_noalloc(C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
                                 first_id, n, target, scale_c, grad_scatterer, C.byref(hist),
                                 loss, dsqe, dsig, stream))
+
+
+def mcv_bragg_table_bytes(n):
+    return lib.mcv_bragg_table_bytes(n)
+
+
+def mcv_bragg_build(d_A, w, n, bragg, tables, nbytes, stream=None):
+    """d_A, w: C double arrays (host); bragg: a Bragg struct (completed in place)."""
+    _check(lib.mcv_bragg_build(d_A, w, n, C.byref(bragg), tables, nbytes, stream))
 
 
 def mcv_phonon_table_bytes(n_modes, n_max):

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcv.so")
 SOURCES = ["mcv_fp32.cu", "mcv_fp64.cu", "mcv_batch_fp32.cu", "mcv_batch_fp64.cu", "mcv_misc.cu",
-           "mcv_api.cu", "mcv_batch.cu", "mcv_noalloc.cu", "mcv_phonon.cu"]
+           "mcv_api.cu", "mcv_batch.cu", "mcv_noalloc.cu", "mcv_phonon.cu",
+           "mcv_bragg.cu"]
 # per-file flags: the FP64 kernels round every operation separately (no FMA contraction)
 FILE_FLAGS = {"mcv_fp64.cu": ["-fmad=false"], "mcv_batch_fp64.cu": ["-fmad=false"],
               "mcv_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"],

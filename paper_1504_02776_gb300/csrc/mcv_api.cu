@@ -66,7 +66,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
   S->ns = s->n_scatterers;
   S->max_orders = s->max_orders;
   S->min_prob = s->min_prob;
-  bool need_sqe = false, need_bvk = false, need_phonon = false;
+  bool need_sqe = false, need_bvk = false, need_phonon = false, need_bragg = false;
   for (int j = 0; j < s->n_scatterers; ++j) {
     const mcv_scatterer& a = s->scat[j];
     mcv::ScatP<double>& d = S->s[j];
@@ -78,8 +78,14 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     double sig = 0.0;
     for (int k = 0; k < a.n_kernels; ++k) {
       if (a.kernel[k] != MCV_KERNEL_ISO && a.kernel[k] != MCV_KERNEL_SQE &&
-          a.kernel[k] != MCV_KERNEL_BVK && a.kernel[k] != MCV_KERNEL_PHONON)
+          a.kernel[k] != MCV_KERNEL_BVK && a.kernel[k] != MCV_KERNEL_PHONON &&
+          a.kernel[k] != MCV_KERNEL_BRAGG)
         return fail(MCV_EINVAL, "unknown kernel kind");
+      if (a.kernel[k] == MCV_KERNEL_BRAGG) {
+        need_bragg = true;
+        if (!(a.kernel_sig_b[k] > 0))
+          return fail(MCV_EINVAL, "the Bragg kernel needs a positive nominal cross section");
+      }
       if (a.kernel[k] == MCV_KERNEL_BVK) need_bvk = true;
       if (a.kernel[k] == MCV_KERNEL_PHONON) need_phonon = true;
       if (a.kernel_sig_b[k] < 0) return fail(MCV_EINVAL, "negative kernel cross section");
@@ -109,6 +115,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     d.ktype0 = a.kernel[0];
     d.ktype1 = a.n_kernels == 2 ? a.kernel[1] : a.kernel[0];
     d.ksig0 = a.kernel_sig_b[0];
+    d.ksig1 = a.n_kernels == 2 ? a.kernel_sig_b[1] : a.kernel_sig_b[0];
     d.ksig_sum = a.n_kernels == 2 ? a.kernel_sig_b[0] + a.kernel_sig_b[1] : a.kernel_sig_b[0];
     d.sig_s = sig;
     d.n100 = 100.0 * a.n_per_A3;
@@ -179,7 +186,16 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     S->ph_p2 = p.p[2];
     S->ph_p01 = p.p[0] + p.p[1];
   }
-  S->wide = (need_bvk || need_phonon) ? 1 : 0;
+  if (need_bragg) {
+    const mcv_bragg& b = s->bragg;
+    if (!b.tables || mcv_bragg_table_bytes(b.n) == 0)
+      return fail(MCV_EINVAL, "Bragg tables missing (mcv_bragg_build)");
+    S->has_bragg = 1;
+    S->n_refl = b.n;
+    S->refl_d = static_cast<const double*>(b.tables);
+    S->refl_w = S->refl_d + b.n;
+  }
+  S->wide = (need_bvk || need_phonon || need_bragg) ? 1 : 0;
   return MCV_OK;
 }
 
@@ -381,6 +397,7 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
     b.sab2200 = (float)a.sab2200;
     b.mu_s = (float)a.mu_s;
     b.ksig0 = (float)a.ksig0;
+    b.ksig1 = (float)a.ksig1;
     b.ksig_sum = (float)a.ksig_sum;
   }
   f->sqe = d.sqe;
@@ -416,6 +433,14 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
   f->ph_p1 = (float)d.ph_p1;
   f->ph_p2 = (float)d.ph_p2;
   f->ph_p01 = (float)d.ph_p01;
+  f->has_bragg = d.has_bragg;
+  f->n_refl = d.n_refl;
+  if (d.has_bragg) {
+    // the float copies follow the doubles (mcv_bragg_build)
+    const float* fb = reinterpret_cast<const float*>(d.refl_d + 2 * (int64_t)d.n_refl);
+    f->refl_d = fb;
+    f->refl_w = fb + d.n_refl;
+  }
   f->wide = d.wide;
 }
 
@@ -479,6 +504,13 @@ mcv_status check_ctx(mcv_ctx* ctx) {
     e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   }
+  return MCV_OK;
+}
+
+mcv_status event_sink(const mcv_event_list* l, uint32_t tag, mcv::EvSink* out) {
+  if (!l->count || !l->pixel || !l->sim || !l->tof || !l->w || l->capacity < 0)
+    return fail(MCV_EINVAL, "an event list needs its four arrays, a counter and capacity >= 0");
+  *out = mcv::EvSink{l->pixel, l->sim, l->tof, l->w, l->capacity, l->count, tag};
   return MCV_OK;
 }
 
@@ -684,6 +716,11 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   }
   if (!fused && !packets && !(hist && hist->tallies))
     return fail(MCV_EINVAL, "no output requested");
+  if (hist && hist->events) {
+    if (!fused) return fail(MCV_EINVAL, "an event list needs a detector");
+    st = event_sink(hist->events, sim_id, &A.ev);
+    if (st != MCV_OK) return st;
+  }
   if (n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;
@@ -745,6 +782,10 @@ mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
   if (st != MCV_OK) return st;
   if (!neutrons_ok(packets, true)) return fail(MCV_EINVAL, "bad packet arrays (id and order required)");
   if (!hist && !events) return fail(MCV_EINVAL, "no output requested");
+  if (hist && hist->events) {
+    st = event_sink(hist->events, sim_id, &A.ev);
+    if (st != MCV_OK) return st;
+  }
   if (packets->n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;

@@ -69,8 +69,8 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
     if (s.n < 0 || s.n > kMaxNeutrons || s.first_id < 0 ||
         s.first_id > (((int64_t)1 << 62) - s.n))
       return fail(MCV_EINVAL, who + "bad neutron range");
-    if (!s.hist.counts && !s.hist.tallies)
-      return fail(MCV_EINVAL, who + "needs a histogram or tallies");
+    if (!s.hist.counts && !s.hist.tallies && !s.hist.events)
+      return fail(MCV_EINVAL, who + "needs a histogram, tallies or an event list");
     if (s.tof_min_s == 0.0 && s.tof_max_s == 0.0) {
       d.win = A->Dd.win;
     } else {
@@ -84,6 +84,10 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
     d.n = s.n;
     d.hist = s.hist.counts;
     d.tallies = s.hist.tallies;
+    if (s.hist.events) {
+      st = event_sink(s.hist.events, s.sim_id, &d.ev);
+      if (st != MCV_OK) return fail(st, who + mcv_last_error());
+    }
     if (total > kMaxNeutrons - s.n) return fail(MCV_EINVAL, "too many neutrons in the batch");
     total += s.n;
     ns = std::max(ns, d.S.ns);
@@ -105,6 +109,7 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
       f.n = d.n;
       f.hist = d.hist;
       f.tallies = d.tallies;
+      f.ev = d.ev;
       put_sim(im, k, f);
     } else {
       put_sim(im, k, d);

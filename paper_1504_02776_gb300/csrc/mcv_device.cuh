@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -705,6 +706,55 @@ __device__ __forceinline__ bool kernel_phonon(const SampleP<R>& S, const Rng& rn
   return true;
 }
 
+// ---- coherent elastic scattering from a powder (supplement S4) --------------------------
+// Per atom, reflection tau scatters sigma_tau = lambda^3 w_tau / (4 sin theta_B) with
+// sin theta_B = lambda / 2 d_tau, for lambda < 2 d_tau (the Debye-Scherrer cone).  The
+// reflections come by decreasing d, so the allowed ones form a prefix; one is picked with
+// probability sigma_tau / sum sigma, the packet leaves on its cone (azimuth uniform, speed
+// unchanged) and its weight takes sum sigma / sig_k (sig_k: the kernel's nominal cross
+// section).  Returns false when no reflection is allowed.
+template <typename R, class Rng>
+__device__ __forceinline__ bool kernel_bragg(const SampleP<R>& S, R sig_k, const Rng& rng,
+                                             int o, Ray<R>* n, Scatter<R>* sc) {
+  using M = Mth<R>;
+  const R ki = (R)kKPerV * n->speed;
+  const R lam = R(2.0 * kPi) / ki;
+  R total = R(0);
+  int allowed = 0;
+  for (int r = 0; r < S.n_refl; ++r) {
+    const R d = __ldg(S.refl_d + r);
+    if (!(lam < R(2) * d)) break;
+    const R s = lam / (R(2) * d);
+    total += lam * lam * lam * __ldg(S.refl_w + r) / (R(4) * s);
+    ++allowed;
+  }
+  if (allowed == 0 || !(total > R(0))) return false;
+  R u0, u1;
+  rng.template pair<R>(o, 1, &u0, &u1);
+  const R x = u0 * total;
+  R acc = R(0);
+  int pick = allowed - 1;
+  for (int r = 0; r < allowed; ++r) {
+    const R s = lam / (R(2) * __ldg(S.refl_d + r));
+    acc += lam * lam * lam * __ldg(S.refl_w + r) / (R(4) * s);
+    if (x < acc) {
+      pick = r;
+      break;
+    }
+  }
+  const R s = lam / (R(2) * __ldg(S.refl_d + pick));
+  const R c2t = R(1) - R(2) * s * s;
+  const R s2t = R(2) * s * M::sqrt((R(1) - s) * (R(1) + s));
+  turn<R>(c2t, s2t, u1, &n->dx, &n->dy, &n->dz);
+  sc->rest = total / sig_k;
+  sc->factor = sc->rest;
+  sc->s_value = R(1);
+  sc->entry = -1;
+  sc->q = R(2) * ki * s;
+  sc->e = R(0);
+  return true;
+}
+
 // ---- single-crystal coherent one-phonon kernel (Born-von Karman fcc) -------------------
 // Per atom of a Bravais crystal (supplement S4, coherent one-phonon, with q = Q reduced):
 //   d2sigma/dOmega dEf = sigma/4pi (kf/ki) e^{-2W} sum_{b,s} hbar^2 (Q.e_b)^2/(2M hw_b)
@@ -1284,6 +1334,23 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
   return __reduce_add_sync(0xffffffffu, v);
+}
+
+// Appends one detected packet to an event list: the lanes that append together take
+// consecutive indexes with one atomic add (warp-aggregated); an index at or beyond the
+// capacity is counted but not written.
+__device__ __forceinline__ void append_event(const EvSink& ev, int pixel, double tof, double w) {
+  cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(ev.count, (unsigned long long)g.size());
+  base = g.shfl(base, 0);
+  const unsigned long long k = base + g.thread_rank();
+  if (k < (unsigned long long)ev.cap) {
+    ev.pixel[k] = pixel;
+    ev.sim[k] = ev.tag;
+    ev.tof[k] = tof;
+    ev.w[k] = w;
+  }
 }
 
 }  // namespace mcv

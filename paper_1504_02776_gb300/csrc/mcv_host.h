@@ -47,6 +47,8 @@ void cast_beam(const BeamP<double>& d, BeamP<float>* f);
 void cast_sample(const SampleP<double>& d, SampleP<float>* f);
 void cast_detector(const DetP<double>& d, DetP<float>* f);
 void cast_all(TraceArgs* A);
+// the device sink of an event list (checks its arrays); tag: the simulation's sim_id
+mcv_status event_sink(const mcv_event_list* l, uint32_t tag, EvSink* out);
 
 }  // namespace host
 

@@ -43,6 +43,7 @@ __device__ __forceinline__ void store_slot(const TraceArgs& A, int64_t slot, con
 struct LaunchOut {
   static __device__ __forceinline__ double* hist(const TraceArgs& A) { return A.hist; }
   static __device__ __forceinline__ double* tallies(const TraceArgs& A) { return A.tallies; }
+  static __device__ __forceinline__ const EvSink& events(const TraceArgs& A) { return A.ev; }
 };
 
 // one thread's running tallies: beam stop, detected and out-of-window weights, counts
@@ -92,6 +93,8 @@ struct Forward {
   // a packet's detector result into the histogram and the tallies
   __device__ __forceinline__ void record(const TraceArgs& A, const Hit<R>& h) {
     Tally<R>& t = store.get();
+    if (h.pixel >= 0 && Out::events(A).count)
+      append_event(Out::events(A), h.pixel, h.tof.value(), (double)h.w_det);
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
@@ -269,6 +272,9 @@ struct SlotOut {
   static __device__ __forceinline__ double* hist(const TraceArgs&) { return batch_warp<R>().sim.hist; }
   static __device__ __forceinline__ double* tallies(const TraceArgs&) {
     return batch_warp<R>().sim.tallies;
+  }
+  static __device__ __forceinline__ const EvSink& events(const TraceArgs&) {
+    return batch_warp<R>().sim.ev;
   }
 };
 
@@ -690,6 +696,7 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const __grid_constant_
     cnt.nemit++;
     const NeutronRng rng(A.keys, A.in_id[i]);
     const Hit<R> h = detect<R, DET>(Dof<R>(A), Dof<R>(A).win, tu, rng, o, n);
+    if (h.pixel >= 0 && A.ev.count) append_event(A.ev, h.pixel, h.tof.value(), (double)h.w_det);
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;

@@ -45,7 +45,7 @@ struct ScatP {
   R sig_s;      // scattering cross section (sum of the kernels')
   R sab2200;    // sigma_abs 2200: mu_tot(v) = 100 n (sigma_s + sab2200 / v)
   R mu_s;       // 100 n sigma_s
-  R ksig0, ksig_sum;
+  R ksig0, ksig1, ksig_sum;  // the kernels' nominal cross sections and their sum
 };
 
 template <typename R>
@@ -76,8 +76,25 @@ struct SampleP {
   const R* ph_b;
   const R* ph_an;
   R ph_de, ph_cw, ph_p0, ph_p1, ph_p2, ph_p01;
+  // coherent elastic powder kernel (mcv_bragg): n_refl reflections by decreasing spacing
+  int has_bragg;
+  int n_refl;
+  const R* refl_d;
+  const R* refl_w;
   // the launch needs the full kernel set (any kernel besides isotropic and S(Q,E))
   int wide;
+};
+
+// Event-mode output: records appended at atomically taken indexes (mcv_event_list); tag =
+// the simulation's sim_id.  count == nullptr: no event list.
+struct EvSink {
+  int32_t* pixel;
+  uint32_t* sim;
+  double* tof;
+  double* w;
+  int64_t cap;
+  unsigned long long* count;
+  uint32_t tag;
 };
 
 // Round keys of a Philox4x32-10 stream keyed by (seed, sim): round r uses
@@ -133,6 +150,7 @@ struct TraceArgs {
   // fused outputs
   double* hist;
   double* tallies;
+  EvSink ev;
   // stored input (null: generate from the beam)
   const void *in_x, *in_y, *in_z, *in_vx, *in_vy, *in_vz, *in_w;
   const double* in_t;
@@ -168,6 +186,7 @@ struct SimP {
   int64_t first_id, n;
   double* hist;
   double* tallies;
+  EvSink ev;
 };
 
 // The work queues of a batched launch: simulation s is cut into items of `chunk` neutron

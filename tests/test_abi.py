@@ -38,10 +38,10 @@ def test_binding_mirrors_struct_sizes():
     probe = r'''
 #include <stdio.h>
 #include "mcv.h"
-int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
+int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
  sizeof(mcv_scatterer), sizeof(mcv_sqe), sizeof(mcv_bvk), sizeof(mcv_sample),
  sizeof(mcv_detector), sizeof(mcv_neutrons), sizeof(mcv_events), sizeof(mcv_sim),
- sizeof(mcv_phonon));return 0;}
+ sizeof(mcv_phonon), sizeof(mcv_bragg), sizeof(mcv_event_list), sizeof(mcv_hist));return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
@@ -51,7 +51,8 @@ int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_p
         sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
                                                 check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (B.BeamParams, B.Scatterer, B.Sqe, B.Bvk, B.Sample,
-                                        B.Detector, B.Neutrons, B.Events, B.Sim, B.Phonon)]
+                                        B.Detector, B.Neutrons, B.Events, B.Sim, B.Phonon,
+                                        B.Bragg, B.EventList, B.Hist)]
     assert sizes == mine
 
 
@@ -91,4 +92,17 @@ def test_phonon_table_sizes_and_argument_checks():
     z[3] = -1.0
     with pytest.raises(B.McvError) as e:
         B.mcv_phonon_build(z.ctypes.data_as(ctypes.c_void_p), p, buf, nb)
+    assert e.value.status == B.MCV_EINVAL
+
+
+def test_bragg_table_sizes_and_argument_checks():
+    import numpy as np
+    from paper_1504_02776_gb300 import binding as B
+    assert B.mcv_bragg_table_bytes(22) == 22 * 24 and B.mcv_bragg_table_bytes(0) == 0
+    d = np.array([2.3, 2.0, -1.0])
+    w = np.array([0.05, 0.04, 0.06])
+    b = B.Bragg()
+    with pytest.raises(B.McvError) as e:
+        B.mcv_bragg_build(d.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                          3, b, ctypes.c_void_p(1), B.mcv_bragg_table_bytes(3))
     assert e.value.status == B.MCV_EINVAL

@@ -43,11 +43,13 @@ def rate_bound(rate, n):
 # ---------------------------------------------------------------- FP64: flat 1e-12
 # Share of packets allowed to need the condition-scaled weight bar.  Powder and isotropic
 # chains: a packet's weight loses more than 1e-12 only after a chord from a point next to a
-# surface or an S(Q,E) draw at the end of its Q range (measured: up to 4.2e-4 of the packets,
-# every one within 0.014 of its condition bar).  Crystal: the outgoing energy is a root found
-# by bisection, whose rounding is amplified by 1/|g'| where the dispersion runs nearly parallel
-# to the kinematic line (measured: 1.9e-3 of the packets, within 0.042 of the bar).
-FLAT_SHARE = {"powder": 1e-3, "crystal": 5e-3}
+# surface or a draw at the end of its Q range (measured: 4.2e-4 of the packets for S(Q,E),
+# 8.3e-4 for the phonon kernel, 1.06e-3 for Bragg scattering, whose packets keep their speed
+# and weight through more orders; every one within 0.014 of its condition bar).  Crystal: the
+# outgoing energy is a root found by bisection, whose rounding is amplified by 1/|g'| where
+# the dispersion runs nearly parallel to the kinematic line (measured: 2.7e-3 of the packets,
+# within 0.042 of the bar).
+FLAT_SHARE = {"powder": 2e-3, "crystal": 5e-3}
 
 
 @pytest.mark.parametrize("make,n,kind", [
@@ -57,6 +59,7 @@ FLAT_SHARE = {"powder": 1e-3, "crystal": 5e-3}
     (lambda n: mi.powder_in_can(n, ei=10.0), 20000, "powder"),
     (lambda n: mi.powder_two_kernels(n), 20000, "powder"),
     (lambda n: mi.vanadium_powder(n), 20000, "powder"),
+    (lambda n: mi.aluminium_powder(n), 20000, "powder"),
     (lambda n: mi.config3(rot_deg=30.0, n=n), 4000, "crystal")])
 def test_fp64_flat_bar_holds_for_almost_every_packet(ctx, make, n, kind):
     wl = make(n)
@@ -81,7 +84,8 @@ W_ABS = 1e-36
 
 @pytest.mark.parametrize("make", [lambda n: mi.config2(n=n), lambda n: mi.powder_in_can(n),
                                   lambda n: mi.powder_two_kernels(n),
-                                  lambda n: mi.vanadium_powder(n)])
+                                  lambda n: mi.vanadium_powder(n),
+                                  lambda n: mi.aluminium_powder(n)])
 def test_fp32_fused_histogram_per_bin_against_oracle(ctx, make):
     n = 1_000_000
     wl = make(n)

@@ -54,7 +54,7 @@ def _can_500mev(n):
 @pytest.mark.parametrize("make,n", [(mi.config1, 20000), (_small_c2, 20000),
                                     (_powder_in_can, 20000), (_can_10mev, 20000),
                                     (_can_500mev, 20000), (mi.powder_two_kernels, 20000),
-                                    (mi.vanadium_powder, 20000)])
+                                    (mi.vanadium_powder, 20000), (mi.aluminium_powder, 20000)])
 def test_fp64_packets_match_oracle(ctx, make, n):
     wl = make(n)
     pk, g = H.packets(ctx, wl, B.FP64)
@@ -81,7 +81,8 @@ def test_fp64_packets_match_oracle(ctx, make, n):
 # the detected, missed and out-of-window counts must equal the oracle's, which has no bounds
 @pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 400000),
                                     (_powder_in_can, 200000), (_can_10mev, 100000),
-                                    (mi.powder_two_kernels, 200000), (mi.vanadium_powder, 200000)])
+                                    (mi.powder_two_kernels, 200000), (mi.vanadium_powder, 200000),
+                                    (mi.aluminium_powder, 200000)])
 def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     wl = make(n)
     counts, tallies = ctx.trace(wl, fp_mode=B.FP64)
@@ -276,7 +277,7 @@ def rate_bound(rate, n):
 
 @pytest.mark.parametrize("make,n", [(mi.config1, 200000), (_small_c2, 200000),
                                     (_powder_in_can, 200000), (mi.powder_two_kernels, 200000),
-                                    (mi.vanadium_powder, 200000)])
+                                    (mi.vanadium_powder, 200000), (mi.aluminium_powder, 200000)])
 def test_fp32_fast_mode_within_bounds(ctx, make, n):
     wl = make(n)
     st = fp32_stats(ctx, wl)
