@@ -24,7 +24,7 @@ BOLTZMANN_MEV_PER_K = 1.380649e-23 / 1.602176634e-22
 ATM_PA = 101325.0
 
 SOLID_CYL, HOLLOW_CYL, BLOCK = 0, 1, 2
-K_ISO, K_SQE, K_BVK, K_PHONON, K_BRAGG = 0, 1, 2, 3, 4
+K_ISO, K_SQE, K_BVK, K_PHONON, K_BRAGG, K_DISP = 0, 1, 2, 3, 4, 5
 DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
 
 
@@ -140,6 +140,15 @@ class BraggList:
 
 
 @dataclass
+class Dispersion:
+    """A dispersion surface E(Q) = amp_mev sqrt(1 - (cos(c_A Qx) cos(c_A Qz))^2) with constant
+    S(Q) = s0, Q in the crystal frame (the paper's example surface: 2.5 meV, 4.4 A)."""
+    amp_mev: float = 2.5
+    c_A: float = 4.4
+    s0: float = 1.0
+
+
+@dataclass
 class Workload:
     name: str
     beam: Beam
@@ -152,6 +161,7 @@ class Workload:
     bvk: Optional[Bvk] = None
     phonon: Optional[PhononDos] = None
     bragg: Optional[BraggList] = None
+    dispersion: Optional[Dispersion] = None
     seed: int = 0
     sim_id: int = 0
 
@@ -330,6 +340,20 @@ def aluminium_powder(n=100_000, ei=100.0, sig_bragg=1.495, sig_inc=0.0082) -> Wo
                   sig_abs_b=0.231, kernels=[(K_BRAGG, sig_bragg), (K_ISO, sig_inc)])
     return Workload(name="aluminium-bragg-%gmeV" % ei, beam=powder_beam(ei=ei), scatterers=[s],
                     detector=tube_detector(), n=n, max_orders=5, bragg=fcc_reflections(a=a))
+
+
+def dispersion_crystal(n=100_000, ei=7.5, rot_deg=0.0) -> Workload:
+    """A 1 cm cube single crystal scattering from the paper's example dispersion surface (a
+    two-dimensional spin-wave-like E(Q) of 2.5 meV bandwidth, S(Q) = 1), n 0.01 A^-3,
+    sigma 2 b, sigma_abs 5 b at 2200 m/s, rotated by rot_deg about the vertical axis; a
+    7.5 meV beam otherwise like the powder runs', its time window scaled to the energy."""
+    s = Scatterer(kind=BLOCK, dims=(0.01, 0.01, 0.01), n_per_A3=0.01, sig_abs_b=5.0,
+                  kernels=[(K_DISP, 2.0)], rot_y=math.radians(rot_deg))
+    t0, t1 = tof_window_for(ei)
+    det = dataclasses.replace(tube_detector(), tof_min_s=t0, tof_max_s=t1)
+    return Workload(name="dispersion-crystal-%g-deg" % rot_deg, beam=powder_beam(ei=ei),
+                    scatterers=[s], detector=det, n=n, max_orders=5, dispersion=Dispersion(),
+                    sim_id=int(round(rot_deg)))
 
 
 def config3_batch(n=2_000_000, orientations=None, detector=None) -> List[Workload]:

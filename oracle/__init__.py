@@ -55,6 +55,7 @@ class Config(C.Structure):
         ("dos_z", C.POINTER(C.c_double)), ("dos_n", C.c_int), ("dos_de", C.c_double),
         ("phonon_mass_u", C.c_double), ("phonon_nmax", C.c_int), ("phonon_p", C.c_double * 3),
         ("refl_d", C.POINTER(C.c_double)), ("refl_w", C.POINTER(C.c_double)), ("n_refl", C.c_int),
+        ("disp_amp", C.c_double), ("disp_c", C.c_double), ("disp_s0", C.c_double),
         ("det_kind", C.c_int), ("det_radius_m", C.c_double), ("det_height_m", C.c_double),
         ("n_phi", C.c_int), ("n_y", C.c_int), ("n_rows", C.c_int), ("packs", C.c_int * 3),
         ("row_y_m", C.c_double * 3), ("tubes_per_pack", C.c_int),
@@ -144,6 +145,9 @@ def make_config(wl):
         c.phonon_mass_u, c.phonon_nmax = ph.mass_u, ph.nmax
         c.phonon_p[:] = list(ph.p)
         c.temperature_K = ph.temperature_K
+    dp = getattr(wl, "dispersion", None)
+    if dp is not None:
+        c.disp_amp, c.disp_c, c.disp_s0 = dp.amp_mev, dp.c_A, dp.s0
     br = getattr(wl, "bragg", None)
     if br is not None:
         d = np.ascontiguousarray(br.d, dtype=np.float64)

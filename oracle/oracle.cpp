@@ -1190,9 +1190,105 @@ bool kernel_bragg(const orc_config& cfg, double sig_kernel, double speed, Vec3 d
   return true;
 }
 
+// ---- scattering from a dispersion surface (supplement S4) ------------------------------
+// d2sigma/dOmega dEf = sigma/4pi (kf/ki) S(Q) delta(E - E(Q)), E = Ei - Ef, with the paper's
+// example surface E(Q) = A sqrt(1 - (cos(c Qx) cos(c Qz))^2) and a constant S(Q) = S0, Q in
+// the crystal frame (the frame of the single-crystal kernel).  1 - cos^2 a cos^2 b is
+// evaluated as sin^2 a + cos^2 a sin^2 b (no cancellation near the zeros of E).
+// Sampling: the outgoing direction uniform; the roots of g(Ef) = Ei - Ef - E(Q(Ef)) bracketed
+// on 32 equal sub-intervals of [max(0, Ei - A), Ei] (E(Q) lies in [0, A]); one picked
+// uniformly and refined by 50 bisections; weight n_roots (kf/ki) S0 / |g'(Ef)| with
+// g' = -1 - grad E . dQ/dEf, dQ/dEf = -df kf / (2 Ef) (the delta function integrated over Ef
+// at the root, over the uniform choice among the roots and the uniform direction).
+struct DispEval {
+  double E, g;
+  Vec3 Qc, grad;
+};
+
+DispEval disp_eval(const orc_config& cfg, double Ei, double ki, Vec3 di, Vec3 df, double Ef,
+                   double c, double sn) {
+  DispEval r;
+  const double kf = kKPerV * std::sqrt(Ef / kMeVPerV2);
+  r.Qc = to_crystal(add(scale(di, ki), scale(df, -kf)), c, sn);
+  const double a = cfg.disp_c * r.Qc.x, b = cfg.disp_c * r.Qc.z;
+  const double sa = std::sin(a), ca = std::cos(a), sb = std::sin(b), cb = std::cos(b);
+  const double root = std::sqrt(sa * sa + ca * ca * sb * sb);
+  r.E = cfg.disp_amp * root;
+  r.g = Ei - Ef - r.E;
+  if (root > 0.0) {
+    r.grad = {cfg.disp_amp * cfg.disp_c * sa * ca * cb * cb / root, 0.0,
+              cfg.disp_amp * cfg.disp_c * ca * ca * sb * cb / root};
+  } else {
+    r.grad = {0.0, 0.0, 0.0};
+  }
+  return r;
+}
+
+bool kernel_disp(const orc_config& cfg, double rot_y, double speed, Vec3 d, const double u[4],
+                 KernelOut* o) {
+  const double c = std::cos(rot_y), sn = std::sin(rot_y);
+  const double ct = 2.0 * u[0] - 1.0;
+  const double st = 2.0 * std::sqrt(u[0] * (1.0 - u[0]));
+  const double ph = 2.0 * kPi * u[1];
+  const Vec3 df = {st * std::cos(ph), st * std::sin(ph), ct};
+  const double Ei = kMeVPerV2 * speed * speed;
+  const double ki = kKPerV * speed;
+  const double lo = std::max(0.0, Ei - cfg.disp_amp), hi = Ei;
+  const int M = 32;
+  const double step = (hi - lo) / M;
+  double gk[M + 1];
+  for (int k = 0; k <= M; ++k) gk[k] = disp_eval(cfg, Ei, ki, d, df, lo + k * step, c, sn).g;
+  int nroots = 0;
+  for (int k = 0; k < M; ++k)
+    if ((gk[k] > 0.0) != (gk[k + 1] > 0.0)) ++nroots;
+  o->nroots = nroots;
+  if (nroots == 0) return false;
+  int pick = (int)std::floor(u[2] * nroots);
+  pick = std::min(std::max(pick, 0), nroots - 1);
+  int kb = -1;
+  for (int k = 0, seen = 0; k < M; ++k) {
+    if ((gk[k] > 0.0) != (gk[k + 1] > 0.0)) {
+      if (seen == pick) {
+        kb = k;
+        break;
+      }
+      ++seen;
+    }
+  }
+  double ea = lo + kb * step, eb = lo + (kb + 1) * step;
+  const bool ga_pos = gk[kb] > 0.0;
+  for (int it = 0; it < 50; ++it) {
+    const double mid = 0.5 * (ea + eb);
+    if ((disp_eval(cfg, Ei, ki, d, df, mid, c, sn).g > 0.0) == ga_pos)
+      ea = mid;
+    else
+      eb = mid;
+  }
+  const double Ef = 0.5 * (ea + eb);
+  if (!(Ef > 0.0)) return false;
+  const DispEval r = disp_eval(cfg, Ei, ki, d, df, Ef, c, sn);
+  if (!(r.E > 0.0)) return false;
+  const double kf = kKPerV * std::sqrt(Ef / kMeVPerV2);
+  const Vec3 dQ = scale(to_crystal(df, c, sn), -kf / (2.0 * Ef));
+  const double gp = -1.0 - dot(r.grad, dQ);
+  o->rest = nroots * (kf / ki) * cfg.disp_s0 / std::fabs(gp);
+  o->factor = o->rest;
+  o->s_value = 1.0;
+  o->entry = -1;
+  o->d = df;
+  o->speed = std::sqrt(Ef / kMeVPerV2);
+  o->ki = ki;
+  o->kf = kf;
+  o->e = Ei - Ef;
+  o->qvec = add(scale(d, ki), scale(df, -kf));
+  o->q = std::sqrt(dot(o->qvec, o->qvec));
+  return true;
+}
+
 bool kernel_scatter(const orc_config& cfg, int ktype, double speed, Vec3 d, const double u[4],
                     KernelOut* o, double rot_y = 0.0, double sig_kernel = 1.0) {
   if (ktype == ORC_K_BRAGG) return kernel_bragg(cfg, sig_kernel, speed, d, u, o);
+  if (ktype == ORC_K_DISP) return kernel_disp(cfg, rot_y, speed, d, u, o);
   if (ktype == ORC_K_ISO) {
     kernel_iso(speed, d, u, o);
     return true;
@@ -1410,6 +1506,9 @@ bool config_ok(const orc_config* cfg) {
       if (s.ktype[k] == ORC_K_SQE && (!cfg->sqe || cfg->nq <= 0 || cfg->ne <= 0)) return false;
       if (s.ktype[k] == ORC_K_BVK && !(cfg->bvk_phi_Nm > 0 && cfg->bvk_mass_u > 0 &&
                                       cfg->bvk_a_A > 0 && cfg->temperature_K > 0))
+        return false;
+      if (s.ktype[k] == ORC_K_DISP &&
+          !(cfg->disp_amp > 0 && cfg->disp_c > 0 && cfg->disp_s0 >= 0))
         return false;
       if (s.ktype[k] == ORC_K_BRAGG) {
         if (!cfg->refl_d || !cfg->refl_w || cfg->n_refl < 1 || !(s.ksig_b[k] > 0)) return false;

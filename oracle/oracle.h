@@ -25,7 +25,8 @@ extern "C" {
 /* shape kinds (all centred at the origin, axis or rotation axis along +y) */
 enum { ORC_SOLID_CYL = 0, ORC_HOLLOW_CYL = 1, ORC_BLOCK = 2 };
 /* kernel kinds */
-enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2, ORC_K_PHONON = 3, ORC_K_BRAGG = 4 };
+enum { ORC_K_ISO = 0, ORC_K_SQE = 1, ORC_K_BVK = 2, ORC_K_PHONON = 3, ORC_K_BRAGG = 4,
+       ORC_K_DISP = 5 };
 /* detector kinds */
 enum { ORC_DET_NONE = 0, ORC_DET_SURFACE = 1, ORC_DET_TUBES = 2 };
 
@@ -68,6 +69,9 @@ typedef struct {
   const double* refl_d;
   const double* refl_w;
   int n_refl;
+  /* scattering from a dispersion surface E(Q) = disp_amp sqrt(1 - (cos(c Qx) cos(c Qz))^2),
+     c = disp_c (A), with S(Q) = disp_s0, Q in the crystal frame of scatterer 0's rotation */
+  double disp_amp, disp_c, disp_s0;
   /* detector */
   int det_kind;
   double det_radius_m, det_height_m; /* SURFACE */
