@@ -57,7 +57,7 @@ typedef enum {
 enum { MCV_MAX_SCATTERERS = 4, MCV_MAX_TUBES_PER_ROW = 512, MCV_NTALLY = 8 };
 enum { MCV_SHAPE_SOLID_CYL = 0, MCV_SHAPE_HOLLOW_CYL = 1, MCV_SHAPE_BLOCK = 2 };
 enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2, MCV_KERNEL_PHONON = 3,
-       MCV_KERNEL_BRAGG = 4 };
+       MCV_KERNEL_BRAGG = 4, MCV_KERNEL_DISP = 5 };
 enum { MCV_DET_NONE = 0, MCV_DET_SURFACE = 1, MCV_DET_TUBES = 2 };
 enum { MCV_FP64 = 0, MCV_FP32 = 1 };
 
@@ -146,6 +146,18 @@ typedef struct {
   int n;
 } mcv_bragg;
 
+/* Scattering from a dispersion surface (supplement "Scattering kernels used in the examples":
+ * d2sigma/dOmega dEf = sigma/4pi (kf/ki) S(Q) delta(E - E(Q))), with the paper's example
+ * surface E(Q) = amp_mev sqrt(1 - (cos(c_A Qx) cos(c_A Qz))^2) and S(Q) = s0, Q in the
+ * crystal frame of the scatterer's rotation ([100] along the beam and [001] vertical at zero
+ * rotation, as the single-crystal kernel).  The outgoing direction is drawn uniformly; the
+ * roots of Ei - Ef - E(Q(Ef)) are bracketed on 32 sub-intervals of [max(0, Ei - amp), Ei],
+ * one is picked uniformly and bisected (50 steps in FP64, 24 in FP32); the weight is
+ * n_roots (kf/ki) s0 / |d(Ei - Ef - E)/dEf|.  No root: no scattering. */
+typedef struct {
+  double amp_mev, c_A, s0;
+} mcv_dispersion;
+
 /* The sample assembly: a flat list of scatterers (the composite of section 2.4.1, one level
  * deep).  max_orders = maximum number of scatterings of a packet; packets whose weight
  * drops below min_prob are discarded (section 2.4.3); fp_mode MCV_FP64 traces in FP64,
@@ -160,6 +172,7 @@ typedef struct {
   mcv_bvk bvk;
   mcv_phonon phonon;
   mcv_bragg bragg;
+  mcv_dispersion dispersion;
 } mcv_sample;
 
 /* Detector system.  SURFACE: ideal cylinder of radius_m, height_m, efficiency 1, n_phi x

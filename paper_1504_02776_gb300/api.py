@@ -149,6 +149,9 @@ def sample_struct(wl, fp_mode, table=None):
     if getattr(wl, "bragg", None) is not None:
         br, _ = bragg_for(wl.bragg)
         C.memmove(C.addressof(s.bragg), C.addressof(br), C.sizeof(br))
+    dp = getattr(wl, "dispersion", None)
+    if dp is not None:
+        s.dispersion.amp_mev, s.dispersion.c_A, s.dispersion.s0 = dp.amp_mev, dp.c_A, dp.s0
     return s
 
 

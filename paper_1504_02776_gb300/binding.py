@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libmcv.so")
 MCV_OK, MCV_EINVAL, MCV_ENOMEM, MCV_ECUDA, MCV_ETIMEOUT, MCV_EDEVICE = range(6)
 MCV_MAX_SCATTERERS, MCV_MAX_TUBES_PER_ROW, MCV_NTALLY = 4, 512, 8
 SHAPE_SOLID_CYL, SHAPE_HOLLOW_CYL, SHAPE_BLOCK = 0, 1, 2
-KERNEL_ISO, KERNEL_SQE, KERNEL_BVK, KERNEL_PHONON, KERNEL_BRAGG = 0, 1, 2, 3, 4
+KERNEL_ISO, KERNEL_SQE, KERNEL_BVK, KERNEL_PHONON, KERNEL_BRAGG, KERNEL_DISP = 0, 1, 2, 3, 4, 5
 DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
 FP64, FP32 = 0, 1
 (T_BEAMSTOP, T_WDET, T_WOVER, T_NDET, T_NOVER, T_NMISS, T_NHIT, T_NEMIT) = range(8)
@@ -63,10 +63,15 @@ class Bragg(C.Structure):
     _fields_ = [("tables", C.c_void_p), ("n", C.c_int)]
 
 
+class Dispersion(C.Structure):
+    _fields_ = [("amp_mev", C.c_double), ("c_A", C.c_double), ("s0", C.c_double)]
+
+
 class Sample(C.Structure):
     _fields_ = [("n_scatterers", C.c_int), ("scat", Scatterer * MCV_MAX_SCATTERERS),
                 ("max_orders", C.c_int), ("min_prob", C.c_double), ("fp_mode", C.c_int),
-                ("sqe", Sqe), ("bvk", Bvk), ("phonon", Phonon), ("bragg", Bragg)]
+                ("sqe", Sqe), ("bvk", Bvk), ("phonon", Phonon), ("bragg", Bragg),
+                ("dispersion", Dispersion)]
 
 
 class Detector(C.Structure):

@@ -67,6 +67,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
   S->max_orders = s->max_orders;
   S->min_prob = s->min_prob;
   bool need_sqe = false, need_bvk = false, need_phonon = false, need_bragg = false;
+  bool need_disp = false;
   for (int j = 0; j < s->n_scatterers; ++j) {
     const mcv_scatterer& a = s->scat[j];
     mcv::ScatP<double>& d = S->s[j];
@@ -79,8 +80,9 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     for (int k = 0; k < a.n_kernels; ++k) {
       if (a.kernel[k] != MCV_KERNEL_ISO && a.kernel[k] != MCV_KERNEL_SQE &&
           a.kernel[k] != MCV_KERNEL_BVK && a.kernel[k] != MCV_KERNEL_PHONON &&
-          a.kernel[k] != MCV_KERNEL_BRAGG)
+          a.kernel[k] != MCV_KERNEL_BRAGG && a.kernel[k] != MCV_KERNEL_DISP)
         return fail(MCV_EINVAL, "unknown kernel kind");
+      if (a.kernel[k] == MCV_KERNEL_DISP) need_disp = true;
       if (a.kernel[k] == MCV_KERNEL_BRAGG) {
         need_bragg = true;
         if (!(a.kernel_sig_b[k] > 0))
@@ -195,7 +197,17 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     S->refl_d = static_cast<const double*>(b.tables);
     S->refl_w = S->refl_d + b.n;
   }
-  S->wide = (need_bvk || need_phonon || need_bragg) ? 1 : 0;
+  if (need_disp) {
+    const mcv_dispersion& q = s->dispersion;
+    if (!(q.amp_mev > 0 && is_finite(q.amp_mev) && q.c_A > 0 && is_finite(q.c_A) &&
+          q.s0 >= 0 && is_finite(q.s0)))
+      return fail(MCV_EINVAL, "bad dispersion surface (amp_mev > 0, c_A > 0, s0 >= 0)");
+    S->has_disp = 1;
+    S->disp_amp = q.amp_mev;
+    S->disp_c = q.c_A;
+    S->disp_s0 = q.s0;
+  }
+  S->wide = (need_bvk || need_phonon || need_bragg || need_disp) ? 1 : 0;
   return MCV_OK;
 }
 
@@ -433,6 +445,10 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
   f->ph_p1 = (float)d.ph_p1;
   f->ph_p2 = (float)d.ph_p2;
   f->ph_p01 = (float)d.ph_p01;
+  f->has_disp = d.has_disp;
+  f->disp_amp = (float)d.disp_amp;
+  f->disp_c = (float)d.disp_c;
+  f->disp_s0 = (float)d.disp_s0;
   f->has_bragg = d.has_bragg;
   f->n_refl = d.n_refl;
   if (d.has_bragg) {

@@ -89,7 +89,7 @@ __device__ __forceinline__ R step_segments(const TraceArgs& A, const SampleP<R>&
 // kernel sets compiled into a launch: the single-crystal kernel only where it is used
 constexpr int kKernelsPowder = (1 << MCV_KERNEL_ISO) | (1 << MCV_KERNEL_SQE);
 constexpr int kKernelsAll = kKernelsPowder | (1 << MCV_KERNEL_BVK) | (1 << MCV_KERNEL_PHONON) |
-                            (1 << MCV_KERNEL_BRAGG);
+                            (1 << MCV_KERNEL_BRAGG) | (1 << MCV_KERNEL_DISP);
 
 template <typename R, int NS, int KS, class P, class Rng>
 __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R>& S,
@@ -143,6 +143,8 @@ __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R
     ok = kernel_phonon<R>(S, rng, L.o, &L.n, &out);
   } else if ((KS & (1 << MCV_KERNEL_BRAGG)) && ktype == MCV_KERNEL_BRAGG) {
     ok = kernel_bragg<R>(S, kk ? sc.ksig1 : sc.ksig0, rng, L.o, &L.n, &out);
+  } else if ((KS & (1 << MCV_KERNEL_DISP)) && ktype == MCV_KERNEL_DISP) {
+    ok = kernel_disp<R>(S, sc.cos_rot, sc.sin_rot, rng, L.o, &L.n, &out);
   }
   if (!ok) {
     pol.clear(A, L.idx, L.o + 1);

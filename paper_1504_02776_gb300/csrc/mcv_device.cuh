@@ -1062,6 +1062,109 @@ __device__ __forceinline__ bool kernel_bvk(const SampleP<R>& S, R crot, R srot,
   return true;
 }
 
+// ---- scattering from a dispersion surface (supplement S4) --------------------------------
+// S(Q) delta(E - E(Q)) with E(Q) = amp sqrt(1 - (cos(c Qx) cos(c Qz))^2) (the paper's example
+// surface, 1 - cos^2 a cos^2 b written as sin^2 a + cos^2 a sin^2 b) and S = s0, Q in the
+// crystal frame.  Direction uniform; roots of g(Ef) = Ei - Ef - E(Q(Ef)) bracketed on 32
+// sub-intervals of [max(0, Ei - amp), Ei], one picked uniformly and bisected; weight
+// n_roots (kf/ki) s0 / |g'|, g' = -1 - grad E . dQ/dEf, dQ/dEf = -df kf / (2 Ef).
+template <typename R>
+struct DispPoint {
+  R g, E, sa, ca, sb, cb, root;
+};
+
+template <typename R>
+__device__ __forceinline__ DispPoint<R> disp_point(const SampleP<R>& S, R c, R s, R Ei, R ki,
+                                                    R dix, R diy, R diz, R dfx, R dfy, R dfz,
+                                                    R Ef) {
+  using M = Mth<R>;
+  DispPoint<R> P;
+  const R kf = (R)kKPerV * M::sqrt(Ef / (R)kMeVPerV2);
+  const R Qx = dix * ki - dfx * kf, Qy = diy * ki - dfy * kf, Qz = diz * ki - dfz * kf;
+  R qx, qy, qz;
+  to_crystal<R>(c, s, Qx, Qy, Qz, &qx, &qy, &qz);
+  const R a = S.disp_c * qx, b = S.disp_c * qz;
+  P.sa = M::sin_(a);
+  P.ca = M::cos_(a);
+  P.sb = M::sin_(b);
+  P.cb = M::cos_(b);
+  P.root = M::sqrt(P.sa * P.sa + P.ca * P.ca * P.sb * P.sb);
+  P.E = S.disp_amp * P.root;
+  P.g = Ei - Ef - P.E;
+  return P;
+}
+
+template <typename R, class Rng>
+__device__ __forceinline__ bool kernel_disp(const SampleP<R>& S, R crot, R srot,
+                                            const Rng& rng, int o, Ray<R>* n, Scatter<R>* sc) {
+  using M = Mth<R>;
+  R u0, u1, u2;
+  rng.template pair<R>(o, 1, &u0, &u1);
+  u2 = rng.template first<R>(o, 2);
+  const R ct = R(2) * u0 - R(1);
+  const R st = R(2) * M::sqrt(u0 * (R(1) - u0));
+  R sp, cp;
+  M::sincos2pi(u1, &sp, &cp);
+  const R dfx = st * cp, dfy = st * sp, dfz = ct;
+  const R Ei = (R)kMeVPerV2 * n->speed * n->speed;
+  const R ki = (R)kKPerV * n->speed;
+  const R lo = M::fmax(R(0), Ei - S.disp_amp), hi = Ei;
+  constexpr int kM = 32;
+  const R step = (hi - lo) / (R)kM;
+  uint64_t pos = 0;  // signs of g on the grid, one bit per node
+  for (int k = 0; k <= kM; ++k) {
+    const DispPoint<R> P = disp_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy,
+                                         dfz, lo + (R)k * step);
+    if (P.g > R(0)) pos |= (uint64_t)1 << k;
+  }
+  const uint64_t change = (pos ^ (pos >> 1)) & ((((uint64_t)1) << kM) - 1);
+  const int nroots = __popcll(change);
+  if (nroots == 0) return false;
+  int pick = (int)M::floor(u2 * (R)nroots);
+  pick = min(max(pick, 0), nroots - 1);
+  uint64_t ch = change;
+  for (int i = 0; i < pick; ++i) ch &= ch - 1;  // drop the lowest set bits
+  const int kb = __ffsll((long long)ch) - 1;
+  R ea = lo + (R)kb * step, eb = lo + (R)(kb + 1) * step;
+  const bool ga_pos = (pos >> kb) & 1;
+  const int iters = sizeof(R) == 8 ? 50 : 24;
+  for (int it = 0; it < iters; ++it) {
+    const R mid = R(0.5) * (ea + eb);
+    const DispPoint<R> P = disp_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy,
+                                         dfz, mid);
+    if ((P.g > R(0)) == ga_pos)
+      ea = mid;
+    else
+      eb = mid;
+  }
+  const R Ef = R(0.5) * (ea + eb);
+  if (!(Ef > R(0))) return false;
+  const DispPoint<R> P = disp_point<R>(S, crot, srot, Ei, ki, n->dx, n->dy, n->dz, dfx, dfy,
+                                       dfz, Ef);
+  if (!(P.E > R(0))) return false;
+  const R kf = (R)kKPerV * M::sqrt(Ef / (R)kMeVPerV2);
+  R dqx, dqy, dqz;
+  to_crystal<R>(crot, srot, dfx, dfy, dfz, &dqx, &dqy, &dqz);
+  const R sc_q = -kf / (R(2) * Ef);
+  dqx *= sc_q;
+  dqz *= sc_q;
+  const R ac = S.disp_amp * S.disp_c;
+  const R gx = ac * P.sa * P.ca * P.cb * P.cb / P.root;
+  const R gz = ac * P.ca * P.ca * P.sb * P.cb / P.root;
+  const R gp = R(-1) - (gx * dqx + gz * dqz);
+  sc->rest = (R)nroots * (kf / ki) * S.disp_s0 / M::fabs(gp);
+  sc->factor = sc->rest;
+  sc->s_value = R(1);
+  sc->entry = -1;
+  sc->q = R(0);
+  sc->e = Ei - Ef;
+  n->dx = dfx;
+  n->dy = dfy;
+  n->dz = dfz;
+  n->speed = M::sqrt(Ef / (R)kMeVPerV2);
+  return true;
+}
+
 // ---- detector system (section 2.4.3, "Ray tracing in a detector system") -----------------
 template <typename R>
 struct Hit {

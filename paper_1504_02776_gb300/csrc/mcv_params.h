@@ -81,6 +81,9 @@ struct SampleP {
   int n_refl;
   const R* refl_d;
   const R* refl_w;
+  // dispersion-surface kernel (mcv_dispersion)
+  int has_disp;
+  R disp_amp, disp_c, disp_s0;
   // the launch needs the full kernel set (any kernel besides isotropic and S(Q,E))
   int wide;
 };

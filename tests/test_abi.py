@@ -38,10 +38,11 @@ def test_binding_mirrors_struct_sizes():
     probe = r'''
 #include <stdio.h>
 #include "mcv.h"
-int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
+int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcv_beam_params),
  sizeof(mcv_scatterer), sizeof(mcv_sqe), sizeof(mcv_bvk), sizeof(mcv_sample),
  sizeof(mcv_detector), sizeof(mcv_neutrons), sizeof(mcv_events), sizeof(mcv_sim),
- sizeof(mcv_phonon), sizeof(mcv_bragg), sizeof(mcv_event_list), sizeof(mcv_hist));return 0;}
+ sizeof(mcv_phonon), sizeof(mcv_bragg), sizeof(mcv_event_list), sizeof(mcv_hist),
+ sizeof(mcv_dispersion));return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
@@ -52,7 +53,7 @@ int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeo
                                                 check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (B.BeamParams, B.Scatterer, B.Sqe, B.Bvk, B.Sample,
                                         B.Detector, B.Neutrons, B.Events, B.Sim, B.Phonon,
-                                        B.Bragg, B.EventList, B.Hist)]
+                                        B.Bragg, B.EventList, B.Hist, B.Dispersion)]
     assert sizes == mine
 
 

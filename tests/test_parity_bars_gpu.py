@@ -60,7 +60,8 @@ FLAT_SHARE = {"powder": 2e-3, "crystal": 5e-3}
     (lambda n: mi.powder_two_kernels(n), 20000, "powder"),
     (lambda n: mi.vanadium_powder(n), 20000, "powder"),
     (lambda n: mi.aluminium_powder(n), 20000, "powder"),
-    (lambda n: mi.config3(rot_deg=30.0, n=n), 4000, "crystal")])
+    (lambda n: mi.config3(rot_deg=30.0, n=n), 4000, "crystal"),
+    (lambda n: mi.dispersion_crystal(n, rot_deg=30.0), 40000, "crystal")])
 def test_fp64_flat_bar_holds_for_almost_every_packet(ctx, make, n, kind):
     wl = make(n)
     _, g = H.packets(ctx, wl, B.FP64)

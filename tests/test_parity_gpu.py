@@ -82,7 +82,7 @@ def test_fp64_packets_match_oracle(ctx, make, n):
 @pytest.mark.parametrize("make,n", [(mi.config1, 50000), (_small_c2, 400000),
                                     (_powder_in_can, 200000), (_can_10mev, 100000),
                                     (mi.powder_two_kernels, 200000), (mi.vanadium_powder, 200000),
-                                    (mi.aluminium_powder, 200000)])
+                                    (mi.aluminium_powder, 200000), (mi.dispersion_crystal, 200000)])
 def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     wl = make(n)
     counts, tallies = ctx.trace(wl, fp_mode=B.FP64)
@@ -379,3 +379,42 @@ def test_phonon_tables_match_the_oracle(ctx):
     np.testing.assert_allclose(f, d.astype(np.float32), rtol=0, atol=0)
     # cumulative masses of A_1 end at 1
     assert abs(d[2 * J] - 1.0) < 1e-13
+
+
+# ---------------------------------------------------------------- dispersion surface
+# The roots of Ei - Ef - E(Q(Ef)) are bracketed on a grid; where the kinematic line runs nearly
+# tangent to the surface, two roots merge and the root (and whether there are 0 or 2 of them in
+# a sub-interval) is ill-conditioned: FP64 rounding moves such a root by eps / |g'|.  Measured:
+# 1 packet in 47,480 beyond the flat 1e-12 bars.  In FP32 the incoming state itself differs by
+# ~1e-7, and the root count or choice differs for 0.4 % of the neutrons that meet the crystal
+# (0.9 % of the detected events), against 0 for the Born-von Karman crystal.
+def test_fp64_dispersion_packets_match_oracle(ctx):
+    wl = mi.dispersion_crystal(40000)
+    pk, g = H.packets(ctx, wl, B.FP64)
+    op = oracle.trace(wl, packets=True, hist=False)["packets"]
+    assert np.array_equal(g["order"], op["order"])
+    dev = H.compare_packets(g, op)
+    m = op["order"] >= 0
+    bad = ((dev["r"] > RT64) | (dev["v"] > RT64) | (dev["t"] > RT64) |
+           (dev["w"] > H.fp64_weight_tol(op["kappa"][m])))
+    print("\n%s: %d of %d packets beyond the FP64 bars" % (wl.name, int(bad.sum()), bad.size))
+    assert bad.sum() <= rate_bound(1e-4, bad.size)
+    counts, tallies, ev = H.run_events(ctx, wl, pk)
+    good = np.zeros(op.size, dtype=bool)
+    good[np.flatnonzero(m)[~bad]] = True
+    sel = good & (op["order"] >= 1)
+    assert np.array_equal(ev["bin"][sel], op["bin"][sel])
+    assert sel.sum() > 1000
+
+
+def test_fp32_dispersion_within_bounds(ctx):
+    wl = mi.dispersion_crystal(400000)
+    st = fp32_stats(ctx, wl)
+    print("\n%s: %d neutrons with another discrete decision in FP32 (%d detected events), "
+          "%d events in another bin, of %d detected events" % (
+              wl.name, st["structure_diff"], st["moved"], st["flips"], st["events_all"]))
+    assert st["moved"] + st["flips"] <= rate_bound(2e-2, st["events_all"])
+    tol = np.maximum(1e-5, 1e-6 * st["kappa"])
+    for f in ("r", "v", "t", "w"):
+        d = st["dev"][f]
+        assert (d > tol).sum() <= rate_bound(1e-3, d.size), (f, float(np.quantile(d / tol, 0.999)))
