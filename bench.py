@@ -32,24 +32,35 @@ WORKLOAD = ("powder S(Q,E), hollow cylinder r_out=1 cm wall 2 mm h=4 cm, Ei=100 
             "(117,760) x 1000 tof bins FP64")
 N_DEFAULT = 100_000_000
 
-# Algorithmic cost model of the path (lane operations: FP32/INT32 arithmetic, each
-# transcendental counted as its instruction sequence, a Philox4x32-10 block as ~110), per
-# event type.  Event counts come from the run's own tallies, and the share of footprints
-# that can lead into the sample from the geometry.  A packet that misses the detector is
-# counted at the cost of the cheapest test that can tell (the height/direction bounds):
-# the model counts the least work the path needs, not the work the kernel happens to do.
-COST = {
-    "footprint": 130,   # 1 Philox block, footprint, sure-miss test
-    "direction": 190,   # 1 Philox block, Box-Muller, 2 tan, normalisation
-    "segments": 85,     # segments ahead (hollow cylinder: 2 cylinder spans + slab), tau, exp
-    "energy": 170,      # 1 Philox block, Box-Muller, speed, time of flight to the sample
-    "scatter": 465,     # scattering point (Philox, exp, move) + S(Q,E) kernel (2 Philox,
-                        # kinematics, 2 sqrt, table lookup, rotation with sincos)
-    "detect": 280,      # circle crossing, atan2, 3 tube chords, absorption (Philox, expm1,
-                        # log1p), pixel, tof -- a detected packet (in or outside the window)
-    "miss": 15,         # a missed packet: height and direction bounds
-    "hist": 6,          # bin index and one FP64 atomic add
-}
+# Lane-op weight of one transcendental or square root: GB300's SFU issues 16 per clock per SM
+# against 128 FP32/INT32 lanes.
+XU_WEIGHT = 8.0
+
+
+def load_opcount():
+    """Operations per incident neutron of the powder run, counted on an instrumented oracle
+    run (oracle/opcount.py; the condition estimate compiled out): fp, int, xu per neutron,
+    and per oracle function with its calls."""
+    p = os.path.join(ROOT, "profiles", "opcount_powder_sqe.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def load_executed():
+    """Executed lane-instructions per neutron of the fused FP32 kernel (ncu
+    smsp__thread_inst_executed.sum on the 1e7-neutron case), if taken on this source."""
+    p = os.path.join(ROOT, "profiles", "wave_kernel_fp32_executed.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    return d.get("lane_inst_per_neutron")
 
 
 def maybe_fraction(wl):
@@ -75,22 +86,22 @@ def maybe_fraction(wl):
     return fx * fy
 
 
-def ops_per_step(n, t, wl):
-    """Lane operations of one step from its event counts (n incident neutrons; tallies t):
-    every incident neutron's footprint, the direction and first segments of the footprints
-    that may lead into the sample, the energy and order-0 step of those that meet it, and
-    per scattering the kernel and the next order's segments; per emitted packet its detector
-    trace (a missed packet: the bounds test that finds it missing); one histogram add per
-    detected event."""
-    from paper_1504_02776_gb300 import binding as B
-    emitted = t[B.T_NEMIT]
-    hits = t[B.T_NHIT]
-    maybe = n * maybe_fraction(wl)
-    return (n * COST["footprint"] + maybe * (COST["direction"] + COST["segments"])
-            + hits * (COST["energy"] + COST["segments"])
-            + emitted * (COST["scatter"] + COST["segments"])
-            + (t[B.T_NDET] + t[B.T_NOVER]) * COST["detect"] + t[B.T_NMISS] * COST["miss"]
-            + t[B.T_NDET] * COST["hist"])
+def ops_per_neutron(opc, wl):
+    """(all, conservative) lane-op equivalents per incident neutron: fp + int + XU_WEIGHT xu
+    of the instrumented oracle run; the conservative figure leaves out, for the footprints
+    the kernel proves to miss the sample, the two further source draws (Philox blocks and
+    the divergence and energy arithmetic) that the oracle makes for every neutron."""
+    pn = opc["per_neutron"]
+    total = pn["fp"] + pn["int"] + XU_WEIGHT * pn["xu"]
+    pf = opc["per_function"]
+    ph, un = pf.get("orc_philox4x32_10"), pf.get("orc_uniforms")
+    block_ops = 0.0
+    if ph and un and ph[3] > 0:
+        block_ops = (ph[0] + ph[1] + un[0] + un[1] + XU_WEIGHT * (ph[2] + un[2])) / ph[3]
+    beam = next((v for k, v in pf.items() if "make_beam" in k), None)
+    beam_rest = 0.0 if beam is None or beam[3] <= 0 else (beam[0] + beam[1] + XU_WEIGHT * beam[2]) / beam[3]
+    skipped = (1.0 - maybe_fraction(wl)) * (2.0 * block_ops + beam_rest)
+    return total, total - skipped
 
 
 def csrc_hash():
@@ -575,24 +586,62 @@ def run_ours(args):
         del dev_bufs, host_bufs
         ctx.sync()
 
-    # ---- roofline of the fused trace kernel (ALU bound)
+    # ---- roofline of the fused trace kernel (ALU bound): operations per neutron counted on an
+    # instrumented oracle run, against the FP32/INT32 lane rate
     props = torch.cuda.get_device_properties(local)
     peaks = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * sm_mhz * 1e6   # FP32/INT32 lanes x clock
-    ops = ops_per_step(N, t_local, wl)
-    achieved = ops / (trace_ms / 1e3)
-    traffic_per_n = load_traffic()
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-            "unit": "Tops/s", "frac": achieved / peak_ops,
-            "traffic": None if traffic_per_n is None else traffic_per_n * N,
-            "kernel": "wave_kernel<float,1,TUBES,powder>", "kernel_ms": trace_ms,
-            "ops_per_launch": ops,
-            "peak_basis": "%d SMs x 128 FP32/INT32 lanes x %.0f MHz (max SM clock, "
-                          "MEASURED_PEAKS.json)" % (props.multi_processor_count, sm_mhz),
-            # histogram read-modify-writes, one 8-byte word per detected event (read + write)
-            "hbm_gbs_algorithmic": t_local[B.T_NDET] * 16 / (trace_ms / 1e3) / 1e9,
-            "hbm_peak_gbs_measured": peaks.get("hbm_gbs")}
+    opc = load_opcount()
+    roof = None
+    if opc is not None:
+        per_n, per_n_cons = ops_per_neutron(opc, wl)
+        ops = per_n * N
+        achieved = ops / (trace_ms / 1e3)
+        traffic_per_n = load_traffic()
+        executed = load_executed()
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops,
+                "traffic": None if traffic_per_n is None else traffic_per_n * N,
+                "kernel": "wave_kernel<float,1,TUBES,powder>", "kernel_ms": trace_ms,
+                "ops_per_launch": ops,
+                "ops_per_neutron": per_n,
+                "ops_source": ("instrumented oracle run, oracle/opcount.py (GCC profile counts "
+                               "of the oracle's GIMPLE, condition estimate compiled out): "
+                               "fp %.1f + int %.1f + %g x xu %.2f per neutron" % (
+                                   opc["per_neutron"]["fp"], opc["per_neutron"]["int"],
+                                   XU_WEIGHT, opc["per_neutron"]["xu"])),
+                "frac_conservative": per_n_cons * N / (trace_ms / 1e3) / peak_ops,
+                "ops_per_neutron_conservative": per_n_cons,
+                "conservative_note": "without the source draws the oracle makes for the "
+                                     "footprints the kernel proves to miss the sample",
+                "executed_lane_inst_per_neutron": executed,
+                "frac_issue": None if executed is None else
+                executed * N / (trace_ms / 1e3) / peak_ops,
+                "peak_basis": "%d SMs x 128 FP32/INT32 lanes x %.0f MHz (max SM clock, "
+                              "MEASURED_PEAKS.json); a transcendental counts %g lane-ops "
+                              "(16 SFU results per clock per SM)" % (
+                                  props.multi_processor_count, sm_mhz, XU_WEIGHT),
+                # histogram read-modify-writes, one 8-byte word per detected event (read + write)
+                "hbm_gbs_algorithmic": t_local[B.T_NDET] * 16 / (trace_ms / 1e3) / 1e9,
+                "hbm_peak_gbs_measured": peaks.get("hbm_gbs")}
+    # the histogram stage's roof: random FP64 atomic adds into the same 942 MB histogram
+    n_at = 50_000_000
+    for _ in range(2):
+        B.mcv_bench_atomics(ctx.handle, counts.data_ptr(), counts.numel(), n_at, 1, sptr)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for k in range(5):
+        B.mcv_bench_atomics(ctx.handle, counts.data_ptr(), counts.numel(), n_at, 2 + k, sptr)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    at_rate = 5 * n_at / (a0.elapsed_time(a1) / 1e3)
+    det_rate_kernel = t_local[B.T_NDET] / (trace_ms / 1e3)
+    atomics = {"random_fp64_atomics_per_s": at_rate,
+               "histogram_adds_per_s_in_trace": det_rate_kernel,
+               "frac": det_rate_kernel / at_rate,
+               "how": "mcv_bench_atomics: 5 x 5e7 adds of 1.0 at hashed uniform bins of the "
+                      "942 MB histogram, CUDA events"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "neutrons/s", "n_gpus": world,
@@ -611,6 +660,7 @@ def run_ours(args):
                          "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                          "speedup_fp32_over_fp64": value / value64},
         "roofline": roof,
+        "atomics": atomics,
         "batched": batched,
         "differentiable": differentiable,
         "cpu_baseline": cpu_base,

@@ -279,6 +279,13 @@ int64_t mcv_phonon_table_bytes(int n_modes, int n_max);
 mcv_status mcv_phonon_build(const double* dos_z, mcv_phonon* ph, void* tables, int64_t bytes,
                             void* stream);
 
+/* Measurement of the histogram stage's roof (no counterpart in the paper): n_adds FP64
+ * atomic adds of 1.0 into hist (n_bins doubles, device) at bins spread uniformly at random by
+ * an integer hash of (seed, add index), the access pattern of the detector's histogram adds
+ * without the tracing work.  Time it with events on `stream`. */
+mcv_status mcv_bench_atomics(mcv_ctx* ctx, double* hist, int64_t n_bins, int64_t n_adds,
+                             uint64_t seed, void* stream);
+
 /* ---- the component chain ------------------------------------------------------------- */
 /* Source: writes n packets with ids first_id..first_id+n-1 into out (slots 0..n-1; out->id
  * and out->order, if given, receive the id and 0).  fp_mode selects the array types. */

@@ -49,6 +49,13 @@ double u01_from(uint32_t hi, uint32_t lo) {
 }
 
 // ---- conditioning ---------------------------------------------------------------------
+// The condition estimate below is test infrastructure of its own: it sets the tolerances the
+// tests compare rounding-sensitive results with and takes no part in the method.  Every
+// statement of it is guarded by ORC_CONDITION, so a build with ORC_CONDITION=0 (the
+// operation count of the method, oracle/opcount.py) compiles it out.
+#ifndef ORC_CONDITION
+#define ORC_CONDITION 1
+#endif
 // Condition estimate of the current packet's weight: each chord or range width that
 // subtracts nearly equal numbers adds its amplification factor (|value| / |difference|).
 // It only sets the tolerances the tests compare rounding-sensitive results with.
@@ -98,11 +105,12 @@ bool cylinder_interval(double R, Vec3 r, Vec3 d, double* s1, double* s2, End* e 
   double cr = r.x * d.z - r.z * d.x;
   double g = R * R - cr * cr / a;
   if (!(g > 0.0)) return false;
-  g_kappa += R * R / g;
+  if (ORC_CONDITION) g_kappa += R * R / g;
   double half = std::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
-  if (e) {
+  if (e && !ORC_CONDITION) e[0] = {*s1, 0.0, 0.0}, e[1] = {*s2, 0.0, 0.0};
+  if (e && ORC_CONDITION) {
     double lever = R / (half * a);
     double er = std::fabs(tc) + half + lever * R;
     double ss[2] = {*s1, *s2};
@@ -136,8 +144,9 @@ bool tube_interval(double R, double ux, double uz, double rt, Vec3 r, Vec3 d, do
   // the chord is sensitive to the tube radius (rt^2/g) and, through the lever arm, to the
   // direction of the ray (closest-approach distance h, distance |tc| sqrt(a))
   // and to the error of the start point (|cr| |dr| / (sqrt(a) g))
-  g_kappa += rt * rt / g + std::fabs(tc) * std::fabs(cr) / g +
-             std::fabs(cr) * (g_err_r + g_err_a) / (std::sqrt(a) * g);
+  if (ORC_CONDITION)
+    g_kappa += rt * rt / g + std::fabs(tc) * std::fabs(cr) / g +
+               std::fabs(cr) * (g_err_r + g_err_a) / (std::sqrt(a) * g);
   double half = std::sqrt(g / a);
   *s1 = tc - half;
   *s2 = tc + half;
@@ -164,7 +173,8 @@ bool slab_interval(double half, double p, double dp, double* s1, double* s2, End
   double b = (half - p) / dp;
   *s1 = std::min(a, b);
   *s2 = std::max(a, b);
-  if (e) {
+  if (e && !ORC_CONDITION) e[0] = {*s1, 0.0, 0.0}, e[1] = {*s2, 0.0, 0.0};
+  if (e && ORC_CONDITION) {
     double ad = std::fabs(dp);
     double er = ((1.0 + p_rounding) * std::fabs(p) + half) / ad;
     double ea = g_err_r + std::fabs(dprev_p) * g_err_a;
@@ -185,10 +195,11 @@ int push_segment(End a, End b, double* sa, double* sb, double* ra, double* rb, d
   double lo = std::max(a.s, 0.0);
   if (b.s > lo) {
     double e_lo = a.s > 0.0 ? a.er + a.ep : 0.0;
-    g_kappa += (std::fabs(a.s) + std::fabs(b.s) + e_lo + b.er + b.ep) / (b.s - lo);
+    if (ORC_CONDITION)
+      g_kappa += (std::fabs(a.s) + std::fabs(b.s) + e_lo + b.er + b.ep) / (b.s - lo);
     sa[n] = lo;
     sb[n] = b.s;
-    if (ra) {
+    if (ORC_CONDITION && ra) {
       ra[n] = e_lo;
       rb[n] = b.er + b.ep;
       ra0[n] = a.s > 0.0 ? a.er : 0.0;
@@ -510,8 +521,10 @@ bool kernel_sqe(const orc_config& cfg, double speed, Vec3 d, const double u[4], 
   double q_hi = std::min(ki + kf, cfg.q_max);
   if (!(q_hi > q_lo)) return false;
   double dQ = q_hi - q_lo;
-  g_kappa += (ki + kf) / dQ + 2.0 * g_kappa_v * (1.0 + (ki + kf) / dQ);
-  g_kappa_v = 1.0 + 0.5 * ((Ei + std::fabs(E) + std::fabs(e_lo)) / Ef + 2.0 * (Ei / Ef) * g_kappa_v);
+  if (ORC_CONDITION) {
+    g_kappa += (ki + kf) / dQ + 2.0 * g_kappa_v * (1.0 + (ki + kf) / dQ);
+    g_kappa_v = 1.0 + 0.5 * ((Ei + std::fabs(E) + std::fabs(e_lo)) / Ef + 2.0 * (Ei / Ef) * g_kappa_v);
+  }
   double Q = q_lo + u[1] * dQ;
   // scattering angle from Q^2 = ki^2 + kf^2 - 2 ki kf cos(2theta), written through
   // 1 - cos = (Q - q_lo)(Q + q_lo) / (2 ki kf) and 1 + cos = (ki + kf - Q)(ki + kf + Q) /
@@ -874,6 +887,7 @@ bool kernel_bvk(const orc_config& cfg, double rot_y, double speed, Vec3 d, const
   o->kf = kf;
   o->qvec = add(scale(d, ki), scale(R.df, -kf));
 
+  if (!ORC_CONDITION) return true;
   // Condition estimate (units of the FP64 epsilon): how far rounding at the scale of the
   // epsilon can move this factor.  Sources: the computed eigenvalue (relative error kl:
   // a few ulps of the largest eigenvalue, plus Q's rounding through the dispersion
@@ -1077,8 +1091,10 @@ bool kernel_phonon(const orc_config& cfg, double speed, Vec3 d, const double u[4
   const double q_lo = std::fabs(ki - kf), q_hi = ki + kf;
   const double dQ = q_hi - q_lo;
   // condition estimate: the width of the Q range and the final speed, as for S(Q,E)
-  g_kappa += (ki + kf) / dQ + 2.0 * g_kappa_v * (1.0 + (ki + kf) / dQ);
-  g_kappa_v = 1.0 + 0.5 * ((Ei + std::fabs(E)) / Ef + 2.0 * (Ei / Ef) * g_kappa_v);
+  if (ORC_CONDITION) {
+    g_kappa += (ki + kf) / dQ + 2.0 * g_kappa_v * (1.0 + (ki + kf) / dQ);
+    g_kappa_v = 1.0 + 0.5 * ((Ei + std::fabs(E)) / Ef + 2.0 * (Ei / Ef) * g_kappa_v);
+  }
   const double Q = q_lo + u[2] * dQ;
   // scattering angle from 1 -/+ cos as products of the offsets from the ends of the range
   const double den = 2.0 * ki * kf;
@@ -1340,14 +1356,18 @@ template <class Emit, class Scat>
 void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Emit emit,
                Scat on_scatter, double* tallies) {
   Neutron n;
-  g_kappa = 1.0;
-  g_kappa_v = 2.0;
+  if (ORC_CONDITION) {
+    g_kappa = 1.0;
+    g_kappa_v = 2.0;
+  }
   if (!make_beam(cfg, nid, &n)) return;
   // the start point's transverse coordinates are rounded once; the direction a few times
-  g_err_r = std::fabs(n.r.x) + std::fabs(n.r.y);
-  g_err_a = 0.0;
-  g_dprev = n.d;
-  g_err_d = 4.0;
+  if (ORC_CONDITION) {
+    g_err_r = std::fabs(n.r.x) + std::fabs(n.r.y);
+    g_err_a = 0.0;
+    g_dprev = n.d;
+    g_err_d = 4.0;
+  }
   for (int o = 0;; ++o) {
     if (n.w < cfg.min_prob) break;
     if (stop_on_zero && n.w == 0.0) break;
@@ -1416,9 +1436,11 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     n.r = add(n.r, scale(n.d, s_pt));
     n.t = n.t + s_pt / n.speed;
     // the new point: the error of s_pt along the ray, and the roundings of its coordinates
-    g_err_a = e_pt;
-    g_dprev = n.d;
-    g_err_r = std::sqrt(dot(n.r, n.r)) + std::fabs(s_pt);
+    if (ORC_CONDITION) {
+      g_err_a = e_pt;
+      g_dprev = n.d;
+      g_err_r = std::sqrt(dot(n.r, n.r)) + std::fabs(s_pt);
+    }
     // kernel choice with probability sigma_k / sigma_s (weight unchanged)
     int k = 0;
     if (sc.nk == 2 && !(u[1] * (sc.ksig_b[0] + sc.ksig_b[1]) < sc.ksig_b[0])) k = 1;
@@ -1433,7 +1455,7 @@ void chain_one(const orc_config& cfg, int64_t nid, bool stop_on_zero, int gs, Em
     n.d = ko.d;
     n.speed = ko.speed;
     // an isotropic direction is drawn afresh; the others are built on the incoming one
-    g_err_d = sc.ktype[k] == ORC_K_ISO ? 4.0 : g_err_d + 8.0;
+    if (ORC_CONDITION) g_err_d = sc.ktype[k] == ORC_K_ISO ? 4.0 : g_err_d + 8.0;
     on_scatter(o + 1, sc.ktype[k], j, ko, rec, n.w);
   }
 }
@@ -1459,10 +1481,10 @@ void record_detection(const orc_config& cfg, int64_t nid, const EmitRecord& em, 
   int32_t pixel;
   double tof, w_det;
   const double k_before = g_kappa;
-  g_kappa = 0.0;
+  if (ORC_CONDITION) g_kappa = 0.0;
   int64_t bin = detect(cfg, em.n.r, em.n.d, em.n.speed, em.n.t, em.w, u[0], &pixel, &tof, &w_det);
   const double k_det = g_kappa;
-  g_kappa = k_before;
+  if (ORC_CONDITION) g_kappa = k_before;
   if (pk) pk->kappa_det = em.kappa + k_det;
   if (bin >= 0) {
     if (hist) hist[bin] += w_det;

@@ -138,6 +138,7 @@ def _load():
                               C.c_double, C.c_int, P, P, P, P, P]
     L.mcv_grad_noalloc.argtypes = [P, P, P, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, P,
                                    C.c_double, C.c_int, P, P, P, P, P]
+    L.mcv_bench_atomics.argtypes = [P, P, C.c_int64, C.c_int64, C.c_uint64, P]
     L.mcv_bragg_table_bytes.argtypes = [C.c_int]
     L.mcv_bragg_table_bytes.restype = C.c_int64
     L.mcv_bragg_build.argtypes = [P, P, C.c_int, P, P, C.c_int64, P]
@@ -153,7 +154,7 @@ def _load():
     L.mcv_trace_batch.argtypes = [P, P, C.c_int, P, C.c_int, P]
     for name in ("mcv_create", "mcv_destroy", "mcv_sync", "mcv_zero", "mcv_beam",
                  "mcv_trace_sample", "mcv_detect", "mcv_grad", "mcv_adjoint", "mcv_grad_noalloc",
-                 "mcv_phonon_build", "mcv_bragg_build",
+                 "mcv_phonon_build", "mcv_bragg_build", "mcv_bench_atomics",
                  "mcv_batch_create", "mcv_batch_run", "mcv_batch_tune", "mcv_batch_shape",
                  "mcv_batch_destroy", "mcv_trace_batch"):
         getattr(L, name).restype = st
@@ -232,6 +233,10 @@ def mcv_grad_noalloc(sample, beam, det, seed, sim_id, first_id, n, target, scale
     _check(lib.mcv_grad_noalloc(C.byref(sample), C.byref(beam), C.byref(det), seed, sim_id,
                                 first_id, n, target, scale_c, grad_scatterer, C.byref(hist),
                                 loss, dsqe, dsig, stream))
+
+
+def mcv_bench_atomics(ctx, hist, n_bins, n_adds, seed=0, stream=None):
+    _check(lib.mcv_bench_atomics(ctx, hist, n_bins, n_adds, seed, stream))
 
 
 def mcv_bragg_table_bytes(n):

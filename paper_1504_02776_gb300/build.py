@@ -14,13 +14,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcv.so")
-SOURCES = ["mcv_fp32.cu", "mcv_fp64.cu", "mcv_batch_fp32.cu", "mcv_batch_fp64.cu", "mcv_misc.cu",
-           "mcv_api.cu", "mcv_batch.cu", "mcv_noalloc.cu", "mcv_phonon.cu",
-           "mcv_bragg.cu"]
+SOURCES = ["mcv_fp32.cu", "mcv_fp64.cu", "mcv_fp32_ev.cu", "mcv_fp64_ev.cu", "mcv_fp32_aux.cu",
+           "mcv_fp64_aux.cu", "mcv_batch_fp32.cu", "mcv_batch_fp64.cu", "mcv_batch_fp32_ev.cu",
+           "mcv_batch_fp64_ev.cu", "mcv_misc.cu", "mcv_api.cu", "mcv_batch.cu", "mcv_noalloc.cu",
+           "mcv_phonon.cu", "mcv_bragg.cu"]
 # per-file flags: the FP64 kernels round every operation separately (no FMA contraction)
-FILE_FLAGS = {"mcv_fp64.cu": ["-fmad=false"], "mcv_batch_fp64.cu": ["-fmad=false"],
-              "mcv_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"],
-              "mcv_batch_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+_F64 = ["-fmad=false"]
+_F32 = ["-prec-div=false", "-prec-sqrt=false"]
+FILE_FLAGS = {f: (_F64 if "fp64" in f else _F32) for f in SOURCES if "_fp" in f or f.startswith("mcv_fp")}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

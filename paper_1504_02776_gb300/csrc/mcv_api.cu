@@ -654,6 +654,17 @@ int64_t mcv_detector_pixels(const mcv_detector* det) {
   return D.n_bins / D.win.n_tof;
 }
 
+mcv_status mcv_bench_atomics(mcv_ctx* ctx, double* hist, int64_t n_bins, int64_t n_adds,
+                             uint64_t seed, void* stream) {
+  mcv_status st = check_ctx(ctx);
+  if (st != MCV_OK) return st;
+  if (n_bins < 1 || n_adds < 0 || !hist) return fail(MCV_EINVAL, "bad histogram or count");
+  cudaError_t e = mcv::launch_atomics(hist, n_bins, n_adds, seed, ctx->sm_count * 16,
+                                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "atomics kernel launch");
+  return MCV_OK;
+}
+
 mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream) {
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;

@@ -24,6 +24,7 @@ constexpr int64_t kMinChunk = 256;
 struct BatchImage {
   int fp = 0, ns = 1, det = 0, bvk = 0;
   int ss = 1;  // every simulation has the same sample (kept in kernel parameter space)
+  int ev = 0;  // some simulation appends to an event list
   int nsims = 0;
   int64_t total_n = 0;
   std::vector<unsigned char> sims;  // SimP<R>[nsims]
@@ -87,6 +88,7 @@ mcv_status build_image(const mcv_sim* sims, int nsims, const mcv_detector* det, 
     if (s.hist.events) {
       st = event_sink(s.hist.events, s.sim_id, &d.ev);
       if (st != MCV_OK) return fail(st, who + mcv_last_error());
+      im->ev = 1;
     }
     if (total > kMaxNeutrons - s.n) return fail(MCV_EINVAL, "too many neutrons in the batch");
     total += s.n;
@@ -223,13 +225,14 @@ mcv_status launch(mcv_batch* b, const mcv::BatchArgs& Q, int64_t n_items, int gr
   if (n_items == 0) return MCV_OK;
   cudaError_t e = cudaMemsetAsync(Q.next, 0, (size_t)Q.nsims * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue counters)");
-  e = mcv::launch_batch(b->A, Q, b->im.fp, b->im.ns, b->im.det, b->im.bvk, b->im.ss, grid, s);
+  e = mcv::launch_batch(b->A, Q, b->im.fp, b->im.ns, b->im.det, b->im.bvk, b->im.ss, b->im.ev,
+                        grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return MCV_OK;
 }
 
 mcv_status occupancy(mcv_ctx* ctx, const BatchImage& im, int* blocks) {
-  cudaError_t e = mcv::batch_blocks_per_sm(im.fp, im.ns, im.det, im.bvk, im.ss, blocks);
+  cudaError_t e = mcv::batch_blocks_per_sm(im.fp, im.ns, im.det, im.bvk, im.ss, im.ev, blocks);
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel occupancy");
   if (*blocks < 1) return fail(MCV_ECUDA, "the batch kernel does not fit on an SM");
   (void)ctx;
@@ -340,11 +343,13 @@ mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream) {
       q->n = m;
       q->hist = scratch;
       q->tallies = scratch + nb;
+      q->ev = mcv::EvSink{};
     } else {
       mcv::SimP<double>* q = reinterpret_cast<mcv::SimP<double>*>(p);
       q->n = m;
       q->hist = scratch;
       q->tallies = scratch + nb;
+      q->ev = mcv::EvSink{};
     }
   }
   void* d_trial = nullptr;

@@ -2,5 +2,5 @@
 #include "mcv_kernels.cuh"
 
 namespace mcv {
-MCV_DEFINE_BATCH_ENTRY_POINTS(float, f32)
+MCV_DEFINE_BATCH_ENTRY_POINTS(float, f32, false)
 }  // namespace mcv

@@ -3,5 +3,5 @@
 #include "mcv_kernels.cuh"
 
 namespace mcv {
-MCV_DEFINE_BATCH_ENTRY_POINTS(double, f64)
+MCV_DEFINE_BATCH_ENTRY_POINTS(double, f64, false)
 }  // namespace mcv

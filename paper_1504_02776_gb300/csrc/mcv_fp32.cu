@@ -1,6 +1,6 @@
-// FP32 fast mode instantiation of the hot-path kernels (FMA contraction on).
+// FP32 fast mode instantiation of the fused trace kernels (FMA contraction on).
 #include "mcv_kernels.cuh"
 
 namespace mcv {
-MCV_DEFINE_ENTRY_POINTS(float, f32)
+MCV_DEFINE_TRACE_ENTRY_POINTS(float, f32)
 }  // namespace mcv

@@ -39,12 +39,16 @@ __device__ __forceinline__ void store_slot(const TraceArgs& A, int64_t slot, con
   A.pk_order[slot] = order;
 }
 
-// Where the forward path's histogram and tallies are: the launch's (kernel parameters)
-struct LaunchOut {
+// Where the forward path's histogram and tallies are: the launch's (kernel parameters).
+// EV: the launch may append to an event list (the code for it is compiled in only then).
+template <bool EV>
+struct LaunchOutT {
+  static constexpr bool kEvents = EV;
   static __device__ __forceinline__ double* hist(const TraceArgs& A) { return A.hist; }
   static __device__ __forceinline__ double* tallies(const TraceArgs& A) { return A.tallies; }
   static __device__ __forceinline__ const EvSink& events(const TraceArgs& A) { return A.ev; }
 };
+using LaunchOut = LaunchOutT<true>;
 
 // one thread's running tallies: beam stop, detected and out-of-window weights, counts
 template <typename R>
@@ -93,8 +97,10 @@ struct Forward {
   // a packet's detector result into the histogram and the tallies
   __device__ __forceinline__ void record(const TraceArgs& A, const Hit<R>& h) {
     Tally<R>& t = store.get();
-    if (h.pixel >= 0 && Out::events(A).count)
-      append_event(Out::events(A), h.pixel, h.tof.value(), (double)h.w_det);
+    if constexpr (Out::kEvents) {
+      if (h.pixel >= 0 && Out::events(A).count)
+        append_event(Out::events(A), h.pixel, h.tof.value(), (double)h.w_det);
+    }
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
@@ -267,8 +273,9 @@ struct QueuedIds {
 };
 
 // the histogram and tallies of the simulation in the warp's slot
-template <typename R>
+template <typename R, bool EV>
 struct SlotOut {
+  static constexpr bool kEvents = EV;
   static __device__ __forceinline__ double* hist(const TraceArgs&) { return batch_warp<R>().sim.hist; }
   static __device__ __forceinline__ double* tallies(const TraceArgs&) {
     return batch_warp<R>().sim.tallies;
@@ -549,12 +556,12 @@ struct WaveBlocks {
   static constexpr int value = sizeof(R) == 4 ? MCV_WAVE_BLOCKS_F32 : MCV_WAVE_BLOCKS_F64;
 };
 
-template <typename R, int NS, int DET, int KS>
+template <typename R, int NS, int DET, int KS, bool EV>
 __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     wave_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
   stage_tubes<R, DET>(A, tu);
-  Forward<R, DET, LaunchOut, SmemTally<R>> pol{SmemTally<R>{wave_smem_bytes<R>()}};
+  Forward<R, DET, LaunchOutT<EV>, SmemTally<R>> pol{SmemTally<R>{wave_smem_bytes<R>()}};
   pol.store.get() = Tally<R>();
   // each warp owns one contiguous range of the launch's neutron ids
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -576,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
 // simulation that still has items.  Each neutron's arithmetic is the single-simulation
 // kernel's.
 // SS: every simulation has the batch's sample (A.Sf / A.Sd), kept in parameter space
-template <typename R, int NS, int DET, int KS, bool SS>
+template <typename R, int NS, int DET, int KS, bool SS, bool EV>
 __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     batch_wave_kernel(const __grid_constant__ TraceArgs A, const __grid_constant__ BatchArgs Q) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
@@ -601,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, WaveBlocks<R>::value)
     }
     __syncwarp();
   }
-  Forward<R, DET, SlotOut<R>, SmemTally<R>> pol{SmemTally<R>{batch_tally_offset<R>()}};
+  Forward<R, DET, SlotOut<R, EV>, SmemTally<R>> pol{SmemTally<R>{batch_tally_offset<R>()}};
   pol.store.get() = Tally<R>();
   const SlotJob<R, SS> job{A};
   QueuedIds<R> src;
@@ -838,18 +845,53 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const __grid_constant
 }
 
 // ---- launchers, one set per real type -----------------------------------------------------
+// The fused waves with an event list are instantiated in translation units of their own
+// (mcv_fp32_ev.cu, mcv_fp64_ev.cu); these declare their entry points.
+cudaError_t launch_waves_ev_f32(const TraceArgs& A, int det, int grid, cudaStream_t s);
+cudaError_t launch_waves_ev_f64(const TraceArgs& A, int det, int grid, cudaStream_t s);
+template <typename R>
+cudaError_t launch_waves_ev(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  return sizeof(R) == 4 ? launch_waves_ev_f32(A, det, grid, s) : launch_waves_ev_f64(A, det, grid, s);
+}
+
 template <typename R, int NS, int DET, int KS>
 cudaError_t launch_trace_k(const TraceArgs& A, int grid, cudaStream_t s) {
   if (DET != MCV_DET_NONE && uses_waves(A, DET)) {
+    if (A.ev.count) return launch_waves_ev<R>(A, DET, grid, s);
     const size_t smem = wave_kernel_smem_bytes<R>();
-    cudaError_t e = cudaFuncSetAttribute(wave_kernel<R, NS, DET, KS>,
+    cudaError_t e = cudaFuncSetAttribute(wave_kernel<R, NS, DET, KS, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    wave_kernel<R, NS, DET, KS><<<grid, kThreads, smem, s>>>(A);
+    wave_kernel<R, NS, DET, KS, false><<<grid, kThreads, smem, s>>>(A);
   } else {
     trace_kernel<R, NS, DET, KS><<<grid, kThreads, 0, s>>>(A);
   }
   return cudaGetLastError();
+}
+
+// the waves with an event list, over the shapes (used by the _ev translation units)
+template <typename R, int NS, int KS>
+cudaError_t launch_waves_ev_k(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  const size_t smem = wave_kernel_smem_bytes<R>();
+  const void* fn = det == MCV_DET_SURFACE ? (const void*)wave_kernel<R, NS, MCV_DET_SURFACE, KS, true>
+                                          : (const void*)wave_kernel<R, NS, MCV_DET_TUBES, KS, true>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<TraceArgs*>(&A)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
+}
+
+template <typename R>
+cudaError_t launch_waves_ev_t(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  const bool all = A.Sd.wide;
+  if (A.Sd.ns <= 1)
+    return all ? launch_waves_ev_k<R, 1, kKernelsAll>(A, det, grid, s)
+               : launch_waves_ev_k<R, 1, kKernelsPowder>(A, det, grid, s);
+  if (A.Sd.ns == 2)
+    return all ? launch_waves_ev_k<R, 2, kKernelsAll>(A, det, grid, s)
+               : launch_waves_ev_k<R, 2, kKernelsPowder>(A, det, grid, s);
+  return all ? launch_waves_ev_k<R, 4, kKernelsAll>(A, det, grid, s)
+             : launch_waves_ev_k<R, 4, kKernelsPowder>(A, det, grid, s);
 }
 
 template <typename R, int NS, int KS>
@@ -880,8 +922,8 @@ cudaError_t launch_trace_t(const TraceArgs& A, int det, int grid, cudaStream_t s
 // the kernel the fused forward of this shape launches (waves when a detector is fused)
 template <typename R, int NS, int KS>
 const void* trace_fn_nk(int det) {
-  if (det == MCV_DET_SURFACE) return (const void*)wave_kernel<R, NS, MCV_DET_SURFACE, KS>;
-  if (det == MCV_DET_TUBES) return (const void*)wave_kernel<R, NS, MCV_DET_TUBES, KS>;
+  if (det == MCV_DET_SURFACE) return (const void*)wave_kernel<R, NS, MCV_DET_SURFACE, KS, false>;
+  if (det == MCV_DET_TUBES) return (const void*)wave_kernel<R, NS, MCV_DET_TUBES, KS, false>;
   return (const void*)trace_kernel<R, NS, MCV_DET_NONE, KS>;
 }
 
@@ -905,40 +947,44 @@ cudaError_t blocks_per_sm_t(int ns, int det, int bvk, int* blocks) {
 // the batched kernel of a shape; its dynamic shared memory limit is set where its occupancy
 // is queried (batch_blocks_per_sm_t), once before the first launch, so that a launch is only
 // the launch (and can be captured in a CUDA graph)
-template <typename R, int NS, int KS, bool SS>
+template <typename R, int NS, int KS, bool SS, bool EV>
 const void* batch_fn_nk(int det) {
   if (det == MCV_DET_SURFACE)
-    return (const void*)batch_wave_kernel<R, NS, MCV_DET_SURFACE, KS, SS>;
-  return (const void*)batch_wave_kernel<R, NS, MCV_DET_TUBES, KS, SS>;
+    return (const void*)batch_wave_kernel<R, NS, MCV_DET_SURFACE, KS, SS, EV>;
+  return (const void*)batch_wave_kernel<R, NS, MCV_DET_TUBES, KS, SS, EV>;
 }
 
-template <typename R, bool SS>
+template <typename R, bool SS, bool EV>
 const void* batch_fn_s(int ns, int det, int bvk) {
   if (ns <= 1)
-    return bvk ? batch_fn_nk<R, 1, kKernelsAll, SS>(det) : batch_fn_nk<R, 1, kKernelsPowder, SS>(det);
+    return bvk ? batch_fn_nk<R, 1, kKernelsAll, SS, EV>(det)
+               : batch_fn_nk<R, 1, kKernelsPowder, SS, EV>(det);
   if (ns == 2)
-    return bvk ? batch_fn_nk<R, 2, kKernelsAll, SS>(det) : batch_fn_nk<R, 2, kKernelsPowder, SS>(det);
-  return bvk ? batch_fn_nk<R, 4, kKernelsAll, SS>(det) : batch_fn_nk<R, 4, kKernelsPowder, SS>(det);
+    return bvk ? batch_fn_nk<R, 2, kKernelsAll, SS, EV>(det)
+               : batch_fn_nk<R, 2, kKernelsPowder, SS, EV>(det);
+  return bvk ? batch_fn_nk<R, 4, kKernelsAll, SS, EV>(det)
+             : batch_fn_nk<R, 4, kKernelsPowder, SS, EV>(det);
 }
 
-template <typename R>
+// EV: the batch appends to event lists (the _ev translation units instantiate those kernels)
+template <typename R, bool EV>
 const void* batch_fn_t(int ns, int det, int bvk, int ss) {
-  return ss ? batch_fn_s<R, true>(ns, det, bvk) : batch_fn_s<R, false>(ns, det, bvk);
+  return ss ? batch_fn_s<R, true, EV>(ns, det, bvk) : batch_fn_s<R, false, EV>(ns, det, bvk);
 }
 
-template <typename R>
+template <typename R, bool EV>
 cudaError_t batch_blocks_per_sm_t(int ns, int det, int bvk, int ss, int* blocks) {
-  const void* fn = batch_fn_t<R>(ns, det, bvk, ss);
+  const void* fn = batch_fn_t<R, EV>(ns, det, bvk, ss);
   const size_t smem = batch_smem_bytes<R>();
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem);
 }
 
-template <typename R>
+template <typename R, bool EV>
 cudaError_t launch_batch_t(const TraceArgs& A, const BatchArgs& Q, int ns, int det, int bvk,
                            int ss, int grid, cudaStream_t s) {
-  const void* fn = batch_fn_t<R>(ns, det, bvk, ss);
+  const void* fn = batch_fn_t<R, EV>(ns, det, bvk, ss);
   void* args[] = {const_cast<TraceArgs*>(&A), const_cast<BatchArgs*>(&Q)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, batch_smem_bytes<R>(), s);
 }
@@ -1000,14 +1046,23 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   return launch_adjoint_ns<R, 4>(A, det, grid, s);
 }
 
-// defines the entry points of one real type (used once in mcv_fp32.cu / mcv_fp64.cu)
-#define MCV_DEFINE_ENTRY_POINTS(R, SUFFIX)                                                  \
+// defines the fused-trace entry points of one real type (mcv_fp32.cu / mcv_fp64.cu)
+#define MCV_DEFINE_TRACE_ENTRY_POINTS(R, SUFFIX)                                            \
   cudaError_t launch_trace_##SUFFIX(const TraceArgs& A, int det, int grid, cudaStream_t s) { \
     return launch_trace_t<R>(A, det, grid, s);                                              \
   }                                                                                         \
   cudaError_t blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int* blocks) {               \
     return blocks_per_sm_t<R>(ns, det, bvk, blocks);                                        \
-  }                                                                                         \
+  }
+
+// the fused waves with an event list (mcv_fp32_ev.cu / mcv_fp64_ev.cu)
+#define MCV_DEFINE_EVENT_ENTRY_POINTS(R, SUFFIX)                                            \
+  cudaError_t launch_waves_ev_##SUFFIX(const TraceArgs& A, int det, int grid, cudaStream_t s) { \
+    return launch_waves_ev_t<R>(A, det, grid, s);                                           \
+  }
+
+// the source, detector and adjoint entry points (mcv_fp32_aux.cu / mcv_fp64_aux.cu)
+#define MCV_DEFINE_AUX_ENTRY_POINTS(R, SUFFIX)                                              \
   cudaError_t launch_beam_##SUFFIX(const TraceArgs& A, int grid, cudaStream_t s) {          \
     return launch_beam_t<R>(A, grid, s);                                                    \
   }                                                                                         \
@@ -1023,14 +1078,15 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
     return adjoint_blocks_per_sm_t<R>(ns, det, bvk, blocks);                                \
   }
 
-// defines the batched entry points of one real type (mcv_batch_fp32.cu / mcv_batch_fp64.cu)
-#define MCV_DEFINE_BATCH_ENTRY_POINTS(R, SUFFIX)                                            \
+// defines the batched entry points of one real type and event flavour EV (mcv_batch_fp32.cu,
+// mcv_batch_fp64.cu; with EV, mcv_batch_fp32_ev.cu and mcv_batch_fp64_ev.cu)
+#define MCV_DEFINE_BATCH_ENTRY_POINTS(R, SUFFIX, EV)                                        \
   cudaError_t batch_blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int ss, int* blocks) { \
-    return batch_blocks_per_sm_t<R>(ns, det, bvk, ss, blocks);                              \
+    return batch_blocks_per_sm_t<R, EV>(ns, det, bvk, ss, blocks);                          \
   }                                                                                         \
   cudaError_t launch_batch_##SUFFIX(const TraceArgs& A, const BatchArgs& Q, int ns, int det, \
                                     int bvk, int ss, int grid, cudaStream_t s) {            \
-    return launch_batch_t<R>(A, Q, ns, det, bvk, ss, grid, s);                              \
+    return launch_batch_t<R, EV>(A, Q, ns, det, bvk, ss, grid, s);                          \
   }
 
 }  // namespace mcv

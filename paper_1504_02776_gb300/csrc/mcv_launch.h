@@ -33,9 +33,14 @@ cudaError_t adjoint_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* bl
 // batched launch: blocks per SM of its kernel (also sets the kernel's shared-memory limit;
 // call before the first launch of a shape), and the launch itself.  ss: every simulation
 // has the sample in A (kept in kernel parameter space).
-cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int ss, int* blocks);
+// ev: some simulation appends to an event list (the kernels that can)
+cudaError_t batch_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int ss, int ev,
+                                int* blocks);
 cudaError_t launch_batch(const TraceArgs& A, const BatchArgs& Q, int fp_mode, int ns, int det,
-                         int bvk, int ss, int grid, cudaStream_t s);
+                         int bvk, int ss, int ev, int grid, cudaStream_t s);
+// random FP64 atomic adds (mcv_bench_atomics)
+cudaError_t launch_atomics(double* hist, int64_t nb, int64_t n_adds, uint64_t seed, int grid,
+                           cudaStream_t s);
 // sets the message mcv_last_error() returns to the calling thread
 void set_last_error(const std::string& msg);
 
