@@ -73,6 +73,9 @@ class Detector:
     phi0_rad: float = math.radians(-30.0)
     he3_n_per_A3: float = 10.0 * ATM_PA / (BOLTZMANN_J_PER_K * 295.0) * 1e-30
     he3_sig_abs_b: float = 5333.0
+    # the weight a tube leaves goes on to the next tubes the packet crosses (the paper's
+    # detector system as a composite of absorbing tubes); False: first tube only
+    multi_tube: bool = False
 
     @property
     def n_pixels(self) -> int:

@@ -55,6 +55,7 @@ class Config(C.Structure):
         ("dos_z", C.POINTER(C.c_double)), ("dos_n", C.c_int), ("dos_de", C.c_double),
         ("phonon_mass_u", C.c_double), ("phonon_nmax", C.c_int), ("phonon_p", C.c_double * 3),
         ("refl_d", C.POINTER(C.c_double)), ("refl_w", C.POINTER(C.c_double)), ("n_refl", C.c_int),
+        ("det_multi_tube", C.c_int),
         ("disp_amp", C.c_double), ("disp_c", C.c_double), ("disp_s0", C.c_double),
         ("det_kind", C.c_int), ("det_radius_m", C.c_double), ("det_height_m", C.c_double),
         ("n_phi", C.c_int), ("n_y", C.c_int), ("n_rows", C.c_int), ("packs", C.c_int * 3),
@@ -84,6 +85,8 @@ def lib():
         L.orc_trace.restype = C.c_int
         L.orc_trace_paper.argtypes = [P, C.c_int64, C.c_int64, P, P]
         L.orc_trace_paper.restype = C.c_int
+        L.orc_detect_multi.argtypes = [P, P, P, C.c_double, C.c_double, P, P, P, P, P]
+        L.orc_detect_multi.restype = C.c_int
         L.orc_n_pixels.argtypes = [P]
         L.orc_n_pixels.restype = C.c_int64
         L.orc_grad.argtypes = [P, C.c_int64, C.c_int64, P, C.c_double, C.c_int, P, P, P, P]
@@ -168,6 +171,7 @@ def make_config(wl):
         c.tube_pitch_m, c.pack_gap_m, c.phi0_rad = det.tube_pitch_m, det.pack_gap_m, det.phi0_rad
         c.he3_n_per_A3, c.he3_sig_abs_b = det.he3_n_per_A3, det.he3_sig_abs_b
         c.tof_min_s, c.tof_max_s, c.n_tof = det.tof_min_s, det.tof_max_s, det.n_tof
+        c.det_multi_tube = int(getattr(det, "multi_tube", False))
     c.seed, c.sim_id = wl.seed, wl.sim_id
     return c
 
@@ -221,6 +225,20 @@ def detect(wl, r, v, t, w, u_det):
     b = lib().orc_detect(C.byref(cfg), _ptr(r), _ptr(v), t, w, u_det, C.byref(pix),
                          C.byref(tof), C.byref(wd))
     return {"bin": b, "pixel": pix.value, "tof": tof.value, "w_det": wd.value}
+
+
+def detect_multi(wl, r, v, t, w, u):
+    """The multi-tube detector on one packet: a list of (bin, pixel, tof, w_det)."""
+    cfg = make_config(wl)
+    r = np.asarray(r, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    pix = np.zeros(3, dtype=np.int32)
+    tof, wd = np.zeros(3), np.zeros(3)
+    b = np.zeros(3, dtype=np.int64)
+    k = lib().orc_detect_multi(C.byref(cfg), _ptr(r), _ptr(v), t, w, _ptr(u), _ptr(pix),
+                               _ptr(tof), _ptr(wd), _ptr(b))
+    return [(int(b[i]), int(pix[i]), float(tof[i]), float(wd[i])) for i in range(k)]
 
 
 def trace(wl, first_id=0, n=None, packets=True, events=False, hist=True, tallies=True):

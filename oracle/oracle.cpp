@@ -1559,33 +1559,39 @@ bool config_ok(const orc_config* cfg) {
 }
 
 // ---- paper-literal recursive estimator ------------------------------------------------
+// The packet's place in the tree of interactions (supplement S3: every interactM1 splits a
+// packet into a transmitted and a scattered one): the incident packet is node 1, the
+// transmitted and scattered packets of an interaction of node x are 2x and 2x + 1.  A node
+// keys its own random numbers, so that the tree may be visited in any order; a tree deeper
+// than 61 interactions is cut (its packet leaves with the attenuation of the material ahead).
 struct PaperPacket {
   Neutron n;
-  int m;  // number of scatterings so far
+  int m;          // number of scatterings so far
+  uint64_t node;  // place in the tree
 };
+
+const uint64_t kPaperMaxNode = (uint64_t)1 << 61;
+
+// the two uniforms of block `block` of node `node` of neutron nid (the paper mode's stream)
+void paper_uniforms(const orc_config& cfg, int64_t nid, uint64_t node, int block, double u[2]) {
+  const uint32_t ctr[4] = {(uint32_t)((uint64_t)nid & 0xffffffffu), (uint32_t)((uint64_t)nid >> 32),
+                           (uint32_t)(((node & 0x3fffffffu) << 2) | (uint32_t)block),
+                           (uint32_t)(node >> 30)};
+  const uint32_t key[2] = {cfg.seed, cfg.sim_id ^ 0x80000000u};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  u[0] = u01_from(out[0], out[1]);
+  u[1] = u01_from(out[2], out[3]);
+}
 
 struct PaperRun {
   const orc_config& cfg;
   int64_t nid;
-  int event = 0;  // running event counter for this neutron's random draws
   double* hist;
   double* tallies;
 };
 
-void paper_emit(PaperRun& pr, const PaperPacket& p) {
-  EmitRecord em;
-  em.order = p.m;
-  em.n = p.n;
-  em.w = p.n.w;
-  if (p.m == 0) {
-    add_tally(pr.tallies, ORC_T_BEAMSTOP, em.w);
-    return;
-  }
-  double u[2];
-  orc_uniforms(pr.cfg.seed, pr.cfg.sim_id ^ 0x80000000u, pr.nid, pr.event++, 3, u);
-  int32_t pixel;
-  double tof, w_det;
-  int64_t bin = detect(pr.cfg, p.n.r, p.n.d, p.n.speed, p.n.t, p.n.w, u[0], &pixel, &tof, &w_det);
+void paper_record(PaperRun& pr, int64_t bin, double w_det) {
   if (bin >= 0) {
     if (pr.hist) pr.hist[bin] += w_det;
     add_tally(pr.tallies, ORC_T_WDET, w_det);
@@ -1593,9 +1599,37 @@ void paper_emit(PaperRun& pr, const PaperPacket& p) {
   } else if (bin == -2) {
     add_tally(pr.tallies, ORC_T_WOVER, w_det);
     add_tally(pr.tallies, ORC_T_NOVER, 1.0);
-  } else {
-    add_tally(pr.tallies, ORC_T_NMISS, 1.0);
   }
+}
+
+// A packet leaving the sample assembly: order 0 to the beam stop, the others to the
+// detector system (every tube crossed, with det_multi_tube).  Detector draws: blocks 3 and 0
+// of the packet's node.
+void paper_emit(PaperRun& pr, const PaperPacket& p) {
+  if (p.m == 0) {
+    add_tally(pr.tallies, ORC_T_BEAMSTOP, p.n.w);
+    return;
+  }
+  double u3[2], u0[2];
+  paper_uniforms(pr.cfg, pr.nid, p.node, 3, u3);
+  if (pr.cfg.det_multi_tube && pr.cfg.det_kind == ORC_DET_TUBES) {
+    paper_uniforms(pr.cfg, pr.nid, p.node, 0, u0);
+    const double u[3] = {u3[0], u3[1], u0[0]};
+    const double v[3] = {p.n.d.x * p.n.speed, p.n.d.y * p.n.speed, p.n.d.z * p.n.speed};
+    const double r[3] = {p.n.r.x, p.n.r.y, p.n.r.z};
+    int32_t pix[3];
+    double tof[3], wd[3];
+    int64_t bins[3];
+    const int k = orc_detect_multi(&pr.cfg, r, v, p.n.t, p.n.w, u, pix, tof, wd, bins);
+    if (k == 0) add_tally(pr.tallies, ORC_T_NMISS, 1.0);
+    for (int i = 0; i < k; ++i) paper_record(pr, bins[i], wd[i]);
+    return;
+  }
+  int32_t pixel;
+  double tof, w_det;
+  int64_t bin = detect(pr.cfg, p.n.r, p.n.d, p.n.speed, p.n.t, p.n.w, u3[0], &pixel, &tof, &w_det);
+  if (bin == -1) add_tally(pr.tallies, ORC_T_NMISS, 1.0);
+  paper_record(pr, bin, w_det);
 }
 
 // interactM1 of a homogeneous scatterer: the transmitted packet leaves the first segment
@@ -1613,9 +1647,9 @@ bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* tr
   transmitted->n.r = add(in.n.r, scale(in.n.d, sb[0]));
   transmitted->n.t = in.n.t + sb[0] / in.n.speed;
   transmitted->n.w = in.n.w * std::exp(-mu * len);
-  const uint32_t sim = cfg.sim_id ^ 0x80000000u;
+  transmitted->node = 2 * in.node;
   double u[2];
-  orc_uniforms(cfg.seed, sim, pr.nid, pr.event, 0, u);
+  paper_uniforms(cfg, pr.nid, in.node, 0, u);
   double ell = u[0] * len;
   double s = sa[0] + ell;
   PaperPacket p = in;
@@ -1625,9 +1659,8 @@ bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* tr
   int k = 0;
   if (sc.nk == 2 && !(u[1] * (sc.ksig_b[0] + sc.ksig_b[1]) < sc.ksig_b[0])) k = 1;
   double a[2], b[2];
-  orc_uniforms(cfg.seed, sim, pr.nid, pr.event, 1, a);
-  orc_uniforms(cfg.seed, sim, pr.nid, pr.event, 2, b);
-  pr.event++;
+  paper_uniforms(cfg, pr.nid, in.node, 1, a);
+  paper_uniforms(cfg, pr.nid, in.node, 2, b);
   double uk[4] = {a[0], a[1], b[0], b[1]};
   KernelOut ko;
   if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko, sc.rot_y, sc.ksig_b[k]))
@@ -1636,6 +1669,7 @@ bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* tr
   p.n.d = ko.d;
   p.n.speed = ko.speed;
   p.m = in.m + 1;
+  p.node = 2 * in.node + 1;
   *scattered = p;
   return true;
 }
@@ -1652,16 +1686,15 @@ PaperPacket paper_propagate_out(const orc_config& cfg, PaperPacket p) {
 }
 
 void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies) {
-  PaperRun pr{cfg, nid, 0, hist, tallies};
+  PaperRun pr{cfg, nid, hist, tallies};
   Neutron n0;
   if (!make_beam(cfg, nid, &n0)) return;
   {
     Segment seg[8];
     if (assembly_segments(cfg, n0.r, n0.d, seg) > 0) add_tally(tallies, ORC_T_NHIT, 1.0);
   }
-  std::vector<PaperPacket> toscatter{PaperPacket{n0, 0}};
-  const int kRoundLimit = 64;
-  for (int rounds = 0; !toscatter.empty() && rounds < kRoundLimit; ++rounds) {
+  std::vector<PaperPacket> toscatter{PaperPacket{n0, 0, 1}};
+  while (!toscatter.empty()) {
     std::vector<PaperPacket> scattered;
     for (const PaperPacket& p : toscatter) {
       if (p.n.w < cfg.min_prob) continue;
@@ -1671,7 +1704,7 @@ void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies
         paper_emit(pr, p);
         continue;
       }
-      if (p.m >= cfg.max_orders) {  // maximum order reached: leave with attenuation
+      if (p.m >= cfg.max_orders || p.node >= kPaperMaxNode) {  // leave with attenuation
         paper_emit(pr, paper_propagate_out(cfg, p));
         continue;
       }
@@ -1681,7 +1714,7 @@ void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies
       bool alive = true;
       // interactM_path1 of the homogeneous scatterer: repeated interactM1 while the
       // scattered packet stays inside; what is left is handed back to the next round
-      while (cur.m < cfg.max_orders) {
+      while (cur.m < cfg.max_orders && cur.node < kPaperMaxNode) {
         if (cur.n.w < cfg.min_prob) {
           alive = false;
           break;
@@ -1700,7 +1733,6 @@ void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies
     }
     toscatter.swap(scattered);
   }
-  for (const PaperPacket& p : toscatter) paper_emit(pr, paper_propagate_out(cfg, p));
 }
 
 }  // namespace
@@ -1789,6 +1821,95 @@ int64_t orc_detect(const orc_config* cfg, const double r[3], const double v[3], 
   double speed = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   Vec3 d = {v[0] / speed, v[1] / speed, v[2] / speed};
   return detect(*cfg, Vec3{r[0], r[1], r[2]}, d, speed, t, w, u_det, pixel, tof, w_det);
+}
+
+int orc_detect_multi(const orc_config* cfg, const double r_[3], const double v[3], double t,
+                     double w, const double u[3], int32_t pixel[3], double tof[3],
+                     double w_det[3], int64_t bin[3]) {
+  // Ray tracing in the detector system as a composite of absorbing tubes (section 2.4.3):
+  // the candidate tubes as in the single-tube detector, every one the ray enters absorbing
+  // its share of the weight the earlier tubes left.
+  if (cfg->det_kind != ORC_DET_TUBES) return 0;
+  const double speed = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const Vec3 d = {v[0] / speed, v[1] / speed, v[2] / speed};
+  const Vec3 r = {r_[0], r_[1], r_[2]};
+  const double R = cfg->det_radius_m;
+  double sR;
+  if (!exit_cylinder(R, r, d, &sR)) return 0;
+  const Vec3 P = add(r, scale(d, sR));
+  int row = -1, row_off = 0;
+  for (int i = 0, off = 0; i < cfg->n_rows; off += cfg->packs[i], ++i) {
+    if (std::fabs(P.y - cfg->row_y_m[i]) <= 0.5 * cfg->tube_len_m) {
+      row = i;
+      row_off = off;
+      break;
+    }
+  }
+  if (row < 0) return 0;
+  const int tpp = cfg->tubes_per_pack;
+  const double period = tpp * cfg->tube_pitch_m + cfg->pack_gap_m;
+  const double arc = (std::atan2(P.x, P.z) - cfg->phi0_rad) * R;
+  const double pk = std::floor(arc / period);
+  double k = std::floor((arc - pk * period) / cfg->tube_pitch_m);
+  if (k > tpp - 1) k = tpp - 1;
+  const int64_t g = (int64_t)pk * tpp + (int64_t)k;
+  const int64_t n_tubes_row = (int64_t)cfg->packs[row] * tpp;
+  const double y_lo = cfg->row_y_m[row] - 0.5 * cfg->tube_len_m;
+  const double y_hi = cfg->row_y_m[row] + 0.5 * cfg->tube_len_m;
+  // the candidates the ray enters, by entry distance
+  int64_t tube[3];
+  double s_in[3], s_out[3];
+  int m = 0;
+  for (int64_t c = g - 1; c <= g + 1; ++c) {
+    if (c < 0 || c >= n_tubes_row) continue;
+    const int64_t pc = c / tpp, tc = c % tpp;
+    const double phic = cfg->phi0_rad + (pc * period + (tc + 0.5) * cfg->tube_pitch_m) / R;
+    double s1, s2;
+    if (!tube_interval(R, std::sin(phic), std::cos(phic), cfg->tube_r_m, r, d, &s1, &s2)) continue;
+    double ys1, ys2;
+    if (d.y == 0.0) {
+      if (!(r.y >= y_lo && r.y <= y_hi)) continue;
+      ys1 = -kInf;
+      ys2 = kInf;
+    } else {
+      const double a = (y_lo - r.y) / d.y, b = (y_hi - r.y) / d.y;
+      ys1 = std::min(a, b);
+      ys2 = std::max(a, b);
+    }
+    const double a_in = std::max(std::max(s1, ys1), 0.0), a_out = std::min(s2, ys2);
+    if (!(a_out > a_in)) continue;
+    int at = m++;
+    while (at > 0 && s_in[at - 1] > a_in) {  // insertion by entry distance
+      tube[at] = tube[at - 1];
+      s_in[at] = s_in[at - 1];
+      s_out[at] = s_out[at - 1];
+      --at;
+    }
+    tube[at] = c;
+    s_in[at] = a_in;
+    s_out[at] = a_out;
+  }
+  const double mu = 100.0 * cfg->he3_n_per_A3 * cfg->he3_sig_abs_b * 2200.0 / speed;
+  const double pix_len = cfg->tube_len_m / cfg->pixels_per_tube;
+  const double dt = (cfg->tof_max_s - cfg->tof_min_s) / cfg->n_tof;
+  double left = w;
+  for (int i = 0; i < m; ++i) {
+    const double L = s_out[i] - s_in[i];
+    const double pabs = -std::expm1(-mu * L);
+    const double x = -std::log1p(-u[i] * pabs) / mu;
+    const double s_abs = s_in[i] + x;
+    const double y_abs = r.y + s_abs * d.y;
+    int64_t j = (int64_t)std::floor((y_abs - y_lo) / pix_len);
+    j = std::min<int64_t>(std::max<int64_t>(j, 0), cfg->pixels_per_tube - 1);
+    const int64_t pc = tube[i] / tpp, tc = tube[i] % tpp;
+    pixel[i] = (int32_t)(((row_off + pc) * tpp + tc) * cfg->pixels_per_tube + j);
+    tof[i] = t + s_abs / speed;
+    w_det[i] = left * pabs;
+    left = left * (1.0 - pabs);
+    const double fb = std::floor((tof[i] - cfg->tof_min_s) / dt);
+    bin[i] = (fb >= 0.0 && fb < (double)cfg->n_tof) ? (int64_t)pixel[i] * cfg->n_tof + (int64_t)fb : -2;
+  }
+  return m;
 }
 
 int64_t orc_n_pixels(const orc_config* cfg) { return n_pixels(*cfg); }

@@ -69,6 +69,9 @@ typedef struct {
   const double* refl_d;
   const double* refl_w;
   int n_refl;
+  /* detector: the packet's weight left after a tube goes on to the next tubes it crosses
+     (the detector system as a composite of absorbing tubes); 0: first tube only */
+  int det_multi_tube;
   /* scattering from a dispersion surface E(Q) = disp_amp sqrt(1 - (cos(c Qx) cos(c Qz))^2),
      c = disp_c (A), with S(Q) = disp_s0, Q in the crystal frame of scatterer 0's rotation */
   double disp_amp, disp_c, disp_s0;
@@ -135,6 +138,14 @@ int orc_kernel_scatter(const orc_config* cfg, int ktype, double speed, const dou
                        const double u[4], double* speed_out, double d_out[3],
                        double* factor, orc_event* ev);
 
+/* the multi-tube detector (tube system): the packet is absorbed in every tube it crosses
+   among the three candidates, in order of entry, each taking its absorption probability of
+   the weight the earlier ones left; u[i] draws the absorption depth in the i-th tube.  Writes
+   up to 3 detections (bin >= 0, -2 out of the time window); returns their number */
+int orc_detect_multi(const orc_config* cfg, const double r[3], const double v[3], double t,
+                     double w, const double u[3], int32_t pixel[3], double tof[3],
+                     double w_det[3], int64_t bin[3]);
+
 /* detect one packet: returns bin (>= 0), -1 miss, -2 tof overflow */
 int64_t orc_detect(const orc_config* cfg, const double r[3], const double v[3], double t,
                    double w, double u_det, int32_t* pixel, double* tof, double* w_det);
@@ -146,7 +157,12 @@ int orc_trace(const orc_config* cfg, int64_t first_id, int64_t n, orc_packet* pa
               orc_event* events, double* hist, double* tallies);
 
 /* paper-literal recursive estimator (scatterM / interactM_path1 / interactM1);
-   histogram and tallies only */
+   histogram and tallies only.  Random numbers: key (seed, sim_id ^ 0x80000000), counter
+   (nid lo, nid hi, 4 (node mod 2^30) + block, node / 2^30) where node is the packet's place
+   in the tree of interactions (the incident packet 1; an interaction of node x gives its
+   transmitted packet 2x and its scattered packet 2x + 1), so that any order of visiting the
+   tree draws the same numbers; blocks 0-2 of a node serve its interaction, blocks 3 and 0 of
+   an emitted packet's node its detector draws */
 int orc_trace_paper(const orc_config* cfg, int64_t first_id, int64_t n, double* hist,
                     double* tallies);
 

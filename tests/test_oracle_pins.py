@@ -614,3 +614,88 @@ def test_gradient_zero_table_entry_continues_path():
         fd = (vals[0][1] - vals[1][1]) / (vals[0][0] - vals[1][0])
         an = g["dsqe"].ravel()[e]
         assert abs(fd - an) < 1e-3 * abs(an), (e, fd, an)
+
+
+def test_multi_tube_detector_absorbs_the_remainder():
+    """The detector system as a composite of absorbing tubes (the paper's section 2.4.3): a
+    packet running nearly along the tube ring crosses several candidate tubes; each absorbs
+    1 - e^{-mu L} of the weight the earlier ones left, L the chord through it (computed here
+    from the closest approach of the line to the tube axis), at a depth drawn from the
+    truncated exponential."""
+    import dataclasses
+    det = dataclasses.replace(mi.tube_detector(), multi_tube=True)
+    wl = mi.config2(n=1).replace(detector=det)
+    R, rt = det.radius_m, det.tube_r_m
+    period = det.tubes_per_pack * det.tube_pitch_m + det.pack_gap_m
+    checked = 0
+    cases = [(pack, tube, off, tilt) for pack in (10, 40, 77) for tube in (1, 4)
+             for off, tilt in ((0.004, 0.02), (0.002, 0.01), (0.006, 0.03))]
+    for pack, tube, off, tilt in cases:
+        # a tube of row 1 (y = 0) and a ray just inside the ring, heading along it
+        phic = det.phi0_rad + (pack * period + (tube + 0.5) * det.tube_pitch_m) / R
+        phi0 = phic - 0.045
+        rad = R - off
+        r0 = np.array([rad * math.sin(phi0), 0.013, rad * math.cos(phi0)])
+        tang = np.array([math.cos(phi0), 0.0, -math.sin(phi0)])
+        d = tang + np.array([math.sin(phi0), 0.0, math.cos(phi0)]) * tilt
+        d /= np.linalg.norm(d)
+        speed = speed_of(50.0)
+        u = np.array([0.3, 0.7, 0.5])
+        hits = oracle.detect_multi(wl, r0, speed * d, 1e-3, 1.0, u)
+        if len(hits) < 2:
+            continue
+        # the expected chain: the three candidates around where the ray leaves the ring
+        sR = -(r0[0] * d[0] + r0[2] * d[2]) / (d[0] ** 2 + d[2] ** 2)
+        a = d[0] ** 2 + d[2] ** 2
+        cr = r0[0] * d[2] - r0[2] * d[0]
+        sR += math.sqrt(R * R * a - cr * cr) / a
+        P = r0 + sR * d
+        arc = (math.atan2(P[0], P[2]) - det.phi0_rad) * R
+        p = math.floor(arc / period)
+        k = min(math.floor((arc - p * period) / det.tube_pitch_m), det.tubes_per_pack - 1)
+        g = p * det.tubes_per_pack + k
+        mu = 100 * det.he3_n_per_A3 * det.he3_sig_abs_b * 2200.0 / speed
+        chords = []
+        for c in (g - 1, g, g + 1):
+            pc, tc = divmod(c, det.tubes_per_pack)
+            ph = det.phi0_rad + (pc * period + (tc + 0.5) * det.tube_pitch_m) / R
+            axis = np.array([R * math.sin(ph), R * math.cos(ph)])
+            rel = np.array([r0[0], r0[2]]) - axis
+            dh = np.array([d[0], d[2]])
+            t_c = -(rel @ dh) / (dh @ dh)
+            b2 = (rel @ rel) - (rel @ dh) ** 2 / (dh @ dh)
+            if b2 >= rt * rt:
+                continue
+            half = math.sqrt((rt * rt - b2) / (dh @ dh))
+            s_in, s_out = max(t_c - half, 0.0), t_c + half
+            if s_out > s_in:
+                chords.append((s_in, s_out, c))
+        chords.sort()
+        assert len(chords) == len(hits)
+        left = 1.0
+        for (s_in, s_out, c), (b, pix, tof, wd), ui in zip(chords, hits, u):
+            pabs = -math.expm1(-mu * (s_out - s_in))
+            assert abs(wd - left * pabs) < 1e-12 * left * pabs
+            x = -math.log1p(-ui * pabs) / mu
+            assert abs(tof - (1e-3 + (s_in + x) / speed)) < 1e-12 * tof
+            assert pix // det.pixels_per_tube == (sum(det.packs[:1]) * det.tubes_per_pack + c)
+            left *= 1 - pabs
+        checked += 1
+    assert checked >= 4, checked
+
+
+def test_paper_recursion_with_multi_tube_detector_agrees_with_chain():
+    """With the multi-tube detector the paper mode still estimates the chain's histogram:
+    packets from the sample cross one tube (a single layer), so the remainder that goes on
+    changes nothing beyond Monte Carlo error."""
+    import dataclasses
+    det = dataclasses.replace(mi.tube_detector(n_tof=25), multi_tube=True)
+    base = mi.config2(n=1).replace(detector=det)
+    tc, tp = [], []
+    for b in range(8):
+        wl = base.replace(seed=200 + b, n=8000)
+        tc.append(oracle.trace(wl, packets=False)["tallies"][oracle.T_WDET])
+        tp.append(oracle.trace_paper(wl)["tallies"][oracle.T_WDET])
+    tc, tp = np.array(tc), np.array(tp)
+    z = (tc.mean() - tp.mean()) / math.sqrt(tc.var(ddof=1) / 8 + tp.var(ddof=1) / 8)
+    assert abs(z) < 4
