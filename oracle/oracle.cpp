@@ -184,17 +184,18 @@ bool slab_interval(double half, double p, double dp, double* s1, double* s2, End
   return true;
 }
 
-// Keep [a,b] clipped to s >= 0 if it has positive length.  Its length b - lo loses the
+// Keep [a,b] clipped to s >= s0 (s0 = 0 but for the paper mode's transmitted packets, which
+// keep their line's origin and the distance s0 travelled along it) if it has positive length.  Its length b - lo loses the
 // relative precision |a| + |b| over b - lo (a point close to the exit surface), and the
 // error scales of the ends over b - lo (a clipped start, lo = 0, is exact).  ra, rb
 // (optional) receive the error scales of the kept ends, ra0 the start's rounding scale
 // alone (an error of the start point or direction moves the point placed beyond the start
 // surface with that surface).
 int push_segment(End a, End b, double* sa, double* sb, double* ra, double* rb, double* ra0,
-                 int n) {
-  double lo = std::max(a.s, 0.0);
+                 int n, double s0) {
+  double lo = std::max(a.s, s0);
   if (b.s > lo) {
-    double e_lo = a.s > 0.0 ? a.er + a.ep : 0.0;
+    double e_lo = a.s > s0 ? a.er + a.ep : 0.0;
     if (ORC_CONDITION)
       g_kappa += (std::fabs(a.s) + std::fabs(b.s) + e_lo + b.er + b.ep) / (b.s - lo);
     sa[n] = lo;
@@ -202,7 +203,7 @@ int push_segment(End a, End b, double* sa, double* sb, double* ra, double* rb, d
     if (ORC_CONDITION && ra) {
       ra[n] = e_lo;
       rb[n] = b.er + b.ep;
-      ra0[n] = a.s > 0.0 ? a.er : 0.0;
+      ra0[n] = a.s > s0 ? a.er : 0.0;
     }
     return n + 1;
   }
@@ -214,7 +215,8 @@ End later(End u, End v) { return v.s > u.s ? v : u; }
 End earlier(End u, End v) { return v.s < u.s ? v : u; }
 
 int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double sb[2],
-                   double ra[2] = nullptr, double rb[2] = nullptr, double ra0[2] = nullptr) {
+                   double ra[2] = nullptr, double rb[2] = nullptr, double ra0[2] = nullptr,
+                   double s0 = 0.0) {
   // Shapes and their combination (the hollow cylinder is a difference of two cylinders),
   // paper section 2.4.2 ("Shapes" and constructive solid geometry).  ra, rb (optional)
   // receive the error scales of the segment ends, ra0 the starts' rounding scales.
@@ -223,7 +225,7 @@ int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double
   if (sc.kind == ORC_SOLID_CYL) {
     if (!cylinder_interval(sc.dims[0], r, d, &c1, &c2, ec)) return 0;
     if (!slab_interval(0.5 * sc.dims[1], r.y, d.y, &y1, &y2, ey, 0.0, g_dprev.y)) return 0;
-    return push_segment(later(ec[0], ey[0]), earlier(ec[1], ey[1]), sa, sb, ra, rb, ra0, 0);
+    return push_segment(later(ec[0], ey[0]), earlier(ec[1], ey[1]), sa, sb, ra, rb, ra0, 0, s0);
   }
   if (sc.kind == ORC_HOLLOW_CYL) {
     if (!cylinder_interval(sc.dims[1], r, d, &c1, &c2, ec)) return 0;
@@ -233,10 +235,10 @@ int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double
     double i1, i2;
     End ei[2];
     if (!cylinder_interval(sc.dims[0], r, d, &i1, &i2, ei))
-      return push_segment(lo, hi, sa, sb, ra, rb, ra0, 0);
+      return push_segment(lo, hi, sa, sb, ra, rb, ra0, 0, s0);
     int n = 0;
-    n = push_segment(lo, earlier(hi, ei[0]), sa, sb, ra, rb, ra0, n);
-    n = push_segment(later(lo, ei[1]), hi, sa, sb, ra, rb, ra0, n);
+    n = push_segment(lo, earlier(hi, ei[0]), sa, sb, ra, rb, ra0, n, s0);
+    n = push_segment(later(lo, ei[1]), hi, sa, sb, ra, rb, ra0, n, s0);
     return n;
   }
   if (sc.kind == ORC_BLOCK) {
@@ -257,7 +259,7 @@ int shape_segments(const orc_scatterer& sc, Vec3 r, Vec3 d, double sa[2], double
     if (!slab_interval(0.5 * sc.dims[2], rb_.z, db.z, &a, &b, e, 3.0, pz)) return 0;
     lo = later(lo, e[0]);
     hi = earlier(hi, e[1]);
-    return push_segment(lo, hi, sa, sb, ra, rb, ra0, 0);
+    return push_segment(lo, hi, sa, sb, ra, rb, ra0, 0, s0);
   }
   return 0;
 }
@@ -271,11 +273,11 @@ struct Segment {
 
 // All material segments ahead of the ray, sorted by entry distance (ray tracing in a
 // composite scatterer, section 2.4.3 "Ray Tracing").
-int assembly_segments(const orc_config& cfg, Vec3 r, Vec3 d, Segment* out) {
+int assembly_segments(const orc_config& cfg, Vec3 r, Vec3 d, Segment* out, double s0 = 0.0) {
   int n = 0;
   for (int j = 0; j < cfg.n_scat; ++j) {
     double sa[2], sb[2], ra[2], rb[2], ra0[2];
-    int m = shape_segments(cfg.scat[j], r, d, sa, sb, ra, rb, ra0);
+    int m = shape_segments(cfg.scat[j], r, d, sa, sb, ra, rb, ra0, s0);
     for (int i = 0; i < m; ++i) out[n++] = {sa[i], sb[i], j, ra[i], rb[i], ra0[i]};
   }
   for (int i = 1; i < n; ++i) {  // insertion sort by entry
@@ -1564,10 +1566,15 @@ bool config_ok(const orc_config* cfg) {
 // transmitted and scattered packets of an interaction of node x are 2x and 2x + 1.  A node
 // keys its own random numbers, so that the tree may be visited in any order; a tree deeper
 // than 61 interactions is cut (its packet leaves with the attenuation of the material ahead).
+// A transmitted packet goes on along its parent's line: it keeps the line's origin (n.r, and
+// n.t there) and the distance s0 travelled along it, and the material ahead is what lies
+// beyond s0 on that line.  (Re-tracing from the exit point instead, rounded onto or just
+// inside the surface it left, would meet a sliver of the material behind it again and again.)
 struct PaperPacket {
   Neutron n;
   int m;          // number of scatterings so far
   uint64_t node;  // place in the tree
+  double s0;      // distance travelled along the line from n.r
 };
 
 const uint64_t kPaperMaxNode = (uint64_t)1 << 61;
@@ -1603,8 +1610,9 @@ void paper_record(PaperRun& pr, int64_t bin, double w_det) {
 }
 
 // A packet leaving the sample assembly: order 0 to the beam stop, the others to the
-// detector system (every tube crossed, with det_multi_tube).  Detector draws: blocks 3 and 0
-// of the packet's node.
+// detector system (every tube crossed, with det_multi_tube), met along the packet's line from
+// its origin (the tubes lie metres beyond the sample, far past s0).  Detector draws: blocks 3
+// and 0 of the packet's node.
 void paper_emit(PaperRun& pr, const PaperPacket& p) {
   if (p.m == 0) {
     add_tally(pr.tallies, ORC_T_BEAMSTOP, p.n.w);
@@ -1632,30 +1640,28 @@ void paper_emit(PaperRun& pr, const PaperPacket& p) {
   paper_record(pr, bin, w_det);
 }
 
-// interactM1 of a homogeneous scatterer: the transmitted packet leaves the first segment
-// attenuated; the scattered one is taken at a uniform point of the first segment.
-bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* transmitted,
-                     PaperPacket* scattered) {
+// interactM1 of homogeneous scatterer j on its first segment [sa, sb] ahead of the packet:
+// the transmitted packet leaves the segment attenuated; the scattered one is taken at a
+// uniform point of it (scattered->m stays negative when the kernel cannot scatter).
+void paper_interact1(PaperRun& pr, int j, double sa, double sb, const PaperPacket& in,
+                     PaperPacket* transmitted, PaperPacket* scattered) {
   const orc_config& cfg = pr.cfg;
   const orc_scatterer& sc = cfg.scat[j];
-  double sa[2], sb[2];
-  int ns = shape_segments(sc, in.n.r, in.n.d, sa, sb);
-  if (ns == 0) return false;
-  double len = sb[0] - sa[0];
+  double len = sb - sa;
   double mu = mu_total(sc, in.n.speed);
   *transmitted = in;
-  transmitted->n.r = add(in.n.r, scale(in.n.d, sb[0]));
-  transmitted->n.t = in.n.t + sb[0] / in.n.speed;
+  transmitted->s0 = sb;
   transmitted->n.w = in.n.w * std::exp(-mu * len);
   transmitted->node = 2 * in.node;
   double u[2];
   paper_uniforms(cfg, pr.nid, in.node, 0, u);
   double ell = u[0] * len;
-  double s = sa[0] + ell;
+  double s = sa + ell;
   PaperPacket p = in;
   p.n.r = add(in.n.r, scale(in.n.d, s));
   p.n.t = in.n.t + s / in.n.speed;
   p.n.w = in.n.w * mu_scatt(sc) * len * std::exp(-mu * ell);
+  p.s0 = 0.0;
   int k = 0;
   if (sc.nk == 2 && !(u[1] * (sc.ksig_b[0] + sc.ksig_b[1]) < sc.ksig_b[0])) k = 1;
   double a[2], b[2];
@@ -1664,21 +1670,20 @@ bool paper_interact1(PaperRun& pr, int j, const PaperPacket& in, PaperPacket* tr
   double uk[4] = {a[0], a[1], b[0], b[1]};
   KernelOut ko;
   if (!kernel_scatter(cfg, sc.ktype[k], p.n.speed, p.n.d, uk, &ko, sc.rot_y, sc.ksig_b[k]))
-    return true;
+    return;
   p.n.w = p.n.w * ko.factor;
   p.n.d = ko.d;
   p.n.speed = ko.speed;
   p.m = in.m + 1;
   p.node = 2 * in.node + 1;
   *scattered = p;
-  return true;
 }
 
 // the packet still inside a scatterer after its last allowed scattering leaves with the
 // attenuation of all material ahead
 PaperPacket paper_propagate_out(const orc_config& cfg, PaperPacket p) {
   Segment seg[8];
-  int ns = assembly_segments(cfg, p.n.r, p.n.d, seg);
+  int ns = assembly_segments(cfg, p.n.r, p.n.d, seg, p.s0);
   double tau = 0.0;
   for (int i = 0; i < ns; ++i) tau += mu_total(cfg.scat[seg[i].j], p.n.speed) * (seg[i].sb - seg[i].sa);
   p.n.w = p.n.w * std::exp(-tau);
@@ -1693,13 +1698,13 @@ void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies
     Segment seg[8];
     if (assembly_segments(cfg, n0.r, n0.d, seg) > 0) add_tally(tallies, ORC_T_NHIT, 1.0);
   }
-  std::vector<PaperPacket> toscatter{PaperPacket{n0, 0, 1}};
+  std::vector<PaperPacket> toscatter{PaperPacket{n0, 0, 1, 0.0}};
   while (!toscatter.empty()) {
     std::vector<PaperPacket> scattered;
     for (const PaperPacket& p : toscatter) {
       if (p.n.w < cfg.min_prob) continue;
       Segment seg[8];
-      int ns = assembly_segments(cfg, p.n.r, p.n.d, seg);
+      int ns = assembly_segments(cfg, p.n.r, p.n.d, seg, p.s0);
       if (ns == 0) {  // exiting: nothing ahead
         paper_emit(pr, p);
         continue;
@@ -1710,24 +1715,31 @@ void paper_one(const orc_config& cfg, int64_t nid, double* hist, double* tallies
       }
       // interactM_path1 of the composite: the first constituent met delegates
       int j = seg[0].j;
+      double sa = seg[0].sa, sb = seg[0].sb;
       PaperPacket cur = p;
       bool alive = true;
-      // interactM_path1 of the homogeneous scatterer: repeated interactM1 while the
-      // scattered packet stays inside; what is left is handed back to the next round
-      while (cur.m < cfg.max_orders && cur.node < kPaperMaxNode) {
+      // interactM_path1 of the homogeneous scatterer: interactM1 on the segment met, then
+      // again on the scatterer's first segment ahead while the scattered packet may scatter;
+      // what is left is handed back to the next round
+      while (true) {
         if (cur.n.w < cfg.min_prob) {
           alive = false;
           break;
         }
         PaperPacket tr, sc;
         sc.m = -1;
-        if (!paper_interact1(pr, j, cur, &tr, &sc)) break;
+        paper_interact1(pr, j, sa, sb, cur, &tr, &sc);
         scattered.push_back(tr);
         if (sc.m < 0) {
           alive = false;
           break;
         }
         cur = sc;
+        if (!(cur.m < cfg.max_orders && cur.node < kPaperMaxNode)) break;
+        double a2[2], b2[2];
+        if (shape_segments(cfg.scat[j], cur.n.r, cur.n.d, a2, b2) == 0) break;
+        sa = a2[0];
+        sb = b2[0];
       }
       if (alive) scattered.push_back(cur);
     }
