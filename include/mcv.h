@@ -60,6 +60,11 @@ enum { MCV_KERNEL_ISO = 0, MCV_KERNEL_SQE = 1, MCV_KERNEL_BVK = 2, MCV_KERNEL_PH
        MCV_KERNEL_BRAGG = 4, MCV_KERNEL_DISP = 5 };
 enum { MCV_DET_NONE = 0, MCV_DET_SURFACE = 1, MCV_DET_TUBES = 2 };
 enum { MCV_FP64 = 0, MCV_FP32 = 1 };
+/* estimators of the sample assembly: the bounded chain (the scattering point drawn over all
+ * the material ahead) or the paper's own recursion (supplement S3: scatterM, interactM_path1,
+ * interactM1; the point drawn on the first segment only, every interaction splitting the
+ * packet in a transmitted and a scattered one) */
+enum { MCV_EST_CHAIN = 0, MCV_EST_PAPER = 1 };
 
 /* tally slots (FP64 accumulators) */
 enum {
@@ -173,6 +178,7 @@ typedef struct {
   mcv_phonon phonon;
   mcv_bragg bragg;
   mcv_dispersion dispersion;
+  int estimator;           /* MCV_EST_CHAIN (0) or MCV_EST_PAPER */
 } mcv_sample;
 
 /* Detector system.  SURFACE: ideal cylinder of radius_m, height_m, efficiency 1, n_phi x
@@ -195,6 +201,8 @@ typedef struct {
   double he3_n_per_A3, he3_sig_abs_b;
   double tof_min_s, tof_max_s;
   int n_tof;
+  int multi_tube;          /* TUBES with MCV_EST_PAPER: the weight a tube leaves goes on to the
+                              next tubes the packet crosses (1), or first tube only (0) */
 } mcv_detector;
 
 /* Structure-of-arrays neutron packets (device).  x..vz and w are float arrays in
@@ -304,6 +312,13 @@ mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint
  *                the same kernel (fused path); order-0 packets go to MCV_T_BEAMSTOP;
  *   packets    : n*(max_orders+1) slots, slot i*(max_orders+1)+o holds the packet of
  *                order o of the i-th neutron (order -1 if none) with its id.
+ * With sample->estimator == MCV_EST_PAPER the sample assembly is traced by the paper's own
+ * recursion (one neutron per GPU thread walking its tree of packets; random numbers keyed
+ * by the packet's place in the tree: key (seed, sim_id ^ 0x80000000), counter (id lo, id hi,
+ * 4 (node mod 2^30) + block, node / 2^30), the incident packet node 1 and the transmitted and
+ * scattered packets of node x nodes 2x and 2x + 1); it needs det and hist and takes no `in`,
+ * `packets` or event list.  A tree that outgrows the thread's stack of 48 waiting packets
+ * loses them and sets the device error flag (MCV_EDEVICE at mcv_sync).
  * Errors: MCV_EINVAL for NULL/ill-formed descriptions, n < 0, unsupported combinations. */
 mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample,
                             const mcv_beam_params* beam, const mcv_neutrons* in,

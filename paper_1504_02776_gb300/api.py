@@ -36,6 +36,7 @@ def detector_struct(det):
     d.pack_gap_m, d.phi0_rad = det.pack_gap_m, det.phi0_rad
     d.he3_n_per_A3, d.he3_sig_abs_b = det.he3_n_per_A3, det.he3_sig_abs_b
     d.tof_min_s, d.tof_max_s, d.n_tof = det.tof_min_s, det.tof_max_s, det.n_tof
+    d.multi_tube = int(getattr(det, "multi_tube", False))
     return d
 
 
@@ -117,7 +118,7 @@ class EventBuffers:
                 "count": self.n()}
 
 
-def sample_struct(wl, fp_mode, table=None):
+def sample_struct(wl, fp_mode, table=None, estimator=B.EST_CHAIN):
     """mcv_sample from a workload; `table` is the device FP32 S(Q,E) tensor (if any); the
     phonon kernel's tables are built on the device once per description (phonon_for)."""
     s = B.Sample()
@@ -133,6 +134,7 @@ def sample_struct(wl, fp_mode, table=None):
             t.kernel[k] = kt
             t.kernel_sig_b[k] = ks
     s.max_orders, s.min_prob, s.fp_mode = wl.max_orders, wl.min_prob, fp_mode
+    s.estimator = estimator
     if wl.sqe is not None:
         if table is None:
             raise ValueError("the S(Q,E) table must be on the device")
@@ -212,10 +214,12 @@ class Context:
         return counts, tallies
 
     def trace(self, wl, fp_mode=B.FP64, n=None, first_id=0, table=None, counts=None,
-              tallies=None, beam_in=None, sync=True, events=None, hist=True):
+              tallies=None, beam_in=None, sync=True, events=None, hist=True,
+              estimator=B.EST_CHAIN):
         """Fused path: source -> sample -> detector -> histogram; returns (counts, tallies).
         events: an EventBuffers that receives every detected packet as well (event mode);
-        hist=False with events: no histogram, only the tallies and the event list."""
+        hist=False with events: no histogram, only the tallies and the event list;
+        estimator=B.EST_PAPER: the paper's recursive estimator instead of the chain."""
         n = wl.n if n is None else n
         if table is None:
             table = self.table(wl)
@@ -224,7 +228,7 @@ class Context:
                 counts, tallies = self.new_hist(wl.detector)
             else:
                 tallies = torch.zeros(B.MCV_NTALLY, dtype=torch.float64, device="cuda")
-        sample = sample_struct(wl, fp_mode, table)
+        sample = sample_struct(wl, fp_mode, table, estimator)
         det = detector_struct(wl.detector)
         hist = B.Hist(_ptr(counts), _ptr(tallies),
                       C.pointer(events.struct()) if events is not None else None)

@@ -19,6 +19,7 @@ SHAPE_SOLID_CYL, SHAPE_HOLLOW_CYL, SHAPE_BLOCK = 0, 1, 2
 KERNEL_ISO, KERNEL_SQE, KERNEL_BVK, KERNEL_PHONON, KERNEL_BRAGG, KERNEL_DISP = 0, 1, 2, 3, 4, 5
 DET_NONE, DET_SURFACE, DET_TUBES = 0, 1, 2
 FP64, FP32 = 0, 1
+EST_CHAIN, EST_PAPER = 0, 1
 (T_BEAMSTOP, T_WDET, T_WOVER, T_NDET, T_NOVER, T_NMISS, T_NHIT, T_NEMIT) = range(8)
 
 STATUS_NAMES = {0: "MCV_OK", 1: "MCV_EINVAL", 2: "MCV_ENOMEM", 3: "MCV_ECUDA",
@@ -71,7 +72,7 @@ class Sample(C.Structure):
     _fields_ = [("n_scatterers", C.c_int), ("scat", Scatterer * MCV_MAX_SCATTERERS),
                 ("max_orders", C.c_int), ("min_prob", C.c_double), ("fp_mode", C.c_int),
                 ("sqe", Sqe), ("bvk", Bvk), ("phonon", Phonon), ("bragg", Bragg),
-                ("dispersion", Dispersion)]
+                ("dispersion", Dispersion), ("estimator", C.c_int)]
 
 
 class Detector(C.Structure):
@@ -83,7 +84,7 @@ class Detector(C.Structure):
                 ("tube_pitch_m", C.c_double), ("pack_gap_m", C.c_double),
                 ("phi0_rad", C.c_double), ("he3_n_per_A3", C.c_double),
                 ("he3_sig_abs_b", C.c_double), ("tof_min_s", C.c_double),
-                ("tof_max_s", C.c_double), ("n_tof", C.c_int)]
+                ("tof_max_s", C.c_double), ("n_tof", C.c_int), ("multi_tube", C.c_int)]
 
 
 class Neutrons(C.Structure):

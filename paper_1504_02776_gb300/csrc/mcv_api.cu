@@ -221,6 +221,8 @@ mcv_status build_detector(const mcv_detector* d, mcv::DetP<double>* D) {
   if (!(d->radius_m > 0) || !is_finite(d->radius_m)) return fail(MCV_EINVAL, "bad detector radius");
   D->kind = d->kind;
   D->radius = d->radius_m;
+  if (d->multi_tube != 0 && d->multi_tube != 1) return fail(MCV_EINVAL, "multi_tube must be 0 or 1");
+  D->multi_tube = d->kind == MCV_DET_TUBES ? d->multi_tube : 0;
   D->win = tof_window(d->tof_min_s, d->tof_max_s, d->n_tof);
   int64_t npix = 0;
   if (d->kind == MCV_DET_SURFACE) {
@@ -462,6 +464,7 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
 
 void cast_detector(const mcv::DetP<double>& d, mcv::DetP<float>* f) {
   f->kind = d.kind;
+  f->multi_tube = d.multi_tube;
   f->n_phi = d.n_phi;
   f->n_y = d.n_y;
   f->n_rows = d.n_rows;
@@ -748,10 +751,16 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
     st = event_sink(hist->events, sim_id, &A.ev);
     if (st != MCV_OK) return st;
   }
+  const bool paper = sample->estimator == MCV_EST_PAPER;
+  if (sample->estimator != MCV_EST_CHAIN && !paper) return fail(MCV_EINVAL, "unknown estimator");
+  if (paper && (!fused || in || packets || (hist && hist->events)))
+    return fail(MCV_EINVAL, "the paper estimator needs a detector and a histogram, and takes no "
+                            "stored beam, packet slots or event list");
   if (n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;
   A.keys = philox_keys(seed, sim_id);
+  A.pkeys = philox_keys(seed, sim_id ^ 0x80000000u);
   A.first_id = first_id;
   A.n = n;
   A.stop_on_zero = 1;
@@ -785,6 +794,14 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   A.err = ctx->d_err;
   const int detk = fused ? A.Dd.kind : MCV_DET_NONE;
   const int fp = sample->fp_mode;
+  if (paper) {
+    cast_all(&A);
+    // one neutron per thread; the thread's stack of packets lives in local memory
+    cudaError_t e = mcv::launch_paper(A, fp, detk, ctx->sm_count * 16,
+                                      static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "paper kernel launch");
+    return MCV_OK;
+  }
   int& occ = ctx->occ[fp][ns_index(A.Sd.ns)][detk][A.Sd.wide ? 1 : 0];
   if (occ == 0) {
     cudaError_t e = mcv::trace_blocks_per_sm(fp, A.Sd.ns, detk, A.Sd.wide, &occ);

@@ -91,6 +91,30 @@ constexpr int kKernelsPowder = (1 << MCV_KERNEL_ISO) | (1 << MCV_KERNEL_SQE);
 constexpr int kKernelsAll = kKernelsPowder | (1 << MCV_KERNEL_BVK) | (1 << MCV_KERNEL_PHONON) |
                             (1 << MCV_KERNEL_BRAGG) | (1 << MCV_KERNEL_DISP);
 
+// One scattering kernel of a scatterer: kernel kk (0 or 1) of sc, draws from rng's blocks 1-2
+// of event o.  Returns whether the packet scatters (false: a parameter-independent zero).
+template <typename R, int KS, class Rng>
+__device__ __forceinline__ bool scatter_kernel(const SampleP<R>& S, const ScatP<R>& sc, int kk,
+                                               const Rng& rng, int o, Ray<R>* n,
+                                               Scatter<R>* out, int* err) {
+  const int ktype = kk ? sc.ktype1 : sc.ktype0;
+  if ((KS & (1 << MCV_KERNEL_ISO)) && ktype == MCV_KERNEL_ISO) {
+    kernel_iso<R>(rng, o, n, out);
+    return true;
+  }
+  if ((KS & (1 << MCV_KERNEL_SQE)) && ktype == MCV_KERNEL_SQE)
+    return kernel_sqe<R>(S, rng, o, n, out, err);
+  if ((KS & (1 << MCV_KERNEL_BVK)) && ktype == MCV_KERNEL_BVK)
+    return kernel_bvk<R>(S, sc.cos_rot, sc.sin_rot, rng, o, n, out);
+  if ((KS & (1 << MCV_KERNEL_PHONON)) && ktype == MCV_KERNEL_PHONON)
+    return kernel_phonon<R>(S, rng, o, n, out);
+  if ((KS & (1 << MCV_KERNEL_BRAGG)) && ktype == MCV_KERNEL_BRAGG)
+    return kernel_bragg<R>(S, kk ? sc.ksig1 : sc.ksig0, rng, o, n, out);
+  if ((KS & (1 << MCV_KERNEL_DISP)) && ktype == MCV_KERNEL_DISP)
+    return kernel_disp<R>(S, sc.cos_rot, sc.sin_rot, rng, o, n, out);
+  return false;
+}
+
 template <typename R, int NS, int KS, class P, class Rng>
 __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R>& S,
                                              const Rng& rng, Lane<R>& L,
@@ -129,23 +153,8 @@ __device__ __forceinline__ bool step_scatter(const TraceArgs& A, const SampleP<R
   L.n.z += s_pt * L.n.dz;
   L.n.t.add(s_pt / L.n.speed);
   const int kk = (sc.nk == 2 && !(u_k * sc.ksig_sum < sc.ksig0)) ? 1 : 0;
-  const int ktype = kk ? sc.ktype1 : sc.ktype0;
   Scatter<R> out;
-  bool ok = false;
-  if ((KS & (1 << MCV_KERNEL_ISO)) && ktype == MCV_KERNEL_ISO) {
-    kernel_iso<R>(rng, L.o, &L.n, &out);
-    ok = true;
-  } else if ((KS & (1 << MCV_KERNEL_SQE)) && ktype == MCV_KERNEL_SQE) {
-    ok = kernel_sqe<R>(S, rng, L.o, &L.n, &out, &pol.err);
-  } else if ((KS & (1 << MCV_KERNEL_BVK)) && ktype == MCV_KERNEL_BVK) {
-    ok = kernel_bvk<R>(S, sc.cos_rot, sc.sin_rot, rng, L.o, &L.n, &out);
-  } else if ((KS & (1 << MCV_KERNEL_PHONON)) && ktype == MCV_KERNEL_PHONON) {
-    ok = kernel_phonon<R>(S, rng, L.o, &L.n, &out);
-  } else if ((KS & (1 << MCV_KERNEL_BRAGG)) && ktype == MCV_KERNEL_BRAGG) {
-    ok = kernel_bragg<R>(S, kk ? sc.ksig1 : sc.ksig0, rng, L.o, &L.n, &out);
-  } else if ((KS & (1 << MCV_KERNEL_DISP)) && ktype == MCV_KERNEL_DISP) {
-    ok = kernel_disp<R>(S, sc.cos_rot, sc.sin_rot, rng, L.o, &L.n, &out);
-  }
+  const bool ok = scatter_kernel<R, KS>(S, sc, kk, rng, L.o, &L.n, &out, &pol.err);
   if (!ok) {
     pol.clear(A, L.idx, L.o + 1);
     return false;

@@ -395,9 +395,11 @@ struct Seg {
   int j;
 };
 
+// [a, b] clipped to s >= s0 (s0 = 0 but for the paper estimator's transmitted packets, which
+// keep their line's origin and the distance s0 travelled along it), kept if not empty
 template <typename R>
-__device__ __forceinline__ void put_seg(R a, R b, int j, Seg<R>* out, int* cnt) {
-  const R lo = Mth<R>::fmax(a, R(0));
+__device__ __forceinline__ void put_seg(R a, R b, int j, R s0, Seg<R>* out, int* cnt) {
+  const R lo = Mth<R>::fmax(a, s0);
   if (b > lo) {
     out[*cnt].a = lo;
     out[*cnt].b = b;
@@ -409,14 +411,15 @@ __device__ __forceinline__ void put_seg(R a, R b, int j, Seg<R>* out, int* cnt) 
 // Segments of one scatterer's shape (section 2.4.2, shapes combined by CSG: the hollow
 // cylinder is a difference).  Writes up to two segments at out[0..1].
 template <typename R>
-__device__ __forceinline__ int shape_segs(const ScatP<R>& S, int j, const Ray<R>& n, Seg<R>* out) {
+__device__ __forceinline__ int shape_segs(const ScatP<R>& S, int j, const Ray<R>& n, Seg<R>* out,
+                                          R s0 = R(0)) {
   using M = Mth<R>;
   int cnt = 0;
   R c1, c2, y1, y2;
   if (S.shape == MCV_SHAPE_SOLID_CYL) {
     if (cyl_span<R>((R)S.dim0, n.x, n.z, n.dx, n.dz, &c1, &c2) &&
         slab_span<R>((R)S.half_h, n.y, n.dy, &y1, &y2))
-      put_seg<R>(M::fmax(c1, y1), M::fmin(c2, y2), j, out, &cnt);
+      put_seg<R>(M::fmax(c1, y1), M::fmin(c2, y2), j, s0, out, &cnt);
   } else if (S.shape == MCV_SHAPE_HOLLOW_CYL) {
     if (cyl_span<R>((R)S.dim1, n.x, n.z, n.dx, n.dz, &c1, &c2) &&
         slab_span<R>((R)S.half_h, n.y, n.dy, &y1, &y2)) {
@@ -424,10 +427,10 @@ __device__ __forceinline__ int shape_segs(const ScatP<R>& S, int j, const Ray<R>
       if (hi > lo) {
         R i1, i2;
         if (!cyl_span<R>((R)S.dim0, n.x, n.z, n.dx, n.dz, &i1, &i2)) {
-          put_seg<R>(lo, hi, j, out, &cnt);
+          put_seg<R>(lo, hi, j, s0, out, &cnt);
         } else {
-          put_seg<R>(lo, M::fmin(hi, i1), j, out, &cnt);
-          put_seg<R>(M::fmax(lo, i2), hi, j, out, &cnt);
+          put_seg<R>(lo, M::fmin(hi, i1), j, s0, out, &cnt);
+          put_seg<R>(M::fmax(lo, i2), hi, j, s0, out, &cnt);
         }
       }
     }
@@ -445,7 +448,7 @@ __device__ __forceinline__ int shape_segs(const ScatP<R>& S, int j, const Ray<R>
     ok = ok && slab_span<R>(R(0.5) * S.dim2, zb, dzb, &a, &b);
     lo = M::fmax(lo, a);
     hi = M::fmin(hi, b);
-    if (ok) put_seg<R>(lo, hi, j, out, &cnt);
+    if (ok) put_seg<R>(lo, hi, j, s0, out, &cnt);
   }
   return cnt;
 }
@@ -453,7 +456,8 @@ __device__ __forceinline__ int shape_segs(const ScatP<R>& S, int j, const Ray<R>
 // All segments ahead in the sample assembly, sorted by entry (ray tracing in a composite,
 // section 2.4.3).  NS = number of scatterers (compile time); unused entries get a = +inf.
 template <typename R, int NS>
-__device__ __forceinline__ int assembly_segs(const SampleP<R>& S, const Ray<R>& n, Seg<R> (&seg)[2 * NS]) {
+__device__ __forceinline__ int assembly_segs(const SampleP<R>& S, const Ray<R>& n, Seg<R> (&seg)[2 * NS],
+                                             R s0 = R(0)) {
   using M = Mth<R>;
   int total = 0;
 #pragma unroll
@@ -463,7 +467,7 @@ __device__ __forceinline__ int assembly_segs(const SampleP<R>& S, const Ray<R>& 
     two[1].a = M::inf();
     two[0].b = two[1].b = R(0);
     two[0].j = two[1].j = j;
-    const int c = (j < S.ns) ? shape_segs<R>(S.s[j], j, n, two) : 0;
+    const int c = (j < S.ns) ? shape_segs<R>(S.s[j], j, n, two, s0) : 0;
     seg[2 * j] = two[0];
     seg[2 * j + 1] = two[1];
     total += c;

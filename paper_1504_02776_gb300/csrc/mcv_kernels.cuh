@@ -844,6 +844,13 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const __grid_constant
   run_chain<R, NS, DET, KS, Adjoint<R, DET>>(A, tu, pol);
 }
 
+}  // namespace mcv
+
+// the paper's recursive estimator (its kernel uses kThreads)
+#include "mcv_paper.cuh"
+
+namespace mcv {
+
 // ---- launchers, one set per real type -----------------------------------------------------
 // The fused waves with an event list are instantiated in translation units of their own
 // (mcv_fp32_ev.cu, mcv_fp64_ev.cu); these declare their entry points.
@@ -1046,6 +1053,29 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   return launch_adjoint_ns<R, 4>(A, det, grid, s);
 }
 
+// the paper's recursive estimator
+template <typename R, int NS, int KS>
+cudaError_t launch_paper_nk(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  if (det == MCV_DET_SURFACE)
+    paper_kernel<R, NS, MCV_DET_SURFACE, KS><<<grid, kPaperThreads, 0, s>>>(A);
+  else
+    paper_kernel<R, NS, MCV_DET_TUBES, KS><<<grid, kPaperThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_paper_t(const TraceArgs& A, int det, int grid, cudaStream_t s) {
+  const bool all = A.Sd.wide;
+  if (A.Sd.ns <= 1)
+    return all ? launch_paper_nk<R, 1, kKernelsAll>(A, det, grid, s)
+               : launch_paper_nk<R, 1, kKernelsPowder>(A, det, grid, s);
+  if (A.Sd.ns == 2)
+    return all ? launch_paper_nk<R, 2, kKernelsAll>(A, det, grid, s)
+               : launch_paper_nk<R, 2, kKernelsPowder>(A, det, grid, s);
+  return all ? launch_paper_nk<R, 4, kKernelsAll>(A, det, grid, s)
+             : launch_paper_nk<R, 4, kKernelsPowder>(A, det, grid, s);
+}
+
 // defines the fused-trace entry points of one real type (mcv_fp32.cu / mcv_fp64.cu)
 #define MCV_DEFINE_TRACE_ENTRY_POINTS(R, SUFFIX)                                            \
   cudaError_t launch_trace_##SUFFIX(const TraceArgs& A, int det, int grid, cudaStream_t s) { \
@@ -1076,6 +1106,9 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
   }                                                                                         \
   cudaError_t adjoint_blocks_per_sm_##SUFFIX(int ns, int det, int bvk, int* blocks) {       \
     return adjoint_blocks_per_sm_t<R>(ns, det, bvk, blocks);                                \
+  }                                                                                         \
+  cudaError_t launch_paper_##SUFFIX(const TraceArgs& A, int det, int grid, cudaStream_t s) { \
+    return launch_paper_t<R>(A, det, grid, s);                                              \
   }
 
 // defines the batched entry points of one real type and event flavour EV (mcv_batch_fp32.cu,

@@ -29,6 +29,8 @@ cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
                         double* g, double* loss, int* err, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
+// the paper's recursive estimator (one neutron per thread, grid-stride)
+cudaError_t launch_paper(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s);
 cudaError_t adjoint_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks);
 // batched launch: blocks per SM of its kernel (also sets the kernel's shared-memory limit;
 // call before the first launch of a shape), and the launch itself.  ss: every simulation

@@ -20,6 +20,8 @@ cudaError_t launch_detect_f64(const TraceArgs& A, const EventsArgs& E, int det, 
                               cudaStream_t s);
 cudaError_t launch_adjoint_f32(const TraceArgs& A, int det, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_f64(const TraceArgs& A, int det, int grid, cudaStream_t s);
+cudaError_t launch_paper_f32(const TraceArgs& A, int det, int grid, cudaStream_t s);
+cudaError_t launch_paper_f64(const TraceArgs& A, int det, int grid, cudaStream_t s);
 cudaError_t adjoint_blocks_per_sm_f32(int ns, int det, int bvk, int* blocks);
 cudaError_t adjoint_blocks_per_sm_f64(int ns, int det, int bvk, int* blocks);
 cudaError_t batch_blocks_per_sm_f32(int ns, int det, int bvk, int ss, int* blocks);
@@ -169,6 +171,10 @@ cudaError_t launch_detect(const TraceArgs& A, const EventsArgs& E, int fp_mode, 
 
 cudaError_t launch_adjoint(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s) {
   return fp_mode == MCV_FP32 ? launch_adjoint_f32(A, det, grid, s) : launch_adjoint_f64(A, det, grid, s);
+}
+
+cudaError_t launch_paper(const TraceArgs& A, int fp_mode, int det, int grid, cudaStream_t s) {
+  return fp_mode == MCV_FP32 ? launch_paper_f32(A, det, grid, s) : launch_paper_f64(A, det, grid, s);
 }
 
 cudaError_t adjoint_blocks_per_sm(int fp_mode, int ns, int det, int bvk, int* blocks) {

@@ -137,6 +137,7 @@ struct DetP {
   R miss_r_in, miss_y_top, miss_y_bot;
   int miss_phi;
   R miss_a_x, miss_a_z, miss_b_x, miss_b_z;
+  int multi_tube;   // the paper estimator's detector: the remainder goes on to the next tubes
   R tube_u[2 * MCV_MAX_TUBES_PER_ROW];  // sin, cos of every tube centre angle of a row
 };
 
@@ -149,6 +150,7 @@ struct TraceArgs {
   BeamP<double> Bd;
   uint32_t seed, sim_id;
   PhiloxKeys keys;  // round keys of (seed, sim_id)
+  PhiloxKeys pkeys; // round keys of (seed, sim_id ^ 0x80000000): the paper estimator's streams
   int64_t first_id, n;
   // fused outputs
   double* hist;
