@@ -37,11 +37,11 @@ N_DEFAULT = 100_000_000
 XU_WEIGHT = 8.0
 
 
-def load_opcount():
-    """Operations per incident neutron of the powder run, counted on an instrumented oracle
-    run (oracle/opcount.py; the condition estimate compiled out): fp, int, xu per neutron,
-    and per oracle function with its calls."""
-    p = os.path.join(ROOT, "profiles", "opcount_powder_sqe.json")
+def load_opcount(name="powder_sqe"):
+    """Operations per incident neutron of a workload, counted on an instrumented oracle run
+    (oracle/opcount.py; the condition estimate compiled out): fp, int, xu per neutron, and per
+    oracle function with its calls."""
+    p = os.path.join(ROOT, "profiles", "opcount_%s.json" % name)
     try:
         with open(p) as f:
             return json.load(f)
@@ -162,6 +162,11 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi's start-up (driver queries) stalled host-device copies: the timed region
+        # starts once it is sampling (3 s at most)
+        t0 = time.monotonic()
+        while not self.rows and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -359,6 +364,87 @@ def batch_extras(ctx, args):
     return out
 
 
+def kernel_extras(ctx, args):
+    """The other scattering kernels, the paper's recursive estimator and event mode, each on
+    its own workload (args.kernel_n neutrons, one launch per step, histogram and tallies
+    cleared before every launch, outside its events), FP32 and FP64: incoming neutrons/s,
+    detected events/s, and the FP32 launch against the ALU roof (operations per neutron from
+    the instrumented oracle run of the same workload)."""
+    import torch
+
+    import mcv_inputs as mi
+    from paper_1504_02776_gb300 import api, binding as B
+    n = args.kernel_n
+    evb = api.EventBuffers(max(1, n // 4))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_mhz = float(load_peaks().get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * sm_mhz * 1e6
+    opcount_of = {"phonon_vanadium": "phonon_vanadium", "bragg_aluminium": "bragg_aluminium",
+                  "dispersion_crystal": "dispersion_crystal",
+                  "paper_estimator_powder": "paper_powder_sqe",
+                  "event_mode_powder": "powder_sqe"}
+    cases = [
+        ("phonon_vanadium", mi.vanadium_powder(n), B.EST_CHAIN, None,
+         "vanadium-like hollow cylinder, incoherent phonon expansion from a DOS (elastic, "
+         "one-phonon, multi-phonon to n=5), 100 meV, up to 5 orders"),
+        ("bragg_aluminium", mi.aluminium_powder(n), B.EST_CHAIN, None,
+         "aluminium-like powder hollow cylinder, Debye-Scherrer reflections + weak incoherent "
+         "elastic, 100 meV, up to 5 orders"),
+        ("dispersion_crystal", mi.dispersion_crystal(n), B.EST_CHAIN, None,
+         "1 cm cube crystal, the paper's example dispersion surface (2.5 meV band), 7.5 meV, "
+         "up to 5 orders"),
+        ("paper_estimator_powder", mi.config2(n=n), B.EST_PAPER, None,
+         "the powder S(Q,E) run of the headline through the paper's recursive estimator "
+         "(every interaction splits into transmitted and scattered packets)"),
+        ("event_mode_powder", mi.config2(n=n), B.EST_CHAIN, evb,
+         "the powder S(Q,E) run of the headline with every detected packet also appended to "
+         "an event list (pixel, simulation, time of flight, weight)"),
+    ]
+    out = {"neutrons_per_launch": n}
+    for name, wl, est, ev, what in cases:
+        table = ctx.table(wl)
+        counts, tallies = ctx.new_hist(wl.detector)
+        res = {"workload": what}
+        for fp, key in ((B.FP32, "fp32"), (B.FP64, "fp64")):
+            reps = args.kernel_reps if fp == B.FP32 else 1
+            marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(reps + 1)]
+            for a, b in marks:  # the first launch warms up; the clears are not timed
+                counts.zero_()
+                tallies.zero_()
+                if ev is not None:
+                    ev.count.zero_()
+                a.record()
+                ctx.trace(wl, fp_mode=fp, table=table, counts=counts, tallies=tallies,
+                          sync=False, estimator=est, events=ev)
+                b.record()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in marks[1:]) / reps
+            ctx.sync()
+            t = tallies.cpu().numpy()
+            res[key] = {"value": n / (ms / 1e3), "unit": "neutrons/s", "ms": ms,
+                        "detected_events_per_s": float(t[B.T_NDET]) / (ms / 1e3)}
+            if ev is not None:
+                res[key]["events_listed"] = min(ev.n(), ev.capacity)
+        opc = load_opcount(opcount_of[name])
+        if opc is not None:
+            per_n, per_n_cons = ops_per_neutron(opc, wl)
+            ms = res["fp32"]["ms"]
+            res["roofline_fp32"] = {
+                "bound": "alu", "achieved": per_n * n / (ms / 1e3) / 1e12,
+                "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": per_n * n / (ms / 1e3) / peak_ops,
+                "frac_conservative": per_n_cons * n / (ms / 1e3) / peak_ops,
+                "ops_per_neutron": per_n,
+                "ops_source": "oracle/opcount.py --workload %s" % opcount_of[name],
+                "timing": "CUDA events around each launch (histogram clears outside)"}
+        out[name] = res
+        del counts, tallies
+    del evb
+    torch.cuda.empty_cache()
+    return out
+
+
 def grad_extras(ctx, value64):
     """The differentiable form (config 4): chi-squared loss of the 1e7-neutron powder run
     against a seeded target and its adjoint gradient w.r.t. the 200 x 400 S(Q,E) table and
@@ -488,36 +574,8 @@ def run_ours(args):
     value = world * N * args.steps / (ms / 1e3)
     det_per_s = t[B.T_NDET] * args.steps / (ms / 1e3)
 
-    # ---- plain FP64 forward, one simulation per launch, same workload and histogram
-    sample64 = api.sample_struct(wl, B.FP64, table)
-    step(sample64)
-    ctx.sync()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    f0.record(stream)
-    for _ in range(args.fp64_steps):
-        step(sample64)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = f0.elapsed_time(f1)
-    fm = torch.tensor([ms64], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(fm, op=dist.ReduceOp.MAX)
-    ms64 = float(fm.item())
-    value64 = world * N * args.fp64_steps / (ms64 / 1e3)
-    ctx.sync()
-
-    # ---- batched forms (rank 0 of a single-GPU run; they hold up to 170 GB of histograms)
-    # and the differentiable form
-    batched = None
-    differentiable = None
-    extras = "none" if args.no_batch else args.extras
-    if world == 1 and extras in ("all", "batch"):
-        batched = batch_extras(ctx, args)
-    if world == 1 and extras in ("all", "grad"):
-        differentiable = grad_extras(ctx, value64)
-
-    # ---- end to end through the public API with host buffers: every step copies the
+    # ---- end to end through the public API with host buffers, right after the device-timed
+    # region and before anything else runs: every step copies the
     # table in from pinned host memory and its histogram and tallies out to pinned host
     # memory; two histogram buffers and a copy stream let step k's read-back overlap step
     # k+1's trace (the timed region ends when the last read-back has landed)
@@ -563,7 +621,9 @@ def run_ours(args):
             e2e_step(k)
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks_e2e = ClockSampler(local)
         barrier()
+        clocks_e2e.start()
         g0.record(stream)
         for k in range(args.e2e_steps):
             e2e_step(k)
@@ -572,6 +632,7 @@ def run_ours(args):
                 stream.wait_event(ev)
         g1.record(stream)
         torch.cuda.synchronize()
+        clk_e2e = clocks_e2e.stop()
         gms = g0.elapsed_time(g1)
         gm = torch.tensor([gms], dtype=torch.float64, device="cuda")
         if world > 1:
@@ -582,9 +643,42 @@ def run_ours(args):
                "d2h_bytes_per_step": int((counts.numel() + tallies.numel()) * 8),
                "ms_per_step": gms / args.e2e_steps, "steps": args.e2e_steps,
                "pipelining": "two histogram buffers; step k's read-back (split over %d copy "
-                             "streams) overlaps step k+1's trace" % n_copy}
+                             "streams) overlaps step k+1's trace" % n_copy,
+               "clocks": clk_e2e}
         del dev_bufs, host_bufs
         ctx.sync()
+
+    # ---- plain FP64 forward, one simulation per launch, same workload and histogram
+    sample64 = api.sample_struct(wl, B.FP64, table)
+    step(sample64)
+    ctx.sync()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    f0.record(stream)
+    for _ in range(args.fp64_steps):
+        step(sample64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    fm = torch.tensor([ms64], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(fm, op=dist.ReduceOp.MAX)
+    ms64 = float(fm.item())
+    value64 = world * N * args.fp64_steps / (ms64 / 1e3)
+    ctx.sync()
+
+    # ---- batched forms (rank 0 of a single-GPU run; they hold up to 170 GB of histograms)
+    # and the differentiable form
+    batched = None
+    differentiable = None
+    extras = "none" if args.no_batch else args.extras
+    if world == 1 and extras in ("all", "batch"):
+        batched = batch_extras(ctx, args)
+    if world == 1 and extras in ("all", "grad"):
+        differentiable = grad_extras(ctx, value64)
+    kernels = None
+    if world == 1 and extras in ("all", "kernels"):
+        kernels = kernel_extras(ctx, args)
 
     # ---- roofline of the fused trace kernel (ALU bound): operations per neutron counted on an
     # instrumented oracle run, against the FP32/INT32 lane rate
@@ -663,6 +757,7 @@ def run_ours(args):
         "atomics": atomics,
         "batched": batched,
         "differentiable": differentiable,
+        "kernels": kernels,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
         "collective": collective,
@@ -693,9 +788,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the batched and the differentiable forms (same as --extras none)")
-    ap.add_argument("--extras", default="all", choices=["all", "batch", "grad", "none"],
-                    help="which of the batched and differentiable forms to run")
+                    help="skip the batched, differentiable and per-kernel forms (same as "
+                         "--extras none)")
+    ap.add_argument("--extras", default="all",
+                    choices=["all", "batch", "grad", "kernels", "none"],
+                    help="which of the batched, differentiable and per-kernel forms to run")
+    ap.add_argument("--kernel-n", type=int, default=10_000_000)
+    ap.add_argument("--kernel-reps", type=int, default=3)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--crystal-fp64-stride", type=int, default=18)
     args = ap.parse_args()

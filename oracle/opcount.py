@@ -18,7 +18,11 @@ statement of a block is classified by its operation and the type of its result:
 and weighted by its block's count.  Loads, stores, copies and control flow are not counted.
 The counts are per incident neutron of the sample, in total and per oracle function.
 
-  python oracle/opcount.py [--n N] [--out profiles/opcount_powder_sqe.json]
+  python oracle/opcount.py [--workload powder_sqe] [--n N] [--out FILE]
+
+Workloads: powder_sqe (the 100 meV powder S(Q,E) run), phonon_vanadium, bragg_aluminium,
+dispersion_crystal (each through the bounded chain, orc_trace) and paper_powder_sqe (the
+powder S(Q,E) run through the paper's recursive estimator, orc_trace_paper).
 """
 from __future__ import annotations
 
@@ -48,25 +52,57 @@ OPS = re.compile(r"\s(\+|-|\*|/|%|&|\||\^|<<|>>|r<<|r>>|w\*|h\*|<=|>=|<|>|==|!=|
                  r"uneq|unlt|unle|ungt|unge|ord|unord)\s")
 
 
-def _run_sample(lib_path, n, first_id=0):
-    """Runs the powder workload's first n neutrons through orc_trace of lib_path (in this
-    process: the profile counters are written when it exits)."""
+# name -> (workload constructor of mcv_inputs, estimator, description)
+WORKLOADS = {
+    "powder_sqe": ("config2", "chain",
+                   "config 2 powder S(Q,E) (hollow cylinder, 100 meV, up to 5 orders, "
+                   "117,760-pixel tube system)"),
+    "phonon_vanadium": ("vanadium_powder", "chain",
+                        "vanadium-like hollow cylinder, incoherent phonon expansion from a DOS, "
+                        "100 meV, up to 5 orders, 117,760-pixel tube system"),
+    "bragg_aluminium": ("aluminium_powder", "chain",
+                        "aluminium-like powder hollow cylinder, Debye-Scherrer reflections + "
+                        "weak incoherent elastic, 100 meV, up to 5 orders"),
+    "dispersion_crystal": ("dispersion_crystal", "chain",
+                           "1 cm cube crystal, the paper's example dispersion surface, 7.5 meV, "
+                           "up to 5 orders"),
+    "paper_powder_sqe": ("config2", "paper",
+                         "config 2 powder S(Q,E) through the paper's recursive estimator"),
+}
+
+
+def workload(name, n):
+    sys.path.insert(0, ROOT)
+    import mcv_inputs as mi
+    make = getattr(mi, WORKLOADS[name][0])
+    return make(n=n)
+
+
+def _run_sample(lib_path, n, name="powder_sqe", first_id=0):
+    """Runs the workload's first n neutrons through orc_trace (orc_trace_paper for the paper
+    estimator) of lib_path, in this process: the profile counters are written when it
+    exits."""
     sys.path.insert(0, ROOT)
     import numpy as np
-    import mcv_inputs as mi
     import oracle as O
     L = C.CDLL(lib_path)
-    L.orc_trace.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
-                            C.c_void_p, C.c_void_p]
-    L.orc_trace.restype = C.c_int
-    wl = mi.config2(n=n)
+    wl = workload(name, n)
     cfg = O.make_config(wl)
     hist = np.zeros(wl.detector.n_bins)
     tal = np.zeros(O.NTALLY)
-    rc = L.orc_trace(C.byref(cfg), first_id, n, None, None, hist.ctypes.data_as(C.c_void_p),
-                     tal.ctypes.data_as(C.c_void_p))
+    if WORKLOADS[name][1] == "paper":
+        L.orc_trace_paper.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
+        L.orc_trace_paper.restype = C.c_int
+        rc = L.orc_trace_paper(C.byref(cfg), first_id, n, hist.ctypes.data_as(C.c_void_p),
+                               tal.ctypes.data_as(C.c_void_p))
+    else:
+        L.orc_trace.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p]
+        L.orc_trace.restype = C.c_int
+        rc = L.orc_trace(C.byref(cfg), first_id, n, None, None,
+                         hist.ctypes.data_as(C.c_void_p), tal.ctypes.data_as(C.c_void_p))
     if rc:
-        raise RuntimeError("orc_trace failed")
+        raise RuntimeError("the oracle's trace failed")
     return tal
 
 
@@ -206,7 +242,7 @@ def parse_dump(text):
     return out
 
 
-def count(n=100_000):
+def count(n=100_000, name="powder_sqe"):
     src = os.path.join(HERE, "oracle.cpp")
     with tempfile.TemporaryDirectory() as d:
         obj = os.path.join(d, "oracle.o")
@@ -218,8 +254,8 @@ def count(n=100_000):
         subprocess.run(["g++", "-shared", "-fprofile-generate", "-o", lib1, obj], check=True)
         # run in a child process so that the profile is written at its exit
         code = ("import sys; sys.path.insert(0, %r); sys.path.insert(0, %r); "
-                "import opcount; t = opcount._run_sample(%r, %d); "
-                "import json; print(json.dumps(t.tolist()))" % (HERE, ROOT, lib1, n))
+                "import opcount; t = opcount._run_sample(%r, %d, %r); "
+                "import json; print(json.dumps(t.tolist()))" % (HERE, ROOT, lib1, n, name))
         r = subprocess.run([sys.executable, "-c", code], check=True, capture_output=True,
                            text=True)
         tallies = json.loads(r.stdout.strip().splitlines()[-1])
@@ -246,14 +282,16 @@ def count(n=100_000):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="powder_sqe", choices=sorted(WORKLOADS))
     ap.add_argument("--n", type=int, default=100_000)
-    ap.add_argument("--out", default=os.path.join(ROOT, "profiles", "opcount_powder_sqe.json"))
+    ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = count(a.n)
-    res["command"] = "python oracle/opcount.py --n %d" % a.n
-    res["workload"] = ("config 2 powder S(Q,E) (hollow cylinder, 100 meV, up to 5 orders, "
-                       "117,760-pixel tube system), neutron ids 0..n-1")
-    with open(a.out, "w") as f:
+    out = a.out or os.path.join(ROOT, "profiles", "opcount_%s.json" % a.workload)
+    res = count(a.n, a.workload)
+    res["command"] = "python oracle/opcount.py --workload %s --n %d" % (a.workload, a.n)
+    res["workload"] = WORKLOADS[a.workload][2] + ", neutron ids 0..n-1"
+    res["estimator"] = WORKLOADS[a.workload][1]
+    with open(out, "w") as f:
         json.dump(res, f, indent=1)
     pn = res["per_neutron"]
     print("per neutron: fp %.1f  int %.1f  xu %.1f" % (pn["fp"], pn["int"], pn["xu"]))

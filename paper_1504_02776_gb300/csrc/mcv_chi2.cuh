@@ -6,7 +6,6 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <math_constants.h>
 
 namespace mcv {
 
@@ -22,8 +21,13 @@ __device__ __forceinline__ double recip_ge1(double d) {
   return x;
 }
 
-// A measured bin must be a finite count >= 0.
-__device__ __forceinline__ bool target_ok(double T) { return T >= 0.0 && T < CUDART_INF; }
+// A measured bin must be a finite count >= 0: from its bits with integer operations (no
+// FP64 comparison: the loss kernel tests every bin), a sign bit clear (or -0) and an
+// exponent below the all-ones one of infinities and NaNs.
+__device__ __forceinline__ bool target_ok(double T) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(T);
+  return ((u >> 63) == 0ull || u == 0x8000000000000000ull) && ((u >> 52) & 0x7ffull) != 0x7ffull;
+}
 
 // One bin: its gradient entry g_b, its loss term added to *part.  A bin with nothing
 // simulated and nothing measured (both values +0: almost all of a large detector's bins) is
