@@ -496,9 +496,12 @@ def run_ours(args):
         # before the first GPU call: spawned processes only
         workers = os.cpu_count() or 1
         v, n_cpu, wall = oracle_throughput(args.cpu_per_worker, workers)
+        v1, n1, wall1 = oracle_throughput(args.cpu_per_worker, 1)
         cpu_base = {"value": v, "unit": "neutrons/s", "cores": workers, "kind": "oracle",
                     "sample": "%d neutrons of the same workload (%d per process, ids from 0), "
-                              "%.1f s wall" % (n_cpu, args.cpu_per_worker, wall)}
+                              "%.1f s wall" % (n_cpu, args.cpu_per_worker, wall),
+                    "single_core": {"value": v1, "unit": "neutrons/s", "neutrons": n1,
+                                    "s": wall1, "s_scaled_to_1e8": 1e8 / v1}}
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
