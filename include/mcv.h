@@ -46,9 +46,13 @@ extern "C" {
 typedef enum {
   MCV_OK = 0,
   MCV_EINVAL = 1,    /* invalid argument: nothing was launched */
-  MCV_ENOMEM = 2,    /* the context could not allocate its own device memory */
+  MCV_ENOMEM = 2,    /* the library could not allocate its own device memory (a context's
+                        block, a batch's parameter block, the tuner's scratch histogram);
+                        nothing was launched and the context stays usable */
   MCV_ECUDA = 3,     /* a CUDA call failed (message in mcv_last_error) */
-  MCV_ETIMEOUT = 4,  /* a bounded device wait ran out */
+  MCV_ETIMEOUT = 4,  /* reserved for a bounded device wait that ran out; no kernel of this
+                        library waits on another thread, block or device, so no call
+                        returns it */
   MCV_EDEVICE = 5    /* a kernel found invalid device data: an out-of-range index, a packet
                         order above 7, a target bin that is negative or not finite
                         (reported by mcv_sync) */

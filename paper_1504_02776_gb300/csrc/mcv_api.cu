@@ -25,6 +25,11 @@ mcv_status cuda_fail(cudaError_t e, const char* where) {
   return fail(MCV_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+mcv_status alloc_fail(const std::string& msg) {
+  (void)cudaGetLastError();
+  return fail(MCV_ENOMEM, msg);
+}
+
 bool is_finite(double v) { return std::isfinite(v); }
 
 // ---- descriptions -> device parameter blocks -------------------------------------------
@@ -610,7 +615,7 @@ mcv_status mcv_create(int device, mcv_ctx** out) {
   e = cudaMalloc(&c->d_err, 256);
   if (e != cudaSuccess) {
     delete c;
-    return fail(MCV_ENOMEM, "cannot allocate the context's device block");
+    return alloc_fail("cannot allocate the context's device block");
   }
   e = cudaMemset(c->d_err, 0, 256);
   if (e != cudaSuccess) {
@@ -659,6 +664,7 @@ int64_t mcv_detector_pixels(const mcv_detector* det) {
 
 mcv_status mcv_bench_atomics(mcv_ctx* ctx, double* hist, int64_t n_bins, int64_t n_adds,
                              uint64_t seed, void* stream) {
+  mcv::host::CallRange range_("mcv_bench_atomics");
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;
   if (n_bins < 1 || n_adds < 0 || !hist) return fail(MCV_EINVAL, "bad histogram or count");
@@ -680,6 +686,7 @@ mcv_status mcv_zero(mcv_ctx* ctx, double* dst, int64_t n, void* stream) {
 mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint32_t seed,
                     uint32_t sim_id, int64_t first_id, int64_t n, mcv_neutrons* out,
                     void* stream) {
+  mcv::host::CallRange range_("mcv_beam");
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;
   if (fp_mode != MCV_FP64 && fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
@@ -716,6 +723,7 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
                             const mcv_neutrons* in, uint32_t seed, uint32_t sim_id,
                             int64_t first_id, int64_t n, const mcv_detector* det, mcv_hist* hist,
                             mcv_neutrons* packets, void* stream) {
+  mcv::host::CallRange range_("mcv_trace_sample");
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;
   mcv::TraceArgs A;
@@ -817,6 +825,7 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
 mcv_status mcv_detect(mcv_ctx* ctx, const mcv_detector* det, int fp_mode,
                       const mcv_neutrons* packets, uint32_t seed, uint32_t sim_id, mcv_hist* hist,
                       mcv_events* events, void* stream) {
+  mcv::host::CallRange range_("mcv_detect");
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;
   if (fp_mode != MCV_FP64 && fp_mode != MCV_FP32) return fail(MCV_EINVAL, "bad fp_mode");
@@ -945,6 +954,7 @@ mcv_status mcv_grad(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_param
                     int64_t n, const double* target, double scale_c, int grad_scatterer,
                     mcv_hist* hist, double* g_work, double* loss, double* dsqe, double* dsig,
                     void* stream) {
+  mcv::host::CallRange range_("mcv_grad");
   mcv::TraceArgs A;
   mcv_status st = grad_args(ctx, sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
                             grad_scatterer, hist ? hist->counts : nullptr, loss, dsqe, dsig, &A);
@@ -976,6 +986,7 @@ mcv_status mcv_adjoint(mcv_ctx* ctx, const mcv_sample* sample, const mcv_beam_pa
                        int64_t first_id, int64_t n, const double* hist, const double* target,
                        double scale_c, int grad_scatterer, double* g_work, double* loss,
                        double* dsqe, double* dsig, void* stream) {
+  mcv::host::CallRange range_("mcv_adjoint");
   mcv::TraceArgs A;
   mcv_status st = grad_args(ctx, sample, beam, det, seed, sim_id, first_id, n, target, scale_c,
                             grad_scatterer, hist, loss, dsqe, dsig, &A);

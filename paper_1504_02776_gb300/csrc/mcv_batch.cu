@@ -245,6 +245,7 @@ extern "C" {
 
 mcv_status mcv_batch_create(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
                             const mcv_detector* det, int fp_mode, mcv_batch** out) {
+  mcv::host::CallRange range_("mcv_batch_create");
   if (!out) return fail(MCV_EINVAL, "out is NULL");
   *out = nullptr;
   mcv_status st = check_ctx(ctx);
@@ -276,7 +277,7 @@ mcv_status mcv_batch_create(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
   cudaError_t e = cudaMalloc(&b->d_block, device_bytes(b->im));
   if (e != cudaSuccess) {
     delete b;
-    return fail(MCV_ENOMEM, "cannot allocate the batch's parameter block");
+    return alloc_fail("cannot allocate the batch's parameter block");
   }
   st = upload(b);
   if (st != MCV_OK) {
@@ -289,6 +290,7 @@ mcv_status mcv_batch_create(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
 }
 
 mcv_status mcv_batch_run(mcv_batch* b, void* stream) {
+  mcv::host::CallRange range_("mcv_batch_run");
   if (!b) return fail(MCV_EINVAL, "batch is NULL");
   mcv_status st = check_ctx(b->ctx);
   if (st != MCV_OK) return st;
@@ -315,6 +317,7 @@ mcv_status mcv_batch_destroy(mcv_batch* b) {
 }
 
 mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream) {
+  mcv::host::CallRange range_("mcv_batch_tune");
   if (!b) return fail(MCV_EINVAL, "batch is NULL");
   mcv_status st = check_ctx(b->ctx);
   if (st != MCV_OK) return st;
@@ -328,7 +331,7 @@ mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream) {
   double* scratch = nullptr;
   const int64_t nb = b->A.Dd.n_bins;
   cudaError_t e = cudaMalloc(&scratch, (size_t)(nb + MCV_NTALLY) * sizeof(double));
-  if (e != cudaSuccess) return fail(MCV_ENOMEM, "cannot allocate the tuner's scratch histogram");
+  if (e != cudaSuccess) return alloc_fail("cannot allocate the tuner's scratch histogram");
   e = cudaMemsetAsync(scratch, 0, (size_t)(nb + MCV_NTALLY) * sizeof(double), s);
   tr.total_n = 0;
   for (int k = 0; k < tr.nsims; ++k) {
@@ -412,6 +415,7 @@ mcv_status mcv_batch_tune(mcv_batch* b, int64_t trial_neutrons, void* stream) {
 
 mcv_status mcv_trace_batch(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
                            const mcv_detector* det, int fp_mode, void* stream) {
+  mcv::host::CallRange range_("mcv_trace_batch");
   mcv_status st = check_ctx(ctx);
   if (st != MCV_OK) return st;
   mcv_batch b;
@@ -436,7 +440,7 @@ mcv_status mcv_trace_batch(mcv_ctx* ctx, const mcv_sim* sims, int nsims,
   const std::vector<unsigned char> img = device_image(b.im);
   void* d = nullptr;
   cudaError_t e = cudaMallocAsync(&d, img.size(), s);
-  if (e != cudaSuccess) return fail(MCV_ENOMEM, "cannot allocate the batch's parameter block");
+  if (e != cudaSuccess) return alloc_fail("cannot allocate the batch's parameter block");
   // pageable source: the copy has taken the host bytes when the call returns
   e = cudaMemcpyAsync(d, img.data(), img.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {

@@ -25,6 +25,7 @@ int64_t mcv_bragg_table_bytes(int n) {
 
 mcv_status mcv_bragg_build(const double* d_A, const double* w, int n, mcv_bragg* out,
                            void* tables, int64_t bytes, void* stream) {
+  mcv::host::CallRange range_("mcv_bragg_build");
   using mcv::host::fail;
   using mcv::host::is_finite;
   if (!d_A || !w || !out || !tables) return fail(MCV_EINVAL, "mcv_bragg_build needs d_A, w, out, tables");

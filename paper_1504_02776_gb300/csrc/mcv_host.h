@@ -7,6 +7,7 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mcv_launch.h"
 
@@ -31,6 +32,19 @@ constexpr int64_t kMaxNeutrons = (int64_t)1 << 40;
 
 mcv_status fail(mcv_status st, const std::string& msg);
 mcv_status cuda_fail(cudaError_t e, const char* where);
+// An NVTX range around one call of the C ABI, named after the call: a profiler's timeline
+// shows the library's calls around their kernels (with no tool attached, a push and a pop
+// cost a few nanoseconds).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
+
+// A device allocation that failed: MCV_ENOMEM, with CUDA's record of the failure cleared
+// (cudaGetLastError), so that the next launch on this thread does not report it again.
+mcv_status alloc_fail(const std::string& msg);
 bool is_finite(double v);
 mcv_status check_ctx(mcv_ctx* ctx);
 int ns_index(int ns);

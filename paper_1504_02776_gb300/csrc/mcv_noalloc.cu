@@ -69,6 +69,7 @@ mcv_status mcv_grad_noalloc(const mcv_sample* sample, const mcv_beam_params* bea
                             int64_t first_id, int64_t n, const double* target, double scale_c,
                             int grad_scatterer, mcv_hist* hist, double* loss, double* dsqe,
                             double* dsig, void* stream) {
+  mcv::host::CallRange range_("mcv_grad_noalloc");
   mcv::TraceArgs A;
   std::memset(&A, 0, sizeof(A));
   mcv_status st = mcv::build_trace_args_for_grad(sample, beam, det, &A);

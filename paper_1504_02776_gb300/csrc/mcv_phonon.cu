@@ -42,6 +42,7 @@ int64_t mcv_phonon_table_bytes(int n_modes, int n_max) {
 
 mcv_status mcv_phonon_build(const double* dos_z, mcv_phonon* ph, void* tables, int64_t bytes,
                             void* stream) {
+  mcv::host::CallRange range_("mcv_phonon_build");
   using mcv::host::fail;
   using mcv::host::is_finite;
   if (!dos_z || !ph || !tables) return fail(MCV_EINVAL, "mcv_phonon_build needs dos_z, ph, tables");

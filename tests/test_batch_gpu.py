@@ -179,6 +179,26 @@ def test_batch_argument_errors(ctx):
         ctx.trace_batch([sims[0], sims[1].replace(detector=mi.tube_detector())])
 
 
+def test_allocation_failure_is_reported_and_the_context_stays_usable(ctx):
+    """MCV_ENOMEM: the tuner's scratch histogram for 117,760 pixels x 1e7 time bins (9.4 TB)
+    cannot be allocated; the call fails before any launch, and the context then traces as
+    before (CUDA's record of the failed allocation is cleared)."""
+    det = dataclasses.replace(mi.tube_detector(), n_tof=10_000_000)
+    wl = mi.config2(n=1000).replace(detector=det)
+    tiny = (torch.zeros(16, dtype=torch.float64, device="cuda"),
+            torch.zeros(B.MCV_NTALLY, dtype=torch.float64, device="cuda"))
+    b = ctx.batch([wl], fp_mode=B.FP32, hists=[tiny])
+    with pytest.raises(B.McvError) as e:
+        b.tune(trial_neutrons=1000)
+    assert e.value.status == B.MCV_ENOMEM
+    assert "scratch" in str(e.value)
+    b.close()
+    assert not tiny[0].any() and not tiny[1].any()
+    ctx.sync()
+    h, t = _np(ctx.trace(mi.config1(2000), fp_mode=B.FP64))
+    assert t[B.T_NHIT] > 0 and t[B.T_NDET] > 0
+
+
 def _free_bytes():
     free, _ = torch.cuda.mem_get_info()
     return free
