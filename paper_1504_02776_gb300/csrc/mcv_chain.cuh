@@ -201,7 +201,9 @@ __device__ __forceinline__ bool chain_step(const TraceArgs& A, const R* tu, Lane
 }
 
 // Warp loop: each warp owns ids [lo, hi) of the launch; lanes whose neutron finished take
-// the next ids at the top of each step, so all 32 lanes run chain_step together.
+// the next ids at the top of each step, again while some lane is still without a live
+// neutron (a policy that keeps only the neutrons meeting the sample drops two thirds of its
+// draws), so all 32 lanes run chain_step together.
 template <typename R, int NS, int DET, int KS, class P>
 __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& pol) {
   const unsigned kFull = 0xffffffffu;
@@ -218,8 +220,8 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
   L.idx = 0;
   L.nid = 0;
   for (;;) {
-    const unsigned idle = __ballot_sync(kFull, !L.active);
-    if (idle != 0u && next < hi) {
+    for (unsigned idle = __ballot_sync(kFull, !L.active); idle != 0u && next < hi;
+         idle = __ballot_sync(kFull, !L.active)) {
       if (!L.active) {
         const int64_t i = next + __popc(idle & lt_mask);
         if (i < hi) {
@@ -242,10 +244,7 @@ __device__ __forceinline__ void run_chain(const TraceArgs& A, const R* tu, P& po
       }
       next += __popc(idle);
     }
-    if (!__any_sync(kFull, L.active)) {
-      if (next >= hi) break;
-      continue;
-    }
+    if (!__any_sync(kFull, L.active)) break;  // every id of the range taken and done
     if (L.active) L.active = chain_step<R, NS, DET, KS, P>(A, tu, L, pol);
   }
   pol.flush(A, lane);

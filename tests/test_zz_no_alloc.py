@@ -3,6 +3,7 @@
 mcv_grad gives, call after call, with its work buffer in the library's fixed device array.
 Collected last so that a failure here does not hide the other tests."""
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -74,6 +75,17 @@ def test_noalloc_allocates_nothing():
     torch.cuda.synchronize()
     outs = [_noalloc(wl, table, tg, c, B.FP32) for _ in range(2)]  # output buffers first
     torch.cuda.synchronize()
+    # tensors left by earlier tests must not be freed in between: collect them now and keep
+    # the collector off while measuring
+    gc.collect()
+    gc.disable()
+    try:
+        _measure_noalloc(wl, table, tg, c, outs)
+    finally:
+        gc.enable()
+
+
+def _measure_noalloc(wl, table, tg, c, outs):
     before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
     sample = api.sample_struct(wl, B.FP32, table)
     det = api.detector_struct(wl.detector)
