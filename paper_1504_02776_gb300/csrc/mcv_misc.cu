@@ -58,44 +58,97 @@ __global__ void zero_kernel(double* __restrict__ p, int64_t n) {
 // g_b = dchi2/dI_b for every bin.  Without g the kernel only reads (16 bytes per bin, streamed
 // past the caches): the adjoint evaluates g_b itself for the bins its packets reach.  A
 // measured bin that is negative or not finite sets the error flag (err, optional).
-__global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hist,
-                                                   const double* __restrict__ target, double c,
-                                                   int64_t nb, double* __restrict__ g,
-                                                   double* __restrict__ loss, int* err) {
+//
+// GB300's FP64 pipe runs a warp instruction at 2 lanes per clock per SM whatever the number of
+// lanes it needs, and almost every bin of a large detector is empty (both values +0).  Each
+// warp therefore streams its range as integers and queues only the non-empty bins in shared
+// memory (value pair and index); the FP64 arithmetic runs on full batches of 32 queued bins
+// (and once on the remainder).
+constexpr int kChi2Threads = 256;
+constexpr int kChi2Warps = kChi2Threads / 32;
+
+struct Chi2Queue {
+  double h[64], T[64];
+  int64_t bin[64];
+};
+
+// one queued bin per lane, lanes [0, n): its loss term into *part, its g_b into g
+__device__ __forceinline__ void chi2_drain(const Chi2Queue& q, int first, int n, double c,
+                                           double* __restrict__ g, double* part) {
+  const int lane = threadIdx.x & 31;
+  if (lane < n) {
+    const double gb = chi2_bin(q.h[first + lane], q.T[first + lane], c, part);
+    if (g) g[q.bin[first + lane]] = gb;
+  }
+}
+
+__global__ void __launch_bounds__(kChi2Threads) chi2_kernel(const double* __restrict__ hist,
+                                                           const double* __restrict__ target,
+                                                           double c, int64_t nb,
+                                                           double* __restrict__ g,
+                                                           double* __restrict__ loss, int* err) {
+  __shared__ Chi2Queue queues[kChi2Warps];
   double part = 0.0;
   bool bad = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const bool aligned = ((reinterpret_cast<uintptr_t>(hist) | reinterpret_cast<uintptr_t>(target) |
                          reinterpret_cast<uintptr_t>(g)) & 15u) == 0;
   if (aligned) {
-    // pairs of bins as 16-byte loads, four pairs of a thread in flight at once
+    // each warp takes a contiguous range of bin pairs, 32 lanes x 4 pairs (16-byte loads)
+    // per step, so that every step and every branch below is the whole warp's
+    Chi2Queue& q = queues[threadIdx.x >> 5];
     const double2* h2 = reinterpret_cast<const double2*>(hist);
     const double2* t2 = reinterpret_cast<const double2*>(target);
-    double2* g2 = reinterpret_cast<double2*>(g);
     const int64_t np = nb / 2;
-    for (; b + 3 * stride < np; b += 4 * stride) {
+    const int64_t nwarps = (int64_t)gridDim.x * kChi2Warps;
+    const int64_t w = (int64_t)blockIdx.x * kChi2Warps + (threadIdx.x >> 5);
+    const int64_t per = ((np + nwarps - 1) / nwarps + 127) / 128 * 128;
+    const int64_t lo = min(np, w * per), hi = min(np, lo + per);
+    int qn = 0;  // queued bins (the same in every lane)
+    for (int64_t p0 = lo; p0 < hi; p0 += 128) {
       double2 h[4], T[4];
+      bool valid[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        h[k] = __ldcs(h2 + b + k * stride);
-        T[k] = __ldcs(t2 + b + k * stride);
+        const int64_t p = p0 + 32 * k + lane;
+        valid[k] = p < hi;  // pairs past hi are the next warp's
+        if (valid[k]) {
+          h[k] = __ldcs(h2 + p);
+          T[k] = __ldcs(t2 + p);
+        } else {
+          h[k] = make_double2(0.0, 0.0);
+          T[k] = make_double2(0.0, 0.0);
+        }
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bad |= !target_ok(T[k].x) || !target_ok(T[k].y);
-        const double gx = chi2_bin(h[k].x, T[k].x, c, &part);
-        const double gy = chi2_bin(h[k].y, T[k].y, c, &part);
-        if (g) g2[b + k * stride] = make_double2(gx, gy);
+      for (int k = 0; k < 8; ++k) {
+        const double hv = (k & 1) ? h[k >> 1].y : h[k >> 1].x;
+        const double Tv = (k & 1) ? T[k >> 1].y : T[k >> 1].x;
+        const int64_t bin = 2 * (p0 + 32 * (k >> 1) + lane) + (k & 1);
+        bad |= !target_ok(Tv);
+        const bool nz = (__double_as_longlong(hv) | __double_as_longlong(Tv)) != 0;
+        const unsigned m = __ballot_sync(kFull, nz);
+        if (nz) {
+          const int at = qn + __popc(m & lt_mask);
+          q.h[at] = hv;
+          q.T[at] = Tv;
+          q.bin[at] = bin;
+        } else if (g && valid[k >> 1]) {
+          g[bin] = 0.0;
+        }
+        qn += __popc(m);
+        if (qn >= 32) {
+          __syncwarp();
+          chi2_drain(q, qn - 32, 32, c, g, &part);
+          __syncwarp();
+          qn -= 32;
+        }
       }
     }
-    for (; b < np; b += stride) {
-      const double2 h = h2[b], T = t2[b];
-      bad |= !target_ok(T.x) || !target_ok(T.y);
-      const double gx = chi2_bin(h.x, T.x, c, &part);
-      const double gy = chi2_bin(h.y, T.y, c, &part);
-      if (g) g2[b] = make_double2(gx, gy);
-    }
+    __syncwarp();
+    chi2_drain(q, 0, qn, c, g, &part);
     // the odd last bin
     if ((nb & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
       const double T = target[nb - 1];
@@ -104,21 +157,22 @@ __global__ void __launch_bounds__(256) chi2_kernel(const double* __restrict__ hi
       if (g) g[nb - 1] = gb;
     }
   } else {
-    for (; b < nb; b += stride) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
       const double T = target[b];
       bad |= !target_ok(T);
       const double gb = chi2_bin(hist[b], T, c, &part);
       if (g) g[b] = gb;
     }
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && err) atomicOr(err, 1);
+  if (__any_sync(kFull, bad) && lane == 0 && err) atomicOr(err, 1);
   part = warp_sum(part);
-  __shared__ double red[8];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) red[w] = part;
+  __shared__ double red[kChi2Warps];
+  const int wi = threadIdx.x >> 5;
+  if (lane == 0) red[wi] = part;
   __syncthreads();
-  if (w == 0) {
-    double v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+  if (wi == 0) {
+    double v = lane < kChi2Warps ? red[lane] : 0.0;
     v = warp_sum(v);
     if (lane == 0) atomicAdd(loss, v);
   }
@@ -208,7 +262,7 @@ cudaError_t launch_zero(double* p, int64_t n, int grid, cudaStream_t s) {
 
 cudaError_t launch_chi2(const double* hist, const double* target, double c, int64_t nb,
                         double* g, double* loss, int* err, int grid, cudaStream_t s) {
-  chi2_kernel<<<grid, 256, 0, s>>>(hist, target, c, nb, g, loss, err);
+  chi2_kernel<<<grid, kChi2Threads, 0, s>>>(hist, target, c, nb, g, loss, err);
   return cudaGetLastError();
 }
 
