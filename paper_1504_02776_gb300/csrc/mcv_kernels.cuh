@@ -836,12 +836,135 @@ struct Adjoint {
   }
 };
 
+// Warp loop of a policy that keeps only the neutrons meeting the sample (the adjoint): the
+// source draws are compacted as in the waves -- footprints 32 new ids at a time, those that
+// may lead into the sample queued; then 32 queued footprints at a time get their direction
+// and, where they meet the sample, their energy, and are queued as neutrons -- and the lanes
+// without a neutron take queued ones, so that the chain steps run on full warps.  The
+// neutrons and their arithmetic are those of run_chain with make_beam_meeting.
+template <typename R, int NS, int DET, int KS, class P>
+__device__ __forceinline__ void run_chain_meeting(const TraceArgs& A, const R* tu, P& pol,
+                                                  QNeutron<R>* hq, QFoot<R>* fq) {
+  const unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
+  const SampleP<R>& S = Sof<R>(A);
+  const BeamP<R>& Bm = Bof<R>(A);
+  int64_t next = lo;
+  int hq_n = 0, fq_n = 0;  // queued neutrons and footprints (each at most 63)
+  Lane<R> L;
+  L.active = false;
+  L.o = 0;
+  L.idx = 0;
+  L.nid = 0;
+  for (;;) {
+    const unsigned idle = __ballot_sync(kFull, !L.active);
+    const int n_idle = __popc(idle);
+    while (hq_n < n_idle && (fq_n > 0 || next < hi)) {
+      if (fq_n < 32 && next < hi) {
+        const int64_t i = next + lane;
+        bool maybe = false;
+        Ray<R> nr;
+        int64_t nid = 0;
+        if (i < hi) {
+          nid = A.first_id + i;
+          const NeutronRng rng(A.keys, nid);
+          beam_footprint(Bm, rng, &nr);
+          maybe = !surely_misses<R>(Bm, nr);
+        }
+        const unsigned mm = __ballot_sync(kFull, maybe);
+        if (maybe) {
+          QFoot<R>& f = fq[fq_n + __popc(mm & lt_mask)];
+          f.x = nr.x;
+          f.y = nr.y;
+          f.nid = nid;
+        }
+        fq_n += __popc(mm);
+        next += 32;
+        __syncwarp();
+        continue;
+      }
+      const int take_f = fq_n < 32 ? fq_n : 32;
+      bool hit = false;
+      Ray<R> nr;
+      int64_t nid = 0;
+      if (lane < take_f) {
+        const QFoot<R>& f = fq[fq_n - take_f + lane];
+        nid = f.nid;
+        nr.x = f.x;
+        nr.y = f.y;
+        nr.z = -Bm.z0;
+        nr.w = R(1);
+      }
+      fq_n -= take_f;
+      __syncwarp();
+      if (lane < take_f) {
+        const NeutronRng rng(A.keys, nid);
+        R aux;
+        beam_divergence(Bm, rng, &nr, &aux);
+        Seg<R> seg[2 * NS];
+        if (assembly_segs<R, NS>(S, nr, seg) > 0 && beam_energy(Bm, rng, aux, &nr))
+          hit = !(nr.w < S.min_prob) && !(A.stop_on_zero && nr.w == R(0));
+      }
+      const unsigned hm = __ballot_sync(kFull, hit);
+      if (hit) {
+        QNeutron<R>& q = hq[hq_n + __popc(hm & lt_mask)];
+        q.x = nr.x;
+        q.y = nr.y;
+        q.z = nr.z;
+        q.dx = nr.dx;
+        q.dy = nr.dy;
+        q.dz = nr.dz;
+        q.speed = nr.speed;
+        q.t = nr.t;
+        q.nid = nid;
+      }
+      hq_n += __popc(hm);
+      __syncwarp();
+    }
+    const int take = min(n_idle, hq_n);
+    if (!L.active) {
+      const int r = __popc(idle & lt_mask);
+      if (r < take) {
+        const QNeutron<R>& q = hq[hq_n - take + r];
+        L.n.x = q.x;
+        L.n.y = q.y;
+        L.n.z = q.z;
+        L.n.dx = q.dx;
+        L.n.dy = q.dy;
+        L.n.dz = q.dz;
+        L.n.speed = q.speed;
+        L.n.t = q.t;
+        L.n.w = R(1);
+        L.nid = q.nid;
+        L.idx = q.nid - A.first_id;
+        L.o = 0;
+        L.active = true;
+        pol.start(L);
+      }
+    }
+    hq_n -= take;
+    __syncwarp();
+    // no lane holds a neutron only once the queues are empty and the range is done
+    if (!__any_sync(kFull, L.active)) break;
+    if (L.active) L.active = chain_step<R, NS, DET, KS, P>(A, tu, L, pol);
+  }
+  pol.flush(A, lane);
+}
+
 template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kThreads) adjoint_kernel(const __grid_constant__ TraceArgs A) {
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  __shared__ QNeutron<R> hq[kWarps * kQueue];
+  __shared__ QFoot<R> fq[kWarps * kQueue];
   stage_tubes<R, DET>(A, tu);
   Adjoint<R, DET> pol;
-  run_chain<R, NS, DET, KS, Adjoint<R, DET>>(A, tu, pol);
+  const int wib = threadIdx.x >> 5;
+  run_chain_meeting<R, NS, DET, KS, Adjoint<R, DET>>(A, tu, pol, hq + wib * kQueue,
+                                                       fq + wib * kQueue);
 }
 
 }  // namespace mcv
