@@ -228,81 +228,205 @@ __device__ __forceinline__ int paper_interact1(const TraceArgs& A, const SampleP
   return 1;
 }
 
+// One step of a lane's walk of its tree: the packet in hand (cur, when have) or the next one
+// off the stack goes through the assembly; it leaves, or interacts once (the transmitted
+// packet onto the stack, the scattered one kept in hand while it may scatter again).
+// jp: the scatterer of the interactM_path1 under way (its scattered packet is cur), or -1
+// for a packet that starts over from the sample assembly.  The segments of every packet come
+// from the one assembly trace here, so that the distance a transmitted packet has travelled
+// (the end of a segment) and the trace that later clips at it are the same arithmetic in
+// FP32 as in FP64.
 template <typename R, int NS, int DET, int KS>
-__global__ void __launch_bounds__(kPaperThreads) paper_kernel(const __grid_constant__ TraceArgs A) {
-  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
-  stage_tubes<R, DET>(A, tu);
+__device__ __forceinline__ void paper_step(const TraceArgs& A, const R* tu, int64_t nid,
+                                           PaperPk<R>& cur, bool& have, int& jp,
+                                           PaperPk<R> (&stack)[kPaperStack], int& sp,
+                                           PaperTally<R>& T) {
   const SampleP<R>& S = Sof<R>(A);
-  PaperTally<R> T;
-  PaperPk<R> stack[kPaperStack];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t nid = A.first_id + i;
-    PaperPk<R> cur;
-    {
-      const NeutronRng rng(A.keys, nid);
-      if (!make_beam<R>(Bof<R>(A), rng, &cur.n)) continue;
-    }
-    cur.m = 0;
-    cur.node = 1;
-    cur.s0 = R(0);
-    int sp = 0;
-    // jp: the scatterer of the interactM_path1 under way (its scattered packet is cur), or -1
-    // for a packet that starts over from the sample assembly.  The segments of every packet
-    // come from the one assembly trace below, so that the distance a transmitted packet has
-    // travelled (the end of a segment) and the trace that later clips at it are the same
-    // arithmetic in FP32 as in FP64.
-    int jp = -1;
-    bool have = true;
-    while (have || sp > 0) {
-      if (!have) {
-        cur = stack[--sp];
-        jp = -1;
-      }
-      have = false;
-      Seg<R> seg[2 * NS];
-      const int ns = assembly_segs<R, NS>(S, cur.n, seg, cur.s0);
-      if (cur.node == 1 && ns > 0) T.cnt.nhit++;
-      if (cur.n.w < S.min_prob) continue;
-      int j = -1;
-      R a = R(0), b = R(0);
-      if (jp >= 0) {  // path1 goes on: the scatterer's first segment ahead, if any
+  if (!have) {
+    cur = stack[--sp];
+    jp = -1;
+  }
+  have = false;
+  Seg<R> seg[2 * NS];
+  const int ns = assembly_segs<R, NS>(S, cur.n, seg, cur.s0);
+  if (cur.node == 1 && ns > 0) T.cnt.nhit++;
+  if (cur.n.w < S.min_prob) return;
+  int j = -1;
+  R a = R(0), b = R(0);
+  if (jp >= 0) {  // path1 goes on: the scatterer's first segment ahead, if any
 #pragma unroll
-        for (int k = 2 * NS - 1; k >= 0; --k) {
-          if (k < ns && seg[k].j == jp) {
-            j = jp;
-            a = seg[k].a;
-            b = seg[k].b;
-          }
-        }
+    for (int k = 2 * NS - 1; k >= 0; --k) {
+      if (k < ns && seg[k].j == jp) {
+        j = jp;
+        a = seg[k].a;
+        b = seg[k].b;
       }
-      if (j < 0) {  // from the sample assembly
-        if (ns == 0) {  // nothing ahead: it leaves
-          paper_emit<R, DET>(A, tu, nid, cur, T);
-          continue;
-        }
-        if (cur.m >= S.max_orders || cur.node >= kPaperMaxNode) {
-          paper_propagate_out<R, NS>(S, seg, ns, &cur);
-          paper_emit<R, DET>(A, tu, nid, cur, T);
-          continue;
-        }
-        j = seg[0].j;  // interactM_path1 of the first scatterer met
-        a = seg[0].a;
-        b = seg[0].b;
-      }
-      PaperPk<R> tr, sc;
-      const int res = paper_interact1<R, KS>(A, S, j, a, b, nid, cur, &tr, &sc, &T.err);
-      if (sp < kPaperStack) stack[sp++] = tr;
-      else T.err = 1;  // the tree outgrew the stack: the packet is lost and reported
-      if (res == 2) continue;
-      // the scattered packet goes on with the same scatterer while it may scatter again
-      // (every interaction at least doubles the node, so the walk ends)
-      cur = sc;
-      have = true;
-      jp = (cur.m < S.max_orders && cur.node < kPaperMaxNode) ? j : -1;
     }
   }
+  if (j < 0) {  // from the sample assembly
+    if (ns == 0) {  // nothing ahead: it leaves
+      paper_emit<R, DET>(A, tu, nid, cur, T);
+      return;
+    }
+    if (cur.m >= S.max_orders || cur.node >= kPaperMaxNode) {
+      paper_propagate_out<R, NS>(S, seg, ns, &cur);
+      paper_emit<R, DET>(A, tu, nid, cur, T);
+      return;
+    }
+    j = seg[0].j;  // interactM_path1 of the first scatterer met
+    a = seg[0].a;
+    b = seg[0].b;
+  }
+  PaperPk<R> tr, sc;
+  const int res = paper_interact1<R, KS>(A, S, j, a, b, nid, cur, &tr, &sc, &T.err);
+  if (sp < kPaperStack) stack[sp++] = tr;
+  else T.err = 1;  // the tree outgrew the stack: the packet is lost and reported
+  if (res == 2) return;
+  // the scattered packet goes on with the same scatterer while it may scatter again (every
+  // interaction at least doubles the node, so the walk ends)
+  cur = sc;
+  have = true;
+  jp = (cur.m < S.max_orders && cur.node < kPaperMaxNode) ? j : -1;
+}
+
+// Each warp takes a contiguous range of neutron ids.  Their source draws are compacted as in
+// the waves (footprints 32 new ids at a time; those that may lead into the sample get their
+// direction and, where needed, their energy 32 at a time); a neutron that misses the sample
+// is one order-0 packet, added to the beam stop there, and those that meet it are queued.
+// A lane without a tree to walk takes a queued neutron, so the warps' lanes walk trees
+// together instead of drifting apart over the two thirds of the beam that misses.
+template <typename R, int NS, int DET, int KS>
+__global__ void __launch_bounds__(kPaperThreads) paper_kernel(const __grid_constant__ TraceArgs A) {
+  constexpr int kPWarps = kPaperThreads / 32;
+  __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
+  __shared__ QNeutron<R> hq_all[kPWarps * kQueue];
+  __shared__ QFoot<R> fq_all[kPWarps * kQueue];
+  stage_tubes<R, DET>(A, tu);
+  const SampleP<R>& S = Sof<R>(A);
+  const BeamP<R>& Bm = Bof<R>(A);
+  const unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  QNeutron<R>* hq = hq_all + (threadIdx.x >> 5) * kQueue;
+  QFoot<R>* fq = fq_all + (threadIdx.x >> 5) * kQueue;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
+  int64_t next = lo;
+  int hq_n = 0, fq_n = 0;  // queued neutrons and footprints (each at most 63)
+  PaperTally<R> T;
+  PaperPk<R> stack[kPaperStack];
+  PaperPk<R> cur;
+  int64_t nid = 0;
+  int sp = 0, jp = -1;
+  bool have = false, busy = false;  // busy: the lane has a tree to walk (have || sp > 0)
+  for (;;) {
+    const unsigned idle = __ballot_sync(kFull, !busy);
+    const int n_idle = __popc(idle);
+    while (hq_n < n_idle && (fq_n > 0 || next < hi)) {
+      if (fq_n < 32 && next < hi) {
+        const int64_t i = next + lane;
+        bool maybe = false;
+        Ray<R> nr;
+        int64_t id = 0;
+        if (i < hi) {
+          id = A.first_id + i;
+          const NeutronRng rng(A.keys, id);
+          beam_footprint(Bm, rng, &nr);
+          if (!surely_misses<R>(Bm, nr))
+            maybe = true;
+          else if (!(nr.w < S.min_prob))
+            T.bs.add(nr.w);  // order-0 packet, no material ahead
+        }
+        const unsigned mm = __ballot_sync(kFull, maybe);
+        if (maybe) {
+          QFoot<R>& f = fq[fq_n + __popc(mm & lt_mask)];
+          f.x = nr.x;
+          f.y = nr.y;
+          f.nid = id;
+        }
+        fq_n += __popc(mm);
+        next += 32;
+        __syncwarp();
+        continue;
+      }
+      const int take_f = fq_n < 32 ? fq_n : 32;
+      bool hit = false;
+      Ray<R> nr;
+      int64_t id = 0;
+      if (lane < take_f) {
+        const QFoot<R>& f = fq[fq_n - take_f + lane];
+        id = f.nid;
+        nr.x = f.x;
+        nr.y = f.y;
+        nr.z = -Bm.z0;
+        nr.w = R(1);
+      }
+      fq_n -= take_f;
+      __syncwarp();
+      if (lane < take_f) {
+        const NeutronRng rng(A.keys, id);
+        R aux;
+        beam_divergence(Bm, rng, &nr, &aux);
+        Seg<R> seg[2 * NS];
+        const bool meets = assembly_segs<R, NS>(S, nr, seg) > 0;
+        const bool ok = (meets || !Bm.energy_positive) ? beam_energy(Bm, rng, aux, &nr) : true;
+        if (ok) {
+          if (meets)
+            hit = true;
+          else if (!(nr.w < S.min_prob))
+            T.bs.add(nr.w);  // order-0 packet, no material ahead
+        }
+      }
+      const unsigned hm = __ballot_sync(kFull, hit);
+      if (hit) {
+        QNeutron<R>& q = hq[hq_n + __popc(hm & lt_mask)];
+        q.x = nr.x;
+        q.y = nr.y;
+        q.z = nr.z;
+        q.dx = nr.dx;
+        q.dy = nr.dy;
+        q.dz = nr.dz;
+        q.speed = nr.speed;
+        q.t = nr.t;
+        q.nid = id;
+      }
+      hq_n += __popc(hm);
+      __syncwarp();
+    }
+    const int take = min(n_idle, hq_n);
+    if (!busy) {
+      const int r = __popc(idle & lt_mask);
+      if (r < take) {
+        const QNeutron<R>& q = hq[hq_n - take + r];
+        cur.n.x = q.x;
+        cur.n.y = q.y;
+        cur.n.z = q.z;
+        cur.n.dx = q.dx;
+        cur.n.dy = q.dy;
+        cur.n.dz = q.dz;
+        cur.n.speed = q.speed;
+        cur.n.t = q.t;
+        cur.n.w = R(1);
+        cur.m = 0;
+        cur.node = 1;
+        cur.s0 = R(0);
+        nid = q.nid;
+        sp = 0;
+        jp = -1;
+        have = true;
+        busy = true;
+      }
+    }
+    hq_n -= take;
+    __syncwarp();
+    // no lane has a tree only once the queues are empty and the range is done
+    if (!__any_sync(kFull, busy)) break;
+    if (busy) {
+      paper_step<R, NS, DET, KS>(A, tu, nid, cur, have, jp, stack, sp, T);
+      busy = have || sp > 0;
+    }
+  }
   if (A.tallies) {
     const double v_bs = warp_sum(T.bs.value());
     const double v_det = warp_sum(T.det.value());
