@@ -1179,11 +1179,13 @@ cudaError_t launch_adjoint_t(const TraceArgs& A, int det, int grid, cudaStream_t
 // the paper's recursive estimator
 template <typename R, int NS, int KS>
 cudaError_t launch_paper_nk(const TraceArgs& A, int det, int grid, cudaStream_t s) {
-  if (det == MCV_DET_SURFACE)
-    paper_kernel<R, NS, MCV_DET_SURFACE, KS><<<grid, kPaperThreads, 0, s>>>(A);
-  else
-    paper_kernel<R, NS, MCV_DET_TUBES, KS><<<grid, kPaperThreads, 0, s>>>(A);
-  return cudaGetLastError();
+  const size_t smem = paper_smem_bytes<R>();
+  const void* fn = det == MCV_DET_SURFACE ? (const void*)paper_kernel<R, NS, MCV_DET_SURFACE, KS>
+                                          : (const void*)paper_kernel<R, NS, MCV_DET_TUBES, KS>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<TraceArgs*>(&A)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kPaperThreads), args, smem, s);
 }
 
 template <typename R>

@@ -146,6 +146,24 @@ struct PaperTally {
   }
 };
 
+// a packet of order >= 1 leaving the sample, queued for the detector stage
+template <typename R>
+struct PaperDet {
+  Ray<R> n;
+  uint64_t node;
+  int64_t nid;
+  int m;
+};
+
+// dynamic shared memory of the paper kernel: per warp, the queues of neutrons, footprints and
+// packets for the detector
+constexpr int kPaperWarps = kPaperThreads / 32;
+template <typename R>
+constexpr size_t paper_smem_bytes() {
+  return (size_t)kPaperWarps * kQueue *
+         (sizeof(QNeutron<R>) + sizeof(QFoot<R>) + sizeof(PaperDet<R>));
+}
+
 // a packet leaving the sample assembly
 template <typename R, int DET>
 __device__ __forceinline__ void paper_emit(const TraceArgs& A, const R* tu, int64_t nid,
@@ -229,18 +247,19 @@ __device__ __forceinline__ int paper_interact1(const TraceArgs& A, const SampleP
 }
 
 // One step of a lane's walk of its tree: the packet in hand (cur, when have) or the next one
-// off the stack goes through the assembly; it leaves, or interacts once (the transmitted
-// packet onto the stack, the scattered one kept in hand while it may scatter again).
+// off the stack goes through the assembly; it leaves (*emit: cur is a packet for the
+// detector), or interacts once (the transmitted packet onto the stack, the scattered one
+// kept in hand while it may scatter again).
 // jp: the scatterer of the interactM_path1 under way (its scattered packet is cur), or -1
 // for a packet that starts over from the sample assembly.  The segments of every packet come
 // from the one assembly trace here, so that the distance a transmitted packet has travelled
 // (the end of a segment) and the trace that later clips at it are the same arithmetic in
 // FP32 as in FP64.
 template <typename R, int NS, int DET, int KS>
-__device__ __forceinline__ void paper_step(const TraceArgs& A, const R* tu, int64_t nid,
-                                           PaperPk<R>& cur, bool& have, int& jp,
+__device__ __forceinline__ void paper_step(const TraceArgs& A, int64_t nid, PaperPk<R>& cur,
+                                           bool& have, int& jp,
                                            PaperPk<R> (&stack)[kPaperStack], int& sp,
-                                           PaperTally<R>& T) {
+                                           PaperTally<R>& T, bool* emit) {
   const SampleP<R>& S = Sof<R>(A);
   if (!have) {
     cur = stack[--sp];
@@ -264,13 +283,14 @@ __device__ __forceinline__ void paper_step(const TraceArgs& A, const R* tu, int6
     }
   }
   if (j < 0) {  // from the sample assembly
-    if (ns == 0) {  // nothing ahead: it leaves
-      paper_emit<R, DET>(A, tu, nid, cur, T);
-      return;
-    }
-    if (cur.m >= S.max_orders || cur.node >= kPaperMaxNode) {
-      paper_propagate_out<R, NS>(S, seg, ns, &cur);
-      paper_emit<R, DET>(A, tu, nid, cur, T);
+    if (ns == 0 || cur.m >= S.max_orders || cur.node >= kPaperMaxNode) {
+      // it leaves (with the attenuation of what is still ahead): order 0 to the beam stop,
+      // the others queued for the detector stage (cur)
+      if (ns > 0) paper_propagate_out<R, NS>(S, seg, ns, &cur);
+      if (cur.m == 0)
+        T.bs.add(cur.n.w);
+      else
+        *emit = true;
       return;
     }
     j = seg[0].j;  // interactM_path1 of the first scatterer met
@@ -294,26 +314,32 @@ __device__ __forceinline__ void paper_step(const TraceArgs& A, const R* tu, int6
 // direction and, where needed, their energy 32 at a time); a neutron that misses the sample
 // is one order-0 packet, added to the beam stop there, and those that meet it are queued.
 // A lane without a tree to walk takes a queued neutron, so the warps' lanes walk trees
-// together instead of drifting apart over the two thirds of the beam that misses.
+// together instead of drifting apart over the two thirds of the beam that misses; the
+// packets that leave for the detector are queued and detected 32 at a time.  Queues in
+// dynamic shared memory (paper_smem_bytes).
 template <typename R, int NS, int DET, int KS>
 __global__ void __launch_bounds__(kPaperThreads) paper_kernel(const __grid_constant__ TraceArgs A) {
-  constexpr int kPWarps = kPaperThreads / 32;
   __shared__ R tu[2 * MCV_MAX_TUBES_PER_ROW];
-  __shared__ QNeutron<R> hq_all[kPWarps * kQueue];
-  __shared__ QFoot<R> fq_all[kPWarps * kQueue];
+  const int wib = threadIdx.x >> 5;
+  QNeutron<R>* hq = reinterpret_cast<QNeutron<R>*>(g_wave_smem) + wib * kQueue;
+  QFoot<R>* fq = reinterpret_cast<QFoot<R>*>(
+                     g_wave_smem + (size_t)kPaperWarps * kQueue * sizeof(QNeutron<R>)) +
+                 wib * kQueue;
+  PaperDet<R>* dq = reinterpret_cast<PaperDet<R>*>(
+                        g_wave_smem + (size_t)kPaperWarps * kQueue *
+                                          (sizeof(QNeutron<R>) + sizeof(QFoot<R>))) +
+                    wib * kQueue;
   stage_tubes<R, DET>(A, tu);
   const SampleP<R>& S = Sof<R>(A);
   const BeamP<R>& Bm = Bof<R>(A);
   const unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  QNeutron<R>* hq = hq_all + (threadIdx.x >> 5) * kQueue;
-  QFoot<R>* fq = fq_all + (threadIdx.x >> 5) * kQueue;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t lo = (A.n * wid) / nw, hi = (A.n * (wid + 1)) / nw;
   int64_t next = lo;
-  int hq_n = 0, fq_n = 0;  // queued neutrons and footprints (each at most 63)
+  int hq_n = 0, fq_n = 0, dq_n = 0;  // queued neutrons, footprints, packets (each <= 63)
   PaperTally<R> T;
   PaperPk<R> stack[kPaperStack];
   PaperPk<R> cur;
@@ -420,11 +446,39 @@ __global__ void __launch_bounds__(kPaperThreads) paper_kernel(const __grid_const
     }
     hq_n -= take;
     __syncwarp();
-    // no lane has a tree only once the queues are empty and the range is done
-    if (!__any_sync(kFull, busy)) break;
+    // no lane has a tree only once the source queues are empty and the range is done
+    if (!__any_sync(kFull, busy) && dq_n == 0) break;
+    bool emit = false;
     if (busy) {
-      paper_step<R, NS, DET, KS>(A, tu, nid, cur, have, jp, stack, sp, T);
+      paper_step<R, NS, DET, KS>(A, nid, cur, have, jp, stack, sp, T, &emit);
       busy = have || sp > 0;
+    }
+    const unsigned em = __ballot_sync(kFull, emit);
+    if (emit) {
+      PaperDet<R>& d = dq[dq_n + __popc(em & lt_mask)];
+      d.n = cur.n;
+      d.node = cur.node;
+      d.nid = nid;
+      d.m = cur.m;
+    }
+    dq_n += __popc(em);
+    __syncwarp();
+    // detector stage: full batches of 32 packets, and the remainder at the end
+    const bool last = !__any_sync(kFull, busy) && hq_n == 0 && fq_n == 0 && next >= hi;
+    while (dq_n >= 32 || (last && dq_n > 0)) {
+      const int take_d = dq_n < 32 ? dq_n : 32;
+      PaperPk<R> p;
+      int64_t id = 0;
+      if (lane < take_d) {
+        const PaperDet<R>& d = dq[dq_n - take_d + lane];
+        p.n = d.n;
+        p.node = d.node;
+        p.m = d.m;
+        id = d.nid;
+      }
+      dq_n -= take_d;
+      __syncwarp();
+      if (lane < take_d) paper_emit<R, DET>(A, tu, id, p, T);
     }
   }
   if (A.tallies) {
