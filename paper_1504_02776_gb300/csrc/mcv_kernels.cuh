@@ -101,13 +101,34 @@ struct Forward {
       if (h.pixel >= 0 && Out::events(A).count)
         append_event(Out::events(A), h.pixel, h.tof.value(), (double)h.w_det);
     }
+    // Equal bins among the lanes recording together (a detector batch) are summed in the
+    // group's lowest lane and added with one FP64 atomic: fewer atomics on the bins that
+    // collect many events (the elastic line; low incident energies concentrate more).
+    const bool valid = h.bin >= 0 && h.bin < Dof<R>(A).n_bins;
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const long long key = valid ? (long long)h.bin : -1ll - lane;
+    const unsigned peers = __match_any_sync(act, key);
+    if (valid) {
+      double* hist = Out::hist(A);
+      const double v = (double)h.w_det;
+      if (peers == (1u << lane)) {
+        if (hist) atomicAdd(hist + h.bin, v);
+      } else {
+        const int leader = __ffs(peers) - 1;
+        double sum = 0.0;
+        for (unsigned m = peers; m; m &= m - 1) {
+          const double x = __shfl_sync(peers, v, __ffs(m) - 1);
+          sum += x;
+        }
+        if (hist && lane == leader) atomicAdd(hist + h.bin, sum);
+      }
+    }
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
         return;
       }
-      double* hist = Out::hist(A);
-      if (hist) atomicAdd(hist + h.bin, (double)h.w_det);
       t.det.add(h.w_det);
       t.cnt.ndet++;
     } else if (h.bin == -2) {
