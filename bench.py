@@ -794,7 +794,7 @@ def main():
     # default: as many steps as the device-timed region (the last read-back, which nothing
     # overlaps, is spread over the same number of steps)
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--e2e-reps", type=int, default=3)
+    ap.add_argument("--e2e-reps", type=int, default=5)
     ap.add_argument("--cpu-per-worker", type=int, default=1_000_000)
     ap.add_argument("--ref-per-worker", type=int, default=400_000)
     ap.add_argument("--no-e2e", action="store_true")
