@@ -6,6 +6,7 @@ relative; histograms per bin within 1e-12 relative (the FP64 summation order dif
 FP32 fast mode: packet states within 1e-5 relative, at most 1e-4 of detected events in
 another pixel or tof bin, and the histogram within those bounds.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -100,6 +101,21 @@ def test_fp64_fused_histogram_matches_oracle(ctx, make, n):
     assert t[B.T_NMISS] == to[oracle.T_NMISS]
     assert t[B.T_NHIT] == to[oracle.T_NHIT]
     assert t[B.T_NEMIT] == to[oracle.T_NPACK0 + 1:oracle.T_NPACK0 + 8].sum()
+
+
+def test_histogram_with_few_bins_sums_repeated_bins(ctx):
+    """Config 1's elastic scattering on a detector of 4 x 2 pixels and one time bin: nearly
+    every detector batch holds several events of the same bin, whose weights the kernel sums
+    within the warp before one FP64 atomic.  FP64 bins equal the oracle's up to the order of
+    the additions; FP32 bins within 2e-4."""
+    det = dataclasses.replace(mi.surface_detector(), n_phi=4, n_y=2, n_tof=1)
+    wl = mi.config1(200000).replace(detector=det)
+    ho = oracle.trace(wl, packets=False)["hist"]
+    assert ho.size == 8 and (ho > 0).sum() >= 4
+    for fp, bar in ((B.FP64, 1e-12), (B.FP32, 2e-4)):
+        counts, tallies = ctx.trace(wl, fp_mode=fp)
+        hc = counts.cpu().numpy()
+        assert np.all(np.abs(hc - ho) <= bar * np.abs(ho) + 1e-300), (fp, hc, ho)
 
 
 def _wide_divergent(n):
