@@ -7,8 +7,9 @@
 // with nothing ahead leaves -- order 0 to the beam stop, the others to the detector system,
 // where (with multi_tube) the weight a tube leaves goes on to the next tubes it crosses.
 //
-// One neutron per thread walks its tree of packets depth first with a stack in local memory.
-// Each packet's random numbers are keyed by its place in the tree (the incident packet is
+// A lane walks one neutron's tree of packets depth first with a stack in local memory; the
+// warp's source draws are compacted and its packets leaving for the detector are queued and
+// detected 32 at a time, as in the chain's waves.  Each packet's random numbers are keyed by its place in the tree (the incident packet is
 // node 1, an interaction of node x gives the transmitted packet 2x and the scattered packet
 // 2x + 1; counter (id lo, id hi, 4 (node mod 2^30) + block, node / 2^30), key (seed,
 // sim_id ^ 0x80000000)), so the walk's order does not change any packet.
