@@ -48,4 +48,12 @@ __device__ __forceinline__ double chi2_grad_bin(double h, double T, double c) {
   return chi2_bin(h, T, c, &unused);
 }
 
+// g_b in FP32 (the FP32 adjoint): the difference c h - T is formed in FP64, where it cancels,
+// and rounded once; the rest is FP32 (relative error a few FP32 units).
+__device__ __forceinline__ float chi2_grad_bin_f32(double h, double T, double c) {
+  if ((__double_as_longlong(h) | __double_as_longlong(T)) == 0) return 0.0f;
+  const float r = (float)(c * h - T);
+  return (2.0f * (float)c) * r / fmaxf((float)T, 1.0f);
+}
+
 }  // namespace mcv

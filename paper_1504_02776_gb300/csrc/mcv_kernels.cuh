@@ -811,10 +811,19 @@ struct Adjoint {
       err = 1;
       return;
     }
-    const double g64 = A.g ? A.g[h.bin]
-                           : chi2_grad_bin(A.hist_in[h.bin], A.target[h.bin], A.scale_c);
-    if (g64 == 0.0) return;
-    const R gb = (R)g64;
+    // g_b = dchi2/dI_b of the bin.  FP32 mode: from the FP64 difference c I_b - T_b rounded
+    // once to FP32 (a warp instruction on GB300's FP64 pipe costs the same whatever lanes it
+    // needs, and only a few lanes of a step detect); FP64 mode: in FP64.
+    double g64 = 0.0;
+    R gb;
+    if constexpr (sizeof(R) == 4) {
+      gb = A.g ? (R)A.g[h.bin] : chi2_grad_bin_f32(A.hist_in[h.bin], A.target[h.bin], A.scale_c);
+      if (gb == R(0)) return;
+    } else {
+      g64 = A.g ? A.g[h.bin] : chi2_grad_bin(A.hist_in[h.bin], A.target[h.bin], A.scale_c);
+      if (g64 == 0.0) return;
+      gb = (R)g64;
+    }
     const ScatP<R>& g = Sof<R>(A).s[A.gs];
     const R w_det = we * h.pabs;
     const R dabs = cum_dabs - g.n100 * (R(2200) / L.n.speed) * lg;
@@ -829,7 +838,10 @@ struct Adjoint {
       R prod = base;
       for (int m = 0; m < L.o; ++m)
         if (m != k) prod *= s[m];
-      atomicAdd(A.dsqe + e[k], g64 * (double)prod);
+      if constexpr (sizeof(R) == 4)
+        atomicAdd(A.dsqe + e[k], (double)(gb * prod));
+      else
+        atomicAdd(A.dsqe + e[k], g64 * (double)prod);
     }
   }
 

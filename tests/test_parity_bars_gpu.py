@@ -220,14 +220,17 @@ def test_gradient_with_and_without_work_buffer(ctx):
     wl = mi.config2(n=5000).replace(detector=det)
     target, c = _target(wl, 5000, 1e4)
     tg = torch.from_numpy(target).cuda()
-    for fp in (B.FP64, B.FP32):
+    # FP64: both evaluate g_b in FP64 (the same function); FP32: the adjoint without a work
+    # buffer evaluates g_b in FP32 from the FP64 difference c I_b - T_b, the one with a buffer
+    # rounds the buffer's FP64 value, so they differ by FP32 roundings of g_b
+    for fp, rt in ((B.FP64, 1e-12), (B.FP32, 1e-6)):
         work = torch.empty(det.n_bins, dtype=torch.float64, device="cuda")
         a = ctx.grad(wl, tg, c, fp_mode=fp, g_work=work)
         b = ctx.grad(wl, tg, c, fp_mode=fp)
         assert a["loss"].item() == pytest.approx(b["loss"].item(), rel=1e-13)
-        np.testing.assert_allclose(a["dsig"].cpu().numpy(), b["dsig"].cpu().numpy(), rtol=1e-12)
+        np.testing.assert_allclose(a["dsig"].cpu().numpy(), b["dsig"].cpu().numpy(), rtol=rt)
         x, y = a["dsqe"].cpu().numpy(), b["dsqe"].cpu().numpy()
-        assert np.abs(x - y).max() <= 1e-12 * np.abs(y).max()
+        assert np.abs(x - y).max() <= rt * np.abs(y).max()
         # the work buffer holds dchi2/dI of every bin
         h = b["hist"].cpu().numpy()
         g_ref = 2 * c * (c * h - target) / np.maximum(target, 1.0)

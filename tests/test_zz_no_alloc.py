@@ -53,15 +53,18 @@ def test_noalloc_gradient_matches_mcv_grad_twice(fp_mode):
     tg = torch.from_numpy(target).cuda()
     table = ctx.table(wl)
     ref = ctx.grad(wl, tg, c, fp_mode=fp_mode, table=table)
+    # the no-allocation call reads dchi2/dI from its work array; mcv_grad without one
+    # evaluates it per packet, in FP32 in the FP32 mode: they differ by FP32 roundings there
+    rt = 1e-10 if fp_mode == B.FP64 else 1e-6
     for _ in range(2):
         out = _noalloc(wl, table, tg, c, fp_mode)
         assert abs(out["loss"].item() - ref["loss"].item()) <= 1e-12 * ref["loss"].item()
         np.testing.assert_allclose(out["hist"].cpu().numpy(), ref["hist"].cpu().numpy(),
                                    rtol=1e-12, atol=1e-300)
         np.testing.assert_allclose(out["dsig"].cpu().numpy(), ref["dsig"].cpu().numpy(),
-                                   rtol=1e-10)
+                                   rtol=rt)
         a, b = out["dsqe"].cpu().numpy(), ref["dsqe"].cpu().numpy()
-        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+        assert np.abs(a - b).max() <= rt * np.abs(b).max()
     ctx.close()
 
 
