@@ -320,9 +320,10 @@ mcv_status mcv_beam(mcv_ctx* ctx, const mcv_beam_params* beam, int fp_mode, uint
  * recursion (one neutron per GPU thread walking its tree of packets; random numbers keyed
  * by the packet's place in the tree: key (seed, sim_id ^ 0x80000000), counter (id lo, id hi,
  * 4 (node mod 2^30) + block, node / 2^30), the incident packet node 1 and the transmitted and
- * scattered packets of node x nodes 2x and 2x + 1); it needs det and hist and takes no `in`,
- * `packets` or event list.  A tree that outgrows the thread's stack of 48 waiting packets
- * loses them and sets the device error flag (MCV_EDEVICE at mcv_sync).
+ * scattered packets of node x nodes 2x and 2x + 1); it needs det and hist (hist->events,
+ * if given, receives every detected packet as with the chain) and takes no `in` or
+ * `packets`.  A tree that outgrows the thread's stack of 48 waiting packets loses them and
+ * sets the device error flag (MCV_EDEVICE at mcv_sync).
  * Errors: MCV_EINVAL for NULL/ill-formed descriptions, n < 0, unsupported combinations. */
 mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample,
                             const mcv_beam_params* beam, const mcv_neutrons* in,

@@ -761,9 +761,9 @@ mcv_status mcv_trace_sample(mcv_ctx* ctx, const mcv_sample* sample, const mcv_be
   }
   const bool paper = sample->estimator == MCV_EST_PAPER;
   if (sample->estimator != MCV_EST_CHAIN && !paper) return fail(MCV_EINVAL, "unknown estimator");
-  if (paper && (!fused || in || packets || (hist && hist->events)))
+  if (paper && (!fused || in || packets))
     return fail(MCV_EINVAL, "the paper estimator needs a detector and a histogram, and takes no "
-                            "stored beam, packet slots or event list");
+                            "stored beam or packet slots");
   if (n == 0) return MCV_OK;
   A.seed = seed;
   A.sim_id = sim_id;

@@ -132,6 +132,8 @@ struct PaperTally {
   Counts cnt;
   int err = 0;
   __device__ __forceinline__ void record(const TraceArgs& A, const Hit<R>& h) {
+    // event mode: every detected packet, in or outside the time window
+    if (h.pixel >= 0 && A.ev.count) append_event(A.ev, h.pixel, h.tof.value(), (double)h.w_det);
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
