@@ -83,11 +83,11 @@ def test_fp32_paper_estimator_against_the_oracle(ctx):
 
 
 def test_fp32_paper_histogram_per_bin(ctx):
-    """The FP32 paper estimator's histogram against the oracle's paper mode.  In the paper's
-    recursion every segment a ray crosses is an interaction; in FP32 a ray that grazes the
-    hollow cylinder's inner surface can cross the wall as one segment or as two, and then
-    the tree below, and the random numbers of its packets (keyed by their nodes), differ:
-    such a neutron's packets land in other bins.  Measured (2e5 neutrons): on the powder
+    """The FP32 paper estimator's histogram against the oracle's paper mode.  Weight moves
+    between bins mostly with the hollow shell; the explanation the measurements point to: in
+    the paper's recursion every segment a ray crosses is an interaction, and in FP32 a ray
+    that grazes the shell's inner surface can cross the wall as one segment or as two, after
+    which the tree below and the node-keyed random numbers of its packets differ.  Measured (2e5 neutrons): on the powder
     shell 1.55e-3 of the weight moves between bins (L1 / total; half of it in bins below
     1e-30, where FP32 weights underflow), with the isotropic kernel on the same shell
     2.7e-4, on config 1's solid cylinder at two orders 1.5e-5 -- against 3.2e-5 for the
