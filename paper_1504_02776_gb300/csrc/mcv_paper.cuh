@@ -125,6 +125,13 @@ __device__ __forceinline__ int tubes_absorb_multi(const DetP<R>& D, const TofWin
   return m;
 }
 
+// event mode of the paper estimator, out of line: runs without an event list keep the
+// registers and code of the append out of their detector stage
+static __device__ __noinline__ void paper_append_event(const EvSink& ev, int pixel, double tof,
+                                                       double w) {
+  append_event(ev, pixel, tof, w);
+}
+
 // the running tallies of a thread (the chain kernels' slots)
 template <typename R>
 struct PaperTally {
@@ -133,7 +140,8 @@ struct PaperTally {
   int err = 0;
   __device__ __forceinline__ void record(const TraceArgs& A, const Hit<R>& h) {
     // event mode: every detected packet, in or outside the time window
-    if (h.pixel >= 0 && A.ev.count) append_event(A.ev, h.pixel, h.tof.value(), (double)h.w_det);
+    if (h.pixel >= 0 && A.ev.count)
+      paper_append_event(A.ev, h.pixel, h.tof.value(), (double)h.w_det);
     if (h.bin >= 0) {
       if (h.bin >= Dof<R>(A).n_bins) {
         err = 1;
