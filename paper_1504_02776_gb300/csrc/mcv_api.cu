@@ -200,7 +200,7 @@ mcv_status build_sample(const mcv_sample* s, mcv::SampleP<double>* S) {
     S->has_bragg = 1;
     S->n_refl = b.n;
     S->refl_d = static_cast<const double*>(b.tables);
-    S->refl_w = S->refl_d + b.n;
+    S->refl_c = S->refl_d + b.n;
   }
   if (need_disp) {
     const mcv_dispersion& q = s->dispersion;
@@ -462,7 +462,7 @@ void cast_sample(const mcv::SampleP<double>& d, mcv::SampleP<float>* f) {
     // the float copies follow the doubles (mcv_bragg_build)
     const float* fb = reinterpret_cast<const float*>(d.refl_d + 2 * (int64_t)d.n_refl);
     f->refl_d = fb;
-    f->refl_w = fb + d.n_refl;
+    f->refl_c = fb + d.n_refl;
   }
   f->wide = d.wide;
 }

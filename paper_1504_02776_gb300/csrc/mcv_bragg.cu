@@ -1,8 +1,11 @@
 // Tables of the coherent elastic powder kernel (host code): the reflections sorted by
 // decreasing lattice spacing (ties in input order), so that the reflections a wavelength can
-// excite (lambda < 2 d) form a prefix of the list.
-// Device layout (mcv_bragg::tables): d[n], w[n] as doubles (FP64 kernels), then d[n], w[n]
-// as floats (FP32 kernels).
+// excite (lambda < 2 d) form a prefix of the list.  A reflection's cross section at
+// wavelength lambda, lambda^3 w / (4 sin theta_B) with sin theta_B = lambda / 2d, is
+// lambda^2 w d / 2: the table holds the prefix sums of w d, so that the sum over the allowed
+// reflections and the choice among them need no per-reflection arithmetic.
+// Device layout (mcv_bragg::tables): d[n], C[n] (C[r] = sum of w d over reflections 0..r) as
+// doubles (FP64 kernels), then d[n], C[n] as floats (FP32 kernels).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -41,14 +44,16 @@ mcv_status mcv_bragg_build(const double* d_A, const double* w, int n, mcv_bragg*
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d_A[a] > d_A[b]; });
   std::vector<unsigned char> buf((size_t)need);
   double* dd = reinterpret_cast<double*>(buf.data());
-  double* dw = dd + n;
-  float* fd = reinterpret_cast<float*>(dw + n);
-  float* fw = fd + n;
+  double* dc = dd + n;
+  float* fd = reinterpret_cast<float*>(dc + n);
+  float* fc = fd + n;
+  double sum = 0.0;
   for (int r = 0; r < n; ++r) {
     dd[r] = d_A[order[r]];
-    dw[r] = w[order[r]];
+    sum += w[order[r]] * dd[r];
+    dc[r] = sum;
     fd[r] = (float)dd[r];
-    fw[r] = (float)dw[r];
+    fc[r] = (float)dc[r];
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(tables, buf.data(), (size_t)need, cudaMemcpyHostToDevice, s);

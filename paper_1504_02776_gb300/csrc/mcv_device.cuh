@@ -712,40 +712,41 @@ __device__ __forceinline__ bool kernel_phonon(const SampleP<R>& S, const Rng& rn
 
 // ---- coherent elastic scattering from a powder (supplement S4) --------------------------
 // Per atom, reflection tau scatters sigma_tau = lambda^3 w_tau / (4 sin theta_B) with
-// sin theta_B = lambda / 2 d_tau, for lambda < 2 d_tau (the Debye-Scherrer cone).  The
-// reflections come by decreasing d, so the allowed ones form a prefix; one is picked with
-// probability sigma_tau / sum sigma, the packet leaves on its cone (azimuth uniform, speed
-// unchanged) and its weight takes sum sigma / sig_k (sig_k: the kernel's nominal cross
-// section).  Returns false when no reflection is allowed.
+// sin theta_B = lambda / 2 d_tau, i.e. lambda^2 w_tau d_tau / 2, for lambda < 2 d_tau (the
+// Debye-Scherrer cone).  The reflections come by decreasing d, so the allowed ones form a
+// prefix, found by a binary search of d; the table's prefix sums C of w d give their sum,
+// lambda^2 C / 2, and the one picked with probability sigma_tau / sum sigma (a binary search
+// of u C); the packet leaves on its cone (azimuth uniform, speed unchanged) and its weight
+// takes sum sigma / sig_k (sig_k: the kernel's nominal cross section).  Returns false when no
+// reflection is allowed.
 template <typename R, class Rng>
 __device__ __forceinline__ bool kernel_bragg(const SampleP<R>& S, R sig_k, const Rng& rng,
                                              int o, Ray<R>* n, Scatter<R>* sc) {
   using M = Mth<R>;
   const R ki = (R)kKPerV * n->speed;
   const R lam = R(2.0 * kPi) / ki;
-  R total = R(0);
-  int allowed = 0;
-  for (int r = 0; r < S.n_refl; ++r) {
-    const R d = __ldg(S.refl_d + r);
-    if (!(lam < R(2) * d)) break;
-    const R s = lam / (R(2) * d);
-    total += lam * lam * lam * __ldg(S.refl_w + r) / (R(4) * s);
-    ++allowed;
+  int lo = 0, hi = S.n_refl;  // allowed: the reflections with lam < 2 d
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lam < R(2) * __ldg(S.refl_d + mid)) lo = mid + 1;
+    else hi = mid;
   }
-  if (allowed == 0 || !(total > R(0))) return false;
+  const int allowed = lo;
+  if (allowed == 0) return false;
+  const R csum = __ldg(S.refl_c + allowed - 1);
+  const R total = R(0.5) * lam * lam * csum;
+  if (!(total > R(0))) return false;
   R u0, u1;
   rng.template pair<R>(o, 1, &u0, &u1);
-  const R x = u0 * total;
-  R acc = R(0);
-  int pick = allowed - 1;
-  for (int r = 0; r < allowed; ++r) {
-    const R s = lam / (R(2) * __ldg(S.refl_d + r));
-    acc += lam * lam * lam * __ldg(S.refl_w + r) / (R(4) * s);
-    if (x < acc) {
-      pick = r;
-      break;
-    }
+  const R x = u0 * csum;
+  lo = 0;
+  hi = allowed - 1;  // the first reflection whose prefix sum exceeds x (the last if none)
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (x < __ldg(S.refl_c + mid)) hi = mid;
+    else lo = mid + 1;
   }
+  const int pick = lo;
   const R s = lam / (R(2) * __ldg(S.refl_d + pick));
   const R c2t = R(1) - R(2) * s * s;
   const R s2t = R(2) * s * M::sqrt((R(1) - s) * (R(1) + s));

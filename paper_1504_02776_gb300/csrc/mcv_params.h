@@ -76,11 +76,12 @@ struct SampleP {
   const R* ph_b;
   const R* ph_an;
   R ph_de, ph_cw, ph_p0, ph_p1, ph_p2, ph_p01;
-  // coherent elastic powder kernel (mcv_bragg): n_refl reflections by decreasing spacing
+  // coherent elastic powder kernel (mcv_bragg): n_refl reflections by decreasing spacing,
+  // their spacings and the prefix sums of strength x spacing
   int has_bragg;
   int n_refl;
   const R* refl_d;
-  const R* refl_w;
+  const R* refl_c;
   // dispersion-surface kernel (mcv_dispersion)
   int has_disp;
   R disp_amp, disp_c, disp_s0;
