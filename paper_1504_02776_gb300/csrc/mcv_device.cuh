@@ -662,15 +662,10 @@ __device__ __forceinline__ bool kernel_phonon(const SampleP<R>& S, const Rng& rn
   const bool one = u0 < S.ph_p01;
   const R p_ch = one ? S.ph_p1 : S.ph_p2;
   const R ue = (u0 - (one ? S.ph_p0 : S.ph_p01)) / p_ch;
-  int i;
-  R mass = R(1);
-  if (one) {
-    i = draw_mass<R>(S.ph_cdf1, 2 * S.ph_J + 1, ue) - S.ph_J;
-  } else {
-    const int k = draw_mass<R>(S.ph_cdfb, S.ph_M, ue);
-    i = k - S.ph_N * S.ph_J;
-    mass = __ldg(S.ph_b + k);
-  }
+  // one search for both channels (the lanes of a warp pick either), from A_1 or from B
+  const int k = draw_mass<R>(one ? S.ph_cdf1 : S.ph_cdfb, one ? 2 * S.ph_J + 1 : S.ph_M, ue);
+  const int i = k - (one ? S.ph_J : S.ph_N * S.ph_J);
+  const R mass = one ? R(1) : __ldg(S.ph_b + k);
   const R E = ((R)i + (u1 - R(0.5))) * S.ph_de;
   const R Ef = Ei - E;
   if (!(Ef > R(0))) return false;
